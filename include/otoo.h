@@ -1,0 +1,287 @@
+/*
+ * otoo.h -- C ABI of the GB300 octree force library.
+ *
+ * The library splits one softened-gravity force step the way the paper's
+ * heterogeneous code does (Section I and the step list of Section V: the CPU
+ * builds the tree and the cell properties, the GPU evaluates the forces):
+ *
+ *   host   otoo_build_tree            octree over one particle system
+ *          otoo_make_groups_and_lists groups of up to n_crit particles and one
+ *                                     shared interaction list per group
+ *          otoo_pack_batch            several systems in one ragged buffer
+ *          otoo_make_plan             load-balanced work items for the device
+ *   device otoo_force                 acceleration and potential of every group
+ *                                     particle against every entry of its list
+ *          otoo_force_host            the same from host buffers (copies inside)
+ *          otoo_mlp_*                 learned opening-angle network (forward,
+ *                                     backward, Adam step, theta choice)
+ *
+ * Conventions
+ *  - Every function returns 0 on success or a negative OTOO_E* code; the
+ *    message of the last error on the calling thread is otoo_last_error().
+ *    No C++ exception crosses this boundary.
+ *  - Host handles (otoo_tree, otoo_lists, otoo_plan) are owned by the library
+ *    and released with their *_free function.  Pointers returned by the
+ *    *_export functions stay valid until that handle is freed.
+ *  - Device buffers are owned by the caller.  Device functions are
+ *    asynchronous on the given stream (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream).  Errors detected by a kernel are written to
+ *    the caller's status word and read by otoo_check_status after a sync.
+ *  - Positions are FP64, masses FP32, G = 1.  Outputs are FP64.
+ *  - Particle ("tree") order: the host library sorts particles along a Hilbert
+ *    curve.  perm[k] is the caller's index of tree particle k; otoo_force writes
+ *    its outputs at perm[k] when a perm array is supplied.
+ */
+#ifndef OTOO_H
+#define OTOO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define OTOO_OK       0
+#define OTOO_EINVAL  -1   /* bad argument: size, pointer, non-finite input, eps <= 0 */
+#define OTOO_ENOMEM  -2   /* host allocation failed */
+#define OTOO_ECUDA   -3   /* a CUDA runtime call failed */
+#define OTOO_EDEVICE -4   /* a kernel reported bad data (status word) */
+
+/* precision of otoo_force */
+#define OTOO_FP32K 0      /* FP32 centre-relative pairs, per-thread Kahan sums, FP64 final sums */
+#define OTOO_FP64  1      /* every pair in FP64 (comparison form) */
+
+/* ---- parameters ----------------------------------------------------------- */
+typedef struct otoo_params {
+    double theta;                  /* opening angle; 0 = open every cell (direct sum) */
+    int32_t leaf_size;             /* max particles per tree leaf (>= 1) */
+    int32_t n_crit;                /* max particles per group (>= 1, <= 1024) */
+    int32_t use_quad;              /* 1 = cells carry a quadrupole */
+    int32_t pad;
+    double eps;                    /* Plummer softening length (> 0) */
+    const float* theta_per_group;  /* host, NULL = fixed theta; else one angle per group
+                                      in the group order of a previous call on the
+                                      same tree with the same n_crit */
+} otoo_params;
+
+typedef struct otoo_tune {
+    int32_t block;                 /* threads per CTA: 128 or 256 */
+    int32_t iblock;                /* target particles per thread: 1 or 2 */
+    int32_t tile;                  /* list entries staged per shared-memory tile: 32..256 */
+    int32_t split;                 /* max list entries per work item (>= tile) */
+    int32_t ctas_per_sm;           /* resident CTAs per SM for the persistent grid (0 = auto) */
+    int32_t pad;
+} otoo_tune;
+
+/* ---- device-side layout (what the host library exports and the caller
+        uploads; every array is 16-byte aligned and tightly packed) ------------ */
+
+/* A source: a particle (index < n_part) or a cell (index >= n_part).  For a
+   cell, (x, y, z) is its centre of mass and m its mass. 32 bytes. */
+typedef struct otoo_src {
+    double x, y, z;
+    float m;
+    int32_t pad;
+} otoo_src;
+
+/* Traceless quadrupole of cell (n_part + k), k in [0, n_cell):
+   Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab), d = x - com.  32 bytes. */
+typedef struct otoo_quad {
+    float xx, yy, zz, xy, xz, yz, pad0, pad1;
+} otoo_quad;
+
+/* One group: particles [first, first + count) in tree order share the list
+   entries [list_off, list_off + n_cell + n_part): n_cell cell indices first,
+   then n_part particle indices.  64 bytes. */
+typedef struct otoo_group {
+    int32_t first, count, n_cell, n_part;
+    int64_t list_off;
+    float eps2;                    /* softening^2 of the group's system */
+    float theta;                   /* opening angle the list was made with */
+    double cx, cy, cz;             /* FP64 group centre (centre of the particles' box) */
+    int32_t sys;                   /* system index within a batch */
+    int32_t pad;
+} otoo_group;
+
+/* One work item: list entries [j0, j1) (relative to the group's list) of
+   group g.  slot < 0: the item covers the whole list and writes the outputs;
+   slot >= 0: the item writes FP64 partial sums at partial[slot * 4 * n_crit_max]
+   and otoo_force merges the chunks of each group in chunk order.  16 bytes. */
+typedef struct otoo_item {
+    int32_t g, j0, j1, slot;
+} otoo_item;
+
+/* A group whose list was split: its chunks' partials start at slot0 and run
+   over n_chunks consecutive slots. 16 bytes. */
+typedef struct otoo_split {
+    int32_t g, slot0, n_chunks, pad;
+} otoo_split;
+
+/* Device view of one step's inputs (all pointers device, caller-owned). */
+typedef struct otoo_dev_system {
+    int64_t n_part;                /* target particles (tree order) */
+    int64_t n_src;                 /* n_part + number of cells */
+    int32_t n_groups, n_items, n_splits, n_crit_max;
+    const otoo_src* src;           /* [n_src] */
+    const otoo_quad* quad;         /* [n_src - n_part], NULL = monopole cells */
+    const otoo_group* groups;      /* [n_groups] */
+    const int32_t* list;           /* CSR source indices */
+    const otoo_item* items;        /* [n_items], in launch order */
+    const otoo_split* splits;      /* [n_splits] */
+    const int64_t* perm;           /* [n_part] output index of each tree particle, NULL = tree order */
+    double* partial;               /* scratch, >= otoo_plan_info.partial_doubles doubles */
+    uint32_t* counter;             /* scratch, >= 4 uint32 (work ticket and status) */
+} otoo_dev_system;
+
+/* ---- opaque host handles ------------------------------------------------- */
+typedef struct otoo_tree otoo_tree;
+typedef struct otoo_lists otoo_lists;
+typedef struct otoo_plan otoo_plan;
+
+/* Host arrays of a lists object (pointers owned by the lists handle). */
+typedef struct otoo_lists_view {
+    int64_t n_part, n_src, n_groups, n_list;
+    int32_t n_sys, use_quad;
+    const otoo_src* src;           /* [n_src] */
+    const otoo_quad* quad;         /* [n_src - n_part] (zeros when use_quad = 0) */
+    const otoo_group* groups;      /* [n_groups] */
+    const int32_t* list;           /* [n_list] */
+    const int64_t* perm;           /* [n_part] caller index of each tree particle */
+    const int64_t* sys_part_off;   /* [n_sys + 1] first tree particle of each system */
+    int64_t interactions;          /* sum over groups of count * (n_cell + n_part) */
+    int64_t cell_interactions;     /* part of it with cell entries */
+} otoo_lists_view;
+
+typedef struct otoo_plan_info {
+    int64_t n_items, n_splits;
+    int64_t partial_doubles;       /* scratch size otoo_force needs */
+    int32_t n_crit_max;
+    int32_t pad;
+    const otoo_item* items;        /* host [n_items] */
+    const otoo_split* splits;      /* host [n_splits] */
+} otoo_plan_info;
+
+/* ---- host library ------------------------------------------------------------ */
+
+/* Build the octree of n particles (Section III-A: root cube, keys, sort,
+   linked cells; Section III-B: cell mass, centre of mass; the quadrupole is
+   this library's extension).  pos: host [n][3] FP64 row-major; mass: host [n]
+   FP32, > 0.  Root cube: centred on the bounding box, side = max extent *
+   (1 + 1e-12); particles are quantised to a 2^21 grid per axis and sorted by
+   (Hilbert key, index).  Copies its inputs.  Errors: OTOO_EINVAL for n < 1,
+   NULL pointers, non-finite positions or masses <= 0; OTOO_ENOMEM. */
+int otoo_build_tree(const double* pos, const float* mass, int64_t n,
+                    const otoo_params* params, otoo_tree** out);
+
+/* Groups and lists (Section III-C, the vectorised walk of Barnes 1990 done on
+   the host): groups are the maximal cells with at most n_crit particles; each
+   group walks the tree once and accepts cell c when c's cube does not overlap
+   the group's box and d_min > l_c / theta + s_c (d_min: distance from c's
+   centre of mass to the box, l_c: cube side, s_c: distance from the centre of
+   mass to the cube centre).  Rejected leaves contribute their particles.
+   params->theta_per_group, when set, overrides theta group by group.
+   Errors: OTOO_EINVAL (eps <= 0, n_crit < 1 or > 1024, theta < 0), OTOO_ENOMEM. */
+int otoo_make_groups_and_lists(const otoo_tree* tree, const otoo_params* params,
+                               otoo_lists** out);
+
+/* Concatenate the lists of n_sys systems into one ragged buffer: particles of
+   all systems first (system by system), then all cells; group and list
+   indices are rebased.  The inputs stay owned by the caller. */
+int otoo_pack_batch(const otoo_lists* const* per_sys, int32_t n_sys, otoo_lists** out);
+
+/* Work items for otoo_force: lists longer than tune->split entries are cut into
+   chunks of at most tune->split entries; items are ordered by decreasing
+   cost count * (j1 - j0) (longest processing time first). */
+int otoo_make_plan(const otoo_lists* lists, const otoo_tune* tune, otoo_plan** out);
+
+int otoo_lists_export(const otoo_lists* lists, otoo_lists_view* view);
+int otoo_plan_export(const otoo_plan* plan, otoo_plan_info* info);
+int otoo_tree_info(const otoo_tree* tree, int64_t* n_part, int64_t* n_cell, int32_t* depth);
+
+/* Per-group features for the learned opening angle (list statistics):
+   feat[g][0..3] = log2(list length), min over cell entries of d_min / l_c
+   (log10; 3.0 when there is no cell entry), log10(box half-diagonal / eps), cell
+   mass fraction of the list. host out [n_groups][4]. */
+int otoo_group_features(const otoo_tree* tree, const otoo_lists* lists, float* feat);
+
+void otoo_tree_free(otoo_tree* tree);
+void otoo_lists_free(otoo_lists* lists);
+void otoo_plan_free(otoo_plan* plan);
+
+/* ---- device -------------------------------------------------------------------- */
+
+/* Default tuning for a given n_crit. */
+int otoo_default_tune(int32_t n_crit, otoo_tune* tune);
+
+/* Softened acceleration and potential (Section II: particle-particle and
+   particle-cell interactions, the monopole and this library's quadrupole
+   extension; Plummer softening with the group's eps2):
+     a_i = sum_j m_j r / (r^2 + eps^2)^(3/2) [+ quadrupole terms],
+     phi_i = -sum_j m_j / (r^2 + eps^2)^(1/2) [+ ...],   r = x_j - x_i, j != i.
+   sys: device view, all arrays device-resident; accel: device [n_part][3] FP64;
+   pot: device [n_part] FP64; both indexed by perm when sys->perm is set.
+   precision: OTOO_FP32K or OTOO_FP64.  tune: the tuning the plan was made with.
+   The step (ticket reset, persistent force kernel, chunk merge) is recorded
+   once per distinct argument set into a CUDA graph and replayed on stream.
+   Errors: OTOO_EINVAL (sizes, NULL pointers, tune), OTOO_ECUDA. */
+int otoo_force(const otoo_dev_system* sys, double* accel, double* pot, int32_t precision,
+               const otoo_tune* tune, void* stream);
+
+/* Same computation from HOST arrays: the library copies the lists view and
+   the plan to its own device buffers, runs otoo_force on stream and copies
+   accel/pot (host, caller order) back; returns after the stream has synced.
+   Device buffers are kept for the next call of the same size. */
+int otoo_force_host(const otoo_lists_view* lists, const otoo_plan_info* plan, double* accel,
+                    double* pot, int32_t precision, const otoo_tune* tune, void* stream);
+
+/* Reads the status word a previous otoo_force wrote (device counter[1]);
+   returns OTOO_EDEVICE if a kernel flagged bad data.  Synchronises stream. */
+int otoo_check_status(const otoo_dev_system* sys, void* stream);
+
+/* ---- learned opening angle (multilayer perceptron 6-32-32-1) ---------------- */
+
+#define OTOO_MLP_IN  6
+#define OTOO_MLP_H   32
+#define OTOO_MLP_NPARAM (OTOO_MLP_H * OTOO_MLP_IN + OTOO_MLP_H + OTOO_MLP_H * OTOO_MLP_H + OTOO_MLP_H + OTOO_MLP_H + 1)
+
+/* Parameter vector layout (FP32 master weights, 1313 floats):
+   W1 [32][6], b1 [32], W2 [32][32], b2 [32], w3 [32], b3 [1].
+   Forward: h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = w3 . h2 + b3.
+   The forward kernel reads bf16 copies of the weights (bf16: device, 1313 uint16). */
+
+/* y[r] = network(x[r]) for r < n_rows; x: device [n_rows][6] FP32; y: device
+   [n_rows] FP32; wbf16: device bf16 parameters. */
+int otoo_mlp_predict(const uint16_t* wbf16, const float* x, float* y, int64_t n_rows, void* stream);
+
+/* One training step on a batch: loss = mean (y - target)^2.  Computes the
+   gradient with the bf16 weights in the forward pass, accumulates it in FP32,
+   applies one Adam step (lr, beta1, beta2, eps_adam, step count t >= 1) to the
+   FP32 master weights w with moments m, v, refreshes wbf16 and writes the
+   batch loss to loss[0] (all device).  grad: device scratch [1313] FP32. */
+int otoo_mlp_train_step(float* w, uint16_t* wbf16, float* m, float* v, float* grad,
+                        const float* x, const float* target, int64_t n_rows, float lr,
+                        float beta1, float beta2, float eps_adam, int32_t t, float* loss,
+                        void* stream);
+
+/* Gradient only (no update): grad = d loss / d w for the bf16 forward pass. */
+int otoo_mlp_grad(const uint16_t* wbf16, const float* x, const float* target, int64_t n_rows,
+                  float* grad, float* loss, void* stream);
+
+/* Round FP32 master weights to the bf16 copy (round to nearest even). */
+int otoo_mlp_to_bf16(const float* w, uint16_t* wbf16, int32_t n, void* stream);
+
+/* Per-group theta choice: x holds n_groups * n_theta rows, row (g, k) being
+   group g's features with feature 5 = theta_grid[k] (grid increasing).
+   theta_out[g] = the largest theta_grid[k] with y(g, k) <= log10_target, or
+   fallback when none qualifies or a prediction is not finite.  Device arrays. */
+int otoo_select_theta(const uint16_t* wbf16, const float* x, const float* theta_grid,
+                      int32_t n_theta, int64_t n_groups, float log10_target, float fallback,
+                      float* theta_out, void* stream);
+
+const char* otoo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OTOO_H */

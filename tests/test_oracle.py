@@ -1,0 +1,190 @@
+"""Pins of the FP64 oracle against closed forms, invariants and analytic
+models (no GPU).  A plausible slip in the oracle -- a dropped term, a wrong
+sign or index, a transposed operand -- breaks at least one of these."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from golden_io import GOLDEN, load_bodies
+from paper_1206_1199_gb300 import ic
+
+
+@pytest.mark.parametrize("name", ["two_body.txt", "three_body.txt"])
+def test_direct_closed_form(name):
+    pos, mass, acc_ref, pot_ref, eps = load_bodies(name)
+    acc, pot = oracle.direct(pos, mass, eps)
+    np.testing.assert_allclose(acc, acc_ref, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(pot, pot_ref, rtol=1e-12, atol=0)
+
+
+def test_direct_targets_subset_and_self_excluded():
+    pos, mass = ic.plummer(300, 11)
+    acc, pot = oracle.direct(pos, mass, 0.05)
+    tgt = np.array([5, 17, 299])
+    a2, p2 = oracle.direct(pos, mass, 0.05, targets=tgt)
+    np.testing.assert_array_equal(a2, acc[tgt])
+    np.testing.assert_array_equal(p2, pot[tgt])
+    # the self pair would add exactly -m_i / eps to phi_i: it must be absent
+    m = mass.astype(np.float64)
+    d = pos[:, None, :] - pos[None, :, :]
+    r = np.sqrt((d * d).sum(-1) + 0.05 ** 2)
+    full = -(m[None, :] / r).sum(1)
+    np.testing.assert_allclose(pot, full + m / 0.05, rtol=1e-12)
+
+
+def test_direct_momentum_conservation():
+    # Newton's third law: sum_i m_i a_i = 0 for a pairwise-antisymmetric force
+    pos, mass = ic.hernquist(4000, 12)
+    acc, _ = oracle.direct(pos, mass, 0.01)
+    m = mass.astype(np.float64)[:, None]
+    tot = np.abs((m * acc).sum(0))
+    scale = np.abs(m * acc).sum(0)
+    assert np.all(tot <= 1e-13 * scale)
+
+
+def test_direct_plummer_analytic():
+    # Plummer model, G = M = a = 1: phi(r) = -1/sqrt(r^2+1),
+    # a_r = -r/(r^2+1)^(3/2), W = (1/2) sum m phi = -3 pi / 32.
+    n = 16384
+    pos, mass = ic.plummer(n, 13)
+    acc, pot = oracle.direct(pos, mass, 0.005)
+    r = np.linalg.norm(pos, axis=1)
+    ar = (acc * pos).sum(1) / r
+    edges = np.array([0.1, 0.3, 0.6, 1.0, 1.5, 2.5, 5.0])
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (r >= lo) & (r < hi)
+        rm = r[sel]
+        np.testing.assert_allclose(pot[sel].mean(), (-1.0 / np.sqrt(rm * rm + 1)).mean(), rtol=0.02)
+        if lo >= 0.3:  # the innermost shell holds too few particles for a_r
+            np.testing.assert_allclose(ar[sel].mean(), (-rm / (rm * rm + 1) ** 1.5).mean(), rtol=0.06)
+    w = 0.5 * float((mass.astype(np.float64) * pot).sum())
+    assert abs(w - (-3 * math.pi / 32)) < 0.03 * 3 * math.pi / 32
+
+
+def test_direct_hernquist_analytic():
+    # Hernquist, truncated at rt = 100 a with M(rt) = 1: inside rt
+    # phi(r) = -M_inf/(r + a) + M_inf a/(rt + a)^2, M_inf = ((rt + a)/rt)^2.
+    n = 16384
+    pos, mass = ic.hernquist(n, 14)
+    _, pot = oracle.direct(pos, mass, 0.005)
+    r = np.linalg.norm(pos, axis=1)
+    minf = (101.0 / 100.0) ** 2
+    for lo, hi in [(0.1, 0.3), (0.3, 1.0), (1.0, 3.0), (3.0, 10.0), (10.0, 50.0)]:
+        sel = (r >= lo) & (r < hi)
+        rm = r[sel]
+        ref = (-minf / (rm + 1.0) + minf / 101.0 ** 2).mean()
+        np.testing.assert_allclose(pot[sel].mean(), ref, rtol=0.02)
+
+
+def test_cell_field_quadrupole_on_axis():
+    rows = [l for l in open(GOLDEN + "/quad_axis.txt") if l.strip() and not l.startswith("#")]
+    v = np.array([float(x) for x in rows[0].split()])
+    x, m, q = v[0:3], v[3], v[4:10]
+    m2, com, q2 = oracle.cell_moments(np.array([[0, 0, 1.0], [0, 0, -1.0]]), np.array([1.0, 1.0]))
+    assert m2 == m
+    np.testing.assert_allclose(com, 0, atol=1e-15)
+    np.testing.assert_allclose(q2, q, atol=1e-14)
+    acc, pot = oracle.cell_field(x, m, com, q, True, 1e-9)
+    np.testing.assert_allclose(acc, v[10:13], atol=1e-12)
+    assert abs(pot - v[13]) < 1e-12
+    acc, pot = oracle.cell_field(x, m, com, q, False, 1e-9)
+    np.testing.assert_allclose(acc, v[14:17], atol=1e-12)
+    assert abs(pot - v[17]) < 1e-12
+
+
+def test_multipole_far_field_slopes():
+    # Relative error of the cell field against the exact sum over the cell's
+    # particles: monopole ~ (l/d)^2 (the dipole vanishes about the centre of
+    # mass), quadrupole ~ (l/d)^3.
+    rng = np.random.default_rng(15)
+    pts = rng.uniform(-0.5, 0.5, (25, 3))
+    ms = rng.uniform(0.5, 1.5, 25)
+    m, com, q = oracle.cell_moments(pts, ms)
+    u = np.array([0.48, -0.6, 0.64])
+    u /= np.linalg.norm(u)
+    ds = np.array([8.0, 16.0, 32.0, 64.0, 128.0])
+    err = {0: [], 1: []}
+    for d in ds:
+        x = com + d * u
+        allp = np.vstack([pts, x])
+        allm = np.concatenate([ms, [0.0]])
+        ex_a, ex_p = oracle.direct(allp, allm, 1e-9, targets=[25])
+        for quad in (0, 1):
+            a, p = oracle.cell_field(x, m, com, q, quad, 1e-9)
+            err[quad].append(np.linalg.norm(a - ex_a[0]) / np.linalg.norm(ex_a[0]))
+    s0 = np.polyfit(np.log(ds), np.log(err[0]), 1)[0]
+    s1 = np.polyfit(np.log(ds), np.log(err[1]), 1)[0]
+    assert abs(s0 + 2) < 0.15, s0
+    assert abs(s1 + 3) < 0.15, s1
+    assert all(e1 < e0 for e0, e1 in zip(err[0], err[1]))
+
+
+@pytest.mark.parametrize("n,leaf,ncrit", [(1, 8, 64), (7, 8, 64), (200, 1, 4), (4096, 8, 64)])
+def test_tree_theta0_is_direct_sum(n, leaf, ncrit):
+    pos, mass = ic.plummer(n, 16)
+    t = oracle.Tree(pos, mass, leaf, ncrit)
+    r = t.eval(0.0, 0.01, use_quad=True)
+    a, p = oracle.direct(pos, mass, 0.01)
+    np.testing.assert_allclose(r["acc"], a, rtol=0, atol=1e-13 * np.abs(a).max())
+    np.testing.assert_allclose(r["pot"], p, rtol=1e-13)
+    assert r["n_cell"].sum() == 0
+    assert np.all(r["n_part"] == n)
+    assert r["count"].sum() == n
+
+
+def test_tree_groups_partition_and_list_mass():
+    pos, mass = ic.hernquist(20000, 17)
+    t = oracle.Tree(pos, mass, 8, 64)
+    r = t.eval(0.6, 1e-3, use_quad=True)
+    assert r["count"].sum() == 20000
+    assert len(np.unique(r["key"])) == t.n_groups
+    assert r["count"].max() <= 64
+    # every group's list covers the whole mass exactly once
+    np.testing.assert_allclose(r["mass"], mass.astype(np.float64).sum(), rtol=1e-12)
+    assert np.all(np.isfinite(r["acc"]))
+
+
+def test_tree_converges_as_theta_to_zero():
+    pos, mass = ic.plummer(8192, 18)
+    a, p = oracle.direct(pos, mass, 0.01)
+    t = oracle.Tree(pos, mass, 8, 64)
+    for quad in (False, True):
+        prev = None
+        for th in (0.9, 0.7, 0.5, 0.3, 0.1):
+            e = oracle.errors(**dict(zip(("acc", "pot"), (lambda r: (r["acc"], r["pot"]))(t.eval(th, 0.01, quad)))),
+                              acc_ref=a, pot_ref=p)["acc_rms"]
+            if prev is not None:
+                assert e < prev
+            prev = e
+        assert prev < (2e-5 if quad else 2e-4)
+    # at equal theta the quadrupole beats the monopole
+    em = oracle.errors(*(lambda r: (r["acc"], r["pot"]))(t.eval(0.5, 0.01, False)), a, p)["acc_rms"]
+    eq = oracle.errors(*(lambda r: (r["acc"], r["pot"]))(t.eval(0.5, 0.01, True)), a, p)["acc_rms"]
+    assert eq < 0.5 * em
+
+
+def test_tree_coincident_particles_over_ncrit():
+    # more than n_crit identical positions land in one maximum-depth leaf,
+    # which is cut into chunks of n_crit
+    pos = np.zeros((100, 3))
+    pos[50:] = 1.0
+    mass = np.full(100, 0.01)
+    t = oracle.Tree(pos, mass, 8, 16)
+    r = t.eval(0.5, 0.1)
+    assert r["count"].sum() == 100 and r["count"].max() <= 16
+    a, p = oracle.direct(pos, mass, 0.1)
+    np.testing.assert_allclose(r["pot"], p, rtol=1e-12)
+
+
+def test_tree_per_group_theta():
+    pos, mass = ic.plummer(4096, 19)
+    t = oracle.Tree(pos, mass, 8, 64)
+    r5 = t.eval(0.5, 0.01)
+    tbk = np.full(4096, 0.5)
+    r = t.eval(0.9, 0.01, theta_by_key=tbk)
+    np.testing.assert_array_equal(r["acc"], r5["acc"])
+    tbk[r5["key"][::2]] = 0.0
+    r = t.eval(0.5, 0.01, theta_by_key=tbk)
+    assert np.all(r["n_cell"][::2] == 0) and np.all(r["n_part"][::2] == 4096)
