@@ -1,0 +1,380 @@
+"""Force-step benchmark: softened gravity of every group against its shared
+interaction list on one GB300 (interactions per second and ms per step).
+
+Default workload: Hernquist halo N = 2^23 (a = 1, truncated at 100 a), eps
+5e-4, theta 0.5, quadrupole cells, FP32 centre-relative pairs with Kahan
+sums (FP64 form timed beside it).  A step is one otoo_force call (CUDA graph:
+ticket reset, persistent force kernel, chunk merge) over device-resident
+groups and lists; the host tree and walk are built once before timing.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(the only reference this method has) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 partitions x 32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hernquist8m")
+    ap.add_argument("--n", type=int, default=0, help="override particle count (testing only)")
+    ap.add_argument("--n-crit", type=int, default=0)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--err-targets", type=int, default=512)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cores():
+    return len(os.sched_getaffinity(0))
+
+
+def workload(args, rank=0):
+    from paper_1206_1199_gb300 import ic
+    w = dict(ic.WORKLOADS[args.workload])
+    if args.n:
+        w["n"] = args.n
+    if args.n_crit:
+        w["n_crit"] = args.n_crit
+    # independent problems per rank (weak scaling): rank r draws seed + 100 r
+    w["seed"] = w["seed"] + 100 * rank
+    pos, mass = ic.make(w["model"], w["n"], w["seed"])
+    return w, pos, mass
+
+
+def load_tune(w, n_crit_max):
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import autotune
+    t = autotune.cached(w, n_crit_max)
+    return t if t is not None else L.default_tune(n_crit_max)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[0][1], "reasons": reasons,
+                "samples": len(rows)}
+
+
+def rel_err(a, ref):
+    d = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return float(np.sqrt(np.mean(d * d))), float(d.max())
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as tdist
+
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import system as S
+
+    rank, world, local = dist_env()
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev_name = "cuda:%d" % local
+    w, pos, mass = workload(args, rank)
+    t0 = time.perf_counter()
+    tree = S.Tree(pos, mass, w["leaf_size"])
+    t1 = time.perf_counter()
+    lists = tree.lists(w["theta"], w["n_crit"], w["eps"], w["use_quad"])
+    t2 = time.perf_counter()
+    ncm = int(lists.groups["count"].max())
+    tune = load_tune(w, ncm)
+    plan = lists.plan(tune)
+    dev = S.DeviceSystem.upload(lists, plan, dev_name)
+    n = lists.n_part
+    accel = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
+    pot = torch.empty(n, dtype=torch.float64, device=dev_name)
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        S.force(dev, accel, pot, precision=prec, tune=tune, stream=stream, check=False)
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            step(prec)
+        L.call("otoo_check_status", __import__("ctypes").byref(dev.struct), __import__("ctypes").c_void_p(stream.cuda_stream))
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for k in range(steps):
+            step(prec)
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+        total = evs[0].elapsed_time(evs[-1])
+        if world > 1:
+            tt = torch.tensor([total], dtype=torch.float64, device=dev_name)
+            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+            total = float(tt.item())
+            tdist.barrier()
+        return total, per
+
+    with Clocks(local) as clk:
+        total_ms, per_ms = timed(L.OTOO_FP32K, args.steps, args.warmup)
+    clocks = clk.summary()
+    a32 = accel.double().cpu().numpy()
+    p32 = pot.double().cpu().numpy()
+    inter = lists.interactions
+    cell_inter = lists.cell_interactions if lists.use_quad else 0
+    mono_inter = inter - cell_inter
+    ms = total_ms / args.steps
+    value = world * inter / (ms * 1e-3)
+
+    # FP64 form (the comparison form), same lists and launch shape
+    fp64 = None
+    if not args.skip_fp64:
+        k64 = max(1, min(3, args.steps))
+        tot64, _ = timed(L.OTOO_FP64, k64, 1)
+        a64 = accel.double().cpu().numpy()
+        p64 = pot.double().cpu().numpy()
+        fp64 = {"value": inter / (tot64 / k64 * 1e-3), "ms_per_step": tot64 / k64,
+                "fp32_vs_fp64_acc_max_rel": rel_err(a32, a64)[1]}
+
+    # accuracy against the FP64 direct sum on a seeded subsample
+    errors = None
+    if rank == 0 and args.err_targets > 0:
+        import oracle
+        from paper_1206_1199_gb300 import ic
+        sub = ic.subsample(n, args.err_targets, 7)
+        ad, pd = oracle.direct(pos, mass, w["eps"], targets=sub)
+        rms, mx = rel_err(a32[sub], ad)
+        errors = {"targets": int(sub.shape[0]), "fp32k_acc_rms": rms, "fp32k_acc_max": mx,
+                  "fp32k_pot_rms": float(np.sqrt(np.mean(((p32[sub] - pd) / pd) ** 2)))}
+        if fp64 is not None:
+            rms64, mx64 = rel_err(a64[sub], ad)
+            errors.update({"fp64_acc_rms": rms64, "fp64_acc_max": mx64})
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.skip_e2e:
+        e2e = run_e2e(args, lists, plan, tune, stream, world)
+
+    flops = 20.0 * mono_inter + (60.0 if lists.use_quad else 20.0) * cell_inter
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (ms * 1e-3) / 1e12
+    line = {
+        "metric": "force interactions/s (FP32 centre-relative + Kahan) at N=2^23",
+        "value": value,
+        "unit": "interactions/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "ms_per_step_min": min(per_ms),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "model": w["model"], "n": n, "eps": w["eps"], "theta": w["theta"],
+                   "leaf_size": w["leaf_size"], "n_crit": w["n_crit"], "quadrupole": bool(lists.use_quad),
+                   "groups": lists.n_groups, "list_entries": lists.n_list, "interactions": inter,
+                   "cell_interactions": cell_inter, "tune": tune.as_dict(), "items": plan.n_items,
+                   "l2": "inputs larger than L2 (%.1f GB resident per step)" % (dev.h2d_bytes() / 1e9),
+                   "host_tree_s": t1 - t0, "host_walk_s": t2 - t1, "parallelism": "replica per rank (weak)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "flops_per_step": flops,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived; no measured FP32 peak)",
+                     "flop_convention": "20 per monopole/particle interaction, 60 per quadrupole cell interaction"},
+        "fp64_form": fp64,
+        "errors": errors,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": args.steps * (1 + (1 if plan.n_splits else 0)),
+    }
+    if rank == 0 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def run_e2e(args, lists, plan, tune, stream, world):
+    """Same metric through otoo_force_host: pinned host inputs copied in and
+    results copied out inside the timed region, every step."""
+    import ctypes
+
+    import torch
+
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import system as S
+
+    v = L.ListsView()
+    ctypes.memmove(ctypes.byref(v), ctypes.byref(lists.view_struct), ctypes.sizeof(v))
+    keep = []
+    h2d = 0
+    for field, arr in (("src", lists.src), ("quad", lists.quad), ("groups", lists.groups), ("list", lists.list),
+                       ("perm", lists.perm)):
+        t = torch.from_numpy(np.ascontiguousarray(arr).view(np.uint8).reshape(-1)).pin_memory()
+        keep.append(t)
+        setattr(v, field, t.data_ptr())
+        if field != "quad" or lists.use_quad:
+            h2d += t.numel()
+    info = L.PlanInfo()
+    ctypes.memmove(ctypes.byref(info), ctypes.byref(plan.info), ctypes.sizeof(info))
+    for field, arr in (("items", plan.items), ("splits", plan.splits)):
+        t = torch.from_numpy(np.ascontiguousarray(arr).view(np.uint8).reshape(-1).copy()
+                             if arr.size else np.zeros(16, np.uint8)).pin_memory()
+        keep.append(t)
+        setattr(info, field, t.data_ptr())
+        h2d += t.numel() if arr.size else 0
+    n = lists.n_part
+    acc = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    pot = torch.empty(n, dtype=torch.float64).pin_memory()
+    d2h = (acc.numel() + pot.numel()) * 8
+    steps = max(1, min(args.steps, 5))
+
+    def one():
+        L.call("otoo_force_host", ctypes.byref(v), ctypes.byref(info), acc.data_ptr(), pot.data_ptr(),
+               L.OTOO_FP32K, ctypes.byref(tune), ctypes.c_void_p(stream.cuda_stream))
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": world * lists.interactions / dt, "unit": "interactions/s", "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+def oracle_tree(w, pos, mass):
+    import oracle
+    return oracle.Tree(pos, mass, w["leaf_size"], w["n_crit"])
+
+
+def cpu_baseline(w, pos, mass, seconds, tree=None):
+    """The FP64 oracle tree code (as it stands) on a bounded sample of the
+    same workload: every k-th group, k chosen so the sample takes about
+    `seconds`; the oracle's own tree build is not timed."""
+    t = tree if tree is not None else oracle_tree(w, pos, mass)
+    stride = max(1, t.n_groups // 64)
+    t0 = time.perf_counter()
+    r = t.eval(w["theta"], w["eps"], w["use_quad"], group_stride=stride)
+    dt = time.perf_counter() - t0
+    rate = r["interactions"] / max(dt, 1e-9)
+    full_estimate = r["interactions"] * stride
+    stride = max(1, int(math.ceil(full_estimate / max(rate * seconds, 1.0))))
+    t0 = time.perf_counter()
+    r = t.eval(w["theta"], w["eps"], w["use_quad"], group_stride=stride)
+    dt = time.perf_counter() - t0
+    return {"value": r["interactions"] / dt, "unit": "interactions/s", "cores": cores(), "kind": "oracle",
+            "sample": "FP64 oracle tree force (walk + evaluation) for every %d-th of %d groups "
+                      "(%d interactions, %.1f s); oracle tree build not timed" % (stride, t.n_groups,
+                                                                                  r["interactions"], dt)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    w, pos, mass = workload(args, 0)
+    steps = []
+    per = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    tree = oracle_tree(w, pos, mass)
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, pos, mass, per, tree)
+        if k >= args.warmup:
+            steps.append(cb)
+    vals = [s["value"] for s in steps]
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": "force interactions/s (FP32 centre-relative + Kahan) at N=2^23",
+            "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "model": w["model"], "n": w["n"], "eps": w["eps"],
+                       "theta": w["theta"], "n_crit": w["n_crit"], "quadrupole": w["use_quad"]},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores(), "kind": "oracle",
+                             "sample": steps[-1]["sample"]},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -97,11 +97,10 @@ typedef struct otoo_quad {
 typedef struct otoo_group {
     int32_t first, count, n_cell, n_part;
     int64_t list_off;
-    float eps2;                    /* softening^2 of the group's system */
-    float theta;                   /* opening angle the list was made with */
+    double eps2;                   /* softening^2 of the group's system */
     double cx, cy, cz;             /* FP64 group centre (centre of the particles' box) */
+    float theta;                   /* opening angle the list was made with */
     int32_t sys;                   /* system index within a batch */
-    int32_t pad;
 } otoo_group;
 
 /* One work item: list entries [j0, j1) (relative to the group's list) of
@@ -122,6 +121,7 @@ typedef struct otoo_split {
 typedef struct otoo_dev_system {
     int64_t n_part;                /* target particles (tree order) */
     int64_t n_src;                 /* n_part + number of cells */
+    int64_t n_list;                /* entries in list */
     int32_t n_groups, n_items, n_splits, n_crit_max;
     const otoo_src* src;           /* [n_src] */
     const otoo_quad* quad;         /* [n_src - n_part], NULL = monopole cells */
@@ -195,14 +195,36 @@ int otoo_pack_batch(const otoo_lists* const* per_sys, int32_t n_sys, otoo_lists*
    cost count * (j1 - j0) (longest processing time first). */
 int otoo_make_plan(const otoo_lists* lists, const otoo_tune* tune, otoo_plan** out);
 
+/* Host arrays of a tree (pointers owned by the tree handle); cells are
+   numbered from 0 (the root), cell k is source n_part + k, the children of a
+   cell are consecutive. */
+typedef struct otoo_tree_view {
+    int64_t n_part, n_cell;
+    int32_t depth, leaf_size;
+    double root_lo[3], root_side;
+    const double* pos;             /* [n_part][3] tree order */
+    const float* mass;             /* [n_part] tree order */
+    const int64_t* perm;           /* [n_part] caller index of each tree particle */
+    const int64_t* cell_begin;     /* [n_cell] first tree particle */
+    const int64_t* cell_end;       /* [n_cell] one past the last */
+    const int32_t* cell_level;     /* [n_cell] 0 = root */
+    const int32_t* cell_nchild;    /* [n_cell] 0 = leaf */
+    const int64_t* cell_child0;    /* [n_cell] first child cell */
+    const int64_t* cell_org;       /* [n_cell][3] integer origin on the 2^21 grid */
+    const double* cell_com;        /* [n_cell][3] */
+    const double* cell_mass;       /* [n_cell] */
+    const double* cell_quad;       /* [n_cell][6] Qxx Qyy Qzz Qxy Qxz Qyz */
+} otoo_tree_view;
+
+int otoo_tree_export(const otoo_tree* tree, otoo_tree_view* view);
 int otoo_lists_export(const otoo_lists* lists, otoo_lists_view* view);
 int otoo_plan_export(const otoo_plan* plan, otoo_plan_info* info);
-int otoo_tree_info(const otoo_tree* tree, int64_t* n_part, int64_t* n_cell, int32_t* depth);
 
-/* Per-group features for the learned opening angle (list statistics):
-   feat[g][0..3] = log2(list length), min over cell entries of d_min / l_c
-   (log10; 3.0 when there is no cell entry), log10(box half-diagonal / eps), cell
-   mass fraction of the list. host out [n_groups][4]. */
+/* Per-group features for the learned opening angle (statistics of each
+   group's list): feat[g][0..4] = log2(list length), log10 of the minimum over
+   cell entries of d_min / l_c (3.0 when the list has no cell entry),
+   log10(box half-diagonal / eps) (box half-diagonal floored at eps / 1000),
+   cell mass fraction of the list, log2(group count).  host out [n_groups][5]. */
 int otoo_group_features(const otoo_tree* tree, const otoo_lists* lists, float* feat);
 
 void otoo_tree_free(otoo_tree* tree);

@@ -1,0 +1,177 @@
+"""ctypes binding of libotoo.so: the C ABI of include/otoo.h with the same
+names, argument marshalling only.  Loading fails loudly when the library is
+missing; there is no fallback implementation."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libotoo.so")
+
+OTOO_OK = 0
+OTOO_EINVAL = -1
+OTOO_ENOMEM = -2
+OTOO_ECUDA = -3
+OTOO_EDEVICE = -4
+OTOO_FP32K = 0
+OTOO_FP64 = 1
+MLP_IN = 6
+MLP_H = 32
+MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+
+i32, i64, f32, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+vp = ctypes.c_void_p
+
+
+class OtooError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("otoo error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("theta", f64), ("leaf_size", i32), ("n_crit", i32), ("use_quad", i32), ("pad", i32),
+                ("eps", f64), ("theta_per_group", ctypes.POINTER(f32))]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("block", i32), ("iblock", i32), ("tile", i32), ("split", i32), ("ctas_per_sm", i32),
+                ("pad", i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class Src(ctypes.Structure):
+    _fields_ = [("x", f64), ("y", f64), ("z", f64), ("m", f32), ("pad", i32)]
+
+
+class Quad(ctypes.Structure):
+    _fields_ = [(k, f32) for k in ("xx", "yy", "zz", "xy", "xz", "yz", "pad0", "pad1")]
+
+
+class Group(ctypes.Structure):
+    _fields_ = [("first", i32), ("count", i32), ("n_cell", i32), ("n_part", i32), ("list_off", i64),
+                ("eps2", f64), ("cx", f64), ("cy", f64), ("cz", f64), ("theta", f32), ("sys", i32)]
+
+
+class Item(ctypes.Structure):
+    _fields_ = [("g", i32), ("j0", i32), ("j1", i32), ("slot", i32)]
+
+
+class Split(ctypes.Structure):
+    _fields_ = [("g", i32), ("slot0", i32), ("n_chunks", i32), ("pad", i32)]
+
+
+class DevSystem(ctypes.Structure):
+    _fields_ = [("n_part", i64), ("n_src", i64), ("n_list", i64), ("n_groups", i32), ("n_items", i32),
+                ("n_splits", i32), ("n_crit_max", i32), ("src", vp), ("quad", vp), ("groups", vp),
+                ("list", vp), ("items", vp), ("splits", vp), ("perm", vp), ("partial", vp), ("counter", vp)]
+
+
+class ListsView(ctypes.Structure):
+    _fields_ = [("n_part", i64), ("n_src", i64), ("n_groups", i64), ("n_list", i64), ("n_sys", i32),
+                ("use_quad", i32), ("src", vp), ("quad", vp), ("groups", vp), ("list", vp), ("perm", vp),
+                ("sys_part_off", vp), ("interactions", i64), ("cell_interactions", i64)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_items", i64), ("n_splits", i64), ("partial_doubles", i64), ("n_crit_max", i32),
+                ("pad", i32), ("items", vp), ("splits", vp)]
+
+
+class TreeView(ctypes.Structure):
+    _fields_ = [("n_part", i64), ("n_cell", i64), ("depth", i32), ("leaf_size", i32),
+                ("root_lo", f64 * 3), ("root_side", f64), ("pos", vp), ("mass", vp), ("perm", vp),
+                ("cell_begin", vp), ("cell_end", vp), ("cell_level", vp), ("cell_nchild", vp),
+                ("cell_child0", vp), ("cell_org", vp), ("cell_com", vp), ("cell_mass", vp), ("cell_quad", vp)]
+
+
+for _s, _n in ((Src, 32), (Quad, 32), (Group, 64), (Item, 16), (Split, 16)):
+    assert ctypes.sizeof(_s) == _n, (_s, ctypes.sizeof(_s))
+
+# name -> (argtypes); every function returns int unless listed in _VOID
+_SIGS = {
+    "otoo_build_tree": [vp, vp, i64, ctypes.POINTER(Params), ctypes.POINTER(vp)],
+    "otoo_make_groups_and_lists": [vp, ctypes.POINTER(Params), ctypes.POINTER(vp)],
+    "otoo_pack_batch": [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)],
+    "otoo_make_plan": [vp, ctypes.POINTER(Tune), ctypes.POINTER(vp)],
+    "otoo_lists_export": [vp, ctypes.POINTER(ListsView)],
+    "otoo_plan_export": [vp, ctypes.POINTER(PlanInfo)],
+    "otoo_tree_export": [vp, ctypes.POINTER(TreeView)],
+    "otoo_group_features": [vp, vp, vp],
+    "otoo_tree_free": [vp],
+    "otoo_lists_free": [vp],
+    "otoo_plan_free": [vp],
+    "otoo_default_tune": [i32, ctypes.POINTER(Tune)],
+    "otoo_force": [ctypes.POINTER(DevSystem), vp, vp, i32, ctypes.POINTER(Tune), vp],
+    "otoo_force_host": [ctypes.POINTER(ListsView), ctypes.POINTER(PlanInfo), vp, vp, i32, ctypes.POINTER(Tune), vp],
+    "otoo_check_status": [ctypes.POINTER(DevSystem), vp],
+    "otoo_last_error": [],
+}
+_VOID = {"otoo_tree_free", "otoo_lists_free", "otoo_plan_free"}
+_OPTIONAL = set()
+
+_lib = None
+
+
+def load():
+    """Load libotoo.so (built by __graft_entry__.build() / build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libotoo.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        if not hasattr(lib, name):
+            if name in _OPTIONAL:
+                continue
+            raise ImportError("libotoo.so lacks %s" % name)
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = None if name in _VOID else (ctypes.c_char_p if name == "otoo_last_error" else ctypes.c_int)
+    _lib = lib
+    return lib
+
+
+def check(rc):
+    if rc != OTOO_OK:
+        raise OtooError(rc, load().otoo_last_error().decode())
+    return rc
+
+
+def call(name, *args):
+    return check(getattr(load(), name)(*args))
+
+
+def ptr(a):
+    """Address of a numpy array or torch tensor (data pointer)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def view(addr, dtype, shape):
+    """numpy view (no copy) of library-owned host memory."""
+    n = int(np.prod(shape))
+    if n == 0:
+        return np.zeros(shape, dtype)
+    buf = (ctypes.c_char * (n * np.dtype(dtype).itemsize)).from_address(addr)
+    return np.frombuffer(buf, dtype=dtype, count=n).reshape(shape)
+
+
+def structs_dtype(st):
+    """numpy structured dtype matching a ctypes Structure."""
+    return np.dtype(st)
+
+
+def default_tune(n_crit):
+    t = Tune()
+    call("otoo_default_tune", n_crit, ctypes.byref(t))
+    return t

@@ -1,0 +1,200 @@
+"""Parity of the CUDA force path with the FP64 CPU oracle (needs a GPU).
+
+Tolerances: the FP64 device form reproduces the oracle's tree force up to
+summation order (<= 1e-6 max relative, expected ~1e-13); the FP32 form has
+the tree error of theta plus FP32 rounding (<= 2e-3 RMS against the direct
+sum at theta = 0.5) and differs from the FP64 form by FP32 rounding only
+(<= 1e-5 max relative on accelerations)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_1199_gb300 import _lib as L
+from paper_1206_1199_gb300 import ic, system as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    L.load()
+    return t
+
+
+def run(pos, mass, theta, n_crit, eps, use_quad, precision, tune=None, leaf=8):
+    tree, lists, plan = S.build_system(pos, mass, theta, n_crit, eps, leaf, use_quad, tune)
+    dev = S.DeviceSystem.upload(lists, plan, "cuda")
+    a, p = S.force(dev, precision=precision)
+    return a.cpu().numpy(), p.cpu().numpy(), lists
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def abs_sum(pos, mass, eps):
+    """Per target: sum over sources of |a_ij| and |phi_ij| (j != i).  A sum's
+    rounding error is bounded by a few ulps of this, not of |sum| (which can
+    be far smaller where the pulls cancel)."""
+    d = pos[None, :, :] - pos[:, None, :]
+    r2 = (d * d).sum(-1) + eps * eps
+    np.fill_diagonal(r2, np.inf)
+    m = mass.astype(np.float64)[None, :]
+    return (m * np.sqrt(r2 - eps * eps) / r2 ** 1.5).sum(1), (m / np.sqrt(r2)).sum(1)
+
+
+def within_bound(a, p, ad, pd, pos, mass, eps, k):
+    """|a - a_ref| <= k * sum_j |a_ij| and the same for phi, per target."""
+    sa, sp = abs_sum(pos, mass, eps)
+    return (np.linalg.norm(a - ad, axis=1) <= k * sa).all() and (np.abs(p - pd) <= k * sp).all()
+
+
+# FP32 pair arithmetic: relative coordinates and sums carry ~2^-24 rounding
+# per term; accumulated over a list with Kahan sums the error stays a few
+# 1e-7 of sum_j |a_ij|.
+FP32_K = 2e-6
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_fp64_matches_oracle_tree_plummer4k(torch, quad):
+    pos, mass = ic.plummer(4096, ic.BASE_SEED + 1)
+    a, p, _ = run(pos, mass, 0.5, 64, 0.01, quad, L.OTOO_FP64)
+    r = oracle.Tree(pos, mass, 8, 64).eval(0.5, 0.01, use_quad=quad)
+    assert rel(a, r["acc"]).max() <= 1e-6
+    assert (np.abs(p - r["pot"]) / np.abs(r["pot"])).max() <= 1e-6
+    # plus: the tree error of this configuration against the direct sum
+    ad, pd = oracle.direct(pos, mass, 0.01)
+    e = oracle.errors(a, p, ad, pd)
+    assert e["acc_rms"] < (1e-3 if quad else 3e-3)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.75])
+def test_fp32k_and_fp64_vs_oracle_plummer(torch, theta):
+    n = 1 << 16
+    pos, mass = ic.plummer(n, ic.BASE_SEED + 2)
+    a64, p64, lists = run(pos, mass, theta, 128, 1e-3, True, L.OTOO_FP64)
+    a32, p32, _ = run(pos, mass, theta, 128, 1e-3, True, L.OTOO_FP32K)
+    r = oracle.Tree(pos, mass, 8, 128).eval(theta, 1e-3, use_quad=True)
+    assert rel(a64, r["acc"]).max() <= 1e-6
+    # FP32 vs FP64 on identical lists: arithmetic error only (RMS; the
+    # largest per-particle value is set by cancelling pulls, see abs_sum)
+    d = rel(a32, a64)
+    assert np.sqrt(np.mean(d * d)) <= 2e-6 and d.max() <= 2e-4
+    assert (np.abs(p32 - p64) / np.abs(p64)).max() <= 1e-5
+    sub = ic.subsample(n, 4096, 7)
+    ad, pd = oracle.direct(pos, mass, 1e-3, targets=sub)
+    e = oracle.errors(a32[sub], p32[sub], ad, pd)
+    if theta <= 0.5:
+        assert e["acc_rms"] <= 2e-3
+
+
+def test_tiny_direct_one_group(torch):
+    # theta = 0, a single group: every pair is evaluated, both precisions
+    pos, mass = ic.plummer(200, 3)
+    ad, pd = oracle.direct(pos, mass, 0.05)
+    for prec, k in ((L.OTOO_FP64, 1e-13), (L.OTOO_FP32K, FP32_K)):
+        a, p, lists = run(pos, mass, 0.0, 256, 0.05, True, prec)
+        assert lists.n_groups == 1
+        assert within_bound(a, p, ad, pd, pos, mass, 0.05, k)
+
+
+def test_theta0_many_groups_ragged(torch):
+    # theta = 0 with groups of every size: lists of all n entries, j-split and
+    # chunked lists (split below the list length) must all give the direct sum
+    pos, mass = ic.hernquist(3001, 4)
+    ad, pd = oracle.direct(pos, mass, 0.02)
+    for split in (100000, 700, 129):
+        tune = L.default_tune(64)
+        tune.split = split
+        for prec, k in ((L.OTOO_FP64, 1e-13), (L.OTOO_FP32K, FP32_K)):
+            a, p, lists = run(pos, mass, 0.0, 64, 0.02, False, prec, tune=tune)
+            assert within_bound(a, p, ad, pd, pos, mass, 0.02, k), (split, prec)
+
+
+@pytest.mark.parametrize("block,iblock,tile", [(128, 1, 32), (128, 2, 64), (256, 1, 128), (256, 2, 256), (256, 4, 96)])
+def test_tuning_invariance(torch, block, iblock, tile):
+    pos, mass = ic.plummer(20000, 5)
+    ref, refp, _ = run(pos, mass, 0.6, 64, 1e-2, True, L.OTOO_FP64)
+    tune = L.Tune(block=block, iblock=iblock, tile=tile, split=max(tile, 300), ctas_per_sm=0)
+    for prec in (L.OTOO_FP64, L.OTOO_FP32K):
+        a, p, _ = run(pos, mass, 0.6, 64, 1e-2, True, prec, tune=tune)
+        a2, p2, _ = run(pos, mass, 0.6, 64, 1e-2, True, prec, tune=tune)
+        np.testing.assert_array_equal(a, a2)  # run to run: bit-identical
+        d = rel(a, ref)
+        if prec == L.OTOO_FP64:
+            assert d.max() <= 1e-10
+        else:
+            assert np.sqrt(np.mean(d * d)) <= 2e-6 and d.max() <= 2e-4
+
+
+def test_edge_cases(torch):
+    # one particle: its list is itself, the self pair is removed exactly
+    a, p, lists = run(np.array([[0.3, -0.2, 0.1]]), np.array([1.0], np.float32), 0.5, 64, 0.1, True, L.OTOO_FP64)
+    assert lists.n_groups == 1 and np.all(a == 0) and abs(p[0]) < 1e-14
+    # coincident particles: softening keeps them finite
+    pos = np.zeros((40, 3))
+    pos[20:] = 1e-9
+    mass = np.full(40, 0.025, np.float32)
+    ad, pd = oracle.direct(pos, mass, 0.01)
+    for prec in (L.OTOO_FP64, L.OTOO_FP32K):
+        a, p, _ = run(pos, mass, 0.5, 16, 0.01, True, prec)
+        assert np.all(np.isfinite(a)) and np.allclose(p, pd, rtol=1e-5)
+    # invalid inputs are rejected on the host with OTOO_EINVAL
+    with pytest.raises(L.OtooError) as ei:
+        S.build_system(np.array([[0.0, 0, 0], [1, 0, 0]]), np.ones(2, np.float32), 0.5, 64, 0.0)
+    assert ei.value.code == L.OTOO_EINVAL
+    with pytest.raises(L.OtooError):
+        S.build_system(np.array([[np.nan, 0, 0], [1, 0, 0]]), np.ones(2, np.float32), 0.5, 64, 0.1)
+
+
+def test_corrupt_list_index_is_reported(torch):
+    # an out-of-range list entry is caught by the kernel's bounds check (the
+    # entry is skipped) and reported as OTOO_EDEVICE; nothing is read out of range
+    pos, mass = ic.plummer(2000, 6)
+    tree, lists, plan = S.build_system(pos, mass, 0.5, 64, 0.01)
+    dev = S.DeviceSystem.upload(lists, plan, "cuda")
+    bad = lists.list.copy()
+    bad[5] = 1 << 30
+    dev.bufs["list"].copy_(torch.from_numpy(bad.view(np.uint8)).cuda())
+    with pytest.raises(L.OtooError) as ei:
+        S.force(dev, precision=L.OTOO_FP32K)
+    assert ei.value.code == L.OTOO_EDEVICE
+
+
+def test_host_entry_point_matches_device(torch):
+    pos, mass = ic.plummer(30000, 8)
+    tree, lists, plan = S.build_system(pos, mass, 0.5, 64, 1e-2)
+    dev = S.DeviceSystem.upload(lists, plan, "cuda")
+    a, p = S.force(dev, precision=L.OTOO_FP32K)
+    ah, ph = S.force_host(lists, plan, precision=L.OTOO_FP32K)
+    np.testing.assert_array_equal(a.cpu().numpy(), ah)
+    np.testing.assert_array_equal(p.cpu().numpy(), ph)
+
+
+def test_batch_packed_equals_separate(torch):
+    systems = ic.batch_systems(n_sys=12, log2_min=8, log2_max=12)
+    per = []
+    for pos, mass, eps in systems:
+        tree = S.Tree(pos, mass, 8)
+        per.append((tree, tree.lists(0.5, 64, eps, True)))
+    packed = S.Lists.pack([l for _, l in per])
+    tune = L.default_tune(64)
+    dev = S.DeviceSystem.upload(packed, packed.plan(tune), "cuda")
+    for prec in (L.OTOO_FP64, L.OTOO_FP32K):
+        a, p = S.force(dev, precision=prec)
+        a, p = a.cpu().numpy(), p.cpu().numpy()
+        off = packed.sys_part_off
+        for k, (tree, lists) in enumerate(per):
+            d = S.DeviceSystem.upload(lists, lists.plan(tune), "cuda")
+            ak, pk = S.force(d, precision=prec)
+            np.testing.assert_array_equal(a[off[k]:off[k + 1]], ak.cpu().numpy())
+            np.testing.assert_array_equal(p[off[k]:off[k + 1]], pk.cpu().numpy())
+    # per-system error against each system's own direct sum
+    a, p = S.force(dev, precision=L.OTOO_FP32K)
+    a = a.cpu().numpy()
+    for k, (pos, mass, eps) in enumerate(systems):
+        ad, _ = oracle.direct(pos, mass, eps)
+        assert np.sqrt(np.mean(rel(a[off[k]:off[k + 1]], ad) ** 2)) < 2e-3
