@@ -66,10 +66,13 @@ typedef struct otoo_params {
 } otoo_params;
 
 typedef struct otoo_tune {
-    int32_t block;                 /* threads per CTA: 128 or 256 */
-    int32_t iblock;                /* target particles per thread: 1 or 2 */
-    int32_t tile;                  /* list entries staged per shared-memory tile: 32..256 */
-    int32_t split;                 /* max list entries per work item (>= tile) */
+    int32_t block;                 /* threads per CTA: 64, 128 or 256 (the FP32 form runs
+                                      one independent work item per warp) */
+    int32_t iblock;                /* target particles per thread: 1, 2 or 4; a work item
+                                      holds at most 32 * iblock targets */
+    int32_t tile;                  /* list entries per staged tile: 32 or 64 (FP32 form; the
+                                      FP64 form stages block entries per tile) */
+    int32_t split;                 /* max list entries per work item (>= 32) */
     int32_t ctas_per_sm;           /* resident CTAs per SM for the persistent grid (0 = auto) */
     int32_t pad;
 } otoo_tune;
@@ -103,12 +106,14 @@ typedef struct otoo_group {
     int32_t sys;                   /* system index within a batch */
 } otoo_group;
 
-/* One work item: list entries [j0, j1) (relative to the group's list) of
-   group g.  slot < 0: the item covers the whole list and writes the outputs;
-   slot >= 0: the item writes FP64 partial sums at partial[slot * 4 * n_crit_max]
-   and otoo_force merges the chunks of each group in chunk order.  16 bytes. */
+/* One work item: target particles [i0, i0 + ni) of group g (relative to the
+   group's first particle) against list entries [j0, j1) (relative to the
+   group's list).  slot < 0: the item covers the whole list and writes the
+   outputs; slot >= 0: the item writes FP64 partial sums at
+   partial[(slot * n_crit_max + i) * 4 + 0..3] and otoo_force merges the list
+   chunks of each group in chunk order.  32 bytes. */
 typedef struct otoo_item {
-    int32_t g, j0, j1, slot;
+    int32_t g, i0, ni, j0, j1, slot, pad0, pad1;
 } otoo_item;
 
 /* A group whose list was split: its chunks' partials start at slot0 and run
@@ -132,6 +137,9 @@ typedef struct otoo_dev_system {
     const int64_t* perm;           /* [n_part] output index of each tree particle, NULL = tree order */
     double* partial;               /* scratch, >= otoo_plan_info.partial_doubles doubles */
     uint32_t* counter;             /* scratch, >= 4 uint32 (work ticket and status) */
+    void* split;                   /* scratch for OTOO_FP32K, >= 32 * n_src bytes: each source's
+                                      position as a float pair (hi = x rounded to FP32,
+                                      lo = x - hi rounded) and its mass */
 } otoo_dev_system;
 
 /* ---- opaque host handles ------------------------------------------------- */
@@ -190,9 +198,12 @@ int otoo_make_groups_and_lists(const otoo_tree* tree, const otoo_params* params,
    indices are rebased.  The inputs stay owned by the caller. */
 int otoo_pack_batch(const otoo_lists* const* per_sys, int32_t n_sys, otoo_lists** out);
 
-/* Work items for otoo_force: lists longer than tune->split entries are cut into
-   chunks of at most tune->split entries; items are ordered by decreasing
-   cost count * (j1 - j0) (longest processing time first). */
+/* Work items for otoo_force: groups with more than 32 * tune->iblock
+   particles are cut into particle chunks of at most that many, lists longer
+   than tune->split entries into chunks of at most tune->split entries (of
+   balanced length); items are ordered by decreasing cost ni * (j1 - j0)
+   (longest processing time first).  Groups with an empty list (a negative
+   per-group angle) get no item. */
 int otoo_make_plan(const otoo_lists* lists, const otoo_tune* tune, otoo_plan** out);
 
 /* Host arrays of a tree (pointers owned by the tree handle); cells are
@@ -273,30 +284,38 @@ int otoo_check_status(const otoo_dev_system* sys, void* stream);
    The forward kernel reads bf16 copies of the weights (bf16: device, 1313 uint16). */
 
 /* y[r] = network(x[r]) for r < n_rows; x: device [n_rows][6] FP32; y: device
-   [n_rows] FP32; wbf16: device bf16 parameters. */
+   [n_rows] FP32; wbf16: device bf16 parameters.  Asynchronous on stream. */
 int otoo_mlp_predict(const uint16_t* wbf16, const float* x, float* y, int64_t n_rows, void* stream);
 
-/* One training step on a batch: loss = mean (y - target)^2.  Computes the
-   gradient with the bf16 weights in the forward pass, accumulates it in FP32,
-   applies one Adam step (lr, beta1, beta2, eps_adam, step count t >= 1) to the
-   FP32 master weights w with moments m, v, refreshes wbf16 and writes the
-   batch loss to loss[0] (all device).  grad: device scratch [1313] FP32. */
-int otoo_mlp_train_step(float* w, uint16_t* wbf16, float* m, float* v, float* grad,
+/* Floats of device scratch the gradient and training calls need for n_rows
+   rows (one gradient partial per 128 rows). */
+int64_t otoo_mlp_scratch_floats(int64_t n_rows);
+
+/* Gradient of loss = (1/n) sum_r (y_r - target_r)^2 for the bf16 forward
+   pass: grad device [1313] FP32, loss device [1] (may be NULL).  The sum over
+   rows runs in a fixed order (deterministic).  scratch: device,
+   otoo_mlp_scratch_floats(n_rows) floats. */
+int otoo_mlp_grad(const uint16_t* wbf16, const float* x, const float* target, int64_t n_rows,
+                  float* scratch, float* grad, float* loss, void* stream);
+
+/* One training step on a batch: the gradient above, then one Adam step
+   (Kingma & Ba: lr, beta1, beta2, eps_adam, step count t >= 1, bias-corrected)
+   on the FP32 master weights w with moments m, v (device [1313] each); the
+   bf16 copy is rounded from the new w (nearest even); the batch loss before
+   the step goes to loss[0] (device, may be NULL). */
+int otoo_mlp_train_step(float* w, uint16_t* wbf16, float* m, float* v, float* scratch,
                         const float* x, const float* target, int64_t n_rows, float lr,
                         float beta1, float beta2, float eps_adam, int32_t t, float* loss,
                         void* stream);
 
-/* Gradient only (no update): grad = d loss / d w for the bf16 forward pass. */
-int otoo_mlp_grad(const uint16_t* wbf16, const float* x, const float* target, int64_t n_rows,
-                  float* grad, float* loss, void* stream);
-
-/* Round FP32 master weights to the bf16 copy (round to nearest even). */
+/* Round FP32 weights to the bf16 copy (round to nearest even). */
 int otoo_mlp_to_bf16(const float* w, uint16_t* wbf16, int32_t n, void* stream);
 
-/* Per-group theta choice: x holds n_groups * n_theta rows, row (g, k) being
-   group g's features with feature 5 = theta_grid[k] (grid increasing).
-   theta_out[g] = the largest theta_grid[k] with y(g, k) <= log10_target, or
-   fallback when none qualifies or a prediction is not finite.  Device arrays. */
+/* Per-group opening angle: x holds n_groups * n_theta rows, row (g, k) being
+   group g's features with the angle theta_grid[k] (grid increasing).
+   theta_out[g] = the largest theta_grid[k] whose prediction y(g, k) <=
+   log10_target, theta_grid[0] when none qualifies, fallback when any
+   prediction of the group is not finite.  Device arrays, async on stream. */
 int otoo_select_theta(const uint16_t* wbf16, const float* x, const float* theta_grid,
                       int32_t n_theta, int64_t n_groups, float log10_target, float fallback,
                       float* theta_out, void* stream);

@@ -59,7 +59,8 @@ class Group(ctypes.Structure):
 
 
 class Item(ctypes.Structure):
-    _fields_ = [("g", i32), ("j0", i32), ("j1", i32), ("slot", i32)]
+    _fields_ = [("g", i32), ("i0", i32), ("ni", i32), ("j0", i32), ("j1", i32), ("slot", i32), ("pad0", i32),
+                ("pad1", i32)]
 
 
 class Split(ctypes.Structure):
@@ -69,7 +70,8 @@ class Split(ctypes.Structure):
 class DevSystem(ctypes.Structure):
     _fields_ = [("n_part", i64), ("n_src", i64), ("n_list", i64), ("n_groups", i32), ("n_items", i32),
                 ("n_splits", i32), ("n_crit_max", i32), ("src", vp), ("quad", vp), ("groups", vp),
-                ("list", vp), ("items", vp), ("splits", vp), ("perm", vp), ("partial", vp), ("counter", vp)]
+                ("list", vp), ("items", vp), ("splits", vp), ("perm", vp), ("partial", vp), ("counter", vp),
+                ("split", vp)]
 
 
 class ListsView(ctypes.Structure):
@@ -90,7 +92,7 @@ class TreeView(ctypes.Structure):
                 ("cell_child0", vp), ("cell_org", vp), ("cell_com", vp), ("cell_mass", vp), ("cell_quad", vp)]
 
 
-for _s, _n in ((Src, 32), (Quad, 32), (Group, 64), (Item, 16), (Split, 16)):
+for _s, _n in ((Src, 32), (Quad, 32), (Group, 64), (Item, 32), (Split, 16)):
     assert ctypes.sizeof(_s) == _n, (_s, ctypes.sizeof(_s))
 
 # name -> (argtypes); every function returns int unless listed in _VOID
@@ -110,8 +112,15 @@ _SIGS = {
     "otoo_force": [ctypes.POINTER(DevSystem), vp, vp, i32, ctypes.POINTER(Tune), vp],
     "otoo_force_host": [ctypes.POINTER(ListsView), ctypes.POINTER(PlanInfo), vp, vp, i32, ctypes.POINTER(Tune), vp],
     "otoo_check_status": [ctypes.POINTER(DevSystem), vp],
+    "otoo_mlp_predict": [vp, vp, vp, i64, vp],
+    "otoo_mlp_scratch_floats": [i64],
+    "otoo_mlp_grad": [vp, vp, vp, i64, vp, vp, vp, vp],
+    "otoo_mlp_train_step": [vp, vp, vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp],
+    "otoo_mlp_to_bf16": [vp, vp, i32, vp],
+    "otoo_select_theta": [vp, vp, vp, i32, i64, f32, f32, vp, vp],
     "otoo_last_error": [],
 }
+_RET_I64 = {"otoo_mlp_scratch_floats"}
 _VOID = {"otoo_tree_free", "otoo_lists_free", "otoo_plan_free"}
 _OPTIONAL = set()
 
@@ -133,7 +142,14 @@ def load():
             raise ImportError("libotoo.so lacks %s" % name)
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = None if name in _VOID else (ctypes.c_char_p if name == "otoo_last_error" else ctypes.c_int)
+        if name in _VOID:
+            fn.restype = None
+        elif name == "otoo_last_error":
+            fn.restype = ctypes.c_char_p
+        elif name in _RET_I64:
+            fn.restype = i64
+        else:
+            fn.restype = ctypes.c_int
     _lib = lib
     return lib
 

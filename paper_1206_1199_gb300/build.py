@@ -16,7 +16,8 @@ LIB = os.path.join(PKG, "libotoo.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["host/tree.cpp"]
-CUDA_SRC = ["cuda/force.cu"]
+CUDA_HDR = ["cuda/force_warp.cuh"]
+CUDA_SRC = ["cuda/force.cu", "cuda/mlp.cu"]
 
 
 def _nvcc():
@@ -32,7 +33,7 @@ def _run(cmd):
 
 
 def sources():
-    return [os.path.join(CSRC, s) for s in HOST_SRC + CUDA_SRC] + [os.path.join(CSRC, "common.h"),
+    return [os.path.join(CSRC, s) for s in HOST_SRC + CUDA_SRC + CUDA_HDR] + [os.path.join(CSRC, "common.h"),
                                                                    os.path.join(INCLUDE, "otoo.h")]
 
 

@@ -10,16 +10,20 @@
 // reading (the paper keeps a softening length per particle but does not print
 // the law).
 //
-// Kernels
-//   k_force<float>   FP32 pairs on group-centre-relative coordinates (the
-//                    centre subtraction is FP64, once per staged entry),
-//                    plain FP32 sums over a tile, Kahan-compensated across
-//                    tiles, FP64 merge of the thread-level j-split and output.
-//   k_force<double>  every pair in FP64 (the comparison form).
-//   k_merge          FP64 sum of the chunk partials of split lists, in chunk
-//                    order (deterministic), plus the self-pair correction.
+// Kernels of one step (recorded into a CUDA graph):
+//   k_split       FP32 form only: each source position as a float pair
+//                 (hi, lo), once per step -- the FP64 work of the step.
+//   k_force_warp  FP32 form: one work item per warp, no block-wide barrier;
+//                 FP32 pairs on group-centre-relative coordinates, plain FP32
+//                 sums between Kahan-compensated flushes, FP64 merge of the
+//                 lane-level j-split and FP64 outputs.
+//   k_force_f64   FP64 form (comparison form): one work item per CTA, every
+//                 pair in FP64.
+//   k_merge       FP64 sum of the chunk partials of split lists, in chunk
+//                 order (deterministic).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -38,15 +42,24 @@ template <typename R> struct V2;
 template <> struct __align__(8) V2<float> { float x, y; };
 template <> struct __align__(16) V2<double> { double x, y; };
 
-__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+// FP32 reciprocal square root: the hardware approximation (PTX
+// rsqrt.approx.ftz.f32, relative error about 2^-23); the argument r^2 + eps^2
+// is never subnormal for eps > 0, so flushing subnormals changes nothing.
+__device__ __forceinline__ float rsqrt_r(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
 // Status bits written to counter[1].
 constexpr uint32_t kBadItem = 1u;
 constexpr uint32_t kBadIndex = 2u;
+constexpr unsigned kFull = 0xffffffffu;
 
-// Accumulator of one target particle: tile partial p, running sum s and
-// Kahan compensation c (FP32); FP64 keeps the running sum only.
+// Running sum of one target particle: FP32 with Kahan compensation c (the sum
+// is s - c), FP64 plain.
 template <typename R> struct Acc {
     R s[4], c[4];
     __device__ __forceinline__ void zero()
@@ -67,10 +80,7 @@ template <> __device__ __forceinline__ void Acc<float>::add(const float p[4])
         s[k] = t;
     }
 }
-template <> __device__ __forceinline__ double Acc<float>::value(int k) const
-{
-    return (double)s[k] - (double)c[k];
-}
+template <> __device__ __forceinline__ double Acc<float>::value(int k) const { return (double)s[k] - (double)c[k]; }
 template <> __device__ __forceinline__ void Acc<double>::add(const double p[4])
 {
 #pragma unroll
@@ -131,19 +141,78 @@ __device__ __forceinline__ void load_src(const otoo_src* src, int64_t idx, doubl
     m = __int_as_float((int)(__double_as_longlong(b.y) & 0xffffffffll));
 }
 
-template <typename R, int B, int IB>
-__global__ void __launch_bounds__(B) k_force(const otoo_dev_system sys, double* __restrict__ accel,
-                                             double* __restrict__ pot, int T)
+// Checks an item against the system's sizes; fills grp.
+__device__ __forceinline__ bool item_ok(const otoo_dev_system& sys, const otoo_item& item, otoo_group& grp, int max_ni)
 {
-    extern __shared__ __align__(32) unsigned char smem[];
-    V4<R>* s_src = reinterpret_cast<V4<R>*>(smem);
-    V4<R>* s_qa = s_src + T;
-    V2<R>* s_qb = reinterpret_cast<V2<R>*>(s_qa + T);
-    double* s_red = reinterpret_cast<double*>(s_qb + T);
+    if (item.g < 0 || item.g >= sys.n_groups) return false;
+    grp = sys.groups[item.g];
+    const int64_t L = (int64_t)grp.n_cell + grp.n_part;
+    return grp.count >= 1 && grp.first >= 0 && (int64_t)grp.first + grp.count <= sys.n_part && grp.n_cell >= 0 &&
+           grp.n_part >= 0 && item.ni >= 1 && item.ni <= max_ni && item.i0 >= 0 &&
+           (int64_t)item.i0 + item.ni <= grp.count && item.j0 >= 0 && item.j0 <= item.j1 && item.j1 <= L &&
+           grp.list_off >= 0 && grp.list_off + L <= sys.n_list && (item.slot < 0 || grp.count <= sys.n_crit_max);
+}
+
+// Final write of one target: the output, or the FP64 partial of the item's
+// list chunk.  The kernels take the self pair (r = 0, which adds -m_i / eps
+// to phi_i) out of the item whose list chunk starts at entry 0.
+__device__ __forceinline__ void write_target(const otoo_dev_system& sys, const otoo_group& grp, const otoo_item& item,
+                                             int i, const double a[4], double* __restrict__ accel,
+                                             double* __restrict__ pot)
+{
+    const int ig = item.i0 + i;
+    if (item.slot < 0) {
+        const int64_t t = (int64_t)grp.first + ig;
+        const int64_t o = sys.perm ? sys.perm[t] : t;
+        accel[3 * o] = a[0];
+        accel[3 * o + 1] = a[1];
+        accel[3 * o + 2] = a[2];
+        pot[o] = a[3];
+    } else {
+        double* dst = sys.partial + ((int64_t)item.slot * sys.n_crit_max + ig) * 4;
+        dst[0] = a[0];
+        dst[1] = a[1];
+        dst[2] = a[2];
+        dst[3] = a[3];
+    }
+}
+
+// Position split for the FP32 form, once per step: hi = x rounded to FP32,
+// lo = (x - hi) rounded to FP32.  A centre-relative coordinate is then
+// (hi - c) + lo in FP32 with c an FP32 value: hi - c is exact for every entry
+// within a factor of two of c (Sterbenz), so near entries keep the accuracy of
+// an FP64 subtraction rounded once to FP32, and far entries stay within about
+// one FP32 ulp of it.
+__global__ void k_split(const otoo_src* __restrict__ src, float4* __restrict__ out, int64_t n)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double x, y, z;
+    float m;
+    load_src(src, s, x, y, z, m);
+    const float hx = __double2float_rn(x), hy = __double2float_rn(y), hz = __double2float_rn(z);
+    out[2 * s] = make_float4(hx, hy, hz, m);
+    out[2 * s + 1] = make_float4(__double2float_rn(x - (double)hx), __double2float_rn(y - (double)hy),
+                                 __double2float_rn(z - (double)hz), 0.f);
+}
+
+#include "force_warp.cuh"
+
+// FP64 form: one work item per CTA of B threads, IB targets per thread,
+// B entries staged per tile, every pair in FP64.
+template <int B, int IB>
+__global__ void __launch_bounds__(B) k_force_f64(const otoo_dev_system sys, double* __restrict__ accel,
+                                                 double* __restrict__ pot)
+{
+    __shared__ V4<double> s_src[B];
+    __shared__ V4<double> s_qa[B];
+    __shared__ V2<double> s_qb[B];
+    __shared__ double s_red[B * IB * 4];
     __shared__ int s_ticket;
 
     const int tid = threadIdx.x;
     uint32_t* status = sys.counter + 1;
+    const bool has_quad = sys.quad != nullptr;
 
     for (;;) {
         if (tid == 0) s_ticket = (int)atomicAdd(sys.counter, 1u);
@@ -153,40 +222,32 @@ __global__ void __launch_bounds__(B) k_force(const otoo_dev_system sys, double* 
         if (it >= sys.n_items) break;
 
         const otoo_item item = sys.items[it];
-        bool ok = item.g >= 0 && item.g < sys.n_groups;
         otoo_group grp;
-        if (ok) grp = sys.groups[item.g];
-        const int L = ok ? grp.n_cell + grp.n_part : 0;
-        ok = ok && grp.count >= 1 && grp.count <= B * IB && grp.first >= 0 &&
-             (int64_t)grp.first + grp.count <= sys.n_part && grp.n_cell >= 0 && grp.n_part >= 0 &&
-             item.j0 >= 0 && item.j0 <= item.j1 && item.j1 <= L && grp.list_off >= 0 &&
-             grp.list_off + L <= sys.n_list && (item.slot < 0 || grp.count <= sys.n_crit_max);
-        if (!ok) {
+        if (!item_ok(sys, item, grp, B * IB)) {
             if (tid == 0) atomicOr(status, kBadItem);
             continue;
         }
-
-        const int ni = grp.count;
+        const int ni = item.ni;
         const int P = (ni + IB - 1) / IB;
         const int nsplit = B / P;
         const int islot = tid % P, js = tid / P;
         const bool active = js < nsplit;
-        const R eps2 = (R)grp.eps2;
+        const double eps2 = grp.eps2;
         const double cx = grp.cx, cy = grp.cy, cz = grp.cz;
 
-        R xi[IB], yi[IB], zi[IB];
-        Acc<R> acc[IB];
+        double xi[IB], yi[IB], zi[IB];
+        Acc<double> acc[IB];
 #pragma unroll
         for (int k = 0; k < IB; ++k) {
             const int i = islot + k * P;
-            xi[k] = yi[k] = zi[k] = R(0);
+            xi[k] = yi[k] = zi[k] = 0.0;
             if (active && i < ni) {
                 double x, y, z;
                 float m;
-                load_src(sys.src, (int64_t)grp.first + i, x, y, z, m);
-                xi[k] = (R)(x - cx);
-                yi[k] = (R)(y - cy);
-                zi[k] = (R)(z - cz);
+                load_src(sys.src, (int64_t)grp.first + item.i0 + i, x, y, z, m);
+                xi[k] = x - cx;
+                yi[k] = y - cy;
+                zi[k] = z - cz;
             }
             acc[k].zero();
         }
@@ -196,25 +257,22 @@ __global__ void __launch_bounds__(B) k_force(const otoo_dev_system sys, double* 
             const bool is_cell = seg == 0;
             const int s0 = is_cell ? item.j0 : max(item.j0, grp.n_cell);
             const int s1 = is_cell ? min(item.j1, grp.n_cell) : item.j1;
-            const bool quad = is_cell && sys.quad != nullptr;
-            for (int base = s0; base < s1; base += T) {
-                const int cnt = min(T, s1 - base);
-                for (int k = tid; k < cnt; k += B) {
-                    const int idx = __ldg(lst + base + k);
+            const bool quad = is_cell && has_quad;
+            for (int base = s0; base < s1; base += B) {
+                const int cnt = min(B, s1 - base);
+                if (tid < cnt) {
+                    const int idx = __ldg(lst + base + tid);
                     const bool good = is_cell ? (idx >= sys.n_part && idx < sys.n_src) : (idx >= 0 && idx < sys.n_part);
-                    V4<R> v = {R(0), R(0), R(0), R(0)};
+                    V4<double> v = {0, 0, 0, 0};
                     if (good) {
                         double x, y, z;
                         float m;
                         load_src(sys.src, idx, x, y, z, m);
-                        v.x = (R)(x - cx);
-                        v.y = (R)(y - cy);
-                        v.z = (R)(z - cz);
-                        v.w = (R)m;
+                        v = V4<double>{x - cx, y - cy, z - cz, (double)m};
                     } else {
                         atomicOr(status, kBadIndex);
                     }
-                    s_src[k] = v;
+                    s_src[tid] = v;
                     if (quad) {
                         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
                         if (good) {
@@ -222,28 +280,26 @@ __global__ void __launch_bounds__(B) k_force(const otoo_dev_system sys, double* 
                             a = __ldg(qp);
                             b = __ldg(qp + 1);
                         }
-                        s_qa[k] = V4<R>{(R)a.x, (R)a.y, (R)a.z, (R)a.w};
-                        s_qb[k] = V2<R>{(R)b.x, (R)b.y};
+                        s_qa[tid] = V4<double>{a.x, a.y, a.z, a.w};
+                        s_qb[tid] = V2<double>{b.x, b.y};
                     }
                 }
                 __syncthreads();
                 if (active) {
-                    R p[IB][4];
+                    double p[IB][4];
 #pragma unroll
-                    for (int k = 0; k < IB; ++k) p[k][0] = p[k][1] = p[k][2] = p[k][3] = R(0);
+                    for (int k = 0; k < IB; ++k) p[k][0] = p[k][1] = p[k][2] = p[k][3] = 0.0;
                     if (quad) {
-#pragma unroll 2
                         for (int j = js; j < cnt; j += nsplit) {
-                            const V4<R> s = s_src[j];
-                            const V4<R> qa = s_qa[j];
-                            const V2<R> qb = s_qb[j];
+                            const V4<double> s = s_src[j];
+                            const V4<double> qa = s_qa[j];
+                            const V2<double> qb = s_qb[j];
 #pragma unroll
                             for (int k = 0; k < IB; ++k) pair_quad(s, qa, qb, xi[k], yi[k], zi[k], eps2, p[k]);
                         }
                     } else {
-#pragma unroll 4
                         for (int j = js; j < cnt; j += nsplit) {
-                            const V4<R> s = s_src[j];
+                            const V4<double> s = s_src[j];
 #pragma unroll
                             for (int k = 0; k < IB; ++k) pair_mono(s, xi[k], yi[k], zi[k], eps2, p[k]);
                         }
@@ -255,7 +311,6 @@ __global__ void __launch_bounds__(B) k_force(const otoo_dev_system sys, double* 
             }
         }
 
-        // merge the thread-level j-split in FP64, in split order
         if (active) {
 #pragma unroll
             for (int k = 0; k < IB; ++k)
@@ -269,42 +324,38 @@ __global__ void __launch_bounds__(B) k_force(const otoo_dev_system sys, double* 
             for (int j = 0; j < nsplit; ++j)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) a[c] += s_red[((j * P + sl) * IB + k) * 4 + c];
-            if (item.slot < 0) {
-                const int64_t t = (int64_t)grp.first + i;
-                const int64_t o = sys.perm ? sys.perm[t] : t;
+            if (item.j0 == 0) {
+                // the self pair added -m_i rsqrt(eps^2) in FP64: take it out
                 double x, y, z;
                 float m;
-                load_src(sys.src, t, x, y, z, m);
-                // the self pair (r = 0) added -m_i / eps; take it out
-                a[3] += (double)m / sqrt(grp.eps2);
-                accel[3 * o] = a[0];
-                accel[3 * o + 1] = a[1];
-                accel[3 * o + 2] = a[2];
-                pot[o] = a[3];
-            } else {
-                double* dst = sys.partial + ((int64_t)item.slot * sys.n_crit_max + i) * 4;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) dst[c] = a[c];
+                load_src(sys.src, (int64_t)grp.first + item.i0 + i, x, y, z, m);
+                a[3] += (double)m * rsqrt(eps2);
             }
+            write_target(sys, grp, item, i, a, accel, pot);
         }
         __syncthreads();
     }
 }
 
-// Sum the chunk partials of each split list in chunk order.
+// Sum the chunk partials of each split list in chunk order (one warp per list).
 __global__ void k_merge(const otoo_dev_system sys, double* __restrict__ accel, double* __restrict__ pot)
 {
-    const otoo_split sp = sys.splits[blockIdx.x];
-    if (sp.g < 0 || sp.g >= sys.n_groups) {
-        if (threadIdx.x == 0) atomicOr(sys.counter + 1, kBadItem);
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= sys.n_splits) return;
+    const otoo_split sp = sys.splits[w];
+    bool ok = sp.g >= 0 && sp.g < sys.n_groups && sp.slot0 >= 0 && sp.n_chunks >= 1;
+    otoo_group grp;
+    if (ok) {
+        grp = sys.groups[sp.g];
+        ok = grp.count >= 1 && grp.count <= sys.n_crit_max && grp.first >= 0 &&
+             (int64_t)grp.first + grp.count <= sys.n_part;
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(sys.counter + 1, kBadItem);
         return;
     }
-    const otoo_group grp = sys.groups[sp.g];
-    if (grp.count > sys.n_crit_max || grp.first < 0 || (int64_t)grp.first + grp.count > sys.n_part) {
-        if (threadIdx.x == 0) atomicOr(sys.counter + 1, kBadItem);
-        return;
-    }
-    for (int i = threadIdx.x; i < grp.count; i += blockDim.x) {
+    for (int i = lane; i < grp.count; i += 32) {
         double a[4] = {0, 0, 0, 0};
         for (int c = 0; c < sp.n_chunks; ++c) {
             const double* s = sys.partial + ((int64_t)(sp.slot0 + c) * sys.n_crit_max + i) * 4;
@@ -313,10 +364,6 @@ __global__ void k_merge(const otoo_dev_system sys, double* __restrict__ accel, d
         }
         const int64_t t = (int64_t)grp.first + i;
         const int64_t o = sys.perm ? sys.perm[t] : t;
-        double x, y, z;
-        float m;
-        load_src(sys.src, t, x, y, z, m);
-        a[3] += (double)m / sqrt(grp.eps2);
         accel[3 * o] = a[0];
         accel[3 * o + 1] = a[1];
         accel[3 * o + 2] = a[2];
@@ -325,35 +372,36 @@ __global__ void k_merge(const otoo_dev_system sys, double* __restrict__ accel, d
 }
 
 // ---------------------------------------------------------------------------
-// host side: launch configuration, CUDA graph cache
+// host side: kernel choice, launch shape, CUDA graph cache
 
-template <typename R>
-size_t smem_bytes(int B, int IB, int T)
+using Kernel = void (*)(const otoo_dev_system, double*, double*);
+
+Kernel pick_f32(int B, int IB, int tile)
 {
-    return (size_t)T * (2 * sizeof(V4<R>) + sizeof(V2<R>)) + (size_t)B * IB * 4 * sizeof(double);
-}
-
-using KernelFn = void (*)(const otoo_dev_system, double*, double*, int);
-
-template <typename R>
-KernelFn pick_kernel(int B, int IB)
-{
-    if (B == 128 && IB == 1) return k_force<R, 128, 1>;
-    if (B == 128 && IB == 2) return k_force<R, 128, 2>;
-    if (B == 256 && IB == 1) return k_force<R, 256, 1>;
-    if (B == 256 && IB == 2) return k_force<R, 256, 2>;
-    if (B == 256 && IB == 4) return k_force<R, 256, 4>;
+    const int spl = tile / 32;
+#define PICK(NW_, IB_, SPL_) \
+    if (B == NW_ * 32 && IB == IB_ && spl == SPL_) return k_force_warp<NW_, IB_, SPL_>;
+    PICK(4, 1, 1) PICK(4, 2, 1) PICK(4, 4, 1) PICK(4, 2, 2) PICK(4, 4, 2)
+    PICK(2, 4, 1) PICK(2, 4, 2) PICK(8, 2, 1) PICK(8, 4, 1) PICK(8, 4, 2)
+#undef PICK
     return nullptr;
 }
 
-int check_tune(const otoo_tune* t, int n_crit_max)
+// FP64 form: B threads per CTA for a plan made with iblock targets per lane
+// (items of at most 32 * iblock targets).
+Kernel pick_f64(int IB)
+{
+    if (IB == 1) return k_force_f64<128, 1>;
+    if (IB == 2) return k_force_f64<128, 2>;
+    return k_force_f64<128, 4>;
+}
+
+int check_tune(const otoo_tune* t)
 {
     OTOO_REQUIRE(t, OTOO_EINVAL, "tune is NULL");
-    OTOO_REQUIRE(t->tile >= 16 && t->tile <= 1024, OTOO_EINVAL, "tile %d out of [16, 1024]", t->tile);
-    OTOO_REQUIRE(pick_kernel<float>(t->block, t->iblock) != nullptr, OTOO_EINVAL,
-                 "unsupported block %d / iblock %d", t->block, t->iblock);
-    OTOO_REQUIRE(t->block * t->iblock >= n_crit_max, OTOO_EINVAL, "block*iblock = %d < largest group %d",
-                 t->block * t->iblock, n_crit_max);
+    OTOO_REQUIRE(pick_f32(t->block, t->iblock, t->tile) != nullptr, OTOO_EINVAL,
+                 "unsupported tune: block %d, iblock %d, tile %d", t->block, t->iblock, t->tile);
+    OTOO_REQUIRE(t->split >= 32, OTOO_EINVAL, "split must be >= 32");
     OTOO_REQUIRE(t->ctas_per_sm >= 0 && t->ctas_per_sm <= 32, OTOO_EINVAL, "ctas_per_sm out of range");
     return OTOO_OK;
 }
@@ -369,24 +417,28 @@ int enqueue_force(const otoo_dev_system* sys, double* accel, double* pot, int pr
                   cudaStream_t s)
 {
     const bool fp64 = precision == OTOO_FP64;
-    KernelFn fn = fp64 ? pick_kernel<double>(t->block, t->iblock) : pick_kernel<float>(t->block, t->iblock);
-    const size_t sm = fp64 ? smem_bytes<double>(t->block, t->iblock, t->tile)
-                           : smem_bytes<float>(t->block, t->iblock, t->tile);
-    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    Kernel fn = fp64 ? pick_f64(t->iblock) : pick_f32(t->block, t->iblock, t->tile);
+    const int block = fp64 ? 128 : t->block;
     int dev = 0, nsm = 0, occ = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t->block, sm));
-    if (occ < 1) return set_error(OTOO_EINVAL, "force kernel does not fit on an SM (smem %zu)", sm);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, 0));
+    if (occ < 1) return set_error(OTOO_EINVAL, "force kernel does not fit on an SM");
     const int per_sm = t->ctas_per_sm > 0 ? std::min(t->ctas_per_sm, occ) : occ;
-    const int grid = (int)std::min<int64_t>(sys->n_items, (int64_t)nsm * per_sm);
+    const int64_t units = fp64 ? sys->n_items : ((int64_t)sys->n_items + block / 32 - 1) / (block / 32);
+    const int grid = (int)std::min<int64_t>(units, (int64_t)nsm * per_sm);
     CUDA_TRY(cudaMemsetAsync(sys->counter, 0, 2 * sizeof(uint32_t), s));
+    if (!fp64) {
+        const int64_t nb = (sys->n_src + 255) / 256;
+        k_split<<<(unsigned)nb, 256, 0, s>>>(sys->src, reinterpret_cast<float4*>(sys->split), sys->n_src);
+        CUDA_TRY(cudaGetLastError());
+    }
     if (grid > 0) {
-        fn<<<grid, t->block, sm, s>>>(*sys, accel, pot, t->tile);
+        fn<<<grid, block, 0, s>>>(*sys, accel, pot);
         CUDA_TRY(cudaGetLastError());
     }
     if (sys->n_splits > 0) {
-        k_merge<<<sys->n_splits, 128, 0, s>>>(*sys, accel, pot);
+        k_merge<<<(sys->n_splits + 3) / 4, 128, 0, s>>>(*sys, accel, pot);
         CUDA_TRY(cudaGetLastError());
     }
     return OTOO_OK;
@@ -417,11 +469,11 @@ int validate_sys(const otoo_dev_system* sys)
     OTOO_REQUIRE(sys, OTOO_EINVAL, "sys is NULL");
     OTOO_REQUIRE(sys->n_part >= 1 && sys->n_src >= sys->n_part && sys->n_src <= INT32_MAX, OTOO_EINVAL,
                  "bad sizes n_part %lld n_src %lld", (long long)sys->n_part, (long long)sys->n_src);
-    OTOO_REQUIRE(sys->n_groups >= 1 && sys->n_items >= 1 && sys->n_splits >= 0 && sys->n_list >= 1, OTOO_EINVAL,
+    OTOO_REQUIRE(sys->n_groups >= 1 && sys->n_items >= 0 && sys->n_splits >= 0 && sys->n_list >= 0, OTOO_EINVAL,
                  "bad counts");
     OTOO_REQUIRE(sys->n_crit_max >= 1 && sys->n_crit_max <= kMaxGroup, OTOO_EINVAL, "n_crit_max out of range");
-    OTOO_REQUIRE(sys->src && sys->groups && sys->list && sys->items && sys->counter, OTOO_EINVAL,
-                 "NULL device array");
+    OTOO_REQUIRE(sys->src && sys->groups && sys->counter && (sys->n_items == 0 || (sys->items && sys->list)),
+                 OTOO_EINVAL, "NULL device array");
     OTOO_REQUIRE(sys->n_splits == 0 || (sys->splits && sys->partial), OTOO_EINVAL, "split lists need partial scratch");
     return OTOO_OK;
 }
@@ -437,8 +489,10 @@ int otoo_force(const otoo_dev_system* sys, double* accel, double* pot, int32_t p
     if (rc) return rc;
     OTOO_REQUIRE(accel && pot, OTOO_EINVAL, "accel/pot is NULL");
     OTOO_REQUIRE(precision == OTOO_FP32K || precision == OTOO_FP64, OTOO_EINVAL, "bad precision %d", precision);
-    rc = check_tune(tune, sys->n_crit_max);
+    rc = check_tune(tune);
     if (rc) return rc;
+    OTOO_REQUIRE(precision == OTOO_FP64 || sys->split != nullptr, OTOO_EINVAL,
+                 "OTOO_FP32K needs the split scratch (32 bytes per source)");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     GraphKey key;
     std::memset(&key, 0, sizeof(key));
@@ -508,10 +562,11 @@ int otoo_check_status(const otoo_dev_system* sys, void* stream)
 
 namespace {
 
+constexpr int kHostBufs = 10;
 struct HostPathBuffers {
     int device = -1;
-    void* p[9] = {nullptr};
-    size_t cap[9] = {0};
+    void* p[kHostBufs] = {nullptr};
+    size_t cap[kHostBufs] = {0};
 };
 std::mutex g_host_mu;
 HostPathBuffers g_host;
@@ -534,26 +589,27 @@ extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* 
                                int32_t precision, const otoo_tune* tune, void* stream)
 {
     OTOO_REQUIRE(lv && pl && accel && pot, OTOO_EINVAL, "otoo_force_host: NULL argument");
-    OTOO_REQUIRE(lv->n_part >= 1 && lv->n_groups >= 1 && lv->n_list >= 1 && pl->n_items >= 1, OTOO_EINVAL,
-                 "otoo_force_host: empty input");
+    OTOO_REQUIRE(lv->n_part >= 1 && lv->n_groups >= 1, OTOO_EINVAL, "otoo_force_host: empty input");
     std::lock_guard<std::mutex> lock(g_host_mu);
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (g_host.device != dev) {
-        for (int k = 0; k < 9; ++k) g_host.p[k] = nullptr, g_host.cap[k] = 0;  // buffers of another device stay
+        // buffers of a previous device are left to that device's context
+        for (int k = 0; k < kHostBufs; ++k) g_host.p[k] = nullptr, g_host.cap[k] = 0;
         g_host.device = dev;
     }
     const int64_t nc = lv->n_src - lv->n_part;
-    const size_t bytes[9] = {sizeof(otoo_src) * (size_t)lv->n_src,
-                             sizeof(otoo_quad) * (size_t)std::max<int64_t>(nc, 1),
-                             sizeof(otoo_group) * (size_t)lv->n_groups,
-                             sizeof(int32_t) * (size_t)lv->n_list,
-                             sizeof(otoo_item) * (size_t)pl->n_items,
-                             sizeof(otoo_split) * (size_t)std::max<int64_t>(pl->n_splits, 1),
-                             sizeof(int64_t) * (size_t)lv->n_part,
-                             sizeof(double) * (size_t)(std::max<int64_t>(pl->partial_doubles, 1) + 4 * lv->n_part),
-                             sizeof(uint32_t) * 4};
-    for (int k = 0; k < 9; ++k) {
+    const size_t bytes[kHostBufs] = {sizeof(otoo_src) * (size_t)lv->n_src,
+                                     sizeof(otoo_quad) * (size_t)std::max<int64_t>(nc, 1),
+                                     sizeof(otoo_group) * (size_t)lv->n_groups,
+                                     sizeof(int32_t) * (size_t)std::max<int64_t>(lv->n_list, 1),
+                                     sizeof(otoo_item) * (size_t)std::max<int64_t>(pl->n_items, 1),
+                                     sizeof(otoo_split) * (size_t)std::max<int64_t>(pl->n_splits, 1),
+                                     sizeof(int64_t) * (size_t)lv->n_part,
+                                     sizeof(double) * (size_t)(std::max<int64_t>(pl->partial_doubles, 1) + 4 * lv->n_part),
+                                     sizeof(uint32_t) * 4,
+                                     32 * (size_t)lv->n_src};
+    for (int k = 0; k < kHostBufs; ++k) {
         int rc = ensure(k, bytes[k]);
         if (rc) return rc;
     }
@@ -561,8 +617,8 @@ extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* 
     CUDA_TRY(cudaMemcpyAsync(g_host.p[0], lv->src, bytes[0], cudaMemcpyHostToDevice, s));
     if (lv->use_quad && nc > 0) CUDA_TRY(cudaMemcpyAsync(g_host.p[1], lv->quad, bytes[1], cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(g_host.p[2], lv->groups, bytes[2], cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(g_host.p[3], lv->list, bytes[3], cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(g_host.p[4], pl->items, bytes[4], cudaMemcpyHostToDevice, s));
+    if (lv->n_list > 0) CUDA_TRY(cudaMemcpyAsync(g_host.p[3], lv->list, bytes[3], cudaMemcpyHostToDevice, s));
+    if (pl->n_items > 0) CUDA_TRY(cudaMemcpyAsync(g_host.p[4], pl->items, bytes[4], cudaMemcpyHostToDevice, s));
     if (pl->n_splits > 0) CUDA_TRY(cudaMemcpyAsync(g_host.p[5], pl->splits, bytes[5], cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(g_host.p[6], lv->perm, bytes[6], cudaMemcpyHostToDevice, s));
     otoo_dev_system sys;
@@ -584,6 +640,7 @@ extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* 
     double* out = (double*)g_host.p[7];
     sys.partial = out + 4 * lv->n_part;
     sys.counter = (uint32_t*)g_host.p[8];
+    sys.split = g_host.p[9];
     int rc = otoo_force(&sys, out, out + 3 * lv->n_part, precision, tune, stream);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(accel, out, sizeof(double) * 3 * (size_t)lv->n_part, cudaMemcpyDeviceToHost, s));

@@ -432,8 +432,8 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
         OTOO_REQUIRE(G <= INT32_MAX, OTOO_EINVAL, "too many groups");
         if (p->theta_per_group) {
             for (int64_t g = 0; g < G; ++g)
-                OTOO_REQUIRE(p->theta_per_group[g] >= 0.0f && std::isfinite(p->theta_per_group[g]), OTOO_EINVAL,
-                             "theta_per_group[%lld] invalid", (long long)g);
+                OTOO_REQUIRE(std::isfinite(p->theta_per_group[g]), OTOO_EINVAL, "theta_per_group[%lld] not finite",
+                             (long long)g);
         }
         otoo_lists* L = new otoo_lists();
         const int64_t n = t->n, nc = (int64_t)t->cells.size();
@@ -467,7 +467,7 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
                 const int64_t start = (int64_t)buf.size();
                 parts.clear();
                 stack.clear();
-                stack.push_back(0);
+                if (theta >= 0.0) stack.push_back(0);  // a negative angle skips the group
                 int64_t ncell = 0;
                 while (!stack.empty()) {
                     const int64_t c = stack.back();
@@ -646,11 +646,10 @@ int otoo_default_tune(int32_t n_crit, otoo_tune* tune)
 {
     OTOO_REQUIRE(tune, OTOO_EINVAL, "otoo_default_tune: NULL");
     OTOO_REQUIRE(n_crit >= 1 && n_crit <= kMaxGroup, OTOO_EINVAL, "n_crit out of range");
-    tune->block = n_crit > 128 ? 256 : 128;
-    tune->iblock = n_crit > 256 ? (n_crit + 255) / 256 : 1;
-    if (tune->iblock > 2) tune->iblock = 4;
-    tune->tile = 128;
-    tune->split = 2048;
+    tune->block = 128;
+    tune->iblock = 4;
+    tune->tile = 32;
+    tune->split = 4096;
     tune->ctas_per_sm = 0;
     tune->pad = 0;
     return OTOO_OK;
@@ -669,28 +668,52 @@ int otoo_make_plan(const otoo_lists* L, const otoo_tune* tune, otoo_plan** out)
         int32_t ncm = 1;
         for (const otoo_group& g : L->groups) ncm = std::max(ncm, g.count);
         P->n_crit_max = ncm;
+        const int32_t ib = std::max(1, tune->iblock);
+        const int32_t imax = 32 * ib;  // targets per item
+        // Device time of one item on a warp: its lanes step through the list
+        // in lockstep, ceil(len / nsub) steps of ib pairs each (nsub = 32 /
+        // ceil(ni / ib) lane subsets), plus staging and a fixed cost.  A group
+        // is cut into the number of particle chunks that minimises the sum.
+        auto item_cost = [&](int32_t ni, int64_t len) {
+            const int32_t P = (ni + ib - 1) / ib;
+            const int32_t nsub = 32 / P;
+            return (double)((len + nsub - 1) / nsub) * ib * 36.0 + 0.5 * (double)len + 300.0;
+        };
         int64_t slot = 0;
-        std::vector<std::pair<int64_t, int64_t>> order;  // (-cost, item index)
         for (size_t g = 0; g < L->groups.size(); ++g) {
             const otoo_group& og = L->groups[g];
             const int64_t len = (int64_t)og.n_cell + og.n_part;
+            if (len == 0) continue;  // skipped group
+            int32_t nic = (og.count + imax - 1) / imax;
+            {
+                double best = 0;
+                int32_t bestc = nic;
+                for (int32_t c = nic; c <= std::min<int32_t>(og.count, nic + 3); ++c) {
+                    const int32_t big = (og.count + c - 1) / c;
+                    const double cost = c * item_cost(big, len);
+                    if (c == nic || cost < best) best = cost, bestc = c;
+                }
+                nic = bestc;
+            }
             const int64_t nch = (len + tune->split - 1) / tune->split;
-            if (nch <= 1) {
-                P->items.push_back({(int32_t)g, 0, (int32_t)len, -1});
-                continue;
+            if (nch > 1) P->splits.push_back({(int32_t)g, (int32_t)slot, (int32_t)nch, 0});
+            for (int32_t ic = 0; ic < nic; ++ic) {
+                // balanced particle chunks
+                const int32_t i0 = (int32_t)((int64_t)og.count * ic / nic);
+                const int32_t i1 = (int32_t)((int64_t)og.count * (ic + 1) / nic);
+                for (int64_t k = 0; k < nch; ++k) {
+                    const int64_t j0 = len * k / nch, j1 = len * (k + 1) / nch;
+                    P->items.push_back({(int32_t)g, i0, i1 - i0, (int32_t)j0, (int32_t)j1,
+                                        nch > 1 ? (int32_t)(slot + k) : -1, 0, 0});
+                }
             }
-            P->splits.push_back({(int32_t)g, (int32_t)slot, (int32_t)nch, 0});
-            for (int64_t k = 0; k < nch; ++k) {
-                const int64_t j0 = len * k / nch, j1 = len * (k + 1) / nch;
-                P->items.push_back({(int32_t)g, (int32_t)j0, (int32_t)j1, (int32_t)(slot + k)});
-            }
-            slot += nch;
+            if (nch > 1) slot += nch;
         }
         OTOO_REQUIRE(slot <= INT32_MAX && P->items.size() <= (size_t)INT32_MAX, OTOO_EINVAL, "plan too large");
         P->partial_doubles = slot * 4 * (int64_t)ncm;
         std::vector<int64_t> cost(P->items.size());
         for (size_t i = 0; i < P->items.size(); ++i)
-            cost[i] = (int64_t)L->groups[P->items[i].g].count * (P->items[i].j1 - P->items[i].j0);
+            cost[i] = (int64_t)P->items[i].ni * (P->items[i].j1 - P->items[i].j0);
         std::vector<int64_t> idx(P->items.size());
         std::iota(idx.begin(), idx.end(), 0);
         std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
@@ -756,7 +779,7 @@ int otoo_group_features(const otoo_tree* t, const otoo_lists* L, float* feat)
         const double eps = std::sqrt(og.eps2);
         hd = std::max(hd, eps * 1e-3);
         float* f = feat + 5 * g;
-        f[0] = (float)std::log2((double)(og.n_cell + og.n_part));
+        f[0] = (float)std::log2((double)std::max(1, og.n_cell + og.n_part));
         f[1] = (float)std::log10(std::max(mincell, 1e-3));
         f[2] = (float)std::log10(hd / eps);
         f[3] = (float)(mall > 0 ? mcell / mall : 0.0);

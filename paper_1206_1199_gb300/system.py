@@ -187,16 +187,17 @@ class DeviceSystem:
         b["perm"] = _to_dev(lists.perm, device) if use_perm else None
         b["partial"] = torch.empty(max(plan.partial_doubles, 1), dtype=torch.float64, device=device)
         b["counter"] = torch.zeros(4, dtype=torch.int32, device=device)
+        b["split"] = torch.empty(lists.n_src * 8, dtype=torch.float32, device=device)
         s = L.DevSystem()
         s.n_part, s.n_src, s.n_list = lists.n_part, lists.n_src, lists.n_list
         s.n_groups, s.n_items, s.n_splits, s.n_crit_max = lists.n_groups, plan.n_items, plan.n_splits, plan.n_crit_max
-        for k in ("src", "quad", "groups", "list", "items", "splits", "perm", "partial", "counter"):
+        for k in ("src", "quad", "groups", "list", "items", "splits", "perm", "partial", "counter", "split"):
             setattr(s, k, b[k].data_ptr() if b[k] is not None else None)
         return cls(lists=lists, plan=plan, bufs=b, struct=s, use_perm=use_perm)
 
     def h2d_bytes(self):
         return sum(v.numel() * v.element_size() for k, v in self.bufs.items()
-                   if v is not None and k not in ("partial", "counter"))
+                   if v is not None and k not in ("partial", "counter", "split"))
 
 
 def force(dev, accel=None, pot=None, precision=L.OTOO_FP32K, tune=None, stream=None, check=True):

@@ -188,3 +188,50 @@ def test_tree_per_group_theta():
     tbk[r5["key"][::2]] = 0.0
     r = t.eval(0.5, 0.01, theta_by_key=tbk)
     assert np.all(r["n_cell"][::2] == 0) and np.all(r["n_part"][::2] == 4096)
+
+
+# ---------------------------------------------------------------------------
+# perceptron oracle
+
+from oracle import mlp as omlp  # noqa: E402
+
+
+def test_mlp_layout_and_bias_only_network():
+    assert omlp.NP == 1313
+    w = np.zeros(omlp.NP)
+    w[-1] = 0.75  # b3 only: y = b3 for every row
+    x = np.random.default_rng(1).normal(size=(10, 6))
+    np.testing.assert_array_equal(omlp.forward(w, x), 0.75)
+    # one hidden path: y = w3[0] tanh(W2[0,0] tanh(W1[0,2] x2))
+    w = np.zeros(omlp.NP)
+    W1, b1, W2, b2, w3, b3 = [a for a in omlp.unpack(np.arange(omlp.NP, dtype=float))]
+    w[2] = 0.5                      # W1[0][2]
+    w[192 + 32] = 2.0               # W2[0][0]
+    w[192 + 32 + 1024 + 32] = 3.0   # w3[0]
+    y = omlp.forward(w, x)
+    np.testing.assert_allclose(y, 3.0 * np.tanh(2.0 * np.tanh(0.5 * x[:, 2])), rtol=1e-15)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    w = rng.normal(scale=0.4, size=omlp.NP)
+    x = rng.normal(size=(40, 6))
+    t = rng.normal(size=40)
+    g = omlp.grad(w, x, t)
+    h = 1e-6
+    idx = np.concatenate([rng.choice(omlp.NP, 60, replace=False), [0, 191, 192, 1311, 1312]])
+    for k in idx:
+        e = np.zeros(omlp.NP)
+        e[k] = h
+        fd = (omlp.loss(w + e, x, t) - omlp.loss(w - e, x, t)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, g[k])
+
+
+def test_adam_first_step_and_bf16_rounding():
+    # first Adam step moves every weight by lr * sign(g) (bias correction)
+    g = np.array([0.3, -2.0, 1e-3])
+    w, m, v = omlp.adam(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, lr=0.01, eps=0.0)
+    np.testing.assert_allclose(w, -0.01 * np.sign(g), rtol=1e-12)
+    # bf16: 8 significand bits, ties to even
+    np.testing.assert_array_equal(omlp.bf16_round([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -3.0]),
+                                  [1.0, 1.0, 1.0 + 2 ** -6, -3.0])
