@@ -67,11 +67,12 @@ typedef struct otoo_params {
 
 typedef struct otoo_tune {
     int32_t block;                 /* threads per CTA: 64, 128 or 256 (the FP32 form runs
-                                      one independent work item per warp) */
+                                      one independent work item per warp; block, iblock
+                                      and tile must name a compiled variant) */
     int32_t iblock;                /* target particles per thread: 1, 2 or 4; a work item
                                       holds at most 32 * iblock targets */
-    int32_t tile;                  /* list entries per staged tile: 32 or 64 (FP32 form; the
-                                      FP64 form stages block entries per tile) */
+    int32_t tile;                  /* list entries per staged tile: 64, 128 or 256 (FP32
+                                      form; the FP64 form stages 128 entries per tile) */
     int32_t split;                 /* max list entries per work item (>= 32) */
     int32_t ctas_per_sm;           /* resident CTAs per SM for the persistent grid (0 = auto) */
     int32_t pad;

@@ -381,8 +381,8 @@ Kernel pick_f32(int B, int IB, int tile)
     const int spl = tile / 32;
 #define PICK(NW_, IB_, SPL_) \
     if (B == NW_ * 32 && IB == IB_ && spl == SPL_) return k_force_warp<NW_, IB_, SPL_>;
-    PICK(4, 1, 1) PICK(4, 2, 1) PICK(4, 4, 1) PICK(4, 2, 2) PICK(4, 4, 2)
-    PICK(2, 4, 1) PICK(2, 4, 2) PICK(8, 2, 1) PICK(8, 4, 1) PICK(8, 4, 2)
+    PICK(4, 1, 4) PICK(4, 2, 2) PICK(4, 2, 4) PICK(4, 2, 8) PICK(4, 4, 4) PICK(4, 4, 8)
+    PICK(2, 2, 4) PICK(2, 4, 4) PICK(8, 2, 4) PICK(8, 1, 4)
 #undef PICK
     return nullptr;
 }

@@ -6,41 +6,33 @@
 // the warp's nsub = 32 / P lane subsets take interleaved entries of each
 // staged tile, so one shared-memory read of an entry feeds IB pairs.
 //
-// Staging: a tile holds TE = (T / nsub) * nsub entries (T = 32 * SPL); the
-// last tile of a segment is padded with zero-mass records to a multiple of
-// nsub, so every active lane runs the same trip count.  Every lane converts
-// SPL entries (centre-relative FP32 from the per-step float pair of k_split)
-// into the warp's double buffer; the global loads of tile t+1 are issued
-// before tile t is evaluated; one __syncwarp per tile, no block barrier.
+// Staging: a tile holds up to T = 32 * SPL list entries.  Every lane loads
+// SPL entries (index, then the source's per-step float pair from k_split and,
+// for a cell, its quadrupole), converts them to group-centre-relative FP32
+// records and writes them to the warp's shared-memory tile; the tile is
+// padded with zero-mass records to a multiple of 2 nsub, so every active lane
+// runs the same even trip count and takes entries two at a time.  Large tiles
+// keep the per-tile work (loads, conversion, two __syncwarp) small against
+// the pairs; other warps cover the load latency.  No block-wide barrier.
 //
 // Records: a cell tile stores 48-byte records (x, y, z, m | Qxx, Qyy, Qzz,
 // Qxy | Qxz, Qyz, -, -), a particle tile 16-byte records (x, y, z, m).
 //
-// Sums: a lane accumulates pairs in plain FP32 per tile and adds the tile
-// sum to a Kahan-compensated running sum every FLUSH tiles; the lane subsets
-// are merged with a compensated FP32 sum in subset order and converted to
-// FP64 once.
+// Sums: a lane accumulates pairs in plain FP32 over a tile and adds the tile
+// sum to its Kahan-compensated running sum; the lane subsets are merged with
+// a compensated FP32 sum in subset order and converted to FP64 once.
 
-#ifndef OTOO_WARP_MINB
-#define OTOO_WARP_MINB 1  // minimum resident CTAs per SM requested from the register allocator
-#endif
-#ifndef OTOO_QUAD_UNROLL
-#define OTOO_QUAD_UNROLL 2
-#endif
-#ifndef OTOO_MONO_UNROLL
-#define OTOO_MONO_UNROLL 4
-#endif
-#define OTOO_PRAGMA(x) _Pragma(#x)
-#define OTOO_UNROLL(n) OTOO_PRAGMA(unroll n)
+// Resident warps per SM asked of the register allocator (more warps hide the
+// latency of the staged loads).
+constexpr int warp_min_blocks(int nw, int ib) { return (ib == 1 ? 24 : ib == 2 ? 20 : 12) / nw; }
 
 template <int NW, int IB, int SPL>
-__global__ void __launch_bounds__(NW * 32, OTOO_WARP_MINB) k_force_warp(const otoo_dev_system sys, double* __restrict__ accel,
-                                                        double* __restrict__ pot)
+__global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp(const otoo_dev_system sys,
+                                                                                 double* __restrict__ accel,
+                                                                                 double* __restrict__ pot)
 {
     constexpr int T = 32 * SPL;
-    constexpr int FLUSH = SPL >= 2 ? 1 : 2;
-    // two buffers of T 48-byte records per warp (float4 units)
-    __shared__ float4 s_rec[NW][2][3 * T];
+    __shared__ float4 s_rec[NW][3 * T];
 
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -67,14 +59,16 @@ __global__ void __launch_bounds__(NW * 32, OTOO_WARP_MINB) k_force_warp(const ot
         const int nsub = 32 / P;
         const int islot = lane % P, js = lane / P;
         const bool active = js < nsub;
-        const int TE = (T / nsub) * nsub;  // entries per tile (a multiple of nsub)
+        // records per tile are padded to a multiple of U = 2 nsub (nsub when a
+        // tile holds fewer than 2 nsub records)
+        const int U = T >= 2 * nsub ? 2 * nsub : nsub;
+        const int TE = (T / U) * U;  // entries per tile
         const float eps2 = (float)grp.eps2;
         // the group centre rounded to FP32 (any point near the group serves)
         const float cx = __double2float_rn(grp.cx), cy = __double2float_rn(grp.cy), cz = __double2float_rn(grp.cz);
 
         float xi[IB], yi[IB], zi[IB];
         Acc<float> acc[IB];
-        float p[IB][4];
 #pragma unroll
         for (int k = 0; k < IB; ++k) {
             const int i = islot + k * P;
@@ -88,7 +82,6 @@ __global__ void __launch_bounds__(NW * 32, OTOO_WARP_MINB) k_force_warp(const ot
                 zi[k] = (h.z - cz) + l.z;
             }
             acc[k].zero();
-            p[k][0] = p[k][1] = p[k][2] = p[k][3] = 0.f;
         }
 
         // tiles: the cell entries of [j0, j1) first, then the particle entries
@@ -98,101 +91,114 @@ __global__ void __launch_bounds__(NW * 32, OTOO_WARP_MINB) k_force_warp(const ot
         const int ntp = p1 > p0 ? (p1 - p0 + TE - 1) / TE : 0;
         const int nt = ntc + ntp;
         const int32_t* __restrict__ lst = sys.list + grp.list_off;
+        float4* __restrict__ rec = s_rec[wid];
 
-        float4 rh[SPL], rl[SPL], rqa[SPL], rqb[SPL];
-        int rstate[SPL];  // 0: no record, 1: zero record (padding), 2: entry
-        auto tile_base = [&](int t) { return t < ntc ? c0 + t * TE : p0 + (t - ntc) * TE; };
-        auto tile_cnt = [&](int t) { return t < ntc ? min(TE, c1 - (c0 + t * TE)) : min(TE, p1 - (p0 + (t - ntc) * TE)); };
-        auto fetch = [&](int t) {
-            const bool cell = t < ntc;
-            const int base = tile_base(t), cnt = tile_cnt(t);
-            const int cnt_pad = (cnt + nsub - 1) / nsub * nsub;
-#pragma unroll
-            for (int e = 0; e < SPL; ++e) {
-                const int k = lane + 32 * e;
-                rstate[e] = k < cnt ? 2 : (k < cnt_pad ? 1 : 0);
-                rh[e] = rl[e] = rqa[e] = rqb[e] = zero4;
-                if (rstate[e] != 2) continue;
-                const int idx = __ldg(lst + base + k);
-                const bool good = cell ? (idx >= sys.n_part && idx < sys.n_src) : (idx >= 0 && idx < sys.n_part);
-                if (!good) {
-                    atomicOr(status, kBadIndex);
-                    rstate[e] = 1;
-                    continue;
-                }
-                rh[e] = __ldg(ff + 2 * (int64_t)idx);
-                rl[e] = __ldg(ff + 2 * (int64_t)idx + 1);
-                if (cell && has_quad) {
-                    const float4* qp = reinterpret_cast<const float4*>(sys.quad + (idx - sys.n_part));
-                    rqa[e] = __ldg(qp);
-                    rqb[e] = __ldg(qp + 1);
-                }
-            }
-        };
-        auto store = [&](int t, int buf) {
-            const bool cq = t < ntc && has_quad;
-            float4* r = s_rec[wid][buf];
-#pragma unroll
-            for (int e = 0; e < SPL; ++e) {
-                if (rstate[e] == 0) continue;
-                const int k = lane + 32 * e;
-                const float4 a = rstate[e] == 2 ? make_float4((rh[e].x - cx) + rl[e].x, (rh[e].y - cy) + rl[e].y,
-                                                              (rh[e].z - cz) + rl[e].z, rh[e].w)
-                                                : zero4;
-                if (cq) {
-                    r[3 * k] = a;
-                    r[3 * k + 1] = rqa[e];
-                    r[3 * k + 2] = rqb[e];
-                } else {
-                    r[k] = a;
-                }
-            }
-        };
-
-        if (nt > 0) fetch(0);
         for (int t = 0; t < nt; ++t) {
-            const int buf = t & 1;
-            store(t, buf);
-            __syncwarp();
-            const int cnt = tile_cnt(t);
-            const int niter = (cnt + nsub - 1) / nsub;
-            const bool cq = t < ntc && has_quad;
-            if (t + 1 < nt) fetch(t + 1);
-            if (active) {
-                if (cq) {
-                    const float4* __restrict__ r = s_rec[wid][buf] + 3 * js;
-                    const int stride = 3 * nsub;
-                    OTOO_UNROLL(OTOO_QUAD_UNROLL)
-                    for (int n = 0; n < niter; ++n, r += stride) {
-                        const float4 sv = r[0];
-                        const float4 qa = r[1];
-                        const float4 qb = r[2];
-                        const V4<float> s4{sv.x, sv.y, sv.z, sv.w};
-                        const V4<float> qa4{qa.x, qa.y, qa.z, qa.w};
-                        const V2<float> qb2{qb.x, qb.y};
+            const bool cell = t < ntc;
+            const bool cq = cell && has_quad;
+            const int base = cell ? c0 + t * TE : p0 + (t - ntc) * TE;
+            const int cnt = cell ? min(TE, c1 - base) : min(TE, p1 - base);
+            const int cnt_pad = (cnt + U - 1) / U * U;
+
+            // stage: two entries per lane at a time, loads first
 #pragma unroll
-                        for (int k = 0; k < IB; ++k) pair_quad(s4, qa4, qb2, xi[k], yi[k], zi[k], eps2, p[k]);
-                    }
-                } else {
-                    const float4* __restrict__ r = s_rec[wid][buf] + js;
-                    OTOO_UNROLL(OTOO_MONO_UNROLL)
-                    for (int n = 0; n < niter; ++n, r += nsub) {
-                        const float4 sv = *r;
-                        const V4<float> s4{sv.x, sv.y, sv.z, sv.w};
+            for (int e0 = 0; e0 < SPL; e0 += 2) {
+                float4 h[2], l[2], qa[2], qb[2];
+                bool real[2], any[2];
 #pragma unroll
-                        for (int k = 0; k < IB; ++k) pair_mono(s4, xi[k], yi[k], zi[k], eps2, p[k]);
+                for (int u = 0; u < 2; ++u) {
+                    const int k = lane + 32 * (e0 + u);
+                    real[u] = k < cnt;
+                    any[u] = k < cnt_pad;
+                    h[u] = l[u] = qa[u] = qb[u] = zero4;
+                    if (real[u]) {
+                        const int idx = __ldg(lst + base + k);
+                        const bool good =
+                            cell ? (idx >= sys.n_part && idx < sys.n_src) : (idx >= 0 && idx < sys.n_part);
+                        if (good) {
+                            h[u] = __ldg(ff + 2 * (int64_t)idx);
+                            l[u] = __ldg(ff + 2 * (int64_t)idx + 1);
+                            if (cq) {
+                                const float4* qp = reinterpret_cast<const float4*>(sys.quad + (idx - sys.n_part));
+                                qa[u] = __ldg(qp);
+                                qb[u] = __ldg(qp + 1);
+                            }
+                        } else {
+                            atomicOr(status, kBadIndex);
+                            real[u] = false;
+                        }
                     }
                 }
-                if ((t + 1) % FLUSH == 0 || t + 1 == nt) {
 #pragma unroll
-                    for (int k = 0; k < IB; ++k) {
-                        acc[k].add(p[k]);
-                        p[k][0] = p[k][1] = p[k][2] = p[k][3] = 0.f;
+                for (int u = 0; u < 2; ++u) {
+                    if (!any[u]) continue;
+                    const int k = lane + 32 * (e0 + u);
+                    const float4 a = real[u] ? make_float4((h[u].x - cx) + l[u].x, (h[u].y - cy) + l[u].y,
+                                                           (h[u].z - cz) + l[u].z, h[u].w)
+                                             : zero4;
+                    if (cq) {
+                        rec[3 * k] = a;
+                        rec[3 * k + 1] = qa[u];
+                        rec[3 * k + 2] = qb[u];
+                    } else {
+                        rec[k] = a;
                     }
                 }
             }
+            __syncwarp();
+
+            if (active) {
+                float p[IB][4];
+#pragma unroll
+                for (int k = 0; k < IB; ++k) p[k][0] = p[k][1] = p[k][2] = p[k][3] = 0.f;
+                const int niter = cnt_pad / nsub;
+                if (cq) {
+                    const int S = 3 * nsub;
+                    const float4* __restrict__ r0 = rec + 3 * js;
+                    const float4* __restrict__ r1 = r0 + S;
+                    const float4* const rend = r0 + (niter & ~1) * S;
+                    for (; r0 < rend; r0 += 2 * S, r1 += 2 * S) {
+                        const float4 sa = r0[0], qa = r0[1], qb = r0[2];
+                        const float4 sb = r1[0], qc = r1[1], qd = r1[2];
+#pragma unroll
+                        for (int k = 0; k < IB; ++k) {
+                            pair_quad(V4<float>{sa.x, sa.y, sa.z, sa.w}, V4<float>{qa.x, qa.y, qa.z, qa.w},
+                                      V2<float>{qb.x, qb.y}, xi[k], yi[k], zi[k], eps2, p[k]);
+                            pair_quad(V4<float>{sb.x, sb.y, sb.z, sb.w}, V4<float>{qc.x, qc.y, qc.z, qc.w},
+                                      V2<float>{qd.x, qd.y}, xi[k], yi[k], zi[k], eps2, p[k]);
+                        }
+                    }
+                    if (niter & 1) {
+                        const float4 sa = r0[0], qa = r0[1], qb = r0[2];
+#pragma unroll
+                        for (int k = 0; k < IB; ++k)
+                            pair_quad(V4<float>{sa.x, sa.y, sa.z, sa.w}, V4<float>{qa.x, qa.y, qa.z, qa.w},
+                                      V2<float>{qb.x, qb.y}, xi[k], yi[k], zi[k], eps2, p[k]);
+                    }
+                } else {
+                    const float4* __restrict__ r0 = rec + js;
+                    const float4* __restrict__ r1 = r0 + nsub;
+                    const float4* const rend = r0 + (niter & ~1) * nsub;
+                    for (; r0 < rend; r0 += 2 * nsub, r1 += 2 * nsub) {
+                        const float4 sa = *r0, sb = *r1;
+#pragma unroll
+                        for (int k = 0; k < IB; ++k) {
+                            pair_mono(V4<float>{sa.x, sa.y, sa.z, sa.w}, xi[k], yi[k], zi[k], eps2, p[k]);
+                            pair_mono(V4<float>{sb.x, sb.y, sb.z, sb.w}, xi[k], yi[k], zi[k], eps2, p[k]);
+                        }
+                    }
+                    if (niter & 1) {
+                        const float4 sa = *r0;
+#pragma unroll
+                        for (int k = 0; k < IB; ++k)
+                            pair_mono(V4<float>{sa.x, sa.y, sa.z, sa.w}, xi[k], yi[k], zi[k], eps2, p[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < IB; ++k) acc[k].add(p[k]);
+            }
+            __syncwarp();
         }
-        __syncwarp();
 
         // merge the lane subsets into the js == 0 lanes, in subset order, with
         // a compensated FP32 sum; one conversion to FP64 per output value
@@ -206,9 +212,9 @@ __global__ void __launch_bounds__(NW * 32, OTOO_WARP_MINB) k_force_warp(const ot
                     const float so = __shfl_sync(kFull, acc[k].s[c], islot + j * P);
                     const float co = __shfl_sync(kFull, acc[k].c[c], islot + j * P);
                     const float y = __fsub_rn(__fsub_rn(so, co), C);
-                    const float t = __fadd_rn(S, y);
-                    C = __fsub_rn(__fsub_rn(t, S), y);
-                    S = t;
+                    const float tt = __fadd_rn(S, y);
+                    C = __fsub_rn(__fsub_rn(tt, S), y);
+                    S = tt;
                 }
                 a[c] = (double)S - (double)C;
             }

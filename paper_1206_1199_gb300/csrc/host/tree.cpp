@@ -647,8 +647,8 @@ int otoo_default_tune(int32_t n_crit, otoo_tune* tune)
     OTOO_REQUIRE(tune, OTOO_EINVAL, "otoo_default_tune: NULL");
     OTOO_REQUIRE(n_crit >= 1 && n_crit <= kMaxGroup, OTOO_EINVAL, "n_crit out of range");
     tune->block = 128;
-    tune->iblock = 4;
-    tune->tile = 32;
+    tune->iblock = 2;
+    tune->tile = 128;
     tune->split = 4096;
     tune->ctas_per_sm = 0;
     tune->pad = 0;

@@ -124,7 +124,7 @@ def test_theta0_many_groups_ragged(torch):
             assert within_bound(a, p, ad, pd, pos, mass, 0.02, k), (split, prec)
 
 
-@pytest.mark.parametrize("block,iblock,tile", [(128, 1, 32), (128, 2, 64), (128, 4, 32), (256, 4, 64), (64, 4, 32), (256, 2, 32)])
+@pytest.mark.parametrize("block,iblock,tile", [(128, 1, 128), (128, 2, 64), (128, 2, 256), (128, 4, 128), (64, 4, 128), (256, 2, 128)])
 def test_tuning_invariance(torch, block, iblock, tile):
     pos, mass = ic.plummer(20000, 5)
     ref, refp, _ = run(pos, mass, 0.6, 64, 1e-2, True, L.OTOO_FP64)
