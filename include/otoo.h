@@ -273,6 +273,39 @@ int otoo_force_host(const otoo_lists_view* lists, const otoo_plan_info* plan, do
    returns OTOO_EDEVICE if a kernel flagged bad data.  Synchronises stream. */
 int otoo_check_status(const otoo_dev_system* sys, void* stream);
 
+/* The force step of otoo_force for callers that cannot allocate device
+   memory: the work ticket, the status word, the per-step float pairs of the
+   FP32 form and the chunk partials of split lists live in a device array
+   that the library declares at file scope, so the call itself allocates
+   nothing (no cudaMalloc or cudaFree, directly or through any library).
+   Such callers include code running under a device-memory budget owned by
+   someone else (a host application's pool allocator that already holds the
+   GPU's memory, an embedding runtime whose allocator must not be bypassed),
+   and latency-critical loops that must not enter the driver's allocator.
+   There is no counterpart in the paper; this is a deployment option.
+     sys:       as for otoo_force; its partial, counter and split fields are
+                ignored (the array is used instead).
+     partial_doubles: the plan's otoo_plan_info.partial_doubles.
+     Scratch limit: otoo_force_static_capacity() bytes (16 MiB), shared as
+                256 bytes + 32 * n_src bytes (OTOO_FP32K only) + 8 *
+                partial_doubles bytes, each part rounded up to 256 bytes;
+                a larger step is rejected with OTOO_EINVAL before any launch.
+   Every GPU that loads the library holds the 16 MiB array until the process
+   exits.  The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress, once per device, with that device current); make
+   that first call before any stream capture.  Every call on a device uses
+   the same array and leaves its contents behind; the ticket and status word
+   are cleared by each call, everything else is overwritten before it is
+   read.  Calls whose work overlaps on the GPU (other streams, other host
+   threads) race on the array: serialise them.  The kernels are launched
+   directly on stream, asynchronously; otoo_check_status cannot read this
+   call's status word (it lives in the array). */
+int otoo_force_static(const otoo_dev_system* sys, int64_t partial_doubles, double* accel, double* pot,
+                      int32_t precision, const otoo_tune* tune, void* stream);
+
+/* Size in bytes of the array otoo_force_static uses. */
+int64_t otoo_force_static_capacity(void);
+
 /* ---- learned opening angle (multilayer perceptron 6-32-32-1) ---------------- */
 
 #define OTOO_MLP_IN  6

@@ -112,6 +112,8 @@ _SIGS = {
     "otoo_force": [ctypes.POINTER(DevSystem), vp, vp, i32, ctypes.POINTER(Tune), vp],
     "otoo_force_host": [ctypes.POINTER(ListsView), ctypes.POINTER(PlanInfo), vp, vp, i32, ctypes.POINTER(Tune), vp],
     "otoo_check_status": [ctypes.POINTER(DevSystem), vp],
+    "otoo_force_static": [ctypes.POINTER(DevSystem), i64, vp, vp, i32, ctypes.POINTER(Tune), vp],
+    "otoo_force_static_capacity": [],
     "otoo_mlp_predict": [vp, vp, vp, i64, vp],
     "otoo_mlp_scratch_floats": [i64],
     "otoo_mlp_grad": [vp, vp, vp, i64, vp, vp, vp, vp],
@@ -120,7 +122,7 @@ _SIGS = {
     "otoo_select_theta": [vp, vp, vp, i32, i64, f32, f32, vp, vp],
     "otoo_last_error": [],
 }
-_RET_I64 = {"otoo_mlp_scratch_floats"}
+_RET_I64 = {"otoo_mlp_scratch_floats", "otoo_force_static_capacity"}
 _VOID = {"otoo_tree_free", "otoo_lists_free", "otoo_plan_free"}
 _OPTIONAL = set()
 

@@ -647,3 +647,74 @@ extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* 
     CUDA_TRY(cudaMemcpyAsync(pot, out + 3 * lv->n_part, sizeof(double) * (size_t)lv->n_part, cudaMemcpyDeviceToHost, s));
     return otoo_check_status(&sys, stream);
 }
+
+// ---------------------------------------------------------------------------
+// otoo_force_static: the force step with its scratch in a library-held device
+// array, for callers that cannot allocate device memory themselves.
+
+namespace {
+
+// Scratch of otoo_force_static: the work ticket and status word, the per-step
+// float pairs of the FP32 form and the chunk partials of split lists.  Every
+// GPU that loads the library holds this array until the process exits.
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxStaticDevices] = {nullptr};
+
+// Device address of the array on the current device, looked up once per
+// device (the symbol's host-side name is not a device address).
+int static_scratch_ptr(void** out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    OTOO_REQUIRE(dev >= 0 && dev < kMaxStaticDevices, OTOO_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+        OTOO_REQUIRE(p != nullptr, OTOO_ECUDA, "cudaGetSymbolAddress returned NULL");
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return OTOO_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int64_t otoo_force_static_capacity(void) { return (int64_t)kStaticScratchBytes; }
+
+extern "C" int otoo_force_static(const otoo_dev_system* sys, int64_t partial_doubles, double* accel, double* pot,
+                                 int32_t precision, const otoo_tune* tune, void* stream)
+{
+    OTOO_REQUIRE(sys, OTOO_EINVAL, "sys is NULL");
+    OTOO_REQUIRE(accel && pot, OTOO_EINVAL, "accel/pot is NULL");
+    OTOO_REQUIRE(precision == OTOO_FP32K || precision == OTOO_FP64, OTOO_EINVAL, "bad precision %d", precision);
+    OTOO_REQUIRE(partial_doubles >= 0, OTOO_EINVAL, "partial_doubles < 0");
+    OTOO_REQUIRE(sys->n_src >= 0 && sys->n_src <= INT32_MAX, OTOO_EINVAL, "bad n_src");
+    const size_t need_counter = 256;
+    const size_t need_split = precision == OTOO_FP32K ? round256(32 * (size_t)sys->n_src) : 0;
+    const size_t need_partial = round256(sizeof(double) * (size_t)partial_doubles);
+    const size_t need = need_counter + need_split + need_partial;
+    OTOO_REQUIRE(need <= kStaticScratchBytes, OTOO_EINVAL,
+                 "otoo_force_static: this step needs %zu bytes of scratch, the library array holds %zu "
+                 "(32 bytes per source for OTOO_FP32K plus 8 per partial double); use otoo_force",
+                 need, kStaticScratchBytes);
+    void* base = nullptr;
+    int rc = static_scratch_ptr(&base);
+    if (rc) return rc;
+    otoo_dev_system s = *sys;
+    unsigned char* b = static_cast<unsigned char*>(base);
+    s.counter = reinterpret_cast<uint32_t*>(b);
+    s.split = need_split ? b + need_counter : nullptr;
+    s.partial = need_partial ? reinterpret_cast<double*>(b + need_counter + need_split) : nullptr;
+    rc = validate_sys(&s);
+    if (rc) return rc;
+    rc = check_tune(tune);
+    if (rc) return rc;
+    return enqueue_force(&s, accel, pot, precision, tune, reinterpret_cast<cudaStream_t>(stream));
+}
