@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--workload", default="hernquist8m")
     ap.add_argument("--n", type=int, default=0, help="override particle count (testing only)")
     ap.add_argument("--n-crit", type=int, default=0)
+    ap.add_argument("--tune", default="", help="block,iblock,tile,split (default: autotuner cache)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -70,11 +71,19 @@ def workload(args, rank=0):
     return w, pos, mass
 
 
-def load_tune(w, n_crit_max):
+def pick_tune(w, args):
+    """The autotuner's cached choice for this GPU and workload (it sets
+    n_crit), else the default tuning at the workload's n_crit."""
     from paper_1206_1199_gb300 import _lib as L
     from paper_1206_1199_gb300 import autotune
-    t = autotune.cached(w, n_crit_max)
-    return t if t is not None else L.default_tune(n_crit_max)
+    if getattr(args, "tune", None):
+        b, ib, tile, split = (int(v) for v in args.tune.split(","))
+        return L.Tune(block=b, iblock=ib, tile=tile, split=split, ctas_per_sm=0), "given"
+    entry = None if args.n_crit else autotune.lookup(w)
+    if entry:
+        w["n_crit"] = int(entry["n_crit"])
+        return L.Tune(**{k: int(v) for k, v in entry["tune"].items()}), "autotuned"
+    return L.default_tune(w["n_crit"]), "default"
 
 
 class Clocks:
@@ -143,13 +152,12 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev_name = "cuda:%d" % local
     w, pos, mass = workload(args, rank)
+    tune, tune_src = pick_tune(w, args)
     t0 = time.perf_counter()
     tree = S.Tree(pos, mass, w["leaf_size"])
     t1 = time.perf_counter()
     lists = tree.lists(w["theta"], w["n_crit"], w["eps"], w["use_quad"])
     t2 = time.perf_counter()
-    ncm = int(lists.groups["count"].max())
-    tune = load_tune(w, ncm)
     plan = lists.plan(tune)
     dev = S.DeviceSystem.upload(lists, plan, dev_name)
     n = lists.n_part
@@ -244,7 +252,8 @@ def run_ours(args):
         "config": {"workload": args.workload, "model": w["model"], "n": n, "eps": w["eps"], "theta": w["theta"],
                    "leaf_size": w["leaf_size"], "n_crit": w["n_crit"], "quadrupole": bool(lists.use_quad),
                    "groups": lists.n_groups, "list_entries": lists.n_list, "interactions": inter,
-                   "cell_interactions": cell_inter, "tune": tune.as_dict(), "items": plan.n_items,
+                   "cell_interactions": cell_inter, "tune": tune.as_dict(), "tune_source": tune_src,
+                   "items": plan.n_items,
                    "l2": "inputs larger than L2 (%.1f GB resident per step)" % (dev.h2d_bytes() / 1e9),
                    "host_tree_s": t1 - t0, "host_walk_s": t2 - t1, "parallelism": "replica per rank (weak)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -326,7 +335,7 @@ def cpu_baseline(w, pos, mass, seconds, tree=None):
     same workload: every k-th group, k chosen so the sample takes about
     `seconds`; the oracle's own tree build is not timed."""
     t = tree if tree is not None else oracle_tree(w, pos, mass)
-    stride = max(1, t.n_groups // 64)
+    stride = max(1, t.n_groups // 2048)
     t0 = time.perf_counter()
     r = t.eval(w["theta"], w["eps"], w["use_quad"], group_stride=stride)
     dt = time.perf_counter() - t0
@@ -347,6 +356,7 @@ def run_reference(args):
     if rank != 0:
         return
     w, pos, mass = workload(args, 0)
+    pick_tune(w, args)  # the same n_crit as the GPU arm
     steps = []
     per = max(2.0, 120.0 / max(1, args.steps + args.warmup))
     tree = oracle_tree(w, pos, mass)
