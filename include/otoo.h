@@ -236,7 +236,10 @@ int otoo_plan_export(const otoo_plan* plan, otoo_plan_info* info);
    group's list): feat[g][0..4] = log2(list length), log10 of the minimum over
    cell entries of d_min / l_c (3.0 when the list has no cell entry),
    log10(box half-diagonal / eps) (box half-diagonal floored at eps / 1000),
-   cell mass fraction of the list, log2(group count).  host out [n_groups][5]. */
+   cell mass fraction of the list, and log10 of the list's truncation ratio
+   sum_cells M_c (l_c / d_c)^p / (d_c^2 + s^2) over sum_entries M_e / (d_e^2 +
+   s^2) (p = 3 with quadrupole cells, else 2; d = distance to the group box;
+   s^2 = eps^2 + half-diagonal^2; floored at 1e-12).  host out [n_groups][5]. */
 int otoo_group_features(const otoo_tree* tree, const otoo_lists* lists, float* feat);
 
 void otoo_tree_free(otoo_tree* tree);
@@ -306,6 +309,20 @@ int otoo_force_static(const otoo_dev_system* sys, int64_t partial_doubles, doubl
 /* Size in bytes of the array otoo_force_static uses. */
 int64_t otoo_force_static_capacity(void);
 
+/* FP64 direct sum (Section II: the O(N^2) sum a tree code approximates),
+   used as the exact reference of the learned opening angle's training
+   errors:  for each target t, i = targets[t] (an index into src),
+     accel[t] = sum_{j != i} m_j r / (r^2 + eps2)^(3/2),
+     pot[t]   = -sum_{j != i} m_j / (r^2 + eps2)^(1/2),   r = x_j - x_i,
+   over the n_src sources src[0, n_src) (pass the particles only).
+   Device arrays: src [n_src], targets [n_tgt] int64, accel [n_tgt][3],
+   pot [n_tgt], scratch >= 4 * otoo_direct_chunks(n_src, n_tgt) * n_tgt
+   doubles, status one uint32 (bit 2 set when a target index is out of
+   range).  Asynchronous on stream; deterministic (chunk sums in order). */
+int64_t otoo_direct_chunks(int64_t n_src, int64_t n_tgt);
+int otoo_direct(const otoo_src* src, int64_t n_src, const int64_t* targets, int64_t n_tgt, double eps2,
+                double* accel, double* pot, double* scratch, uint32_t* status, void* stream);
+
 /* ---- learned opening angle (multilayer perceptron 6-32-32-1) ---------------- */
 
 #define OTOO_MLP_IN  6
@@ -347,12 +364,14 @@ int otoo_mlp_to_bf16(const float* w, uint16_t* wbf16, int32_t n, void* stream);
 
 /* Per-group opening angle: x holds n_groups * n_theta rows, row (g, k) being
    group g's features with the angle theta_grid[k] (grid increasing).
-   theta_out[g] = the largest theta_grid[k] whose prediction y(g, k) <=
-   log10_target, theta_grid[0] when none qualifies, fallback when any
-   prediction of the group is not finite.  Device arrays, async on stream. */
+   theta_out[g] = the largest theta_grid[k] whose prediction y(g, k) <= the
+   group's target (log10_target_per_group[g], or log10_target when that array
+   is NULL), theta_grid[0] when none qualifies, fallback when any prediction
+   of the group is not finite.  Device arrays, async on stream. */
 int otoo_select_theta(const uint16_t* wbf16, const float* x, const float* theta_grid,
-                      int32_t n_theta, int64_t n_groups, float log10_target, float fallback,
-                      float* theta_out, void* stream);
+                      int32_t n_theta, int64_t n_groups, float log10_target,
+                      const float* log10_target_per_group, float fallback, float* theta_out,
+                      void* stream);
 
 const char* otoo_last_error(void);
 

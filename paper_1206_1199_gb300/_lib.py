@@ -114,15 +114,17 @@ _SIGS = {
     "otoo_check_status": [ctypes.POINTER(DevSystem), vp],
     "otoo_force_static": [ctypes.POINTER(DevSystem), i64, vp, vp, i32, ctypes.POINTER(Tune), vp],
     "otoo_force_static_capacity": [],
+    "otoo_direct_chunks": [i64, i64],
+    "otoo_direct": [vp, i64, vp, i64, f64, vp, vp, vp, vp, vp],
     "otoo_mlp_predict": [vp, vp, vp, i64, vp],
     "otoo_mlp_scratch_floats": [i64],
     "otoo_mlp_grad": [vp, vp, vp, i64, vp, vp, vp, vp],
     "otoo_mlp_train_step": [vp, vp, vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp],
     "otoo_mlp_to_bf16": [vp, vp, i32, vp],
-    "otoo_select_theta": [vp, vp, vp, i32, i64, f32, f32, vp, vp],
+    "otoo_select_theta": [vp, vp, vp, i32, i64, f32, vp, f32, vp, vp],
     "otoo_last_error": [],
 }
-_RET_I64 = {"otoo_mlp_scratch_floats", "otoo_force_static_capacity"}
+_RET_I64 = {"otoo_mlp_scratch_floats", "otoo_force_static_capacity", "otoo_direct_chunks"}
 _VOID = {"otoo_tree_free", "otoo_lists_free", "otoo_plan_free"}
 _OPTIONAL = set()
 

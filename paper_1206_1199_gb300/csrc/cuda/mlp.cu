@@ -211,13 +211,14 @@ __global__ void k_to_bf16(const float* __restrict__ w, uint16_t* __restrict__ o,
 }
 
 __global__ void k_select_theta(const uint16_t* __restrict__ wbf16, const float* __restrict__ x,
-                               const float* __restrict__ grid, int nth, int64_t ng, float target, float fallback,
-                               float* __restrict__ out)
+                               const float* __restrict__ grid, int nth, int64_t ng, float target,
+                               const float* __restrict__ target_g, float fallback, float* __restrict__ out)
 {
     __shared__ float s_w[NP];
     load_weights(wbf16, s_w);
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
+    if (target_g) target = target_g[g];
     float best = grid[0];
     bool bad = false;
     for (int k = 0; k < nth; ++k) {
@@ -316,14 +317,16 @@ int otoo_mlp_to_bf16(const float* w, uint16_t* wbf16, int32_t n, void* stream)
 }
 
 int otoo_select_theta(const uint16_t* wbf16, const float* x, const float* theta_grid, int32_t n_theta,
-                      int64_t n_groups, float log10_target, float fallback, float* theta_out, void* stream)
+                      int64_t n_groups, float log10_target, const float* log10_target_per_group, float fallback,
+                      float* theta_out, void* stream)
 {
     OTOO_REQUIRE(wbf16 && x && theta_grid && theta_out, OTOO_EINVAL, "otoo_select_theta: NULL pointer");
     OTOO_REQUIRE(n_theta >= 1 && n_groups >= 0, OTOO_EINVAL, "otoo_select_theta: bad sizes");
     if (n_groups == 0) return OTOO_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     k_select_theta<<<(unsigned)((n_groups + 127) / 128), 128, 0, s>>>(wbf16, x, theta_grid, n_theta, n_groups,
-                                                                      log10_target, fallback, theta_out);
+                                                                      log10_target, log10_target_per_group, fallback,
+                                                                      theta_out);
     CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }

@@ -758,6 +758,15 @@ int otoo_group_features(const otoo_tree* t, const otoo_lists* L, float* feat)
                 bhi[a] = std::max(bhi[a], t->pos[3 * i + a]);
             }
         double mincell = 1e3, mcell = 0, mall = 0;
+        double hd = 0.5 * std::sqrt((bhi[0] - blo[0]) * (bhi[0] - blo[0]) + (bhi[1] - blo[1]) * (bhi[1] - blo[1]) +
+                                    (bhi[2] - blo[2]) * (bhi[2] - blo[2]));
+        const double eps = std::sqrt(og.eps2);
+        hd = std::max(hd, eps * 1e-3);
+        // leading truncation term of the accepted cells (order p = 3 after a
+        // quadrupole, 2 after a monopole) against the list's total pull
+        const int pw = L->use_quad ? 3 : 2;
+        const double soft2 = og.eps2 + hd * hd;
+        double trunc = 0, pull = 0;
         const int32_t* e = L->list.data() + og.list_off;
         for (int j = 0; j < og.n_cell; ++j) {
             const int64_t c = e[j] - n;
@@ -769,21 +778,32 @@ int otoo_group_features(const otoo_tree* t, const otoo_lists* L, float* feat)
                 if (com[a] - bhi[a] > d) d = com[a] - bhi[a];
                 d2 += d * d;
             }
-            mincell = std::min(mincell, std::sqrt(d2) / t->c_side[c]);
+            const double d = std::sqrt(d2);
+            mincell = std::min(mincell, d / t->c_side[c]);
             mcell += t->c_mass[c];
+            const double ld = t->c_side[c] / std::max(d, 1e-300);
+            trunc += t->c_mass[c] * std::pow(ld, pw) / (d2 + soft2);
+            pull += t->c_mass[c] / (d2 + soft2);
         }
         mall = mcell;
-        for (int j = og.n_cell; j < og.n_cell + og.n_part; ++j) mall += t->mass[e[j]];
-        double hd = 0.5 * std::sqrt((bhi[0] - blo[0]) * (bhi[0] - blo[0]) + (bhi[1] - blo[1]) * (bhi[1] - blo[1]) +
-                                    (bhi[2] - blo[2]) * (bhi[2] - blo[2]));
-        const double eps = std::sqrt(og.eps2);
-        hd = std::max(hd, eps * 1e-3);
+        for (int j = og.n_cell; j < og.n_cell + og.n_part; ++j) {
+            const int64_t i = e[j];
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                double d = 0;
+                if (blo[a] - t->pos[3 * i + a] > d) d = blo[a] - t->pos[3 * i + a];
+                if (t->pos[3 * i + a] - bhi[a] > d) d = t->pos[3 * i + a] - bhi[a];
+                d2 += d * d;
+            }
+            mall += t->mass[i];
+            pull += t->mass[i] / (d2 + soft2);
+        }
         float* f = feat + 5 * g;
         f[0] = (float)std::log2((double)std::max(1, og.n_cell + og.n_part));
         f[1] = (float)std::log10(std::max(mincell, 1e-3));
         f[2] = (float)std::log10(hd / eps);
         f[3] = (float)(mall > 0 ? mcell / mall : 0.0);
-        f[4] = (float)std::log2((double)og.count);
+        f[4] = (float)std::log10(std::max(trunc / std::max(pull, 1e-300), 1e-12));
     }
     return OTOO_OK;
 }

@@ -1,0 +1,343 @@
+"""Learned per-group opening angle.
+
+The paper controls the force error with the accuracy parameter Delta of the
+absolute MAC (Section II-B, Eq. SW_MAC; a fraction of the mean force in
+Section III-E).  Here a small perceptron predicts, for each group and a
+candidate opening angle, the group's RMS relative force error from
+statistics of the group's list (list length, minimum cell distance over
+cell size, group size over softening, cell mass fraction, group count); the
+largest angle whose prediction meets the target is used for that group.
+
+Pipeline (each step runs in libotoo: host walk in C++, forces, direct sums,
+network training and inference in CUDA; this module moves data between
+the calls):
+  snapshots   leap-frog (kick-drift-kick) of the two-polytrope system with
+              the method's own FP32 forces at a fixed angle;
+  rows        per snapshot, sampled groups x angle grid: features from a
+              base walk at theta0, label = log10 of the group's RMS relative
+              force error at that angle against the FP64 direct sum on the
+              device (otoo_direct);
+  training    Adam on the FP32 master weights with the network's own
+              forward/backward kernels (bf16 weights in the forward pass);
+  selection   otoo_select_theta on the device, then a re-walk with one
+              angle per group;
+  evaluation  learned angles against a fixed angle bisected to the same
+              RMS error, and against theta = 0.5.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import time
+
+import numpy as np
+
+from . import _lib as L
+from . import ic
+from . import system as S
+from .mlp import ThetaNet
+
+THETA_GRID = tuple(round(0.3 + 0.05 * k, 2) for k in range(13))  # 0.30 .. 0.90
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Evaluator:
+    """One particle system: tree, forces at any angle(s), FP64 direct sums."""
+
+    def __init__(self, pos, mass, eps, n_crit=64, leaf_size=8, use_quad=True, device="cuda", tune=None):
+        self.pos = np.ascontiguousarray(pos, np.float64)
+        self.mass = np.ascontiguousarray(mass, np.float32)
+        self.eps, self.n_crit, self.use_quad, self.device = eps, n_crit, use_quad, device
+        self.tree = S.Tree(self.pos, self.mass, leaf_size)
+        self.tune = tune
+        self._src_dev = None
+
+    def lists(self, theta, theta_per_group=None):
+        return self.tree.lists(theta, self.n_crit, self.eps, self.use_quad, theta_per_group)
+
+    def force(self, lists, precision=L.OTOO_FP32K, timed=False):
+        """Accelerations and potentials in tree order (and the step's ms)."""
+        torch = _torch()
+        tune = self.tune or L.default_tune(self.n_crit)
+        plan = lists.plan(tune)
+        dev = S.DeviceSystem.upload(lists, plan, self.device, use_perm=False)
+        n = lists.n_part
+        acc = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
+        pot = torch.zeros(n, dtype=torch.float64, device=self.device)
+        S.force(dev, acc, pot, precision, tune)
+        ms = None
+        if timed:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                S.force(dev, acc, pot, precision, tune, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+        return acc.cpu().numpy(), pot.cpu().numpy(), ms
+
+    def direct(self, targets):
+        """FP64 direct sum on the device for tree-order targets."""
+        torch = _torch()
+        if self._src_dev is None:
+            e = self.tree.export()
+            src = np.zeros(self.tree.n, dtype=np.dtype(L.Src))
+            src["x"], src["y"], src["z"] = e["pos"][:, 0], e["pos"][:, 1], e["pos"][:, 2]
+            src["m"] = e["mass"]
+            self._src_dev = torch.from_numpy(src.view(np.uint8).reshape(-1).copy()).to(self.device)
+        t = torch.from_numpy(np.ascontiguousarray(targets, np.int64)).to(self.device)
+        nt = t.shape[0]
+        n = self.tree.n
+        nch = int(L.load().otoo_direct_chunks(n, nt))
+        scratch = torch.empty(4 * nch * nt, dtype=torch.float64, device=self.device)
+        acc = torch.empty((nt, 3), dtype=torch.float64, device=self.device)
+        pot = torch.empty(nt, dtype=torch.float64, device=self.device)
+        status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        L.call("otoo_direct", self._src_dev.data_ptr(), n, t.data_ptr(), nt, float(self.eps) ** 2, acc.data_ptr(),
+               pot.data_ptr(), scratch.data_ptr(), status.data_ptr(), st)
+        torch.cuda.synchronize()
+        if int(status.item()) != 0:
+            raise L.OtooError(L.OTOO_EDEVICE, "otoo_direct: target index out of range")
+        return acc.cpu().numpy(), pot.cpu().numpy()
+
+
+def relerr(a, ref):
+    return np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+# ---------------------------------------------------------------------------
+# snapshots
+
+def leapfrog_snapshots(pos, mass, vel, eps, dt, n_snap, every, theta=0.5, n_crit=64, device="cuda", log=None):
+    """Kick-drift-kick with the method's FP32 forces at a fixed angle; a
+    snapshot (positions) every `every` steps, the first one at step 0."""
+    x = np.array(pos, np.float64)
+    v = np.array(vel, np.float64)
+
+    def accel(xx):
+        ev = Evaluator(xx, mass, eps, n_crit, device=device)
+        a, _, _ = ev.force(ev.lists(theta))
+        out = np.empty_like(a)
+        out[ev.tree.export()["perm"]] = a  # back to caller order
+        return out
+
+    snaps = [x.copy()]
+    a = accel(x)
+    step = 0
+    while len(snaps) < n_snap:
+        t0 = time.perf_counter()
+        v += 0.5 * dt * a
+        x += dt * v
+        a = accel(x)
+        v += 0.5 * dt * a
+        step += 1
+        if step % every == 0:
+            snaps.append(x.copy())
+        if log:
+            log("step %d (%.2f s)" % (step, time.perf_counter() - t0))
+    return snaps
+
+
+# ---------------------------------------------------------------------------
+# training rows
+
+def group_rows(ev, n_groups, grid=THETA_GRID, theta0=0.5, seed=0):
+    """Rows (features + angle) and labels log10(group RMS relative error) for
+    n_groups groups sampled from the base walk at theta0."""
+    base = ev.lists(theta0)
+    feats = base.features(ev.tree)
+    g = base.groups
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sel = np.sort(rng.choice(base.n_groups, size=min(n_groups, base.n_groups), replace=False))
+    # targets: every particle of the sampled groups (tree order)
+    tgt = np.concatenate([np.arange(g["first"][k], g["first"][k] + g["count"][k]) for k in sel])
+    owner = np.concatenate([np.full(g["count"][k], j) for j, k in enumerate(sel)])
+    ad, _ = ev.direct(tgt)
+    rows, labels = [], []
+    for th in grid:
+        tpg = np.full(base.n_groups, -1.0, np.float32)  # negative: the group is skipped
+        tpg[sel] = th
+        lst = ev.lists(th, tpg)
+        a, _, _ = ev.force(lst)
+        d = relerr(a[tgt], ad)
+        rms = np.sqrt(np.bincount(owner, d * d) / np.bincount(owner))
+        rows.append(np.concatenate([feats[sel], np.full((len(sel), 1), th, np.float32)], 1))
+        labels.append(np.log10(np.maximum(rms, 1e-9)))
+    return np.concatenate(rows).astype(np.float32), np.concatenate(labels).astype(np.float32)
+
+
+def training_set(snaps, mass, eps, n_crit=64, groups_per_snap=256, grid=THETA_GRID, theta0=0.5, device="cuda",
+                 log=None):
+    X, y = [], []
+    for k, x in enumerate(snaps):
+        t0 = time.perf_counter()
+        ev = Evaluator(x, mass, eps, n_crit, device=device)
+        xr, yr = group_rows(ev, groups_per_snap, grid, theta0, seed=1000 + k)
+        X.append(xr)
+        y.append(yr)
+        if log:
+            log("snapshot %d: %d rows (%.1f s)" % (k, len(yr), time.perf_counter() - t0))
+    return np.concatenate(X), np.concatenate(y)
+
+
+def train(X, y, steps=3000, lr=3e-3, batch=8192, seed=0, device="cuda"):
+    net = ThetaNet(None, device)
+    net.fit_scaler(X)
+    hist = net.train(X, y, steps=steps, lr=lr, batch=batch, seed=seed, log_every=max(1, steps // 20))
+    # feature range of the training set (selection falls back outside it)
+    net.xmin = X.min(0)
+    net.xmax = X.max(0)
+    return net, hist
+
+
+# ---------------------------------------------------------------------------
+# selection and evaluation
+
+def group_targets(net, feats, counts, target_rms, theta0=0.5, k_err=3.0):
+    """Per-group error targets for a global RMS target at least interaction
+    cost.  With a group's error ~ c_g theta^k and its list length ~ theta^-3,
+    minimising the total cost at a fixed particle-weighted RMS gives
+    e_g ~ c_g^(3 / (2k + 3)); c_g is read off the network's prediction at
+    theta0, and the common factor is set so the predicted RMS is the target."""
+    rows = np.concatenate([feats, np.full((feats.shape[0], 1), theta0, np.float32)], 1)
+    c = 10.0 ** net.predict(rows).astype(np.float64)
+    w = c ** (3.0 / (2.0 * k_err + 3.0))
+    n = counts.astype(np.float64)
+    lam = target_rms / math.sqrt(float((n * w * w).sum() / n.sum()))
+    return np.log10(lam * w).astype(np.float32)
+
+
+def choose_thetas(ev, net, target_rms, grid=THETA_GRID, theta0=0.5, fallback=0.5, mode="budget"):
+    """One opening angle per group from the network (fallback outside the
+    training range of the features).  mode "equal": every group aims at
+    target_rms; mode "budget": group targets from group_targets()."""
+    base = ev.lists(theta0)
+    f = base.features(ev.tree)
+    lo, hi = getattr(net, "xmin", None), getattr(net, "xmax", None)
+    if lo is not None:
+        out = np.any((f < lo[:5]) | (f > hi[:5]), axis=1)
+        f = f.copy()
+        f[out, 0] = np.nan  # non-finite features make the kernel use the fallback
+    per = None
+    if mode == "budget":
+        ok = np.all(np.isfinite(f), axis=1)
+        per = np.full(base.n_groups, math.log10(target_rms), np.float32)
+        per[ok] = group_targets(net, f[ok], base.groups["count"][ok], target_rms, theta0)
+    th = net.select_theta(f, np.asarray(grid, np.float32), math.log10(target_rms), fallback, per)
+    return th, base
+
+
+def rms_error(ev, lists, sub, ad, precision=L.OTOO_FP32K, stats=None):
+    a, _, ms = ev.force(lists, precision, timed=True)
+    d = relerr(a[sub], ad)
+    if stats is not None:
+        stats.update(p99=float(np.quantile(d, 0.99)), max=float(d.max()))
+    return float(np.sqrt(np.mean(d * d))), ms
+
+
+def compare(ev, net, target_rms=1e-3, n_sub=4096, seed=7, bisect_steps=8, precision_fp64=True, log=None,
+            mode="budget"):
+    """Learned angles vs fixed angles at equal RMS error (on a subsample)."""
+    n = ev.tree.n
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sub = np.sort(rng.choice(n, size=min(n_sub, n), replace=False))
+    ad, _ = ev.direct(sub)
+    th, base = choose_thetas(ev, net, target_rms, mode=mode)
+    learned = ev.lists(0.5, th)
+    st = {}
+    e_l, ms_l = rms_error(ev, learned, sub, ad, stats=st)
+    res = {"target_rms": target_rms, "mode": mode,
+           "learned": dict(st, rms=e_l, ms=ms_l, interactions=learned.interactions, theta_mean=float(th.mean()),
+                           theta_min=float(th.min()), theta_max=float(th.max()))}
+    l5 = ev.lists(0.5)
+    e5, ms5 = rms_error(ev, l5, sub, ad)
+    res["fixed_0.5"] = {"rms": e5, "ms": ms5, "interactions": l5.interactions}
+    # fixed angle with the learned RMS, by bisection on theta
+    lo, hi = 0.05, 1.0
+    best = None
+    for _ in range(bisect_steps):
+        mid = 0.5 * (lo + hi)
+        lm = ev.lists(mid)
+        sm = {}
+        em, msm = rms_error(ev, lm, sub, ad, stats=sm)
+        if log:
+            log("bisect theta %.4f rms %.3e" % (mid, em))
+        if em > e_l:
+            hi = mid
+        else:
+            lo = mid
+            best = (mid, em, msm, lm.interactions, sm)
+    if best is None:
+        lm = ev.lists(lo)
+        sm = {}
+        em, msm = rms_error(ev, lm, sub, ad, stats=sm)
+        best = (lo, em, msm, lm.interactions, sm)
+    res["fixed_equal_rms"] = dict(best[4], theta=best[0], rms=best[1], ms=best[2], interactions=best[3])
+    if precision_fp64:
+        lf = ev.lists(best[0])
+        e64, ms64 = rms_error(ev, lf, sub, ad, L.OTOO_FP64)
+        res["fp64_equal_rms"] = {"theta": best[0], "rms": e64, "ms": ms64, "interactions": lf.interactions}
+    res["gain_interactions"] = best[3] / learned.interactions
+    res["gain_time"] = best[2] / ms_l
+    return res
+
+
+def merger_ic(n, seed=ic.BASE_SEED + 5):
+    pos, mass, vel = ic.polytrope_pair(n, seed, velocities=True)
+    return pos, mass, vel
+
+
+def orbital_period(m_total=1.5, sep=0.05):
+    return 2 * math.pi * math.sqrt(sep ** 3 / m_total)
+
+
+def main():
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="train the opening-angle network on method-generated snapshots")
+    ap.add_argument("--n", type=int, default=1 << 22)
+    ap.add_argument("--snaps", type=int, default=16)
+    ap.add_argument("--every", type=int, default=5)
+    ap.add_argument("--dt-frac", type=float, default=1.0 / 200, help="time step as a fraction of the orbital period")
+    ap.add_argument("--groups", type=int, default=256)
+    ap.add_argument("--eps", type=float, default=ic.WORKLOADS["merger4m"]["eps"])
+    ap.add_argument("--n-crit", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--target", type=float, default=1e-3)
+    ap.add_argument("--weights", default=None, help="write the trained network here (.npz)")
+    ap.add_argument("--summary", default=None, help="write the evaluation here (.json)")
+    args = ap.parse_args()
+    log = lambda s: print(s, flush=True)  # noqa: E731
+    pos, mass, vel = merger_ic(args.n)
+    dt = args.dt_frac * orbital_period()
+    t0 = time.perf_counter()
+    snaps = leapfrog_snapshots(pos, mass, vel, args.eps, dt, args.snaps + 1, args.every, n_crit=args.n_crit, log=None)
+    t1 = time.perf_counter()
+    log("snapshots: %d in %.1f s" % (len(snaps), t1 - t0))
+    train_snaps, held_out = snaps[:args.snaps], snaps[args.snaps]
+    X, y = training_set(train_snaps, mass, args.eps, args.n_crit, args.groups, log=log)
+    t2 = time.perf_counter()
+    log("rows: %d in %.1f s" % (len(y), t2 - t1))
+    net, hist = train(X, y, steps=args.steps)
+    t3 = time.perf_counter()
+    log("training: loss %.4g -> %.4g in %.1f s" % (hist[0], hist[-1], t3 - t2))
+    if args.weights:
+        net.save(args.weights)
+    ev = Evaluator(held_out, mass, args.eps, args.n_crit)
+    res = compare(ev, net, args.target, log=log, mode="budget")
+    res["equal_targets"] = compare(ev, net, args.target, mode="equal", precision_fp64=False)
+    res.update(n=args.n, snapshots=args.snaps, every=args.every, dt=dt, rows=int(len(y)), loss_first=hist[0],
+               loss_last=hist[-1], times_s=dict(snapshots=t1 - t0, rows=t2 - t1, training=t3 - t2))
+    print(json.dumps(res))
+    if args.summary:
+        with open(args.summary, "w") as f:
+            json.dump(res, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

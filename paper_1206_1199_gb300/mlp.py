@@ -109,7 +109,7 @@ class ThetaNet:
                 hist.append(float(loss.item()))
         return hist
 
-    def select_theta(self, feats, grid, log10_target, fallback=0.5):
+    def select_theta(self, feats, grid, log10_target, fallback=0.5, log10_target_per_group=None):
         """feats [g][5] (list statistics); rows (g, k) = feats[g] + grid[k]."""
         import torch
         g = feats.shape[0]
@@ -117,9 +117,10 @@ class ThetaNet:
         rows = np.concatenate([np.repeat(feats, k, axis=0), np.tile(np.asarray(grid, np.float32), g)[:, None]], 1)
         xs = self._dev(self.scale(rows))
         gd = self._dev(np.asarray(grid, np.float32))
+        tg = None if log10_target_per_group is None else self._dev(log10_target_per_group)
         out = torch.empty(g, dtype=torch.float32, device=self.device)
-        L.call("otoo_select_theta", _vp(self.wbf16), _vp(xs), _vp(gd), k, g, float(log10_target), float(fallback),
-               _vp(out), _stream(self.device))
+        L.call("otoo_select_theta", _vp(self.wbf16), _vp(xs), _vp(gd), k, g, float(log10_target),
+               _vp(tg) if tg is not None else None, float(fallback), _vp(out), _stream(self.device))
         return out.cpu().numpy()
 
     def weights(self):

@@ -1,0 +1,78 @@
+"""Learned opening angle on the GPU: the device direct sum, the training
+labels (group errors) and the selection against the FP64 CPU oracle, and
+the gain of the trained network over a fixed angle at equal error."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_1199_gb300 import _lib as L
+from paper_1206_1199_gb300 import ic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def LR():
+    import torch  # noqa: F401
+    L.load()
+    from paper_1206_1199_gb300 import learned
+    return learned
+
+
+def test_device_direct_sum_matches_oracle(LR):
+    pos, mass = ic.plummer(5000, 41)
+    ev = LR.Evaluator(pos, mass, 0.01)
+    perm = ev.tree.export()["perm"]
+    tgt = np.array([0, 1, 17, 2500, 4999])
+    a, p = ev.direct(tgt)
+    ar, pr = oracle.direct(pos, mass, 0.01, targets=perm[tgt])
+    np.testing.assert_allclose(a, ar, rtol=0, atol=1e-12 * np.abs(ar).max())
+    np.testing.assert_allclose(p, pr, rtol=1e-12)
+
+
+def test_group_labels_match_oracle(LR):
+    # the label of (group, angle) = RMS over the group's particles of the
+    # relative force error of the tree force against the direct sum
+    pos, mass = ic.polytrope_pair(20000, 42)
+    eps = 1e-4
+    ev = LR.Evaluator(pos, mass, eps, n_crit=64)
+    grid = (0.3, 0.6, 0.9)
+    X, y = LR.group_rows(ev, 40, grid=grid, seed=3)
+    base = ev.lists(0.5)
+    g = base.groups
+    perm = base.perm
+    rng = np.random.Generator(np.random.PCG64(3))
+    sel = np.sort(rng.choice(base.n_groups, size=40, replace=False))
+    keys = np.array([perm[g["first"][k]:g["first"][k] + g["count"][k]].min() for k in sel])
+    ot = oracle.Tree(pos, mass, 8, 64)
+    members = [perm[g["first"][k]:g["first"][k] + g["count"][k]] for k in sel]
+    tg = np.concatenate(members)
+    ad, _ = oracle.direct(pos, mass, eps, targets=tg)
+    off = np.cumsum([0] + [len(m) for m in members])
+    for a_i, th in enumerate(grid):
+        tbk = np.full(len(pos), 0.5)
+        tbk[keys] = th
+        r = ot.eval(0.5, eps, True, theta_by_key=tbk)
+        d = np.linalg.norm(r["acc"][tg] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        rms = np.array([np.sqrt(np.mean(d[off[j]:off[j + 1]] ** 2)) for j in range(len(sel))])
+        got = 10.0 ** y[a_i * len(sel):(a_i + 1) * len(sel)]
+        np.testing.assert_allclose(got, rms, rtol=2e-2, atol=2e-6)
+        np.testing.assert_array_equal(X[a_i * len(sel):(a_i + 1) * len(sel), 5], np.float32(th))
+
+
+def test_learned_angles_gain_over_fixed_angle(LR):
+    # a network trained on method-generated snapshots of the two-polytrope
+    # system meets the error target with fewer interactions than the fixed
+    # angle that reaches the same RMS error
+    pos, mass, vel = LR.merger_ic(1 << 16)
+    eps = 4e-4
+    dt = LR.orbital_period() / 200
+    snaps = LR.leapfrog_snapshots(pos, mass, vel, eps, dt, 5, 2)
+    X, y = LR.training_set(snaps[:4], mass, eps, groups_per_snap=128)
+    net, hist = LR.train(X, y, steps=1500, batch=4096)
+    assert hist[-1] < 0.5 * hist[0]
+    ev = LR.Evaluator(snaps[4], mass, eps)
+    res = LR.compare(ev, net, target_rms=1e-3, n_sub=2048, precision_fp64=False)
+    assert 0.2e-3 < res["learned"]["rms"] < 3e-3
+    assert abs(res["fixed_equal_rms"]["rms"] - res["learned"]["rms"]) < 0.25 * res["learned"]["rms"]
+    assert res["gain_interactions"] > 1.0, res

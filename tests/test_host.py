@@ -248,9 +248,13 @@ def test_features_are_finite_and_consistent():
     assert f.shape == (lists.n_groups, 5) and np.all(np.isfinite(f))
     g = lists.groups
     np.testing.assert_allclose(f[:, 0], np.log2(g["n_cell"] + g["n_part"]), rtol=1e-6)
-    np.testing.assert_allclose(f[:, 4], np.log2(g["count"]), rtol=1e-6)
     assert np.all((f[:, 3] >= 0) & (f[:, 3] <= 1))
-    # with theta = 0 no cell is accepted: fraction 0, min distance sentinel
+    # the truncation estimate grows with the opening angle (accepted cells are
+    # larger relative to their distance)
+    f9 = t.lists(0.9, 64, 5e-4, True).features(t)
+    assert np.median(f9[:, 4]) > np.median(f[:, 4]) + 0.5
+    # with theta = 0 no cell is accepted: fraction 0, min distance and
+    # truncation at their sentinels
     _, l0 = tree_and_lists(pos[:2000], mass[:2000], 0.0, 64, 5e-4)
     f0 = l0.features(S.Tree(pos[:2000], mass[:2000]))
-    assert np.all(f0[:, 3] == 0) and np.all(f0[:, 1] == np.float32(3.0))
+    assert np.all(f0[:, 3] == 0) and np.all(f0[:, 1] == np.float32(3.0)) and np.all(f0[:, 4] == np.float32(-12.0))
