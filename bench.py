@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--err-targets", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="skip the batched 64-system step and the learned-angle comparison")
     return ap.parse_args()
 
 
@@ -134,6 +136,24 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def max_over_ranks(value, device="cpu"):
+    """Largest value over the ranks of the default process group (the value
+    itself without one)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Whole-job throughput of weak scaling: every rank processes its own
+    units, the job takes the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def rel_err(a, ref):
     d = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
     return float(np.sqrt(np.mean(d * d))), float(d.max())
@@ -184,9 +204,7 @@ def run_ours(args):
         per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
         total = evs[0].elapsed_time(evs[-1])
         if world > 1:
-            tt = torch.tensor([total], dtype=torch.float64, device=dev_name)
-            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-            total = float(tt.item())
+            total = max_over_ranks(total, dev_name)
             tdist.barrier()
         return total, per
 
@@ -199,7 +217,7 @@ def run_ours(args):
     cell_inter = lists.cell_interactions if lists.use_quad else 0
     mono_inter = inter - cell_inter
     ms = total_ms / args.steps
-    value = world * inter / (ms * 1e-3)
+    value = whole_job_rate(inter, world, ms)
 
     # FP64 form (the comparison form), same lists and launch shape
     fp64 = None
@@ -269,10 +287,90 @@ def run_ours(args):
     }
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_seconds)
+    if rank == 0 and not args.skip_extras and args.workload == "hernquist8m":
+        line["batch64"] = guarded_extra(run_batch, args, dev_name)
+        line["learned_merger4m"] = guarded_extra(run_learned, args, dev_name)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         tdist.destroy_process_group()
+
+
+def guarded_extra(fn, *a):
+    """An extra measurement must not cost the headline line."""
+    try:
+        return fn(*a)
+    except Exception as e:  # reported in the JSON line
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
+def run_batch(args, dev_name):
+    """64 independent Plummer/King systems of uneven size packed into one
+    ragged buffer and evaluated by one graph-launched force step."""
+    import torch
+
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import ic
+    from paper_1206_1199_gb300 import system as S
+    w = ic.WORKLOADS["batch64"]
+    systems = ic.batch_systems(w["n_sys"], w["seed"])
+    t0 = time.perf_counter()
+    per = [S.Tree(p, m, w["leaf_size"]).lists(w["theta"], w["n_crit"], e, w["use_quad"]) for p, m, e in systems]
+    packed = S.Lists.pack(per)
+    host_s = time.perf_counter() - t0
+    tune = L.default_tune(w["n_crit"])
+    dev = S.DeviceSystem.upload(packed, packed.plan(tune), dev_name)
+    n = packed.n_part
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
+    pot = torch.empty(n, dtype=torch.float64, device=dev_name)
+    for _ in range(3):
+        S.force(dev, acc, pot, L.OTOO_FP32K, tune)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        S.force(dev, acc, pot, L.OTOO_FP32K, tune, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    a = acc.cpu().numpy()
+    # FP64 error check of every system against its own direct sum on the device
+    from paper_1206_1199_gb300.learned import Evaluator
+    worst = 0.0
+    off = packed.sys_part_off
+    for k, (p, m, e) in enumerate(systems):
+        ev = Evaluator(p, m, e, w["n_crit"], device=dev_name)
+        sub = ic.subsample(len(p), 256, 11 + k)
+        perm = ev.tree.export()["perm"]
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(len(perm))
+        ad, _ = ev.direct(inv[sub])
+        rms, _ = rel_err(a[off[k] + sub], ad)
+        worst = max(worst, rms)
+    return {"systems": len(systems), "n_total": int(n), "interactions": int(packed.interactions),
+            "ms_per_step": ms, "value": packed.interactions / (ms * 1e-3), "unit": "interactions/s",
+            "host_tree_walk_s": host_s, "worst_system_acc_rms": worst, "error_targets_per_system": 256}
+
+
+def run_learned(args, dev_name):
+    """Learned per-group angles (network trained on method-generated
+    snapshots of the two-polytrope system) against the fixed angle with the
+    same RMS error, on an independent realisation of that system."""
+    from paper_1206_1199_gb300 import ic, learned
+    from paper_1206_1199_gb300.mlp import ThetaNet
+    wpath = os.path.join(ROOT, "paper_1206_1199_gb300", "thetanet_merger4m.npz")
+    if not os.path.exists(wpath):
+        return {"error": "no trained network file"}
+    w = ic.WORKLOADS["merger4m"]
+    net = ThetaNet.load(wpath, dev_name)
+    d = np.load(wpath)
+    if "xmin" in d:
+        net.xmin, net.xmax = d["xmin"], d["xmax"]
+    pos, mass, _ = learned.merger_ic(w["n"], w["seed"] + 100)
+    ev = learned.Evaluator(pos, mass, w["eps"], w["n_crit"], device=dev_name)
+    res = learned.compare(ev, net, 1e-3, n_sub=2048, bisect_steps=7)
+    res["n"] = w["n"]
+    return res
 
 
 def run_e2e(args, lists, plan, tune, stream, world):

@@ -173,8 +173,8 @@ typedef struct otoo_plan_info {
 
 /* ---- host library ------------------------------------------------------------ */
 
-/* Build the octree of n particles (Section III-A: root cube, keys, sort,
-   linked cells; Section III-B: cell mass, centre of mass; the quadrupole is
+/* Build the octree of n particles (Section III-B: root cube, keys, sort,
+   linked cells; Section III-C: cell mass, centre of mass; the quadrupole is
    this library's extension).  pos: host [n][3] FP64 row-major; mass: host [n]
    FP32, > 0.  Root cube: centred on the bounding box, side = max extent *
    (1 + 1e-12); particles are quantised to a 2^21 grid per axis and sorted by
@@ -183,7 +183,7 @@ typedef struct otoo_plan_info {
 int otoo_build_tree(const double* pos, const float* mass, int64_t n,
                     const otoo_params* params, otoo_tree** out);
 
-/* Groups and lists (Section III-C, the vectorised walk of Barnes 1990 done on
+/* Groups and lists (Section III-D, the vectorised walk of Barnes 1990 done on
    the host): groups are the maximal cells with at most n_crit particles; each
    group walks the tree once and accepts cell c when c's cube does not overlap
    the group's box and d_min > l_c / theta + s_c (d_min: distance from c's

@@ -8,8 +8,8 @@ with the GPU path (the two sides read the same seeded inputs and nothing else).
                   particle-particle interaction; pair law is a reading, the
                   paper does not print it).
 * ``Tree``        octree, groups, group walk with the opening-angle MAC, and
-                  the force over each group's walk (Sections II, III-A, III-B,
-                  III-C), monopole or quadrupole cells.
+                  the force over each group's walk (Sections II, III-B, III-C,
+                  III-D), monopole or quadrupole cells.
 * ``cell_moments`` / ``cell_field``  the multipole of one particle set and
                   its field at a point.
 * ``errors``      relative force error statistics against a reference.

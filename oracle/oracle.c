@@ -7,12 +7,12 @@
  * the same seeded inputs and nothing else.
  *
  * What it computes (paper: Section II "Octree Method", II-A "Tree
- * Representation", II-B "MAC Condition", III-A/III-B tree construction and
- * cell properties, III-C vectorised group walk):
+ * Representation", II-B "MAC Condition", III-B/III-C tree construction and
+ * cell properties, III-D vectorised group walk):
  *
  *   oracle_direct      Plummer-softened direct sum, j != i excluded.  The paper
  *                      never prints the pair law; it only says particles carry a
- *                      softening length (Section III-C).  Reading: a_i = sum_j
+ *                      softening length (Section III-D).  Reading: a_i = sum_j
  *                      m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2),
  *                      phi_i = -sum_j m_j / (|x_j - x_i|^2 + eps^2)^(1/2), G = 1.
  *   oracle_cell_*      monopole (Section II, p = 1) and, as an extension, the
@@ -182,7 +182,7 @@ int oracle_cell_field(const double* x, double m, const double* com, const double
 }
 
 /* ------------------------------------------------------------------------- */
-/* Octree (Sections II, III-A, III-B).                                       */
+/* Octree (Sections II, III-B, III-C).                                       */
 /* ------------------------------------------------------------------------- */
 
 typedef struct Node {
@@ -341,7 +341,7 @@ void oracle_tree_free(void* handle)
 }
 
 /*
- * Build the octree of n particles.  Root cube (Section III-A, first step):
+ * Build the octree of n particles.  Root cube (Section III-B, first step):
  * centred on the bounding-box centre, side S = max extent * (1 + 1e-12)
  * (S = 1 when all particles coincide).  Quantised coordinate on the 2^21 grid:
  * g = floor((x - lo) * (2^21 / S)) clamped to [0, 2^21 - 1], lo = centre - S/2;
@@ -405,7 +405,7 @@ void* oracle_tree_new(int64_t n, const double* pos, const double* mass, int leaf
 int64_t oracle_tree_n_groups(const void* handle) { return ((const OracleTree*)handle)->n_groups; }
 int64_t oracle_tree_n_cells(const void* handle) { return ((const OracleTree*)handle)->n_cells; }
 
-/* The group MAC (Barnes 1990 vectorised walk, Section III-C; notation of
+/* The group MAC (Barnes 1990 vectorised walk, Section III-D; notation of
    Section II-B): accept cell c for the group box [blo, bhi] iff the cube
    does not overlap the box and d_min > l / theta + s, where d_min is the
    distance from the cell's centre of mass to the box and s the distance from

@@ -2,7 +2,7 @@
 // entry of the group's shared interaction list.
 //
 // Paper: Section II (particle-particle and particle-cell interactions, the
-// cell acting as a virtual particle at its centre of mass), Section III-C
+// cell acting as a virtual particle at its centre of mass), Section III-D
 // (the GPU evaluates the interactions of a group that shares one walk).  The
 // quadrupole cell term, the FP32 centre-relative arithmetic with per-thread
 // Kahan sums, the persistent load-balanced launch and the CUDA graph are this

@@ -1,7 +1,7 @@
 // Learned opening angle: a 6-32-32-1 multilayer perceptron that predicts a
 // group's log10 RMS relative force error from statistics of its interaction
 // list and a candidate opening angle.  The paper controls accuracy with the
-// absolute MAC parameter Delta (Section II-B, Eq. SW_MAC; Section III-E); this
+// absolute MAC parameter Delta (Section II-B, Eq. SW_MAC; Section III-F); this
 // network replaces that control by choosing an angle per group.
 //
 // Kernels

@@ -1,9 +1,9 @@
 // Host half of the force step: octree, groups, interaction lists, batch
 // packing and the device work plan.
 //
-// Paper: Section III-A (tree construction in four steps: root cube, keys,
-// sort, linked cells), Section III-B (cell mass and centre of mass), Section
-// III-C (vectorised group walk of Barnes 1990, the group shares one list).
+// Paper: Section III-B (tree construction in four steps: root cube, keys,
+// sort, linked cells), Section III-C (cell mass and centre of mass), Section
+// III-D (vectorised group walk of Barnes 1990, the group shares one list).
 // The walk runs here on the host and hands each group's list to the device.
 #include <omp.h>
 
@@ -137,7 +137,7 @@ int guarded(F&& f)
 }
 
 // Cell moments by direct summation over the cell's particle range (the
-// "direct summation for each cell" variant of Section III-B; it parallelises
+// "direct summation for each cell" variant of Section III-C; it parallelises
 // over cells): mass, centre of mass, traceless quadrupole about it.
 void cell_moments(otoo_tree* t, int64_t c)
 {
@@ -177,7 +177,7 @@ void cell_moments(otoo_tree* t, int64_t c)
     }
 }
 
-// Build the cell hierarchy from the sorted keys (Section III-A, last step):
+// Build the cell hierarchy from the sorted keys (Section III-B, last step):
 // a cell holding more than leaf_size particles (and above the last grid
 // level) is sliced into the runs of equal 3-bit key digit of the next level.
 void build_cells(otoo_tree* t)
@@ -442,7 +442,7 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
         L->use_quad = p->use_quad ? 1 : 0;
         L->eps = p->eps;
         L->groups.resize(G);
-        // the walk: one shared list per group (Barnes 1990, Section III-C),
+        // the walk: one shared list per group (Barnes 1990, Section III-D),
         // entries buffered per thread, then placed in group order
         const int nthr = omp_get_max_threads();
         std::vector<std::vector<int32_t>> tbuf(nthr);

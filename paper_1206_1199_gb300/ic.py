@@ -5,7 +5,7 @@ Both the GPU path and the CPU oracle read these arrays.  Positions are FP64
 integer seed and uses NumPy's PCG64.
 
 The paper measures on synthetic models too: a Plummer sphere and a uniform
-sphere of N = 8M (Section IV-B), a cold-collapse sphere and a white-dwarf
+sphere of N = 8M (Sections III-D and IV-A), a cold-collapse sphere and a white-dwarf
 merger (Section V).  The merger's stars are replaced here by n = 1.5
 polytropes (gravity only; no equation-of-state tables are involved).
 """

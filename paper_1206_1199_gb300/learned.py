@@ -2,7 +2,7 @@
 
 The paper controls the force error with the accuracy parameter Delta of the
 absolute MAC (Section II-B, Eq. SW_MAC; a fraction of the mean force in
-Section III-E).  Here a small perceptron predicts, for each group and a
+Section III-F).  Here a small perceptron predicts, for each group and a
 candidate opening angle, the group's RMS relative force error from
 statistics of the group's list (list length, minimum cell distance over
 cell size, group size over softening, cell mass fraction, group count); the
@@ -37,7 +37,7 @@ from . import ic
 from . import system as S
 from .mlp import ThetaNet
 
-THETA_GRID = tuple(round(0.3 + 0.05 * k, 2) for k in range(13))  # 0.30 .. 0.90
+THETA_GRID = tuple(round(0.3 + 0.05 * k, 2) for k in range(15))  # 0.30 .. 1.00
 
 
 def _torch():

@@ -130,8 +130,11 @@ class ThetaNet:
         return self.wbf16.cpu().numpy().view(np.uint16)
 
     def save(self, path):
+        extra = {}
+        if getattr(self, "xmin", None) is not None:
+            extra = dict(xmin=self.xmin, xmax=self.xmax)
         np.savez(path, w=self.weights(), m=self.m.cpu().numpy(), v=self.v.cpu().numpy(), t=self.t,
-                 mean=self.mean, std=self.std)
+                 mean=self.mean, std=self.std, **extra)
 
     @classmethod
     def load(cls, path, device="cuda"):
@@ -141,4 +144,6 @@ class ThetaNet:
         net.m = torch.tensor(d["m"], device=device)
         net.v = torch.tensor(d["v"], device=device)
         net.t = int(d["t"])
+        if "xmin" in d:
+            net.xmin, net.xmax = d["xmin"], d["xmax"]
         return net
