@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--workload", default="hernquist8m")
     ap.add_argument("--n", type=int, default=0, help="override particle count (testing only)")
     ap.add_argument("--n-crit", type=int, default=0)
-    ap.add_argument("--tune", default="", help="block,iblock,tile,split (default: autotuner cache)")
+    ap.add_argument("--tune", default="", help="block,iblock,tile,split[,packed] (default: autotuner cache)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -79,8 +79,9 @@ def pick_tune(w, args):
     from paper_1206_1199_gb300 import _lib as L
     from paper_1206_1199_gb300 import autotune
     if getattr(args, "tune", None):
-        b, ib, tile, split = (int(v) for v in args.tune.split(","))
-        return L.Tune(block=b, iblock=ib, tile=tile, split=split, ctas_per_sm=0), "given"
+        v = [int(x) for x in args.tune.split(",")]
+        packed = v[4] if len(v) > 4 else 0
+        return L.Tune(block=v[0], iblock=v[1], tile=v[2], split=v[3], ctas_per_sm=0, packed=packed), "given"
     entry = None if args.n_crit else autotune.lookup(w)
     if entry:
         w["n_crit"] = int(entry["n_crit"])

@@ -75,7 +75,8 @@ typedef struct otoo_tune {
                                       form; the FP64 form stages 128 entries per tile) */
     int32_t split;                 /* max list entries per work item (>= 32) */
     int32_t ctas_per_sm;           /* resident CTAs per SM for the persistent grid (0 = auto) */
-    int32_t pad;
+    int32_t packed;                /* FP32 form: 1 = pairs of list entries evaluated with packed
+                                      two-wide FP32 instructions, 0 = one entry at a time */
 } otoo_tune;
 
 /* ---- device-side layout (what the host library exports and the caller

@@ -39,10 +39,10 @@ class Params(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("block", i32), ("iblock", i32), ("tile", i32), ("split", i32), ("ctas_per_sm", i32),
-                ("pad", i32)]
+                ("packed", i32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Src(ctypes.Structure):

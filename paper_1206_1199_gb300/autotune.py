@@ -1,11 +1,11 @@
 """Autotuner for the force step.
 
 Knobs: the group size n_crit (it changes the host walk, so every candidate
-re-walks the tree), target particles per lane (iblock), list entries per
-staged tile (tile), list-split threshold (split) and threads per CTA
-(block).  Objective: device time of one FP32 force step at fixed theta, the
+re-walks the tree), packed two-wide FP32 arithmetic or not (packed), target
+particles per lane (iblock), list entries per staged tile (tile),
+list-split threshold (split) and threads per CTA (block).  Objective: device time of one FP32 force step at fixed theta, the
 minimum over repeated CUDA-event timings.  The search is coordinate descent
-per n_crit (iblock, then tile, then split, then block) over the compiled
+per n_crit (packed, then iblock, tile, split, block) over the compiled
 kernel variants; the winner over all n_crit is cached per GPU name and
 workload in tune_cache.json next to this file.
 
@@ -22,9 +22,11 @@ from . import _lib as L
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
 
-# compiled FP32 kernel variants: (block, iblock, tile)
-VARIANTS = {(128, 1, 128), (128, 2, 64), (128, 2, 128), (128, 2, 256), (128, 4, 128), (128, 4, 256),
-            (64, 2, 128), (64, 4, 128), (256, 2, 128), (256, 1, 128)}
+# compiled FP32 kernel variants: (block, iblock, tile, packed)
+VARIANTS = {(128, 1, 128, 0), (128, 2, 64, 0), (128, 2, 128, 0), (128, 2, 256, 0), (128, 4, 128, 0),
+            (128, 4, 256, 0), (64, 2, 128, 0), (64, 4, 128, 0), (256, 2, 128, 0), (256, 1, 128, 0),
+            (128, 1, 128, 1), (128, 2, 128, 1), (128, 2, 256, 1), (64, 2, 128, 1), (64, 1, 128, 1),
+            (128, 1, 256, 1)}
 
 
 def workload_key(gpu, w):
@@ -92,27 +94,27 @@ def search(pos, mass, w, n_crits=(32, 64, 128, 256), device="cuda", log=print):
         lists = tree.lists(w["theta"], nc, w["eps"], w["use_quad"])
         cache = {}
 
-        def run(block, ib, tile, split):
-            key = (block, ib, tile, split)
+        def run(block, ib, tile, split, packed):
+            key = (block, ib, tile, split, packed)
             if key in cache:
                 return cache[key]
-            if (block, ib, tile) not in VARIANTS:
+            if (block, ib, tile, packed) not in VARIANTS:
                 cache[key] = float("inf")
                 return cache[key]
-            tune = L.Tune(block=block, iblock=ib, tile=tile, split=split, ctas_per_sm=0)
+            tune = L.Tune(block=block, iblock=ib, tile=tile, split=split, ctas_per_sm=0, packed=packed)
             plan = lists.plan(tune)
             dev = S.DeviceSystem.upload(lists, plan, device)
             ms = _time_step(dev, lists, tune)
             del dev
             cache[key] = ms
-            row = dict(n_crit=nc, block=block, iblock=ib, tile=tile, split=split, ms=ms,
+            row = dict(n_crit=nc, block=block, iblock=ib, tile=tile, split=split, packed=packed, ms=ms,
                        interactions=lists.interactions, groups=lists.n_groups)
             table.append(row)
             log(json.dumps(row))
             return ms
 
-        cur = [128, 2, 128, 4096]
-        for pos_k, cands in ((1, (1, 2, 4)), (2, (64, 128, 256)), (3, (2048, 4096, 8192, 16384)),
+        cur = [128, 2, 128, 4096, 1]
+        for pos_k, cands in ((4, (0, 1)), (1, (1, 2, 4)), (2, (64, 128, 256)), (3, (2048, 4096, 8192, 16384)),
                              (0, (64, 128, 256))):
             res = []
             for v in cands:
@@ -122,7 +124,8 @@ def search(pos, mass, w, n_crits=(32, 64, 128, 256), device="cuda", log=print):
             cur = min(res)[1]
         ms = run(*cur)
         if best is None or ms < best["ms"]:
-            best = dict(n_crit=nc, tune=dict(block=cur[0], iblock=cur[1], tile=cur[2], split=cur[3], ctas_per_sm=0),
+            best = dict(n_crit=nc, tune=dict(block=cur[0], iblock=cur[1], tile=cur[2], split=cur[3], ctas_per_sm=0,
+                                             packed=cur[4]),
                         ms=ms, interactions=lists.interactions)
     return best, table
 

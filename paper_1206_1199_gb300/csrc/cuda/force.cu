@@ -197,6 +197,7 @@ __global__ void k_split(const otoo_src* __restrict__ src, float4* __restrict__ o
 }
 
 #include "force_warp.cuh"
+#include "force_warp2.cuh"
 
 // FP64 form: one work item per CTA of B threads, IB targets per thread,
 // B entries staged per tile, every pair in FP64.
@@ -376,14 +377,21 @@ __global__ void k_merge(const otoo_dev_system sys, double* __restrict__ accel, d
 
 using Kernel = void (*)(const otoo_dev_system, double*, double*);
 
-Kernel pick_f32(int B, int IB, int tile)
+Kernel pick_f32(int B, int IB, int tile, int packed)
 {
     const int spl = tile / 32;
 #define PICK(NW_, IB_, SPL_) \
     if (B == NW_ * 32 && IB == IB_ && spl == SPL_) return k_force_warp<NW_, IB_, SPL_>;
+#define PICK2(NW_, IB_, SPL_) \
+    if (B == NW_ * 32 && IB == IB_ && spl == SPL_) return k_force_warp2<NW_, IB_, SPL_>;
+    if (packed) {
+        PICK2(4, 1, 4) PICK2(4, 2, 4) PICK2(4, 2, 8) PICK2(2, 2, 4) PICK2(2, 1, 4) PICK2(4, 1, 8)
+        return nullptr;
+    }
     PICK(4, 1, 4) PICK(4, 2, 2) PICK(4, 2, 4) PICK(4, 2, 8) PICK(4, 4, 4) PICK(4, 4, 8)
     PICK(2, 2, 4) PICK(2, 4, 4) PICK(8, 2, 4) PICK(8, 1, 4)
 #undef PICK
+#undef PICK2
     return nullptr;
 }
 
@@ -399,7 +407,7 @@ Kernel pick_f64(int IB)
 int check_tune(const otoo_tune* t)
 {
     OTOO_REQUIRE(t, OTOO_EINVAL, "tune is NULL");
-    OTOO_REQUIRE(pick_f32(t->block, t->iblock, t->tile) != nullptr, OTOO_EINVAL,
+    OTOO_REQUIRE(pick_f32(t->block, t->iblock, t->tile, t->packed) != nullptr, OTOO_EINVAL,
                  "unsupported tune: block %d, iblock %d, tile %d", t->block, t->iblock, t->tile);
     OTOO_REQUIRE(t->split >= 32, OTOO_EINVAL, "split must be >= 32");
     OTOO_REQUIRE(t->ctas_per_sm >= 0 && t->ctas_per_sm <= 32, OTOO_EINVAL, "ctas_per_sm out of range");
@@ -417,7 +425,7 @@ int enqueue_force(const otoo_dev_system* sys, double* accel, double* pot, int pr
                   cudaStream_t s)
 {
     const bool fp64 = precision == OTOO_FP64;
-    Kernel fn = fp64 ? pick_f64(t->iblock) : pick_f32(t->block, t->iblock, t->tile);
+    Kernel fn = fp64 ? pick_f64(t->iblock) : pick_f32(t->block, t->iblock, t->tile, t->packed);
     const int block = fp64 ? 128 : t->block;
     int dev = 0, nsm = 0, occ = 0;
     CUDA_TRY(cudaGetDevice(&dev));

@@ -93,6 +93,21 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
         const int32_t* __restrict__ lst = sys.list + grp.list_off;
         float4* __restrict__ rec = s_rec[wid];
 
+        // list indices of the next tile, loaded while the current one is
+        // evaluated (one of the two dependent global round trips per tile)
+        int nidx[SPL];
+        auto load_idx = [&](int t) {
+            const bool cell = t < ntc;
+            const int base = cell ? c0 + t * TE : p0 + (t - ntc) * TE;
+            const int cnt = cell ? min(TE, c1 - base) : min(TE, p1 - base);
+#pragma unroll
+            for (int e = 0; e < SPL; ++e) {
+                const int k = lane + 32 * e;
+                nidx[e] = k < cnt ? __ldg(lst + base + k) : 0;
+            }
+        };
+        if (nt > 0) load_idx(0);
+
         for (int t = 0; t < nt; ++t) {
             const bool cell = t < ntc;
             const bool cq = cell && has_quad;
@@ -112,7 +127,7 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
                     any[u] = k < cnt_pad;
                     h[u] = l[u] = qa[u] = qb[u] = zero4;
                     if (real[u]) {
-                        const int idx = __ldg(lst + base + k);
+                        const int idx = nidx[e0 + u];
                         const bool good =
                             cell ? (idx >= sys.n_part && idx < sys.n_src) : (idx >= 0 && idx < sys.n_part);
                         if (good) {
@@ -145,6 +160,7 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
                     }
                 }
             }
+            if (t + 1 < nt) load_idx(t + 1);
             __syncwarp();
 
             if (active) {

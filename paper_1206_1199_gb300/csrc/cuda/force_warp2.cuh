@@ -1,0 +1,342 @@
+// FP32 force kernel with packed two-wide FP32 arithmetic (included by
+// force.cu after force_warp.cuh).
+//
+// The same work decomposition as k_force_warp (one work item per warp, IB
+// targets per lane, lane subsets interleaved over the staged entries), but a
+// lane evaluates two consecutive list entries at once: the shared-memory tile
+// holds "pair records" whose fields are (entry 2m, entry 2m+1) float pairs,
+// and every FP32 operation of the pair law is a packed fma/mul/add.f32x2
+// (PTX) acting on both entries.  A packed instruction issues once for two
+// FP32 operations, so the FP32 pipe rather than instruction issue bounds the
+// kernel.  The reciprocal square root stays two scalar MUFU operations.
+//
+// Pair records: a cell tile stores 80 bytes per pair (x | y | z | m | -Qxx |
+// -Qyy | -Qzz | -Qxy | -Qxz | -Qyz, each two floats); a particle tile 32
+// bytes (x | y | z | m).  The quadrupole is stored negated so that the law
+// needs no negation: with n = -Q r and u = r.n = -(r.Q.r),
+//   phi -= m q - (1/2) u q^5,  a += (m q^3 - (5/2) u q^7) r + q^5 n.
+// The potential is accumulated as a positive sum and negated at the end.
+
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2pack(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(f2 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2rsqrt(f2 a)
+{
+    float lo, hi;
+    f2unpack(a, lo, hi);
+    return f2pack(rsqrt_r(lo), rsqrt_r(hi));
+}
+
+// Accumulator of one target over packed entry pairs: A[0..2] acceleration,
+// A[3] the positive potential sum.
+struct Acc2 {
+    f2 v[4];
+};
+
+// Two particle entries (or monopole cells) against one target; nx = -x_i
+// broadcast.
+__device__ __forceinline__ void pair_mono2(f2 sx, f2 sy, f2 sz, f2 m, f2 nx, f2 ny, f2 nz, f2 e2, Acc2& A)
+{
+    const f2 rx = f2add(sx, nx), ry = f2add(sy, ny), rz = f2add(sz, nz);
+    const f2 r2 = f2fma(rx, rx, f2fma(ry, ry, f2fma(rz, rz, e2)));
+    const f2 q = f2rsqrt(r2);
+    const f2 mq = f2mul(m, q);
+    const f2 mq3 = f2mul(mq, f2mul(q, q));
+    A.v[3] = f2add(A.v[3], mq);
+    A.v[0] = f2fma(mq3, rx, A.v[0]);
+    A.v[1] = f2fma(mq3, ry, A.v[1]);
+    A.v[2] = f2fma(mq3, rz, A.v[2]);
+}
+
+// Two quadrupole cells against one target (the fields of -Q as above);
+// mhalf = (-1/2, -1/2), m5half = (-5/2, -5/2).
+__device__ __forceinline__ void pair_quad2(f2 sx, f2 sy, f2 sz, f2 m, f2 nqxx, f2 nqyy, f2 nqzz, f2 nqxy, f2 nqxz,
+                                           f2 nqyz, f2 nx, f2 ny, f2 nz, f2 e2, f2 mhalf, f2 m5half, Acc2& A)
+{
+    const f2 rx = f2add(sx, nx), ry = f2add(sy, ny), rz = f2add(sz, nz);
+    const f2 r2 = f2fma(rx, rx, f2fma(ry, ry, f2fma(rz, rz, e2)));
+    const f2 q = f2rsqrt(r2);
+    const f2 q2 = f2mul(q, q);
+    const f2 mq = f2mul(m, q);
+    const f2 mq3 = f2mul(mq, q2);
+    const f2 n0 = f2fma(nqxx, rx, f2fma(nqxy, ry, f2mul(nqxz, rz)));
+    const f2 n1 = f2fma(nqxy, rx, f2fma(nqyy, ry, f2mul(nqyz, rz)));
+    const f2 n2 = f2fma(nqxz, rx, f2fma(nqyz, ry, f2mul(nqzz, rz)));
+    const f2 u = f2fma(rx, n0, f2fma(ry, n1, f2mul(rz, n2)));
+    const f2 q5 = f2mul(q, f2mul(q2, q2));
+    const f2 tu = f2mul(u, q5);
+    A.v[3] = f2add(A.v[3], f2fma(mhalf, tu, mq));
+    const f2 cr = f2fma(f2mul(m5half, tu), q2, mq3);
+    A.v[0] = f2fma(cr, rx, f2fma(q5, n0, A.v[0]));
+    A.v[1] = f2fma(cr, ry, f2fma(q5, n1, A.v[1]));
+    A.v[2] = f2fma(cr, rz, f2fma(q5, n2, A.v[2]));
+}
+
+// Packed operands take register pairs: fewer resident warps than the scalar
+// kernel, each with twice the independent FP32 work per instruction.
+#ifndef OTOO_W2_WARPS
+#define OTOO_W2_WARPS 16  // resident warps per SM asked for at IB >= 2
+#endif
+#ifndef OTOO_W2_QUNROLL
+#define OTOO_W2_QUNROLL 2  // pair records per step of the cell loop
+#endif
+#define OTOO_PRAGMA_(x) _Pragma(#x)
+#define OTOO_UNROLL_(n) OTOO_PRAGMA_(unroll n)
+constexpr int warp2_min_blocks(int nw, int ib) { return (ib == 1 ? 20 : OTOO_W2_WARPS) / nw; }
+
+template <int NW, int IB, int SPL>
+__global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_warp2(const otoo_dev_system sys,
+                                                                                  double* __restrict__ accel,
+                                                                                  double* __restrict__ pot)
+{
+    constexpr int T = 32 * SPL;          // entries per tile at most
+    constexpr int TP = T / 2;            // pair records per tile at most
+    constexpr int PPL = (TP + 31) / 32;  // pair records staged per lane
+    __shared__ float4 s_rec[NW][5 * TP];
+
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    uint32_t* status = sys.counter + 1;
+    const float4* __restrict__ ff = reinterpret_cast<const float4*>(sys.split);
+    const bool has_quad = sys.quad != nullptr;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const f2 mhalf = f2pack(-0.5f, -0.5f), m5half = f2pack(-2.5f, -2.5f), zero2 = f2pack(0.f, 0.f);
+
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(sys.counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= sys.n_items) break;
+
+        const otoo_item item = sys.items[it];
+        otoo_group grp;
+        if (!item_ok(sys, item, grp, 32 * IB)) {
+            if (lane == 0) atomicOr(status, kBadItem);
+            continue;
+        }
+
+        const int ni = item.ni;
+        const int P = (ni + IB - 1) / IB;
+        const int nsub = 32 / P;
+        const int islot = lane % P, js = lane / P;
+        const bool active = js < nsub;
+        // pair records per tile: a multiple of nsub (a tile with fewer records
+        // than nsub holds nsub, some of them zero)
+        const int TEP = TP >= nsub ? (TP / nsub) * nsub : nsub;
+        const int TE = 2 * TEP;  // entries per tile
+        const float eps2 = (float)grp.eps2;
+        const f2 e2 = f2pack(eps2, eps2);
+        const float cx = __double2float_rn(grp.cx), cy = __double2float_rn(grp.cy), cz = __double2float_rn(grp.cz);
+
+        f2 nx[IB], ny[IB], nz[IB];
+        Acc<float> acc[IB];
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            const int i = islot + k * P;
+            float x = 0.f, y = 0.f, z = 0.f;
+            if (active && i < ni) {
+                const int64_t t = (int64_t)grp.first + item.i0 + i;
+                const float4 h = __ldg(ff + 2 * t);
+                const float4 l = __ldg(ff + 2 * t + 1);
+                x = (h.x - cx) + l.x;
+                y = (h.y - cy) + l.y;
+                z = (h.z - cz) + l.z;
+            }
+            nx[k] = f2pack(-x, -x);
+            ny[k] = f2pack(-y, -y);
+            nz[k] = f2pack(-z, -z);
+            acc[k].zero();
+        }
+
+        const int c0 = item.j0, c1 = min(item.j1, grp.n_cell);
+        const int p0 = max(item.j0, grp.n_cell), p1 = item.j1;
+        const int ntc = c1 > c0 ? (c1 - c0 + TE - 1) / TE : 0;
+        const int ntp = p1 > p0 ? (p1 - p0 + TE - 1) / TE : 0;
+        const int nt = ntc + ntp;
+        const int32_t* __restrict__ lst = sys.list + grp.list_off;
+        float4* __restrict__ rec = s_rec[wid];
+
+        // list indices of the next tile (entries 2m, 2m+1 of this lane's pairs)
+        int nidx[PPL][2];
+        auto load_idx = [&](int t) {
+            const bool cell = t < ntc;
+            const int base = cell ? c0 + t * TE : p0 + (t - ntc) * TE;
+            const int cnt = cell ? min(TE, c1 - base) : min(TE, p1 - base);
+#pragma unroll
+            for (int pp = 0; pp < PPL; ++pp)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 2 * (lane + 32 * pp) + h;
+                    nidx[pp][h] = k < cnt ? __ldg(lst + base + k) : 0;
+                }
+        };
+        if (nt > 0) load_idx(0);
+
+        for (int t = 0; t < nt; ++t) {
+            const bool cell = t < ntc;
+            const bool cq = cell && has_quad;
+            const int base = cell ? c0 + t * TE : p0 + (t - ntc) * TE;
+            const int cnt = cell ? min(TE, c1 - base) : min(TE, p1 - base);
+            const int npair = (cnt + 1) / 2;
+            const int npair_pad = (npair + nsub - 1) / nsub * nsub;
+
+            // stage this lane's pair records: loads of both entries first
+#pragma unroll
+            for (int pp = 0; pp < PPL; ++pp) {
+                const int m = lane + 32 * pp;
+                if (m >= npair_pad) continue;
+                float4 hh[2], ll[2], qa[2], qb[2];
+                bool real[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 2 * m + h;
+                    real[h] = k < cnt;
+                    hh[h] = ll[h] = qa[h] = qb[h] = zero4;
+                    if (real[h]) {
+                        const int idx = nidx[pp][h];
+                        const bool good =
+                            cell ? (idx >= sys.n_part && idx < sys.n_src) : (idx >= 0 && idx < sys.n_part);
+                        if (good) {
+                            hh[h] = __ldg(ff + 2 * (int64_t)idx);
+                            ll[h] = __ldg(ff + 2 * (int64_t)idx + 1);
+                            if (cq) {
+                                const float4* qp = reinterpret_cast<const float4*>(sys.quad + (idx - sys.n_part));
+                                qa[h] = __ldg(qp);
+                                qb[h] = __ldg(qp + 1);
+                            }
+                        } else {
+                            atomicOr(status, kBadIndex);
+                            real[h] = false;
+                        }
+                    }
+                }
+                float x[2], y[2], z[2], w[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    x[h] = real[h] ? (hh[h].x - cx) + ll[h].x : 0.f;
+                    y[h] = real[h] ? (hh[h].y - cy) + ll[h].y : 0.f;
+                    z[h] = real[h] ? (hh[h].z - cz) + ll[h].z : 0.f;
+                    w[h] = real[h] ? hh[h].w : 0.f;
+                }
+                if (cq) {
+                    float4* r = rec + 5 * m;
+                    r[0] = make_float4(x[0], x[1], y[0], y[1]);
+                    r[1] = make_float4(z[0], z[1], w[0], w[1]);
+                    // qa = (xx, yy, zz, xy), qb = (xz, yz, -, -), stored negated
+                    r[2] = make_float4(-qa[0].x, -qa[1].x, -qa[0].y, -qa[1].y);
+                    r[3] = make_float4(-qa[0].z, -qa[1].z, -qa[0].w, -qa[1].w);
+                    r[4] = make_float4(-qb[0].x, -qb[1].x, -qb[0].y, -qb[1].y);
+                } else {
+                    float4* r = rec + 2 * m;
+                    r[0] = make_float4(x[0], x[1], y[0], y[1]);
+                    r[1] = make_float4(z[0], z[1], w[0], w[1]);
+                }
+            }
+            if (t + 1 < nt) load_idx(t + 1);
+            __syncwarp();
+
+            if (active) {
+                Acc2 P2[IB];
+#pragma unroll
+                for (int k = 0; k < IB; ++k) P2[k].v[0] = P2[k].v[1] = P2[k].v[2] = P2[k].v[3] = zero2;
+                const int niter = npair_pad / nsub;
+                if (cq) {
+                    const float4* __restrict__ r = rec + 5 * js;
+                    const int S = 5 * nsub;
+                    OTOO_UNROLL_(OTOO_W2_QUNROLL)
+                    for (int n = 0; n < niter; ++n, r += S) {
+                        const float4 a = r[0], b = r[1], c = r[2], d = r[3], e = r[4];
+                        const f2 sx = f2pack(a.x, a.y), sy = f2pack(a.z, a.w), sz = f2pack(b.x, b.y);
+                        const f2 sm = f2pack(b.z, b.w);
+                        const f2 qxx = f2pack(c.x, c.y), qyy = f2pack(c.z, c.w), qzz = f2pack(d.x, d.y);
+                        const f2 qxy = f2pack(d.z, d.w), qxz = f2pack(e.x, e.y), qyz = f2pack(e.z, e.w);
+#pragma unroll
+                        for (int k = 0; k < IB; ++k)
+                            pair_quad2(sx, sy, sz, sm, qxx, qyy, qzz, qxy, qxz, qyz, nx[k], ny[k], nz[k], e2, mhalf,
+                                       m5half, P2[k]);
+                    }
+                } else {
+                    const float4* __restrict__ r = rec + 2 * js;
+                    const int S = 2 * nsub;
+#pragma unroll 2
+                    for (int n = 0; n < niter; ++n, r += S) {
+                        const float4 a = r[0], b = r[1];
+                        const f2 sx = f2pack(a.x, a.y), sy = f2pack(a.z, a.w), sz = f2pack(b.x, b.y);
+                        const f2 sm = f2pack(b.z, b.w);
+#pragma unroll
+                        for (int k = 0; k < IB; ++k) pair_mono2(sx, sy, sz, sm, nx[k], ny[k], nz[k], e2, P2[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < IB; ++k) {
+                    float s[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float lo, hi;
+                        f2unpack(P2[k].v[c], lo, hi);
+                        s[c] = lo + hi;
+                    }
+                    acc[k].add(s);
+                }
+            }
+            __syncwarp();
+        }
+
+        // merge the lane subsets into the js == 0 lanes, in subset order, with
+        // a compensated FP32 sum; one conversion to FP64 per output value
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            double a[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float S = acc[k].s[c], C = acc[k].c[c];
+                for (int j = 1; j < nsub; ++j) {
+                    const float so = __shfl_sync(kFull, acc[k].s[c], islot + j * P);
+                    const float co = __shfl_sync(kFull, acc[k].c[c], islot + j * P);
+                    const float y = __fsub_rn(__fsub_rn(so, co), C);
+                    const float tt = __fadd_rn(S, y);
+                    C = __fsub_rn(__fsub_rn(tt, S), y);
+                    S = tt;
+                }
+                a[c] = (double)S - (double)C;
+            }
+            a[3] = -a[3];  // the potential was summed with the opposite sign
+            const int i = islot + k * P;
+            if (js == 0 && i < ni) {
+                if (item.j0 == 0) {
+                    // the self pair added exactly -m_i rsqrt(eps^2) in FP32: take the same value out
+                    const float4 h = __ldg(ff + 2 * ((int64_t)grp.first + item.i0 + i));
+                    a[3] += (double)(h.w * rsqrt_r(eps2));
+                }
+                write_target(sys, grp, item, i, a, accel, pot);
+            }
+        }
+    }
+}

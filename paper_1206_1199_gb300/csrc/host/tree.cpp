@@ -651,7 +651,7 @@ int otoo_default_tune(int32_t n_crit, otoo_tune* tune)
     tune->tile = 128;
     tune->split = 4096;
     tune->ctas_per_sm = 0;
-    tune->pad = 0;
+    tune->packed = 0;
     return OTOO_OK;
 }
 

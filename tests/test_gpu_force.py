@@ -124,11 +124,14 @@ def test_theta0_many_groups_ragged(torch):
             assert within_bound(a, p, ad, pd, pos, mass, 0.02, k), (split, prec)
 
 
-@pytest.mark.parametrize("block,iblock,tile", [(128, 1, 128), (128, 2, 64), (128, 2, 256), (128, 4, 128), (64, 4, 128), (256, 2, 128)])
-def test_tuning_invariance(torch, block, iblock, tile):
+@pytest.mark.parametrize("block,iblock,tile,packed", [(128, 1, 128, 0), (128, 2, 64, 0), (128, 2, 256, 0),
+                                                      (128, 4, 128, 0), (64, 4, 128, 0), (256, 2, 128, 0),
+                                                      (128, 2, 128, 1), (64, 2, 128, 1), (128, 1, 128, 1),
+                                                      (128, 2, 256, 1)])
+def test_tuning_invariance(torch, block, iblock, tile, packed):
     pos, mass = ic.plummer(20000, 5)
     ref, refp, _ = run(pos, mass, 0.6, 64, 1e-2, True, L.OTOO_FP64)
-    tune = L.Tune(block=block, iblock=iblock, tile=tile, split=max(tile, 300), ctas_per_sm=0)
+    tune = L.Tune(block=block, iblock=iblock, tile=tile, split=max(tile, 300), ctas_per_sm=0, packed=packed)
     for prec in (L.OTOO_FP64, L.OTOO_FP32K):
         a, p, _ = run(pos, mass, 0.6, 64, 1e-2, True, prec, tune=tune)
         a2, p2, _ = run(pos, mass, 0.6, 64, 1e-2, True, prec, tune=tune)
