@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the batched 64-system step and the learned-angle comparison")
+    ap.add_argument("--skip-walk", action="store_true", help="skip the device-walk step")
     return ap.parse_args()
 
 
@@ -180,6 +181,7 @@ def run_ours(args):
     lists = tree.lists(w["theta"], w["n_crit"], w["eps"], w["use_quad"])
     t2 = time.perf_counter()
     plan = lists.plan(tune)
+    t3 = time.perf_counter()
     dev = S.DeviceSystem.upload(lists, plan, dev_name)
     n = lists.n_part
     accel = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
@@ -274,7 +276,8 @@ def run_ours(args):
                    "cell_interactions": cell_inter, "tune": tune.as_dict(), "tune_source": tune_src,
                    "items": plan.n_items,
                    "l2": "inputs larger than L2 (%.1f GB resident per step)" % (dev.h2d_bytes() / 1e9),
-                   "host_tree_s": t1 - t0, "host_walk_s": t2 - t1, "parallelism": "replica per rank (weak)"},
+                   "host_tree_s": t1 - t0, "host_walk_s": t2 - t1, "host_plan_s": t3 - t2,
+                   "parallelism": "replica per rank (weak)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "flops_per_step": flops,
@@ -286,6 +289,9 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": args.steps * (1 + (1 if plan.n_splits else 0)),
     }
+    if rank == 0 and not args.skip_walk:
+        line["device_walk"] = guarded_extra(run_device_walk, args, dev_name, tree, w, tune, lists, a32, stream,
+                                            t2 - t1, t3 - t2)
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_seconds)
     if rank == 0 and not args.skip_extras and args.workload == "hernquist8m":
@@ -303,6 +309,62 @@ def guarded_extra(fn, *a):
         return fn(*a)
     except Exception as e:  # reported in the JSON line
         return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
+def run_device_walk(args, dev_name, tree, w, tune, lists, a32, stream, host_walk_s, host_plan_s):
+    """The step with the walk and the plan on the device: otoo_walk_count,
+    (host reads the list length), otoo_walk_fill, otoo_plan_count, (host
+    reads the item count), otoo_plan_fill, otoo_force; buffers reused between
+    steps.  Checked against the host walk's lists at full size (per-group
+    entry counts, totals) and the FP32 forces on the host lists."""
+    import torch
+
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import system as S
+    t0 = time.perf_counter()
+    dt = S.DeviceTree(tree, w["n_crit"], w["use_quad"], dev_name)
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    pool = S.BufferPool(dev_name)
+    n = lists.n_part
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
+    pot = torch.empty(n, dtype=torch.float64, device=dev_name)
+
+    def one():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool)
+        ev[1].record(stream)
+        dp = dl.plan(tune, stream=stream)
+        ev[2].record(stream)
+        S.force(S.DeviceStep(dl, dp), acc, pot, L.OTOO_FP32K, tune, stream=stream, check=False)
+        ev[3].record(stream)
+        return dl, dp, ev
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    times = []
+    k = max(3, min(args.steps, 10))
+    tw = time.perf_counter()
+    for _ in range(k):
+        dl, dp, ev = one()
+        torch.cuda.synchronize()
+        times.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+    wall = (time.perf_counter() - tw) / k
+    med = np.median(np.array(times), axis=0)
+    g, hg = dl.groups, lists.groups
+    same = bool(np.array_equal(g["n_cell"], hg["n_cell"]) and np.array_equal(g["n_part"], hg["n_part"])
+                and np.array_equal(g["list_off"], hg["list_off"]))
+    rms, mx = rel_err(acc.cpu().numpy(), a32)
+    return {"walk_ms": float(med[0]), "plan_ms": float(med[1]), "force_ms": float(med[2]),
+            "step_ms": float(med.sum()), "step_wall_ms": wall * 1e3, "steps": k,
+            "host_walk_ms": host_walk_s * 1e3, "host_plan_ms": host_plan_s * 1e3,
+            "walk_speedup_vs_host": host_walk_s * 1e3 / float(med[0]),
+            "tree_arrays_s": prep_s, "tree_arrays_bytes": int(dt.h2d_bytes()),
+            "group_counts_equal_host": same, "n_list": int(dl.n_list),
+            "interactions_equal_host": bool(dl.interactions == lists.interactions),
+            "items": int(dp.n_items), "fp32_vs_host_lists_acc_rms": rms, "fp32_vs_host_lists_acc_max": mx}
 
 
 def run_batch(args, dev_name):

@@ -324,6 +324,122 @@ int64_t otoo_direct_chunks(int64_t n_src, int64_t n_tgt);
 int otoo_direct(const otoo_src* src, int64_t n_src, const int64_t* targets, int64_t n_tgt, double eps2,
                 double* accel, double* pot, double* scratch, uint32_t* status, void* stream);
 
+/* ---- the walk on the device ------------------------------------------------------
+   Section III-D: the paper walks the tree on the GPU, one group of particles
+   sharing one traversal (Barnes 1990), with the group-to-cell minimum
+   distance in the acceptance test.  Here one warp walks one group.  The
+   lists are the ones otoo_make_groups_and_lists makes on the host for the
+   same tree and parameters: the same cell entries and the same particle
+   entries per group (each run -- cells, then particles -- in the walk's own
+   order, which may differ from the host's), because every acceptance test
+   takes the host's decision: an FP32 filter decides when the FP32 value is
+   provably on the same side of the threshold (margin 2^-16 of the squared
+   scale of the test; the rounding bound is below 2^-18), otherwise the FP64
+   test of the host walk runs, operation for operation.
+
+   Host preparation: otoo_find_groups (group ranges), otoo_tree_device_arrays
+   (sources, quadrupoles and walk records); device: otoo_walk_count,
+   otoo_walk_fill, then otoo_plan_count / otoo_plan_fill for the work items of
+   otoo_force. */
+
+/* Walk record of cell k (64 bytes): the FP32 data of the filter and the
+   tree links. */
+typedef struct otoo_wcell {
+    float com_hi[3];               /* centre of mass rounded to FP32 */
+    float com_lo[3];               /* (com - com_hi) rounded to FP32 */
+    float e[3];                    /* (com - cube lower corner) rounded, in [0, side] */
+    float side;                    /* cube side rounded */
+    float s;                       /* |com - cube centre| (FP64, as the host test computes it) rounded */
+    int32_t child0, nchild;        /* children [child0, child0 + nchild), nchild = 0 for a leaf */
+    int32_t begin, end;            /* tree-order particle range */
+    int32_t pad;
+} otoo_wcell;
+
+/* FP64 geometry of cell k (80 bytes): what the exact test reads. */
+typedef struct otoo_wcell64 {
+    double lo[3];                  /* cube lower corner */
+    double side;                   /* cube side */
+    double com[3];                 /* centre of mass */
+    double gc[3];                  /* cube centre */
+} otoo_wcell64;
+
+/* Groups of otoo_make_groups_and_lists (maximal cells with at most n_crit
+   particles, in tree order; a last-level leaf with more particles cut into
+   chunks of n_crit): first[g], count[g], host arrays of capacity entries.
+   *n_groups receives the number of groups.  first/count may be NULL with
+   capacity 0 to query the number.  Errors: OTOO_EINVAL (n_crit outside
+   [1, 1024], capacity too small when arrays are given). */
+int otoo_find_groups(const otoo_tree* tree, int32_t n_crit, int32_t* first, int32_t* count,
+                     int64_t capacity, int64_t* n_groups);
+
+/* Device inputs of the walk and the force step from a tree, into host arrays
+   the caller allocated (any may be NULL to skip it): src [n_part + n_cell]
+   (particles in tree order, then cells: centre of mass, mass) and quad
+   [n_cell] exactly as otoo_make_groups_and_lists stores them (zeros when
+   use_quad = 0); cell [n_cell] and cell64 [n_cell] walk records. */
+int otoo_tree_device_arrays(const otoo_tree* tree, int32_t use_quad, otoo_src* src, otoo_quad* quad,
+                            otoo_wcell* cell, otoo_wcell64* cell64);
+
+/* Device view of one walk (all pointers device, caller-owned). */
+typedef struct otoo_dev_walk {
+    int64_t n_part, n_cell;        /* the tree's particles and cells */
+    int32_t n_groups;
+    int32_t exact;                 /* 1 = every acceptance test in FP64 (no FP32 filter) */
+    double theta;                  /* opening angle when theta_per_group is NULL (>= 0) */
+    double eps2;                   /* softening^2, copied into every group record */
+    const otoo_src* src;           /* [n_part + n_cell]: particle positions (tree order) */
+    const otoo_wcell* cell;        /* [n_cell] */
+    const otoo_wcell64* cell64;    /* [n_cell] */
+    const int32_t* group_first;    /* [n_groups] */
+    const int32_t* group_count;    /* [n_groups], each in [1, 1024] */
+    const float* theta_per_group;  /* [n_groups] or NULL; a negative angle skips the group */
+    uint32_t* counter;             /* scratch, >= 4 uint32: work ticket, status */
+    int64_t* totals;               /* >= otoo_walk_totals_len(n_groups) int64: [0] list
+                                      entries, [1] interactions, [2] cell interactions
+                                      (written by otoo_walk_count), then scratch */
+} otoo_dev_walk;
+
+/* Length of otoo_dev_walk.totals for n_groups groups. */
+int64_t otoo_walk_totals_len(int64_t n_groups);
+
+/* Pass 1 of the device walk: every group walks the tree once and
+   groups[g] (device, n_groups records) receives first, count, n_cell,
+   n_part, eps2, the centre of the particles' box, theta and sys = 0;
+   list_off is the exclusive prefix sum of n_cell + n_part in group order.
+   totals[0..2] = list entries, sum of count * (n_cell + n_part), sum of
+   count * n_cell.  Asynchronous on stream; clears the status word. */
+int otoo_walk_count(const otoo_dev_walk* walk, otoo_group* groups, void* stream);
+
+/* Pass 2: walks again and writes each group's entries at list[list_off]:
+   n_cell cell entries (source index n_part + k), then n_part particle
+   entries.  list: device, capacity entries; when totals[0] > capacity the
+   call writes no entry and sets the status word (checked by
+   otoo_walk_check_status). */
+int otoo_walk_fill(const otoo_dev_walk* walk, const otoo_group* groups, int32_t* list, int64_t capacity,
+                   void* stream);
+
+/* Reads the walk's status word after a sync: OTOO_EDEVICE when a record
+   failed its bounds check, a group's stack overflowed, the two passes
+   disagreed, or the list did not fit. */
+int otoo_walk_check_status(const otoo_dev_walk* walk, void* stream);
+
+/* Work items on the device with the rules of otoo_make_plan (the same
+   items, splits and slot numbers; launch order: descending cost class
+   instead of a sort, which changes no result).  groups: device records of
+   otoo_walk_count.  Scratch: plan_scratch, >= otoo_plan_scratch_ints
+   (n_groups) int32 (device).  plan_totals: device int64 [4] = items,
+   splits, slots, n_crit_max, written by otoo_plan_count; the caller reads
+   them (after a sync) to size items [plan_totals[0]], splits
+   [plan_totals[1]] and the force step's partial scratch (plan_totals[2] *
+   4 * plan_totals[3] doubles).  otoo_plan_fill writes nothing beyond the
+   capacities it is given (status bit set in counter[1] instead). */
+int64_t otoo_plan_scratch_ints(int64_t n_groups);
+int otoo_plan_count(const otoo_group* groups, int32_t n_groups, const otoo_tune* tune, int32_t* plan_scratch,
+                    int64_t* plan_totals, void* stream);
+int otoo_plan_fill(const otoo_group* groups, int32_t n_groups, const otoo_tune* tune, int32_t* plan_scratch,
+                   const int64_t* plan_totals, otoo_item* items, int64_t items_capacity, otoo_split* splits,
+                   int64_t splits_capacity, uint32_t* counter, void* stream);
+
 /* ---- learned opening angle (multilayer perceptron 6-32-32-1) ---------------- */
 
 #define OTOO_MLP_IN  6

@@ -92,7 +92,22 @@ class TreeView(ctypes.Structure):
                 ("cell_child0", vp), ("cell_org", vp), ("cell_com", vp), ("cell_mass", vp), ("cell_quad", vp)]
 
 
-for _s, _n in ((Src, 32), (Quad, 32), (Group, 64), (Item, 32), (Split, 16)):
+class WCell(ctypes.Structure):
+    _fields_ = [("com_hi", f32 * 3), ("com_lo", f32 * 3), ("e", f32 * 3), ("side", f32), ("s", f32),
+                ("child0", i32), ("nchild", i32), ("begin", i32), ("end", i32), ("pad", i32)]
+
+
+class WCell64(ctypes.Structure):
+    _fields_ = [("lo", f64 * 3), ("side", f64), ("com", f64 * 3), ("gc", f64 * 3)]
+
+
+class DevWalk(ctypes.Structure):
+    _fields_ = [("n_part", i64), ("n_cell", i64), ("n_groups", i32), ("exact", i32), ("theta", f64),
+                ("eps2", f64), ("src", vp), ("cell", vp), ("cell64", vp), ("group_first", vp),
+                ("group_count", vp), ("theta_per_group", vp), ("counter", vp), ("totals", vp)]
+
+
+for _s, _n in ((Src, 32), (Quad, 32), (Group, 64), (Item, 32), (Split, 16), (WCell, 64), (WCell64, 80)):
     assert ctypes.sizeof(_s) == _n, (_s, ctypes.sizeof(_s))
 
 # name -> (argtypes); every function returns int unless listed in _VOID
@@ -122,9 +137,19 @@ _SIGS = {
     "otoo_mlp_train_step": [vp, vp, vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp],
     "otoo_mlp_to_bf16": [vp, vp, i32, vp],
     "otoo_select_theta": [vp, vp, vp, i32, i64, f32, vp, f32, vp, vp],
+    "otoo_find_groups": [vp, i32, vp, vp, i64, ctypes.POINTER(i64)],
+    "otoo_tree_device_arrays": [vp, i32, vp, vp, vp, vp],
+    "otoo_walk_totals_len": [i64],
+    "otoo_walk_count": [ctypes.POINTER(DevWalk), vp, vp],
+    "otoo_walk_fill": [ctypes.POINTER(DevWalk), vp, vp, i64, vp],
+    "otoo_walk_check_status": [ctypes.POINTER(DevWalk), vp],
+    "otoo_plan_scratch_ints": [i64],
+    "otoo_plan_count": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp],
+    "otoo_plan_fill": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp, i64, vp, i64, vp, vp],
     "otoo_last_error": [],
 }
-_RET_I64 = {"otoo_mlp_scratch_floats", "otoo_force_static_capacity", "otoo_direct_chunks"}
+_RET_I64 = {"otoo_mlp_scratch_floats", "otoo_force_static_capacity", "otoo_direct_chunks", "otoo_walk_totals_len",
+            "otoo_plan_scratch_ints"}
 _VOID = {"otoo_tree_free", "otoo_lists_free", "otoo_plan_free"}
 _OPTIONAL = set()
 

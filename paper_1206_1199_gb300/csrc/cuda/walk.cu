@@ -1,0 +1,761 @@
+// The tree walk on the device and the device work plan.
+//
+// Paper: Section III-D (the walk runs on the GPU; a group of particles
+// shares one traversal and the acceptance test uses the group-to-cell
+// minimum distance, after Barnes 1990) and Section II-A (the traversal rules:
+// accept a cell, open a cell into its children, take a leaf's particles).
+// The paper walks with one work-item per group along next/more links; here
+// one warp walks one group over a shared-memory stack, 32 cells at a time,
+// and writes the group's list for the force kernels (the host walk's lists,
+// entry for entry, as sets per group).
+//
+// Kernels
+//   k_walk<false>   pass 1: the group's box (warp min/max over its particles),
+//                   the walk, entry counts into the group record.
+//   k_scan_*        exclusive prefix sums in group order (list offsets, plan
+//                   slots): block sums, one-CTA scan of the block sums,
+//                   block-level scans with the block offsets.
+//   k_walk<true>    pass 2: the same walk, entries written at the offsets.
+//   k_plan_count    per group: particle and list chunks (the cost model of the
+//                   host plan), cost class histogram.
+//   k_plan_cursor   start of each cost class, most expensive class first.
+//   k_plan_fill     work items and split records.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../common.h"
+
+using namespace otoo;
+
+namespace {
+
+constexpr int kWalkWarps = 8;       // warps per CTA
+constexpr int kStack = 1024;        // stack entries per warp (shared memory)
+constexpr int kReserve = 160;       // entries kept free for one-node steps
+constexpr int kScanThreads = 1024;  // scan kernels: threads per CTA
+constexpr int kScanBlock = 2048;    // elements per scan block
+constexpr int kClasses = 128;       // cost classes of the plan's launch order
+constexpr unsigned kFull = 0xffffffffu;
+
+// status bits (counter[1])
+constexpr uint32_t kWalkBadRecord = 1u;   // a cell record failed its bounds check
+constexpr uint32_t kWalkOverflow = 2u;    // a group's stack or node budget ran out
+constexpr uint32_t kWalkMismatch = 4u;    // pass 2 counted other entries than pass 1
+constexpr uint32_t kWalkNoRoom = 8u;      // the output array is too small
+constexpr uint32_t kWalkBadGroup = 16u;   // a group range failed its check
+
+struct WalkArgs {
+    int64_t n_part, n_cell;
+    int32_t n_groups, exact;
+    double theta, eps2;
+    const otoo_src* src;
+    const otoo_wcell* cell;
+    const otoo_wcell64* cell64;
+    const int32_t* gfirst;
+    const int32_t* gcount;
+    const float* tpg;
+    uint32_t* counter;
+    int64_t* totals;
+};
+
+// Per-group FP32 data of the filter: the group centre c as a float pair and
+// the box relative to c.
+struct BoxF {
+    float c32[3], cl32[3], bl[3], bh[3];
+    float B;    // sum over axes of max(|bl|, |bh|)
+    float A;    // sum of |c32|: scale of the float-pair truncation error
+};
+
+// The acceptance test of the host walk, operation for operation in FP64
+// (no contraction: every operation is an explicitly rounded intrinsic).
+__device__ bool mac_exact(const otoo_wcell64* __restrict__ c64, int k, const double blo[3], const double bhi[3],
+                          double theta)
+{
+    if (!(theta > 0.0)) return false;
+    const otoo_wcell64 c = c64[k];
+    bool overlap = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double chi = __dadd_rn(c.lo[a], c.side);
+        if (!(c.lo[a] <= bhi[a] && blo[a] <= chi)) overlap = false;
+    }
+    if (overlap) return false;
+    double d2 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double d = 0.0;
+        const double t0 = __dsub_rn(blo[a], c.com[a]);
+        if (t0 > d) d = t0;
+        const double t1 = __dsub_rn(c.com[a], bhi[a]);
+        if (t1 > d) d = t1;
+        d2 = __dadd_rn(d2, __dmul_rn(d, d));
+        const double e = __dsub_rn(c.com[a], c.gc[a]);
+        s2 = __dadd_rn(s2, __dmul_rn(e, e));
+    }
+    return __dsqrt_rn(d2) > __dadd_rn(__ddiv_rn(c.side, theta), __dsqrt_rn(s2));
+}
+
+// FP32 filter of the acceptance test: 1 = accept, 0 = reject, -1 = too close
+// to call.  u = com - c from the float pairs; every rounded quantity is
+// within 2^-20 K of its exact value (K: sum of the magnitudes the test
+// combines, plus 2^-24 of the absolute coordinates for the truncated low
+// words), so a comparison decided by more than 2^-18 K (box overlap) or
+// 2^-16 K^2 (squared distances) is decided the same way by the exact
+// arithmetic and by the host's FP64.
+__device__ __forceinline__ int mac_filter(const otoo_wcell& w, const BoxF& g, float invth)
+{
+    float u[3], au = 0.f, A = g.A;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        u[a] = __fadd_rn(__fsub_rn(w.com_hi[a], g.c32[a]), __fsub_rn(w.com_lo[a], g.cl32[a]));
+        au += fabsf(u[a]);
+        A += fabsf(w.com_hi[a]);
+    }
+    const float thr = __fadd_rn(__fmul_rn(w.side, invth), w.s);
+    const float K = au + g.B + thr + w.side + A * 0x1p-24f;
+    const float del = K * 0x1p-18f;
+    bool sep = false, ovl = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = __fsub_rn(u[a], w.e[a]);
+        const float hi = __fadd_rn(lo, w.side);
+        sep = sep || (lo > g.bh[a] + del) || (g.bl[a] > hi + del);
+        ovl = ovl && (lo < g.bh[a] - del) && (g.bl[a] < hi - del);
+    }
+    if (ovl) return 0;
+    if (!sep) return -1;
+    float d2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d = fmaxf(0.f, fmaxf(g.bl[a] - u[a], u[a] - g.bh[a]));
+        d2 = fmaf(d, d, d2);
+    }
+    const float thr2 = thr * thr, m = K * K * 0x1p-16f;
+    if (d2 > thr2 + m) return 1;
+    if (d2 < thr2 - m) return 0;
+    return -1;
+}
+
+__device__ __forceinline__ otoo_wcell load_wcell(const otoo_wcell* __restrict__ cell, int k)
+{
+    const float4* p = reinterpret_cast<const float4*>(cell + k);
+    const float4 v0 = __ldg(p), v1 = __ldg(p + 1), v2 = __ldg(p + 2), v3 = __ldg(p + 3);
+    otoo_wcell w;
+    w.com_hi[0] = v0.x, w.com_hi[1] = v0.y, w.com_hi[2] = v0.z;
+    w.com_lo[0] = v0.w, w.com_lo[1] = v1.x, w.com_lo[2] = v1.y;
+    w.e[0] = v1.z, w.e[1] = v1.w, w.e[2] = v2.x;
+    w.side = v2.y;
+    w.s = v2.z;
+    w.child0 = __float_as_int(v2.w);
+    w.nchild = __float_as_int(v3.x);
+    w.begin = __float_as_int(v3.y);
+    w.end = __float_as_int(v3.z);
+    w.pad = 0;
+    return w;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// One warp per group (atomic ticket).  The stack holds cell indices; each
+// step pops up to 32 of them (fewer when the stack is nearly full: a popped
+// cell pushes at most 8 children, and kReserve entries stay free so that
+// one-node steps -- a depth-first descent adds at most 7 entries per level --
+// always fit), tests them, emits accepted cells and rejected leaves' particles
+// and pushes the children of rejected inner cells.
+template <bool kFill>
+__global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a, otoo_group* __restrict__ groups,
+                                                          int32_t* __restrict__ list, int64_t capacity)
+{
+    __shared__ int32_t stack_s[kWalkWarps][kStack];
+    const int lane = threadIdx.x & 31;
+    int32_t* stk = stack_s[threadIdx.x >> 5];
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t* status = a.counter + 1;
+    if (kFill && a.totals[0] > capacity) {
+        if (threadIdx.x == 0) atomicOr(status, kWalkNoRoom);
+        return;
+    }
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(a.counter, 1u);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= a.n_groups) break;
+        const int32_t first = a.gfirst[g], count = a.gcount[g];
+        if (first < 0 || count < 1 || count > kMaxGroup || (int64_t)first + count > a.n_part) {
+            if (lane == 0) {
+                atomicOr(status, kWalkBadGroup);
+                if (!kFill) {
+                    otoo_group z = {};
+                    z.first = first;
+                    z.eps2 = a.eps2;
+                    z.theta = -1.f;
+                    groups[g] = z;
+                }
+            }
+            continue;
+        }
+        // the group's box: FP64 min/max, exact
+        double blo[3], bhi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) blo[k] = __longlong_as_double(0x7ff0000000000000LL), bhi[k] = -blo[k];
+        for (int i = lane; i < count; i += 32) {
+            const otoo_src s = a.src[first + i];
+            blo[0] = fmin(blo[0], s.x), bhi[0] = fmax(bhi[0], s.x);
+            blo[1] = fmin(blo[1], s.y), bhi[1] = fmax(bhi[1], s.y);
+            blo[2] = fmin(blo[2], s.z), bhi[2] = fmax(bhi[2], s.z);
+        }
+        double c[3];
+        BoxF bf;
+        bf.B = 0.f;
+        bf.A = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            blo[k] = warp_min(blo[k]);
+            bhi[k] = warp_max(bhi[k]);
+            c[k] = __dmul_rn(__dadd_rn(blo[k], bhi[k]), 0.5);
+            bf.c32[k] = __double2float_rn(c[k]);
+            bf.cl32[k] = __double2float_rn(__dsub_rn(c[k], (double)bf.c32[k]));
+            bf.bl[k] = __double2float_rn(__dsub_rn(blo[k], c[k]));
+            bf.bh[k] = __double2float_rn(__dsub_rn(bhi[k], c[k]));
+            bf.B += fmaxf(fabsf(bf.bl[k]), fabsf(bf.bh[k]));
+            bf.A += fabsf(bf.c32[k]);
+        }
+        const double theta = a.tpg ? (double)a.tpg[g] : a.theta;
+        const bool open_all = !(theta > 0.0);
+        const float invth = open_all ? 0.f : __double2float_rn(1.0 / theta);
+        int64_t off_c = 0, off_p = 0;
+        int32_t want_c = 0, want_p = 0;
+        if (kFill) {
+            const otoo_group gr = groups[g];
+            off_c = gr.list_off;
+            want_c = gr.n_cell;
+            want_p = gr.n_part;
+            off_p = off_c + want_c;
+            if (off_c < 0 || want_c < 0 || want_p < 0 || off_p + want_p > capacity) {
+                if (lane == 0) atomicOr(status, kWalkNoRoom);
+                continue;
+            }
+        }
+        int32_t ncell = 0, npart = 0;
+        int sp = 0;
+        if (theta >= 0.0) {
+            if (lane == 0) stk[0] = 0;
+            sp = 1;
+        }
+        __syncwarp();
+        int64_t budget = a.n_cell + 1;  // a tree pops each cell at most once
+        bool failed = false;
+        while (sp > 0) {
+            int W = sp < 32 ? sp : 32;
+            const int wfit = (kStack - kReserve - sp) / 7;
+            if (W > wfit) W = wfit;
+            if (W < 1) W = (sp + 7 <= kStack) ? 1 : 0;
+            budget -= W;
+            if (W < 1 || budget < 0) {
+                failed = true;
+                break;
+            }
+            int node = -1;
+            if (lane < W) node = stk[sp - 1 - lane];
+            __syncwarp();
+            sp -= W;
+            int kind = 0;  // 1 accept, 2 leaf, 3 open
+            int c0 = 0, nch = 0, pb = 0, pe = 0;
+            if (lane < W) {
+                bool ok = node >= 0 && node < a.n_cell;
+                if (ok) {
+                    const otoo_wcell w = load_wcell(a.cell, node);
+                    nch = w.nchild;
+                    c0 = w.child0;
+                    pb = w.begin;
+                    pe = w.end;
+                    ok = nch >= 0 && nch <= 8 && (nch == 0 || (c0 > node && (int64_t)c0 + nch <= a.n_cell)) &&
+                         pb >= 0 && pb <= pe && (int64_t)pe <= a.n_part;
+                    if (ok) {
+                        int dec = 0;
+                        if (!open_all) {
+                            dec = a.exact ? -1 : mac_filter(w, bf, invth);
+                            if (dec < 0) dec = mac_exact(a.cell64, node, blo, bhi, theta) ? 1 : 0;
+                        }
+                        kind = dec ? 1 : (nch == 0 ? 2 : 3);
+                    }
+                }
+                if (!ok) atomicOr(status, kWalkBadRecord);
+            }
+            // accepted cells
+            const unsigned am = __ballot_sync(kFull, kind == 1);
+            if (kFill && kind == 1) {
+                const int32_t r = ncell + __popc(am & lt);
+                if (r < want_c) list[off_c + r] = (int32_t)(a.n_part + node);
+            }
+            ncell += __popc(am);
+            // particles of rejected leaves
+            const int np = kind == 2 ? pe - pb : 0;
+            const int pin = warp_incl_scan(np, lane);
+            if (kFill && np > 0) {
+                const int32_t base = npart + pin - np;
+                for (int k = 0; k < np; ++k)
+                    if (base + k < want_p) list[off_p + base + k] = pb + k;
+            }
+            npart += __shfl_sync(kFull, pin, 31);
+            // children of rejected inner cells, first child on top
+            const int nc = kind == 3 ? nch : 0;
+            const int cin = warp_incl_scan(nc, lane);
+            if (nc > 0) {
+                const int base = sp + cin - nc;
+                for (int k = 0; k < nc; ++k) stk[base + k] = c0 + nc - 1 - k;
+            }
+            sp += __shfl_sync(kFull, cin, 31);
+            __syncwarp();
+        }
+        if (failed && lane == 0) atomicOr(status, kWalkOverflow);
+        if (!kFill) {
+            if (lane == 0) {
+                otoo_group r;
+                r.first = first;
+                r.count = count;
+                r.n_cell = ncell;
+                r.n_part = npart;
+                r.list_off = 0;
+                r.eps2 = a.eps2;
+                r.cx = c[0];
+                r.cy = c[1];
+                r.cz = c[2];
+                r.theta = (float)theta;
+                r.sys = 0;
+                groups[g] = r;
+                const int64_t len = (int64_t)ncell + npart;
+                atomicAdd(reinterpret_cast<unsigned long long*>(a.totals), (unsigned long long)len);
+                atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 1), (unsigned long long)(len * count));
+                atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 2),
+                          (unsigned long long)((int64_t)ncell * count));
+            }
+        } else if (lane == 0 && (ncell != want_c || npart != want_p)) {
+            atomicOr(status, kWalkMismatch);
+        }
+    }
+}
+
+// ---- exclusive prefix sums in index order ---------------------------------
+// In: functor int64 operator()(int64 i); Out: functor void operator()(int64 i,
+// int64 prefix).  Three launches: sums of blocks of kScanBlock elements, a
+// one-CTA exclusive scan of those sums (total to *total), block-level scans.
+
+struct GroupLen {
+    const otoo_group* g;
+    __device__ int64_t operator()(int64_t i) const { return (int64_t)g[i].n_cell + g[i].n_part; }
+};
+struct GroupOff {
+    otoo_group* g;
+    __device__ void operator()(int64_t i, int64_t v) const { g[i].list_off = v; }
+};
+struct I32In {
+    const int32_t* p;
+    __device__ int64_t operator()(int64_t i) const { return p[i]; }
+};
+struct I32Out {
+    int32_t* p;
+    __device__ void operator()(int64_t i, int64_t v) const { p[i] = (int32_t)v; }
+};
+
+__device__ int64_t block_excl_scan(int64_t v, int64_t* warp_s, int64_t* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_s[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? warp_s[lane] : 0;
+        int64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += t;
+        }
+        warp_s[lane] = wi - w;
+        if (lane == 31) warp_s[32] = wi;
+    }
+    __syncthreads();
+    const int64_t r = warp_s[wid] + inc - v;
+    *total = warp_s[32];
+    __syncthreads();
+    return r;
+}
+
+template <class In>
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(In in, int64_t n, int64_t* __restrict__ bsum)
+{
+    __shared__ int64_t ws[33];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanBlock;
+    int64_t v = 0;
+    for (int k = 0; k < kScanBlock / kScanThreads; ++k) {
+        const int64_t i = b0 + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) v += in(i);
+    }
+    int64_t tot;
+    block_excl_scan(v, ws, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int64_t* __restrict__ bsum, int64_t nblk,
+                                                            int64_t* __restrict__ total)
+{
+    __shared__ int64_t ws[33];
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nblk; b0 += kScanThreads) {
+        const int64_t i = b0 + threadIdx.x;
+        const int64_t v = i < nblk ? bsum[i] : 0;
+        int64_t tot;
+        const int64_t e = block_excl_scan(v, ws, &tot);
+        if (i < nblk) bsum[i] = carry + e;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <class In, class Out>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(In in, Out out, int64_t n,
+                                                              const int64_t* __restrict__ bsum)
+{
+    __shared__ int64_t ws[33];
+    constexpr int kPer = kScanBlock / kScanThreads;
+    const int64_t b0 = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kPer;
+    int64_t v[kPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        v[k] = b0 + k < n ? in(b0 + k) : 0;
+        s += v[k];
+    }
+    int64_t tot;
+    int64_t e = block_excl_scan(s, ws, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        if (b0 + k < n) out(b0 + k, e);
+        e += v[k];
+    }
+}
+
+template <class In, class Out>
+cudaError_t excl_scan(In in, Out out, int64_t n, int64_t* bsum, int64_t* total, cudaStream_t s)
+{
+    const int64_t nblk = (n + kScanBlock - 1) / kScanBlock;
+    if (nblk == 0) return cudaSuccess;
+    k_scan_sums<In><<<(unsigned)nblk, kScanThreads, 0, s>>>(in, n, bsum);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nblk, total);
+    k_scan_apply<In, Out><<<(unsigned)nblk, kScanThreads, 0, s>>>(in, out, n, bsum);
+    return cudaGetLastError();
+}
+
+int64_t scan_blocks(int64_t n) { return (n + kScanBlock - 1) / kScanBlock; }
+
+// ---- device plan ------------------------------------------------------------
+
+struct PlanScratch {
+    int64_t* bsum;    // scan block sums (2 scans, one after the other)
+    int32_t* hist;    // [kClasses] items per cost class
+    int32_t* cursor;  // [kClasses] next free item position of each class
+    int32_t* nic;     // [G] particle chunks
+    int32_t* nch;     // [G] list chunks
+    int32_t* slot0;   // [G] slots (n_chunks when > 1), then their exclusive prefix
+    int32_t* sidx;    // [G] 1 when the list is split, then the split record index
+    int32_t* cls;     // [G] cost class
+};
+
+PlanScratch plan_layout(int32_t* base, int64_t G)
+{
+    PlanScratch p;
+    const int64_t nb = scan_blocks(G) + 1;
+    p.bsum = reinterpret_cast<int64_t*>(base);
+    int32_t* q = base + 2 * nb;
+    p.hist = q;
+    p.cursor = q + kClasses;
+    q += 2 * kClasses;
+    p.nic = q;
+    p.nch = q + G;
+    p.slot0 = q + 2 * G;
+    p.sidx = q + 3 * G;
+    p.cls = q + 4 * G;
+    return p;
+}
+
+// The host plan's cost of one item on a warp (steps through the list in
+// lockstep plus staging and a fixed cost); exact in FP64 (integers and
+// halves far below 2^53), so the choice below matches the host's.
+__device__ __forceinline__ double item_cost(int32_t ni, int64_t len, int32_t ib)
+{
+    const int32_t P = (ni + ib - 1) / ib;
+    const int32_t nsub = 32 / P;
+    return (double)((len + nsub - 1) / nsub) * ib * 36.0 + 0.5 * (double)len + 300.0;
+}
+
+__global__ void k_plan_count(const otoo_group* __restrict__ groups, int32_t G, int32_t ib, int32_t split,
+                             PlanScratch p, int64_t* __restrict__ totals)
+{
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const otoo_group gr = groups[g];
+    atomicMax(reinterpret_cast<unsigned long long*>(totals + 3), (unsigned long long)(gr.count > 1 ? gr.count : 1));
+    const int64_t len = (int64_t)gr.n_cell + gr.n_part;
+    int32_t nic = 0, nch = 0, cls = 0;
+    if (len > 0 && gr.count > 0) {
+        const int32_t imax = 32 * ib;
+        nic = (gr.count + imax - 1) / imax;
+        double best = 0;
+        int32_t bestc = nic;
+        const int32_t cmax = gr.count < nic + 3 ? gr.count : nic + 3;
+        for (int32_t c = nic; c <= cmax; ++c) {
+            const int32_t big = (gr.count + c - 1) / c;
+            const double cost = c * item_cost(big, len, ib);
+            if (c == nic || cost < best) best = cost, bestc = c;
+        }
+        nic = bestc;
+        nch = (int32_t)((len + split - 1) / split);
+        // cost class: 4 * log2 of the first item's ni * (j1 - j0), in quarter octaves
+        const int64_t c0 = (int64_t)((gr.count + nic - 1) / nic) * ((len + nch - 1) / nch);
+        const int msb = 63 - __clzll((long long)c0);
+        const int frac = msb >= 2 ? (int)((c0 >> (msb - 2)) & 3) : (int)((c0 << (2 - msb)) & 3);
+        cls = 4 * msb + frac;
+        if (cls >= kClasses) cls = kClasses - 1;
+        atomicAdd(p.hist + cls, nic * nch);
+        atomicAdd(reinterpret_cast<unsigned long long*>(totals), (unsigned long long)(nic * nch));
+        if (nch > 1) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(totals + 1), 1ull);
+            atomicAdd(reinterpret_cast<unsigned long long*>(totals + 2), (unsigned long long)nch);
+        }
+    }
+    p.nic[g] = nic;
+    p.nch[g] = nch;
+    p.slot0[g] = nch > 1 ? nch : 0;
+    p.sidx[g] = nch > 1 ? 1 : 0;
+    p.cls[g] = cls;
+}
+
+__global__ void k_plan_cursor(PlanScratch p)
+{
+    if (threadIdx.x != 0) return;
+    int32_t pos = 0;
+    for (int c = kClasses - 1; c >= 0; --c) {
+        p.cursor[c] = pos;
+        pos += p.hist[c];
+    }
+}
+
+__global__ void k_plan_fill(const otoo_group* __restrict__ groups, int32_t G, PlanScratch p,
+                            otoo_item* __restrict__ items, int64_t items_cap, otoo_split* __restrict__ splits,
+                            int64_t splits_cap, uint32_t* __restrict__ status)
+{
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const int32_t nic = p.nic[g], nch = p.nch[g];
+    if (nic == 0 || nch == 0) return;
+    const otoo_group gr = groups[g];
+    const int64_t len = (int64_t)gr.n_cell + gr.n_part;
+    const int32_t slot0 = p.slot0[g];
+    const int32_t pos = atomicAdd(p.cursor + p.cls[g], nic * nch);
+    if ((int64_t)pos + nic * nch > items_cap) {
+        atomicOr(status, kWalkNoRoom);
+        return;
+    }
+    if (nch > 1) {
+        const int32_t si = p.sidx[g];
+        if (si >= splits_cap) {
+            atomicOr(status, kWalkNoRoom);
+            return;
+        }
+        otoo_split s;
+        s.g = g;
+        s.slot0 = slot0;
+        s.n_chunks = nch;
+        s.pad = 0;
+        splits[si] = s;
+    }
+    int32_t k = pos;
+    for (int32_t ic = 0; ic < nic; ++ic) {
+        const int32_t i0 = (int32_t)((int64_t)gr.count * ic / nic);
+        const int32_t i1 = (int32_t)((int64_t)gr.count * (ic + 1) / nic);
+        for (int32_t q = 0; q < nch; ++q) {
+            otoo_item it;
+            it.g = g;
+            it.i0 = i0;
+            it.ni = i1 - i0;
+            it.j0 = (int32_t)(len * q / nch);
+            it.j1 = (int32_t)(len * (q + 1) / nch);
+            it.slot = nch > 1 ? slot0 + q : -1;
+            it.pad0 = it.pad1 = 0;
+            items[k++] = it;
+        }
+    }
+}
+
+#define CUDA_TRY(expr)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess) return set_error(OTOO_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));  \
+    } while (0)
+
+int check_walk(const otoo_dev_walk* w)
+{
+    OTOO_REQUIRE(w, OTOO_EINVAL, "walk is NULL");
+    OTOO_REQUIRE(w->src && w->cell && w->cell64 && w->group_first && w->group_count && w->counter && w->totals,
+                 OTOO_EINVAL, "walk: NULL device pointer");
+    OTOO_REQUIRE(w->n_part >= 1 && w->n_cell >= 1 && w->n_part + w->n_cell <= INT32_MAX, OTOO_EINVAL,
+                 "walk: n_part/n_cell out of range");
+    OTOO_REQUIRE(w->n_groups >= 1, OTOO_EINVAL, "walk: n_groups < 1");
+    OTOO_REQUIRE(w->eps2 > 0.0, OTOO_EINVAL, "walk: eps2 must be > 0");
+    OTOO_REQUIRE(w->theta >= 0.0 && w->theta < 1e300, OTOO_EINVAL, "walk: theta must be finite and >= 0");
+    return OTOO_OK;
+}
+
+WalkArgs walk_args(const otoo_dev_walk* w)
+{
+    WalkArgs a;
+    a.n_part = w->n_part;
+    a.n_cell = w->n_cell;
+    a.n_groups = w->n_groups;
+    a.exact = w->exact ? 1 : 0;
+    a.theta = w->theta;
+    a.eps2 = w->eps2;
+    a.src = w->src;
+    a.cell = w->cell;
+    a.cell64 = w->cell64;
+    a.gfirst = w->group_first;
+    a.gcount = w->group_count;
+    a.tpg = w->theta_per_group;
+    a.counter = w->counter;
+    a.totals = w->totals;
+    return a;
+}
+
+template <bool kFill>
+int launch_walk(const otoo_dev_walk* w, otoo_group* groups, int32_t* list, int64_t capacity, cudaStream_t s)
+{
+    int dev = 0, sms = 0, occ = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk<kFill>, kWalkWarps * 32, 0));
+    if (occ < 1) occ = 1;
+    int64_t blocks = (int64_t)sms * occ;
+    const int64_t need = ((int64_t)w->n_groups + kWalkWarps - 1) / kWalkWarps;
+    if (blocks > need) blocks = need;
+    CUDA_TRY(cudaMemsetAsync(w->counter, 0, sizeof(uint32_t), s));
+    k_walk<kFill><<<(unsigned)blocks, kWalkWarps * 32, 0, s>>>(walk_args(w), groups, list, capacity);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t otoo_walk_totals_len(int64_t n_groups) { return 4 + scan_blocks(n_groups < 0 ? 0 : n_groups) + 1; }
+
+int otoo_walk_count(const otoo_dev_walk* w, otoo_group* groups, void* stream)
+{
+    const int rc = check_walk(w);
+    if (rc) return rc;
+    OTOO_REQUIRE(groups, OTOO_EINVAL, "otoo_walk_count: groups is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(w->counter, 0, 4 * sizeof(uint32_t), s));
+    CUDA_TRY(cudaMemsetAsync(w->totals, 0, 4 * sizeof(int64_t), s));
+    const int r2 = launch_walk<false>(w, groups, nullptr, 0, s);
+    if (r2) return r2;
+    CUDA_TRY(excl_scan(GroupLen{groups}, GroupOff{groups}, w->n_groups, w->totals + 4, nullptr, s));
+    return OTOO_OK;
+}
+
+int otoo_walk_fill(const otoo_dev_walk* w, const otoo_group* groups, int32_t* list, int64_t capacity, void* stream)
+{
+    const int rc = check_walk(w);
+    if (rc) return rc;
+    OTOO_REQUIRE(groups && list, OTOO_EINVAL, "otoo_walk_fill: NULL pointer");
+    OTOO_REQUIRE(capacity >= 0, OTOO_EINVAL, "otoo_walk_fill: negative capacity");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return launch_walk<true>(w, const_cast<otoo_group*>(groups), list, capacity, s);
+}
+
+int otoo_walk_check_status(const otoo_dev_walk* w, void* stream)
+{
+    OTOO_REQUIRE(w && w->counter, OTOO_EINVAL, "walk/counter is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t h[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(h, w->counter, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (h[1] & kWalkBadGroup) return set_error(OTOO_EDEVICE, "walk: a group range failed its bounds check");
+    if (h[1] & kWalkBadRecord) return set_error(OTOO_EDEVICE, "walk: a cell record failed its bounds check");
+    if (h[1] & kWalkOverflow) return set_error(OTOO_EDEVICE, "walk: a group's stack or node budget ran out");
+    if (h[1] & kWalkMismatch) return set_error(OTOO_EDEVICE, "walk: the two passes counted different entries");
+    if (h[1] & kWalkNoRoom) return set_error(OTOO_EDEVICE, "walk/plan: output array too small");
+    return OTOO_OK;
+}
+
+int64_t otoo_plan_scratch_ints(int64_t n_groups)
+{
+    if (n_groups < 0) n_groups = 0;
+    return 2 * (scan_blocks(n_groups) + 1) + 2 * kClasses + 5 * n_groups;
+}
+
+int otoo_plan_count(const otoo_group* groups, int32_t n_groups, const otoo_tune* tune, int32_t* plan_scratch,
+                    int64_t* plan_totals, void* stream)
+{
+    OTOO_REQUIRE(groups && tune && plan_scratch && plan_totals, OTOO_EINVAL, "otoo_plan_count: NULL pointer");
+    OTOO_REQUIRE(n_groups >= 1, OTOO_EINVAL, "otoo_plan_count: n_groups < 1");
+    OTOO_REQUIRE(tune->split >= 1, OTOO_EINVAL, "split must be >= 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t ib = tune->iblock > 1 ? tune->iblock : 1;
+    PlanScratch p = plan_layout(plan_scratch, n_groups);
+    CUDA_TRY(cudaMemsetAsync(plan_totals, 0, 4 * sizeof(int64_t), s));
+    CUDA_TRY(cudaMemsetAsync(p.hist, 0, kClasses * sizeof(int32_t), s));
+    k_plan_count<<<(n_groups + 255) / 256, 256, 0, s>>>(groups, n_groups, ib, tune->split, p, plan_totals);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(excl_scan(I32In{p.slot0}, I32Out{p.slot0}, n_groups, p.bsum, nullptr, s));
+    CUDA_TRY(excl_scan(I32In{p.sidx}, I32Out{p.sidx}, n_groups, p.bsum, nullptr, s));
+    k_plan_cursor<<<1, 32, 0, s>>>(p);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+int otoo_plan_fill(const otoo_group* groups, int32_t n_groups, const otoo_tune* tune, int32_t* plan_scratch,
+                   const int64_t* plan_totals, otoo_item* items, int64_t items_capacity, otoo_split* splits,
+                   int64_t splits_capacity, uint32_t* counter, void* stream)
+{
+    OTOO_REQUIRE(groups && tune && plan_scratch && plan_totals && counter, OTOO_EINVAL,
+                 "otoo_plan_fill: NULL pointer");
+    OTOO_REQUIRE(items || items_capacity == 0, OTOO_EINVAL, "otoo_plan_fill: items is NULL");
+    OTOO_REQUIRE(splits || splits_capacity == 0, OTOO_EINVAL, "otoo_plan_fill: splits is NULL");
+    OTOO_REQUIRE(n_groups >= 1, OTOO_EINVAL, "otoo_plan_fill: n_groups < 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    PlanScratch p = plan_layout(plan_scratch, n_groups);
+    k_plan_fill<<<(n_groups + 255) / 256, 256, 0, s>>>(groups, n_groups, p, items, items_capacity, splits,
+                                                        splits_capacity, counter + 1);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+}  // extern "C"

@@ -412,6 +412,48 @@ inline bool mac_accept(const otoo_tree* t, int64_t c, const double blo[3], const
     return std::sqrt(d2) > side / theta + std::sqrt(s2);
 }
 
+// Sources of the force step: particles in tree order, then cells (centre of
+// mass, mass) and their quadrupoles (zeros for monopole cells).
+void fill_sources(const otoo_tree* t, int use_quad, otoo_src* src, otoo_quad* quad)
+{
+    const int64_t n = t->n, nc = (int64_t)t->cells.size();
+    if (src) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            otoo_src& s = src[i];
+            s.x = t->pos[3 * i];
+            s.y = t->pos[3 * i + 1];
+            s.z = t->pos[3 * i + 2];
+            s.m = t->mass[i];
+            s.pad = 0;
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t c = 0; c < nc; ++c) {
+            otoo_src& s = src[n + c];
+            s.x = t->c_com[3 * c];
+            s.y = t->c_com[3 * c + 1];
+            s.z = t->c_com[3 * c + 2];
+            s.m = (float)t->c_mass[c];
+            s.pad = 0;
+        }
+    }
+    if (quad) {
+#pragma omp parallel for schedule(static)
+        for (int64_t c = 0; c < nc; ++c) {
+            otoo_quad& q = quad[c];
+            const double* qq = &t->c_quad[6 * c];
+            const bool u = use_quad != 0;
+            q.xx = u ? (float)qq[0] : 0.f;
+            q.yy = u ? (float)qq[1] : 0.f;
+            q.zz = u ? (float)qq[2] : 0.f;
+            q.xy = u ? (float)qq[3] : 0.f;
+            q.xz = u ? (float)qq[4] : 0.f;
+            q.yz = u ? (float)qq[5] : 0.f;
+            q.pad0 = q.pad1 = 0.f;
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -520,37 +562,9 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
         tbuf.clear();
         L->interactions = inter;
         L->cell_interactions = cinter;
-        // sources: particles in tree order, then cells (centre of mass, mass)
         L->src.resize(n + nc);
         L->quad.resize(nc);
-#pragma omp parallel for schedule(static)
-        for (int64_t i = 0; i < n; ++i) {
-            otoo_src& s = L->src[i];
-            s.x = t->pos[3 * i];
-            s.y = t->pos[3 * i + 1];
-            s.z = t->pos[3 * i + 2];
-            s.m = t->mass[i];
-            s.pad = 0;
-        }
-#pragma omp parallel for schedule(static)
-        for (int64_t c = 0; c < nc; ++c) {
-            otoo_src& s = L->src[n + c];
-            s.x = t->c_com[3 * c];
-            s.y = t->c_com[3 * c + 1];
-            s.z = t->c_com[3 * c + 2];
-            s.m = (float)t->c_mass[c];
-            s.pad = 0;
-            otoo_quad& q = L->quad[c];
-            const double* qq = &t->c_quad[6 * c];
-            const bool u = L->use_quad != 0;
-            q.xx = u ? (float)qq[0] : 0.f;
-            q.yy = u ? (float)qq[1] : 0.f;
-            q.zz = u ? (float)qq[2] : 0.f;
-            q.xy = u ? (float)qq[3] : 0.f;
-            q.xz = u ? (float)qq[4] : 0.f;
-            q.yz = u ? (float)qq[5] : 0.f;
-            q.pad0 = q.pad1 = 0.f;
-        }
+        fill_sources(t, L->use_quad, L->src.data(), L->quad.data());
         L->perm = t->perm;
         L->sys_part_off = {0, n};
         *out = L;
@@ -579,6 +593,83 @@ int otoo_lists_export(const otoo_lists* L, otoo_lists_view* v)
 }
 
 void otoo_lists_free(otoo_lists* L) { delete L; }
+
+int otoo_find_groups(const otoo_tree* t, int32_t n_crit, int32_t* first, int32_t* count, int64_t capacity,
+                     int64_t* n_groups)
+{
+    OTOO_REQUIRE(t && n_groups, OTOO_EINVAL, "otoo_find_groups: NULL argument");
+    OTOO_REQUIRE(n_crit >= 1 && n_crit <= kMaxGroup, OTOO_EINVAL, "n_crit out of [1, %d]", kMaxGroup);
+    OTOO_REQUIRE(capacity >= 0, OTOO_EINVAL, "otoo_find_groups: negative capacity");
+    return guarded([&]() -> int {
+        std::vector<GroupRange> gr;
+        find_groups(t, n_crit, gr);
+        const int64_t G = (int64_t)gr.size();
+        *n_groups = G;
+        if (!first && !count && capacity == 0) return OTOO_OK;
+        OTOO_REQUIRE(first && count, OTOO_EINVAL, "otoo_find_groups: first/count NULL with capacity %lld",
+                     (long long)capacity);
+        OTOO_REQUIRE(G <= capacity, OTOO_EINVAL, "otoo_find_groups: %lld groups, capacity %lld", (long long)G,
+                     (long long)capacity);
+        for (int64_t g = 0; g < G; ++g) {
+            first[g] = (int32_t)gr[g].begin;
+            count[g] = (int32_t)(gr[g].end - gr[g].begin);
+        }
+        return OTOO_OK;
+    });
+}
+
+// Walk records: the FP32 filter data (centre of mass as a float pair, its
+// offset from the cube's lower corner, side, and the centre-of-mass offset s
+// computed with the host test's FP64 operations) and the FP64 geometry the
+// exact test reads.
+int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, otoo_src* src, otoo_quad* quad,
+                            otoo_wcell* cell, otoo_wcell64* cell64)
+{
+    OTOO_REQUIRE(t, OTOO_EINVAL, "otoo_tree_device_arrays: NULL tree");
+    OTOO_REQUIRE(t->n <= INT32_MAX / 2 && (int64_t)t->cells.size() <= INT32_MAX / 2, OTOO_EINVAL,
+                 "otoo_tree_device_arrays: tree too large for 32-bit indices");
+    return guarded([&]() -> int {
+        fill_sources(t, use_quad, src, quad);
+        const int64_t nc = (int64_t)t->cells.size();
+        if (cell) {
+#pragma omp parallel for schedule(static)
+            for (int64_t c = 0; c < nc; ++c) {
+                otoo_wcell& w = cell[c];
+                const double* com = &t->c_com[3 * c];
+                const double* lo = &t->c_lo[3 * c];
+                const double* gc = &t->c_gc[3 * c];
+                double s2 = 0;
+                for (int a = 0; a < 3; ++a) {
+                    w.com_hi[a] = (float)com[a];
+                    w.com_lo[a] = (float)(com[a] - (double)w.com_hi[a]);
+                    w.e[a] = (float)(com[a] - lo[a]);
+                    const double e = com[a] - gc[a];
+                    s2 += e * e;
+                }
+                w.side = (float)t->c_side[c];
+                w.s = (float)std::sqrt(s2);
+                w.nchild = t->c_nchild[c];
+                w.child0 = w.nchild > 0 ? (int32_t)t->c_child0[c] : 0;
+                w.begin = (int32_t)t->c_begin[c];
+                w.end = (int32_t)t->c_end[c];
+                w.pad = 0;
+            }
+        }
+        if (cell64) {
+#pragma omp parallel for schedule(static)
+            for (int64_t c = 0; c < nc; ++c) {
+                otoo_wcell64& w = cell64[c];
+                for (int a = 0; a < 3; ++a) {
+                    w.lo[a] = t->c_lo[3 * c + a];
+                    w.com[a] = t->c_com[3 * c + a];
+                    w.gc[a] = t->c_gc[3 * c + a];
+                }
+                w.side = t->c_side[c];
+            }
+        }
+        return OTOO_OK;
+    });
+}
 
 int otoo_pack_batch(const otoo_lists* const* per, int32_t n_sys, otoo_lists** out)
 {

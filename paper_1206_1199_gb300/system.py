@@ -195,6 +195,14 @@ class DeviceSystem:
             setattr(s, k, b[k].data_ptr() if b[k] is not None else None)
         return cls(lists=lists, plan=plan, bufs=b, struct=s, use_perm=use_perm)
 
+    @property
+    def n_part(self):
+        return self.lists.n_part
+
+    @property
+    def tune(self):
+        return self.plan.tune
+
     def h2d_bytes(self):
         return sum(v.numel() * v.element_size() for k, v in self.bufs.items()
                    if v is not None and k not in ("partial", "counter", "split"))
@@ -204,13 +212,13 @@ def force(dev, accel=None, pot=None, precision=L.OTOO_FP32K, tune=None, stream=N
     """otoo_force on a DeviceSystem; returns (accel [n][3], pot [n]) FP64
     tensors in caller order (tree order when the system has no perm)."""
     import torch
-    n = dev.lists.n_part
+    n = dev.n_part
     device = dev.bufs["src"].device
     if accel is None:
         accel = torch.empty((n, 3), dtype=torch.float64, device=device)
     if pot is None:
         pot = torch.empty(n, dtype=torch.float64, device=device)
-    tune = tune if tune is not None else dev.plan.tune
+    tune = tune if tune is not None else dev.tune
     st = stream if stream is not None else torch.cuda.current_stream(device)
     L.call("otoo_force", ctypes.byref(dev.struct), accel.data_ptr(), pot.data_ptr(), int(precision),
            ctypes.byref(tune), ctypes.c_void_p(st.cuda_stream))
@@ -241,3 +249,192 @@ def build_system(pos, mass, theta, n_crit, eps, leaf_size=8, use_quad=True, tune
     lists = tree.lists(theta, n_crit, eps, use_quad)
     tune = tune if tune is not None else L.default_tune(max(n_crit, int(lists.groups["count"].max())))
     return tree, lists, lists.plan(tune)
+
+
+def _stream(stream, device):
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(st.cuda_stream)
+
+
+class BufferPool:
+    """Device buffers kept between steps (grown when too small), so that a
+    loop of device walks and force steps reuses the same memory and the
+    force step's recorded graph."""
+
+    def __init__(self, device):
+        self.device = device
+        self.bufs = {}
+
+    def get(self, name, n, dtype):
+        import torch
+        t = self.bufs.get(name)
+        if t is None or t.dtype != dtype or t.numel() < n:
+            t = torch.empty(max(int(n), 1), dtype=dtype, device=self.device)
+            self.bufs[name] = t
+        return t[:max(int(n), 1)]
+
+
+def _alloc(pool, device):
+    import torch
+    if pool is None:
+        return lambda name, n, dtype: torch.empty(max(int(n), 1), dtype=dtype, device=device)
+    return pool.get
+
+
+class DeviceTree:
+    """Inputs of the device walk for one tree, uploaded once: sources and
+    quadrupoles (as the host lists store them), walk records
+    (otoo_tree_device_arrays), the group ranges (otoo_find_groups) and the
+    tree-to-caller permutation."""
+
+    def __init__(self, tree, n_crit, use_quad=True, device="cuda"):
+        v = L.TreeView()
+        L.call("otoo_tree_export", tree._h, ctypes.byref(v))
+        n, nc = int(v.n_part), int(v.n_cell)
+        src = np.empty(n + nc, np.dtype(L.Src))
+        quad = np.empty(nc, np.dtype(L.Quad))
+        cell = np.empty(nc, np.dtype(L.WCell))
+        cell64 = np.empty(nc, np.dtype(L.WCell64))
+        L.call("otoo_tree_device_arrays", tree._h, int(bool(use_quad)), src.ctypes.data, quad.ctypes.data,
+               cell.ctypes.data, cell64.ctypes.data)
+        G = ctypes.c_int64()
+        L.call("otoo_find_groups", tree._h, int(n_crit), None, None, 0, ctypes.byref(G))
+        first = np.empty(G.value, np.int32)
+        count = np.empty(G.value, np.int32)
+        L.call("otoo_find_groups", tree._h, int(n_crit), first.ctypes.data, count.ctypes.data, G.value,
+               ctypes.byref(G))
+        self.n_part, self.n_cell, self.n_groups = n, nc, int(G.value)
+        self.n_src = n + nc
+        self.use_quad = bool(use_quad)
+        self.n_crit = int(n_crit)
+        self.device = device
+        perm = L.view(v.perm, np.int64, (n,))
+        self.bufs = dict(src=_to_dev(src, device), quad=_to_dev(quad, device) if use_quad else None,
+                         cell=_to_dev(cell, device), cell64=_to_dev(cell64, device),
+                         first=_to_dev(first, device), count=_to_dev(count, device), perm=_to_dev(perm, device))
+        self._tree = tree
+
+    def h2d_bytes(self):
+        return sum(b.numel() for b in self.bufs.values() if b is not None)
+
+    def walk(self, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None):
+        """otoo_walk_count + otoo_walk_fill: groups and lists on the device.
+        With a BufferPool the buffers of the previous walk are reused (and
+        overwritten)."""
+        return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool)
+
+
+class DeviceLists:
+    """Groups and lists made by the device walk (device buffers)."""
+
+    def __init__(self, dtree, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None):
+        import torch
+        dev = dtree.device
+        G = dtree.n_groups
+        self.tree = dtree
+        self.pool = pool
+        self.n_part, self.n_src, self.n_groups = dtree.n_part, dtree.n_src, G
+        self.use_quad = dtree.use_quad
+        alloc = _alloc(pool, dev)
+        b = dict(groups=alloc("groups", G * 64, torch.uint8), counter=alloc("wcounter", 4, torch.int32),
+                 totals=alloc("totals", L.load().otoo_walk_totals_len(G), torch.int64))
+        if theta_per_group is not None:
+            tpg = np.ascontiguousarray(theta_per_group, dtype=np.float32)
+            assert tpg.shape == (G,)
+            b["tpg"] = alloc("tpg", G, torch.float32)
+            b["tpg"].copy_(torch.from_numpy(tpg))
+        w = L.DevWalk()
+        w.n_part, w.n_cell, w.n_groups, w.exact = dtree.n_part, dtree.n_cell, G, int(bool(exact))
+        w.theta, w.eps2 = float(theta), float(eps) * float(eps)
+        tb = dtree.bufs
+        w.src, w.cell, w.cell64 = tb["src"].data_ptr(), tb["cell"].data_ptr(), tb["cell64"].data_ptr()
+        w.group_first, w.group_count = tb["first"].data_ptr(), tb["count"].data_ptr()
+        w.theta_per_group = b["tpg"].data_ptr() if "tpg" in b else None
+        w.counter, w.totals = b["counter"].data_ptr(), b["totals"].data_ptr()
+        self.struct = w
+        self.bufs = b
+        st = _stream(stream, dev)
+        L.call("otoo_walk_count", ctypes.byref(w), b["groups"].data_ptr(), st)
+        tot = b["totals"][:3].tolist()
+        self.n_list, self.interactions, self.cell_interactions = (int(x) for x in tot)
+        b["list"] = alloc("list", self.n_list, torch.int32)
+        L.call("otoo_walk_fill", ctypes.byref(w), b["groups"].data_ptr(), b["list"].data_ptr(), self.n_list, st)
+        L.call("otoo_walk_check_status", ctypes.byref(w), st)
+
+    @property
+    def groups(self):
+        """Group records copied to the host (numpy structured array)."""
+        return self.bufs["groups"].cpu().numpy().view(np.dtype(L.Group))
+
+    @property
+    def list(self):
+        return self.bufs["list"][:self.n_list].cpu().numpy()
+
+    def plan(self, tune, stream=None):
+        return DevicePlan(self, tune, stream)
+
+
+class DevicePlan:
+    """Work items made on the device (otoo_plan_count + otoo_plan_fill)."""
+
+    def __init__(self, dl, tune, stream=None):
+        import torch
+        dev = dl.tree.device
+        G = dl.n_groups
+        self.tune = tune
+        st = _stream(stream, dev)
+        alloc = _alloc(dl.pool, dev)
+        scratch = alloc("pscratch", L.load().otoo_plan_scratch_ints(G), torch.int32)
+        ptot = alloc("ptotals", 4, torch.int64)
+        gp = dl.bufs["groups"].data_ptr()
+        L.call("otoo_plan_count", gp, G, ctypes.byref(tune), scratch.data_ptr(), ptot.data_ptr(), st)
+        n_items, n_splits, slots, ncm = (int(x) for x in ptot.tolist())
+        self.n_items, self.n_splits, self.n_crit_max = n_items, n_splits, max(ncm, 1)
+        self.partial_doubles = slots * 4 * self.n_crit_max
+        self.items_buf = alloc("items", n_items * 32, torch.uint8)
+        self.splits_buf = alloc("splits", n_splits * 16, torch.uint8)
+        L.call("otoo_plan_fill", gp, G, ctypes.byref(tune), scratch.data_ptr(), ptot.data_ptr(),
+               self.items_buf.data_ptr(), n_items, self.splits_buf.data_ptr(), n_splits,
+               dl.bufs["counter"].data_ptr(), st)
+        L.call("otoo_walk_check_status", ctypes.byref(dl.struct), st)
+
+    @property
+    def items(self):
+        return self.items_buf[:self.n_items * 32].cpu().numpy().view(np.dtype(L.Item))
+
+    @property
+    def splits(self):
+        return self.splits_buf[:self.n_splits * 16].cpu().numpy().view(np.dtype(L.Split))
+
+
+class DeviceStep:
+    """A force step whose lists and plan were made on the device; usable
+    with force() like a DeviceSystem."""
+
+    def __init__(self, dl, plan, use_perm=True):
+        import torch
+        dev = dl.tree.device
+        tb = dl.tree.bufs
+        alloc = _alloc(dl.pool, dev)
+        self.lists, self.plan = dl, plan
+        self.bufs = dict(src=tb["src"], quad=tb["quad"], groups=dl.bufs["groups"], list=dl.bufs["list"],
+                         items=plan.items_buf, splits=plan.splits_buf if plan.n_splits else None,
+                         perm=tb["perm"] if use_perm else None,
+                         partial=alloc("partial", plan.partial_doubles, torch.float64),
+                         counter=alloc("fcounter", 4, torch.int32),
+                         split=alloc("split", dl.n_src * 8, torch.float32))
+        s = L.DevSystem()
+        s.n_part, s.n_src, s.n_list = dl.n_part, dl.n_src, dl.n_list
+        s.n_groups, s.n_items, s.n_splits, s.n_crit_max = dl.n_groups, plan.n_items, plan.n_splits, plan.n_crit_max
+        for k in ("src", "quad", "groups", "list", "items", "splits", "perm", "partial", "counter", "split"):
+            setattr(s, k, self.bufs[k].data_ptr() if self.bufs[k] is not None else None)
+        self.struct = s
+
+    @property
+    def n_part(self):
+        return self.lists.n_part
+
+    @property
+    def tune(self):
+        return self.plan.tune

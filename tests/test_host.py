@@ -43,6 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(L.Src) == 32 and ctypes.sizeof(L.Quad) == 32 and ctypes.sizeof(L.Group) == 64
     assert ctypes.sizeof(L.Item) == 32 and ctypes.sizeof(L.Split) == 16
+    assert ctypes.sizeof(L.WCell) == 64 and ctypes.sizeof(L.WCell64) == 80
 
 
 def tree_and_lists(pos, mass, theta=0.5, n_crit=64, eps=0.01, quad=True, leaf=8):
@@ -258,3 +259,138 @@ def test_features_are_finite_and_consistent():
     _, l0 = tree_and_lists(pos[:2000], mass[:2000], 0.0, 64, 5e-4)
     f0 = l0.features(S.Tree(pos[:2000], mass[:2000]))
     assert np.all(f0[:, 3] == 0) and np.all(f0[:, 1] == np.float32(3.0)) and np.all(f0[:, 4] == np.float32(-12.0))
+
+
+def device_arrays(t, use_quad):
+    e = t.export()
+    n, nc = e["n_part"], e["n_cell"]
+    src = np.empty(n + nc, np.dtype(L.Src))
+    quad = np.empty(nc, np.dtype(L.Quad))
+    cell = np.empty(nc, np.dtype(L.WCell))
+    cell64 = np.empty(nc, np.dtype(L.WCell64))
+    L.call("otoo_tree_device_arrays", t._h, int(use_quad), src.ctypes.data, quad.ctypes.data, cell.ctypes.data,
+           cell64.ctypes.data)
+    return e, src, quad, cell, cell64
+
+
+def find_groups(t, n_crit):
+    G = ctypes.c_int64()
+    L.call("otoo_find_groups", t._h, n_crit, None, None, 0, ctypes.byref(G))
+    first = np.empty(G.value, np.int32)
+    count = np.empty(G.value, np.int32)
+    L.call("otoo_find_groups", t._h, n_crit, first.ctypes.data, count.ctypes.data, G.value, ctypes.byref(G))
+    return first, count
+
+
+@pytest.mark.parametrize("use_quad", [0, 1])
+def test_device_arrays_match_lists_and_geometry(use_quad):
+    pos, mass = ic.hernquist(12000, 31)
+    t, lists = tree_and_lists(pos, mass, 0.6, 48, 0.01, bool(use_quad))
+    e, src, quad, cell, cell64 = device_arrays(t, use_quad)
+    # the force step's sources are the ones the host lists carry
+    np.testing.assert_array_equal(src.view(np.uint8), lists.src.view(np.uint8))
+    np.testing.assert_array_equal(quad.view(np.uint8), lists.quad.view(np.uint8))
+    first, count = find_groups(t, 48)
+    np.testing.assert_array_equal(first, lists.groups["first"])
+    np.testing.assert_array_equal(count, lists.groups["count"])
+    # FP64 geometry: cube_lo = lo + org * h, side = h * 2^(21 - level), centre = cube_lo + side / 2
+    h = e["root_side"] / 2097152.0
+    lo = e["root_lo"][None, :] + e["org"].astype(np.float64) * h
+    side = h * (2.0 ** (21 - e["level"])).astype(np.float64)
+    np.testing.assert_array_equal(cell64["lo"], lo)
+    np.testing.assert_array_equal(cell64["side"], side)
+    np.testing.assert_array_equal(cell64["gc"], lo + (side / 2)[:, None])
+    np.testing.assert_array_equal(cell64["com"], e["com"])
+    # FP32 walk records
+    com = e["com"]
+    np.testing.assert_array_equal(cell["com_hi"], com.astype(np.float32))
+    np.testing.assert_array_equal(cell["com_lo"], (com - cell["com_hi"].astype(np.float64)).astype(np.float32))
+    assert np.all(np.abs(cell["com_hi"].astype(np.float64) + cell["com_lo"] - com) <= 2.0 ** -46 * np.abs(com))
+    np.testing.assert_array_equal(cell["e"], (com - lo).astype(np.float32))
+    assert np.all(cell["e"] >= 0) and np.all(cell["e"] <= cell["side"][:, None])
+    gc = lo + (side / 2)[:, None]
+    dd = com - gc
+    s2 = dd[:, 0] * dd[:, 0] + dd[:, 1] * dd[:, 1] + dd[:, 2] * dd[:, 2]
+    np.testing.assert_array_equal(cell["s"], np.sqrt(s2).astype(np.float32))
+    np.testing.assert_array_equal(cell["side"], side.astype(np.float32))
+    np.testing.assert_array_equal(cell["nchild"], e["nchild"])
+    np.testing.assert_array_equal(cell["child0"], np.where(e["nchild"] > 0, e["child0"], 0))
+    np.testing.assert_array_equal(cell["begin"], e["begin"])
+    np.testing.assert_array_equal(cell["end"], e["end"])
+
+
+def exact_accept(blo, bhi, cell64, theta):
+    """The host walk's FP64 acceptance test for one box against every cell
+    (numpy, the same operations in the same order)."""
+    if not theta > 0:
+        return np.zeros(len(cell64), bool)
+    lo, side, com, gc = cell64["lo"], cell64["side"], cell64["com"], cell64["gc"]
+    chi = lo + side[:, None]
+    overlap = np.all((lo <= bhi) & (blo <= chi), axis=1)
+    d = np.maximum(np.maximum(blo - com, 0.0), com - bhi)
+    d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    e = com - gc
+    s2 = (e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2]
+    return ~overlap & (np.sqrt(d2) > side / theta + np.sqrt(s2))
+
+
+def filter_accept(blo, bhi, cell, theta):
+    """FP32 filter of the device walk, restated in numpy float32: +1 accept,
+    0 reject, -1 undecided (the device then runs the FP64 test)."""
+    f = np.float32
+    c = (blo + bhi) * 0.5
+    c32 = c.astype(f)
+    cl32 = (c - c32.astype(np.float64)).astype(f)
+    bl = (blo - c).astype(f)
+    bh = (bhi - c).astype(f)
+    B = np.maximum(np.abs(bl), np.abs(bh)).sum(dtype=f)
+    A0 = np.abs(c32).sum(dtype=f)
+    invth = f(1.0 / theta)
+    u = (cell["com_hi"] - c32) + (cell["com_lo"] - cl32)
+    side = cell["side"]
+    thr = side * invth + cell["s"]
+    A = A0 + np.abs(cell["com_hi"]).sum(1, dtype=f)
+    K = np.abs(u).sum(1, dtype=f) + B + thr + side + A * f(2.0 ** -24)
+    dl = K * f(2.0 ** -18)
+    lo = u - cell["e"]
+    hi = lo + side[:, None]
+    sep = np.any((lo > bh + dl[:, None]) | (bl > hi + dl[:, None]), axis=1)
+    ovl = np.all((lo < bh - dl[:, None]) & (bl < hi - dl[:, None]), axis=1)
+    d = np.maximum(f(0), np.maximum(bl - u, u - bh))
+    d2 = (d * d).sum(1, dtype=f)
+    thr2 = thr * thr
+    m = K * K * f(2.0 ** -16)
+    out = np.full(len(cell), -1, np.int8)
+    out[sep & (d2 > thr2 + m)] = 1
+    out[sep & (d2 < thr2 - m)] = 0
+    out[ovl] = 0
+    return out
+
+
+@pytest.mark.parametrize("model,n,theta", [("plummer", 6000, 0.5), ("hernquist", 6000, 0.75),
+                                           ("lattice", 4096, 0.5), ("lattice", 4096, 1.0)])
+def test_fp32_filter_never_contradicts_fp64(model, n, theta):
+    """Wherever the FP32 filter decides, the FP64 test decides the same; the
+    undecided share stays small.  The lattice puts many cells exactly on the
+    acceptance threshold."""
+    if model == "lattice":
+        k = round(n ** (1 / 3))
+        g = (np.arange(k) + 0.5) / k
+        pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) * 2.0 + 10.0
+        mass = np.full(len(pos), 1.0 / len(pos), np.float32)
+    else:
+        pos, mass = ic.make(model, n, 32)
+    t = S.Tree(pos, mass, 8)
+    e, _, _, cell, cell64 = device_arrays(t, 1)
+    first, count = find_groups(t, 32)
+    undecided = total = 0
+    for gi in range(0, len(first), 3):
+        p = e["pos"][first[gi]:first[gi] + count[gi]]
+        blo, bhi = p.min(0), p.max(0)
+        ex = exact_accept(blo, bhi, cell64, theta)
+        fl = filter_accept(blo, bhi, cell, theta)
+        dec = fl >= 0
+        np.testing.assert_array_equal(fl[dec] == 1, ex[dec])
+        undecided += int((~dec).sum())
+        total += len(fl)
+    assert undecided <= 0.01 * total
