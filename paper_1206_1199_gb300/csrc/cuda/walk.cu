@@ -31,8 +31,8 @@ using namespace otoo;
 namespace {
 
 constexpr int kWalkWarps = 8;       // warps per CTA
-constexpr int kStack = 1024;        // stack entries per warp (shared memory)
-constexpr int kReserve = 160;       // entries kept free for one-node steps
+constexpr int kStack = 512;         // stack entries (runs of sibling cells) per warp
+constexpr int kMaxLevels = 22;      // tree levels (root level 0 to the 2^21 grid level)
 constexpr int kScanThreads = 1024;  // scan kernels: threads per CTA
 constexpr int kScanBlock = 2048;    // elements per scan block
 constexpr int kClasses = 128;       // cost classes of the plan's launch order
@@ -137,20 +137,30 @@ __device__ __forceinline__ int mac_filter(const otoo_wcell& w, const BoxF& g, fl
     return -1;
 }
 
+// One 32-byte sector per load (256-bit vector loads, sm_100 and later): the
+// 64-byte record in two requests instead of four.
+__device__ __forceinline__ void ld256(const void* p, float v[8])
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+}
+
 __device__ __forceinline__ otoo_wcell load_wcell(const otoo_wcell* __restrict__ cell, int k)
 {
-    const float4* p = reinterpret_cast<const float4*>(cell + k);
-    const float4 v0 = __ldg(p), v1 = __ldg(p + 1), v2 = __ldg(p + 2), v3 = __ldg(p + 3);
+    float v[16];
+    ld256(cell + k, v);
+    ld256(reinterpret_cast<const char*>(cell + k) + 32, v + 8);
     otoo_wcell w;
-    w.com_hi[0] = v0.x, w.com_hi[1] = v0.y, w.com_hi[2] = v0.z;
-    w.com_lo[0] = v0.w, w.com_lo[1] = v1.x, w.com_lo[2] = v1.y;
-    w.e[0] = v1.z, w.e[1] = v1.w, w.e[2] = v2.x;
-    w.side = v2.y;
-    w.s = v2.z;
-    w.child0 = __float_as_int(v2.w);
-    w.nchild = __float_as_int(v3.x);
-    w.begin = __float_as_int(v3.y);
-    w.end = __float_as_int(v3.z);
+    w.com_hi[0] = v[0], w.com_hi[1] = v[1], w.com_hi[2] = v[2];
+    w.com_lo[0] = v[3], w.com_lo[1] = v[4], w.com_lo[2] = v[5];
+    w.e[0] = v[6], w.e[1] = v[7], w.e[2] = v[8];
+    w.side = v[9];
+    w.s = v[10];
+    w.child0 = __float_as_int(v[11]);
+    w.nchild = __float_as_int(v[12]);
+    w.begin = __float_as_int(v[13]);
+    w.end = __float_as_int(v[14]);
     w.pad = 0;
     return w;
 }
@@ -165,32 +175,55 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
     return v;
 }
 
-__device__ __forceinline__ double warp_min(double v)
+// Order-preserving integer key of a double (for non-NaN values): min/max on
+// the keys is min/max on the values, on the integer pipe.
+__device__ __forceinline__ long long dkey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dval(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL)); }
+
+__device__ __forceinline__ long long warp_min(long long v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(kFull, v, o);
+        v = t < v ? t : v;
+    }
     return v;
 }
-__device__ __forceinline__ double warp_max(double v)
+__device__ __forceinline__ long long warp_max(long long v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(kFull, v, o);
+        v = t > v ? t : v;
+    }
     return v;
 }
 
-// One warp per group (atomic ticket).  The stack holds cell indices; each
-// step pops up to 32 of them (fewer when the stack is nearly full: a popped
-// cell pushes at most 8 children, and kReserve entries stay free so that
-// one-node steps -- a depth-first descent adds at most 7 entries per level --
-// always fit), tests them, emits accepted cells and rejected leaves' particles
-// and pushes the children of rejected inner cells.
+// A stack entry is a run of consecutive cells (the children of one cell):
+// first cell in the low 28 bits, run length - 1 (0..7) above.
+constexpr uint32_t kRunShift = 28;
+constexpr uint32_t kRunMask = (1u << kRunShift) - 1u;
+__device__ __forceinline__ uint32_t run(int first, int n) { return (uint32_t)first | ((uint32_t)(n - 1) << kRunShift); }
+
+// One warp per group (atomic ticket).  The stack holds runs of sibling
+// cells; each step takes up to 32 cells from the top runs (the last run may
+// be split, its rest goes back), tests them, emits accepted cells and
+// rejected leaves' particles and pushes one run per rejected inner cell (its
+// children).  A 32-cell step adds at most 32 entries and runs only with
+// 33 + kMaxLevels entries free; otherwise the step takes one cell, which adds
+// at most one entry, and only when it descends a level (a tree has at most
+// kMaxLevels levels below any cell), so the stack never overflows.
 template <bool kFill>
-__global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a, otoo_group* __restrict__ groups,
+__global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_group* __restrict__ groups,
                                                           int32_t* __restrict__ list, int64_t capacity)
 {
-    __shared__ int32_t stack_s[kWalkWarps][kStack];
+    __shared__ uint32_t stack_s[kWalkWarps][kStack];
     const int lane = threadIdx.x & 31;
-    int32_t* stk = stack_s[threadIdx.x >> 5];
+    uint32_t* stk = stack_s[threadIdx.x >> 5];
     const unsigned lt = (1u << lane) - 1u;
     uint32_t* status = a.counter + 1;
     if (kFill && a.totals[0] > capacity) {
@@ -216,24 +249,26 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a, otoo_group
             }
             continue;
         }
-        // the group's box: FP64 min/max, exact
-        double blo[3], bhi[3];
+        // the group's box: min/max on order-preserving integer keys (exact)
+        long long klo[3], khi[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) blo[k] = __longlong_as_double(0x7ff0000000000000LL), bhi[k] = -blo[k];
+        for (int k = 0; k < 3; ++k) klo[k] = 0x7fffffffffffffffLL, khi[k] = -klo[k] - 1;
         for (int i = lane; i < count; i += 32) {
-            const otoo_src s = a.src[first + i];
-            blo[0] = fmin(blo[0], s.x), bhi[0] = fmax(bhi[0], s.x);
-            blo[1] = fmin(blo[1], s.y), bhi[1] = fmax(bhi[1], s.y);
-            blo[2] = fmin(blo[2], s.z), bhi[2] = fmax(bhi[2], s.z);
+            const double2* ps = reinterpret_cast<const double2*>(a.src + first + i);
+            const double2 xy = __ldg(ps), zm = __ldg(ps + 1);
+            const long long kx = dkey(xy.x), ky = dkey(xy.y), kz = dkey(zm.x);
+            klo[0] = kx < klo[0] ? kx : klo[0], khi[0] = kx > khi[0] ? kx : khi[0];
+            klo[1] = ky < klo[1] ? ky : klo[1], khi[1] = ky > khi[1] ? ky : khi[1];
+            klo[2] = kz < klo[2] ? kz : klo[2], khi[2] = kz > khi[2] ? kz : khi[2];
         }
-        double c[3];
+        double blo[3], bhi[3], c[3];
         BoxF bf;
         bf.B = 0.f;
         bf.A = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            blo[k] = warp_min(blo[k]);
-            bhi[k] = warp_max(bhi[k]);
+            blo[k] = dval(warp_min(klo[k]));
+            bhi[k] = dval(warp_max(khi[k]));
             c[k] = __dmul_rn(__dadd_rn(blo[k], bhi[k]), 0.5);
             bf.c32[k] = __double2float_rn(c[k]);
             bf.cl32[k] = __double2float_rn(__dsub_rn(c[k], (double)bf.c32[k]));
@@ -244,7 +279,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a, otoo_group
         }
         const double theta = a.tpg ? (double)a.tpg[g] : a.theta;
         const bool open_all = !(theta > 0.0);
-        const float invth = open_all ? 0.f : __double2float_rn(1.0 / theta);
+        // 1/theta within 2^-23 (the filter's margins allow 2^-21)
+        const float invth = open_all ? 0.f : __frcp_rn(__double2float_rn(theta));
         int64_t off_c = 0, off_p = 0;
         int32_t want_c = 0, want_p = 0;
         if (kFill) {
@@ -261,26 +297,57 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a, otoo_group
         int32_t ncell = 0, npart = 0;
         int sp = 0;
         if (theta >= 0.0) {
-            if (lane == 0) stk[0] = 0;
+            if (lane == 0) stk[0] = run(0, 1);
             sp = 1;
         }
         __syncwarp();
-        int64_t budget = a.n_cell + 1;  // a tree pops each cell at most once
+        int64_t budget = a.n_cell;  // a tree visits each cell at most once
         bool failed = false;
         while (sp > 0) {
-            int W = sp < 32 ? sp : 32;
-            const int wfit = (kStack - kReserve - sp) / 7;
-            if (W > wfit) W = wfit;
-            if (W < 1) W = (sp + 7 <= kStack) ? 1 : 0;
-            budget -= W;
-            if (W < 1 || budget < 0) {
+            if (sp + 2 > kStack) {
                 failed = true;
                 break;
             }
+            const int wcap = sp + 33 + kMaxLevels <= kStack ? 32 : 1;
+            // the top runs: lane l reads the l-th entry from the top
+            const int nr = sp < 32 ? sp : 32;
+            uint32_t e = 0;
+            int rn = 0;
+            if (lane < nr) {
+                e = stk[sp - 1 - lane];
+                rn = (int)(e >> kRunShift) + 1;
+            }
+            const int rinc = warp_incl_scan(rn, lane);
+            const int rstart = rinc - rn;
+            // runs wholly taken, and a run cut at wcap
+            const bool whole = lane < nr && rinc <= wcap;
+            const bool cut = lane < nr && rstart < wcap && rinc > wcap;
+            const int nwhole = __popc(__ballot_sync(kFull, whole));
+            const unsigned cutm = __ballot_sync(kFull, cut);
+            const int in_whole = __shfl_sync(kFull, rinc, nwhole > 0 ? nwhole - 1 : 0);
+            const int W = cutm ? wcap : (nwhole > 0 ? in_whole : 0);
+            const unsigned starts = __reduce_or_sync(kFull, (whole || cut) ? (1u << rstart) : 0u);
+            // the run that continues after the cut goes back on the stack first
+            sp -= nwhole + (cutm ? 1 : 0);
+            if (cut) {
+                const int taken = wcap - rstart;
+                stk[sp] = run((int)(e & kRunMask) + taken, rn - taken);
+            }
+            sp += cutm ? 1 : 0;
+            budget -= W;
+            if (budget < 0) {
+                failed = true;
+                break;
+            }
+            // lane j < W takes the cell at position j of the taken runs
             int node = -1;
-            if (lane < W) node = stk[sp - 1 - lane];
+            {
+                const int r = __popc(starts & ((2u << lane) - 1u)) - 1;
+                const uint32_t er = __shfl_sync(kFull, e, r < 0 ? 0 : r);
+                const int sr = __shfl_sync(kFull, rstart, r < 0 ? 0 : r);
+                if (lane < W) node = (int)(er & kRunMask) + (lane - sr);
+            }
             __syncwarp();
-            sp -= W;
             int kind = 0;  // 1 accept, 2 leaf, 3 open
             int c0 = 0, nch = 0, pb = 0, pe = 0;
             if (lane < W) {
@@ -320,14 +387,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a, otoo_group
                     if (base + k < want_p) list[off_p + base + k] = pb + k;
             }
             npart += __shfl_sync(kFull, pin, 31);
-            // children of rejected inner cells, first child on top
-            const int nc = kind == 3 ? nch : 0;
-            const int cin = warp_incl_scan(nc, lane);
-            if (nc > 0) {
-                const int base = sp + cin - nc;
-                for (int k = 0; k < nc; ++k) stk[base + k] = c0 + nc - 1 - k;
-            }
-            sp += __shfl_sync(kFull, cin, 31);
+            // one run per rejected inner cell, the lowest lane's on top
+            const unsigned om = __ballot_sync(kFull, kind == 3);
+            const int no = __popc(om);
+            if (kind == 3) stk[sp + no - 1 - __popc(om & lt)] = run(c0, nch);
+            sp += no;
             __syncwarp();
         }
         if (failed && lane == 0) atomicOr(status, kWalkOverflow);
@@ -627,6 +691,7 @@ int check_walk(const otoo_dev_walk* w)
                  OTOO_EINVAL, "walk: NULL device pointer");
     OTOO_REQUIRE(w->n_part >= 1 && w->n_cell >= 1 && w->n_part + w->n_cell <= INT32_MAX, OTOO_EINVAL,
                  "walk: n_part/n_cell out of range");
+    OTOO_REQUIRE(w->n_cell <= (int64_t)kRunMask + 1, OTOO_EINVAL, "walk: more than 2^28 cells");
     OTOO_REQUIRE(w->n_groups >= 1, OTOO_EINVAL, "walk: n_groups < 1");
     OTOO_REQUIRE(w->eps2 > 0.0, OTOO_EINVAL, "walk: eps2 must be > 0");
     OTOO_REQUIRE(w->theta >= 0.0 && w->theta < 1e300, OTOO_EINVAL, "walk: theta must be finite and >= 0");
