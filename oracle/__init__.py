@@ -7,9 +7,11 @@ with the GPU path (the two sides read the same seeded inputs and nothing else).
 * ``direct``      Plummer-softened direct sum, G = 1, j != i (Section II,
                   particle-particle interaction; pair law is a reading, the
                   paper does not print it).
-* ``Tree``        octree, groups, group walk with the opening-angle MAC, and
-                  the force over each group's walk (Sections II, III-B, III-C,
-                  III-D), monopole or quadrupole cells.
+* ``Tree``        octree, groups, group walk with the opening-angle MAC or
+                  the Salmon-Warren absolute MAC (Section II-B, Eq. SW_MAC),
+                  and the force over each group's walk (Sections II, III-B,
+                  III-C, III-D), monopole or quadrupole cells.
+* ``sw_radius``   B_2 (Eq. B2), b_max and r_b (Eq. SW_MAC) of one particle set.
 * ``cell_moments`` / ``cell_field``  the multipole of one particle set and
                   its field at a point.
 * ``errors``      relative force error statistics against a reference.
@@ -65,9 +67,12 @@ def _load():
         lib.oracle_tree_n_groups.restype = _i64
         lib.oracle_tree_n_cells.argtypes = [ctypes.c_void_p]
         lib.oracle_tree_n_cells.restype = _i64
-        lib.oracle_tree_eval.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, ctypes.c_double,
-                                         ctypes.c_int, _i64, _dp, _dp, _lp, _lp, _lp, _lp, _dp, _lp]
+        lib.oracle_tree_eval.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _i64, _dp, _dp, _lp,
+                                         _lp, _lp, _lp, _dp, _lp]
         lib.oracle_tree_eval.restype = ctypes.c_int
+        lib.oracle_sw_radius.argtypes = [_dp, _dp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
+        lib.oracle_sw_radius.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -110,6 +115,18 @@ def cell_moments(pos, mass):
     return float(m[0]), com, q
 
 
+def sw_radius(pos, mass, delta, m_limit=0.0, s_root=1.0):
+    """(B_2, b_max, r_b) of one particle set for the absolute MAC."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    out = np.zeros(3)
+    if lib.oracle_sw_radius(_d(pos), _d(mass), pos.shape[0], float(delta), float(m_limit), float(s_root),
+                            _d(out)) != 0:
+        raise ValueError("empty cell")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
 def cell_field(x, m, com, q, use_quad, eps):
     """Field (acc[3], pot) at point x of a cell with the given moments."""
     lib = _load()
@@ -142,9 +159,12 @@ class Tree:
             self._lib.oracle_tree_free(h)
             self._h = None
 
-    def eval(self, theta, eps, use_quad=False, theta_by_key=None, group_stride=1):
-        """Tree force.  Returns dict with acc, pot (caller order; NaN for
-        particles of skipped groups) and per-group statistics."""
+    def eval(self, theta, eps, use_quad=False, theta_by_key=None, group_stride=1, mac="theta", delta=0.0,
+             m_limit=0.0):
+        """Tree force.  mac = "theta" (opening angle theta, or theta_by_key)
+        or "sw" (absolute MAC with accuracy delta; cells heavier than m_limit
+        > 0 are never accepted).  Returns dict with acc, pot (caller order;
+        NaN for particles of skipped groups) and per-group statistics."""
         ng = self.n_groups
         acc = np.full((self.n, 3), np.nan)
         pot = np.full(self.n, np.nan)
@@ -158,8 +178,9 @@ class Tree:
         if theta_by_key is not None:
             tbk = np.ascontiguousarray(theta_by_key, dtype=np.float64)
             assert tbk.shape[0] == self.n
+        kind = {"theta": 0, "sw": 1}[mac]
         rc = self._lib.oracle_tree_eval(self._h, float(theta), _d(tbk) if tbk is not None else None,
-                                        float(eps), int(bool(use_quad)), int(group_stride),
+                                        kind, float(delta), float(m_limit), float(eps), int(bool(use_quad)), int(group_stride),
                                         _d(acc), _d(pot), _l(key), _l(cnt), _l(ncell), _l(npart),
                                         _d(gmass), _l(inter))
         if rc != 0:

@@ -21,8 +21,13 @@
  *   oracle_tree_*      pointer-free recursive octree on a 2^21 grid per axis,
  *                      leaves of at most leaf_size particles, groups = maximal
  *                      cells with at most n_crit particles, one shared walk per
- *                      group with the opening-angle group MAC, forces summed
- *                      over the walk's cell and particle entries.
+ *                      group with a group MAC -- the opening angle, or the
+ *                      Salmon-Warren absolute MAC of Section II-B (Eq. SW_MAC
+ *                      with B_2 of Eq. B2 and the m_limit rule of Section
+ *                      III-C) -- forces summed over the walk's cell and
+ *                      particle entries.
+ *   oracle_sw_radius   B_2, b_max and the bounding radius r_b of one particle
+ *                      set (Eq. B2, Eq. SW_MAC).
  *
  * Everything is written for a reader to check by eye: no blocking, no fusion,
  * summation in plain loops.  Compile with -ffp-contract=off so that no FMA
@@ -155,6 +160,58 @@ static void cell_field(const double x[3], double m, const double com[3], const d
     *pot -= 0.5 * rQr * rinv5;
 }
 
+/*
+ * Spread of a particle set about its centre of mass com (Section II-B):
+ * B_2 = sum m |com - x|^2 (Eq. B2, the trace of the second moment) and
+ * b_max = max |com - x|.
+ */
+static void spread(const double* pos, const double* mass, const int64_t* idx, int64_t n, const double com[3],
+                   double* b2_out, double* bmax_out)
+{
+    double b2 = 0.0, dmax2 = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t i = idx[k];
+        double dx = com[0] - pos[3 * i], dy = com[1] - pos[3 * i + 1], dz = com[2] - pos[3 * i + 2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        b2 += mass[i] * d2;
+        if (d2 > dmax2) dmax2 = d2;
+    }
+    *b2_out = b2;
+    *bmax_out = sqrt(dmax2);
+}
+
+/*
+ * Bounding radius of the absolute MAC (Eq. SW_MAC): the distance d at which
+ * the monopole error bound 3 B_2 / (d^2 (d - b_max)^2) equals the accuracy
+ * parameter delta (an acceleration),
+ *     r_b = b_max / 2 + sqrt(b_max^2 / 4 + sqrt(3 B_2 / delta)).
+ * A cell heavier than m_limit (> 0) gets r_b = 2 S_root, so that it is never
+ * accepted (Section III-C).  delta <= 0 accepts nothing (r_b infinite).
+ */
+static double sw_radius(double b2, double bmax, double m, double delta, double m_limit, double s_root)
+{
+    if (m_limit > 0.0 && m > m_limit) return 2.0 * s_root;
+    if (!(delta > 0.0)) return INFINITY;
+    double h = 0.5 * bmax;
+    return h + sqrt(h * h + sqrt(3.0 * b2 / delta));
+}
+
+/* Exposed for the tests: B_2, b_max and r_b of the particle set (out[0..2]). */
+int oracle_sw_radius(const double* pos, const double* mass, int64_t n, double delta, double m_limit,
+                     double s_root, double* out)
+{
+    if (n <= 0) return -1;
+    int64_t* idx = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    if (!idx) return -2;
+    for (int64_t k = 0; k < n; ++k) idx[k] = k;
+    double m, com[3], q[6];
+    moments(pos, mass, idx, n, &m, com, q);
+    spread(pos, mass, idx, n, com, &out[0], &out[1]);
+    free(idx);
+    out[2] = sw_radius(out[0], out[1], m, delta, m_limit, s_root);
+    return 0;
+}
+
 /* Exposed for the tests: moments of a particle set and the field they make. */
 int oracle_cell_moments(const double* pos, const double* mass, int64_t n,
                         double* m_out, double* com, double* q)
@@ -192,6 +249,7 @@ typedef struct Node {
     int n_child;
     struct Node* child[8];     /* children in octant order, NULL where empty */
     double m, com[3], q[6];
+    double b2, bmax;           /* spread about the centre of mass (Eq. B2) */
     double cube_lo[3], side, gc[3];   /* geometry for the MAC */
 } Node;
 
@@ -243,6 +301,7 @@ static Node* build_node(OracleTree* t, int level, const int64_t org[3], int64_t 
     c->end = end;
     set_geometry(t, c);
     moments(t->pos, t->mass, t->idx + begin, end - begin, &c->m, c->com, c->q);
+    spread(t->pos, t->mass, t->idx + begin, end - begin, c->com, &c->b2, &c->bmax);
     int64_t count = end - begin;
     if (count <= t->leaf_size || level == ORACLE_LEVELS) return c;
 
@@ -405,13 +464,35 @@ void* oracle_tree_new(int64_t n, const double* pos, const double* mass, int leaf
 int64_t oracle_tree_n_groups(const void* handle) { return ((const OracleTree*)handle)->n_groups; }
 int64_t oracle_tree_n_cells(const void* handle) { return ((const OracleTree*)handle)->n_cells; }
 
+/* Acceptance rule of a walk: kind 0 = opening angle theta, kind 1 = the
+   Salmon-Warren absolute MAC with accuracy delta and the m_limit rule. */
+typedef struct Mac {
+    int kind;
+    double theta;
+    double delta, m_limit, s_root;
+} Mac;
+
 /* The group MAC (Barnes 1990 vectorised walk, Section III-D; notation of
-   Section II-B): accept cell c for the group box [blo, bhi] iff the cube
-   does not overlap the box and d_min > l / theta + s, where d_min is the
-   distance from the cell's centre of mass to the box and s the distance from
-   the centre of mass to the cube's geometric centre. */
-static int accept(const Node* c, const double blo[3], const double bhi[3], double theta)
+   Section II-B), with d_min the distance from the cell's centre of mass to
+   the group box [blo, bhi]:
+   kind 0: accept cell c iff the cube does not overlap the box and
+           d_min > l / theta + s (s: distance from the centre of mass to the
+           cube's geometric centre);
+   kind 1: accept iff d_min > r_b (Eq. SW_MAC).  No particle of the group
+           can lie in such a cell: r_b >= b_max. */
+static int accept(const Node* c, const double blo[3], const double bhi[3], const Mac* mac)
 {
+    if (mac->kind == 1) {
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double d = 0.0;
+            if (blo[a] - c->com[a] > d) d = blo[a] - c->com[a];
+            if (c->com[a] - bhi[a] > d) d = c->com[a] - bhi[a];
+            d2 += d * d;
+        }
+        return sqrt(d2) > sw_radius(c->b2, c->bmax, c->m, mac->delta, mac->m_limit, mac->s_root);
+    }
+    double theta = mac->theta;
     if (!(theta > 0.0)) return 0;
     int overlap = 1;
     for (int a = 0; a < 3; ++a) {
@@ -467,25 +548,27 @@ static int push_part(Entries* e, int64_t i)
    cell becomes one cell entry; a rejected cell opens into its children; a
    rejected leaf contributes each of its particles. */
 static int walk(const OracleTree* t, const Node* c, const double blo[3], const double bhi[3],
-                double theta, Entries* e)
+                const Mac* mac, Entries* e)
 {
-    if (accept(c, blo, bhi, theta)) return push_cell(e, c);
+    if (accept(c, blo, bhi, mac)) return push_cell(e, c);
     if (c->n_child == 0) {
         for (int64_t k = c->begin; k < c->end; ++k)
             if (push_part(e, t->idx[k])) return -1;
         return 0;
     }
     for (int k = 0; k < c->n_child; ++k)
-        if (walk(t, c->child[k], blo, bhi, theta, e)) return -1;
+        if (walk(t, c->child[k], blo, bhi, mac, e)) return -1;
     return 0;
 }
 
 /*
  * Evaluate the tree force.  For each group (every group_stride-th one, in the
- * tree's own order) walk the tree with the group's opening angle and sum the
- * pair law over particle entries (j != i) and the cell field over cell
- * entries.  theta_by_key, if not NULL, gives the group's opening angle at the
- * index of its lowest-numbered particle (length n); otherwise theta is used.
+ * tree's own order) walk the tree with the group MAC and sum the pair law
+ * over particle entries (j != i) and the cell field over cell entries.
+ * mac_kind 0: opening angle; theta_by_key, if not NULL, gives the group's
+ * angle at the index of its lowest-numbered particle (length n), otherwise
+ * theta is used.  mac_kind 1: the absolute MAC with accuracy delta and mass
+ * limit m_limit (<= 0: none); theta and theta_by_key are not used.
  * Outputs in the caller's particle order: acc [n][3], pot [n]; entries of
  * particles in skipped groups are left untouched.
  * Per-group statistics (arrays of length n_groups, any may be NULL):
@@ -494,13 +577,13 @@ static int walk(const OracleTree* t, const Node* c, const double blo[3], const d
  *   g_mass   mass of all entries (equals the total mass when the walk is complete).
  * *interactions receives sum over evaluated groups of count * (ncell + npart).
  */
-int oracle_tree_eval(const void* handle, double theta, const double* theta_by_key, double eps,
-                     int use_quad, int64_t group_stride, double* acc, double* pot,
+int oracle_tree_eval(const void* handle, double theta, const double* theta_by_key, int mac_kind, double delta,
+                     double m_limit, double eps, int use_quad, int64_t group_stride, double* acc, double* pot,
                      int64_t* g_key, int64_t* g_count, int64_t* g_ncell, int64_t* g_npart,
                      double* g_mass, int64_t* interactions)
 {
     const OracleTree* t = (const OracleTree*)handle;
-    if (!t || !(eps > 0.0) || group_stride < 1) return -1;
+    if (!t || !(eps > 0.0) || group_stride < 1 || mac_kind < 0 || mac_kind > 1) return -1;
     double eps2 = eps * eps;
     int64_t total = 0;
     int err = 0;
@@ -519,10 +602,15 @@ int oracle_tree_eval(const void* handle, double theta, const double* theta_by_ke
                 if (t->pos[3 * i + a] > bhi[a]) bhi[a] = t->pos[3 * i + a];
             }
         }
-        double th = theta_by_key ? theta_by_key[key] : theta;
+        Mac mac;
+        mac.kind = mac_kind;
+        mac.theta = theta_by_key ? theta_by_key[key] : theta;
+        mac.delta = delta;
+        mac.m_limit = m_limit;
+        mac.s_root = t->S;
         Entries ent;
         memset(&ent, 0, sizeof(ent));
-        if (walk(t, t->root, blo, bhi, th, &ent)) {
+        if (walk(t, t->root, blo, bhi, &mac, &ent)) {
             err |= 1;
             free((void*)ent.cell);
             free(ent.part);

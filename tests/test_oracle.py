@@ -193,6 +193,97 @@ def test_tree_per_group_theta():
 # ---------------------------------------------------------------------------
 # perceptron oracle
 
+# ---- Salmon-Warren absolute MAC (Section II-B, Eq. SW_MAC, Eq. B2) ----------
+
+
+@pytest.mark.parametrize("m,L,delta", [(1.0, 1.0, 0.01), (0.3, 2.0, 1e-4), (2.0, 0.5, 10.0), (1.0, 1.0, 1e-8)])
+def test_sw_radius_two_particle_example(m, L, delta):
+    """The paper's worked example: two particles of mass m a distance L apart
+    have b_max = L/2 and B_2 = m L^2 / 2, so r_b = L/4 + sqrt(L^2/16 +
+    sqrt(3 m L^2 / (2 delta))) (the printed sqrt(L/16) read as sqrt(L^2/16),
+    which Eq. SW_MAC gives for b_max = L/2)."""
+    pos = np.array([[0.1, -0.2, 0.3], [0.1 + L, -0.2, 0.3]])
+    b2, bmax, rb = oracle.sw_radius(pos, np.array([m, m]), delta)
+    assert b2 == pytest.approx(m * L * L / 2, rel=1e-14)
+    assert bmax == pytest.approx(L / 2, rel=1e-14)
+    assert rb == pytest.approx(L / 4 + math.sqrt(L * L / 16 + math.sqrt(3 * m * L * L / (2 * delta))), rel=1e-14)
+
+
+def test_sw_radius_limits_and_mass_limit():
+    rng = np.random.default_rng(5)
+    pos = rng.normal(size=(40, 3))
+    mass = rng.uniform(0.5, 1.5, 40)
+    b2, bmax, rb_big = oracle.sw_radius(pos, mass, 1e30)
+    # large delta: r_b -> b_max (the b_max MAC); small delta: r_b ~ delta^(-1/4)
+    assert rb_big == pytest.approx(bmax, rel=1e-6)
+    r1 = oracle.sw_radius(pos, mass, 1e-16)[2]
+    r2 = oracle.sw_radius(pos, mass, 1e-16 / 16)[2]
+    assert r2 / r1 == pytest.approx(2.0, rel=1e-3)
+    # parallel-axis identity: B_2 = sum m |x|^2 - M |x_cm|^2
+    M = mass.sum()
+    xcm = (mass[:, None] * pos).sum(0) / M
+    assert b2 == pytest.approx((mass * (pos ** 2).sum(1)).sum() - M * (xcm ** 2).sum(), rel=1e-12)
+    # a cell heavier than m_limit gets r_b = 2 S_root
+    assert oracle.sw_radius(pos, mass, 1e-3, m_limit=0.5 * M, s_root=7.0)[2] == 14.0
+    assert oracle.sw_radius(pos, mass, 1e-3, m_limit=2.0 * M, s_root=7.0)[2] == oracle.sw_radius(pos, mass, 1e-3)[2]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_sw_monopole_error_within_delta(seed):
+    """r_b is where the monopole error bound 3 B_2 / (d^2 (d - b_max)^2)
+    equals delta: every point farther than r_b from the centre of mass sees
+    the monopole within delta of the exact (unsoftened) acceleration."""
+    rng = np.random.default_rng(seed)
+    n = 30 if seed < 3 else 2
+    pos = rng.uniform(-0.5, 0.5, size=(n, 3)) * (1.0 if seed < 3 else np.array([1.0, 0.0, 0.0]))
+    mass = rng.uniform(0.1, 1.0, n)
+    m, com, q = oracle.cell_moments(pos, mass)
+    worst = 0.0
+    for delta in (1e-1, 1e-3, 1e-5):
+        b2, bmax, rb = oracle.sw_radius(pos, mass, delta)
+        dirs = rng.normal(size=(200, 3))
+        dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+        if seed == 3:
+            dirs[:20] = [1.0, 0.0, 0.0]   # on the axis of the pair: the tight direction
+        d = rb * (1.0 + 1e-9 + rng.uniform(0, 1, 200) ** 2)
+        tgt = com + dirs * d[:, None]
+        allp = np.vstack([pos, tgt])
+        allm = np.concatenate([mass, np.zeros(len(tgt))])
+        ad, _ = oracle.direct(allp, allm, 1e-12, targets=np.arange(n, n + len(tgt)))
+        for k in range(len(tgt)):
+            am, _ = oracle.cell_field(tgt[k], m, com, q, False, 1e-12)
+            err = np.linalg.norm(am - ad[k])
+            assert err <= delta * (1 + 1e-9), (delta, k, err)
+            worst = max(worst, err / delta)
+    # the bound is not vacuous: nearly reached on the axis of a pair
+    assert worst > (0.5 if seed == 3 else 0.05)
+
+
+def test_sw_tree_error_bound_and_cost():
+    """Monopole tree with the absolute MAC: each accepted cell errs by at most
+    delta, so a particle's error is at most delta times its group's cell
+    entries; the cost grows and the error falls as delta shrinks; a mass
+    limit below every cell's mass accepts nothing (the direct sum)."""
+    pos, mass = ic.plummer(3000, 31)
+    mass = mass.astype(np.float64)
+    ad, _ = oracle.direct(pos, mass, 1e-9)
+    t = oracle.Tree(pos, mass, 8, 32)
+    inter, rms = [], []
+    for delta in (1e-2, 1e-3, 1e-4):
+        r = t.eval(0.0, 1e-9, use_quad=False, mac="sw", delta=delta)
+        err = np.linalg.norm(r["acc"] - ad, axis=1)
+        assert np.all(err <= delta * r["n_cell"].max() * (1 + 1e-9))
+        inter.append(r["interactions"])
+        rms.append(float(np.sqrt(np.mean((err / np.linalg.norm(ad, axis=1)) ** 2))))
+        assert r["n_cell"].sum() > 0
+    assert inter[0] < inter[1] < inter[2]
+    assert rms[0] > rms[1] > rms[2]
+    r = t.eval(0.0, 0.01, use_quad=True, mac="sw", delta=1e-3, m_limit=0.5 * mass.min())
+    assert np.all(r["n_cell"] == 0) and r["interactions"] == 3000 * 3000
+    a2, p2 = oracle.direct(pos, mass, 0.01)
+    np.testing.assert_allclose(r["acc"], a2, rtol=1e-10, atol=1e-12)
+
+
 from oracle import mlp as omlp  # noqa: E402
 
 
