@@ -53,16 +53,24 @@ extern "C" {
 #define OTOO_FP64  1      /* every pair in FP64 (comparison form) */
 
 /* ---- parameters ----------------------------------------------------------- */
+/* acceptance rule of the walk (otoo_params.mac) */
+#define OTOO_MAC_THETA 0  /* opening angle theta (group MAC of Barnes 1990, Section III-D) */
+#define OTOO_MAC_SW    1  /* Salmon-Warren absolute MAC, Section II-B Eq. SW_MAC */
+
 typedef struct otoo_params {
     double theta;                  /* opening angle; 0 = open every cell (direct sum) */
     int32_t leaf_size;             /* max particles per tree leaf (>= 1) */
     int32_t n_crit;                /* max particles per group (>= 1, <= 1024) */
     int32_t use_quad;              /* 1 = cells carry a quadrupole */
-    int32_t pad;
+    int32_t mac;                   /* OTOO_MAC_THETA or OTOO_MAC_SW */
     double eps;                    /* Plummer softening length (> 0) */
     const float* theta_per_group;  /* host, NULL = fixed theta; else one angle per group
                                       in the group order of a previous call on the
-                                      same tree with the same n_crit */
+                                      same tree with the same n_crit (OTOO_MAC_THETA only) */
+    double delta;                  /* OTOO_MAC_SW: accuracy parameter (an acceleration,
+                                      G = 1); 0 = accept no cell */
+    double m_limit;                /* OTOO_MAC_SW: cells heavier than this are never
+                                      accepted (Section III-C); <= 0 = no limit */
 } otoo_params;
 
 typedef struct otoo_tune {
@@ -186,12 +194,17 @@ int otoo_build_tree(const double* pos, const float* mass, int64_t n,
 
 /* Groups and lists (Section III-D, the vectorised walk of Barnes 1990 done on
    the host): groups are the maximal cells with at most n_crit particles; each
-   group walks the tree once and accepts cell c when c's cube does not overlap
-   the group's box and d_min > l_c / theta + s_c (d_min: distance from c's
-   centre of mass to the box, l_c: cube side, s_c: distance from the centre of
-   mass to the cube centre).  Rejected leaves contribute their particles.
-   params->theta_per_group, when set, overrides theta group by group.
-   Errors: OTOO_EINVAL (eps <= 0, n_crit < 1 or > 1024, theta < 0), OTOO_ENOMEM. */
+   group walks the tree once.  With OTOO_MAC_THETA it accepts cell c when c's
+   cube does not overlap the group's box and d_min > l_c / theta + s_c (d_min:
+   distance from c's centre of mass to the box, l_c: cube side, s_c: distance
+   from the centre of mass to the cube centre); params->theta_per_group, when
+   set, overrides theta group by group.  With OTOO_MAC_SW it accepts c when
+   d_min > r_b = b_max / 2 + sqrt(b_max^2 / 4 + sqrt(3 B_2 / delta)) (Eq.
+   SW_MAC; B_2 = sum m |x - com|^2, Eq. B2; b_max = max |x - com|), with r_b
+   = 2 S_root for cells heavier than m_limit (S_root: root cube side), and
+   the group records carry theta = 0.  Rejected leaves contribute their
+   particles.  Errors: OTOO_EINVAL (eps <= 0, n_crit < 1 or > 1024, theta < 0,
+   unknown mac, delta < 0 or not finite), OTOO_ENOMEM. */
 int otoo_make_groups_and_lists(const otoo_tree* tree, const otoo_params* params,
                                otoo_lists** out);
 
@@ -227,6 +240,8 @@ typedef struct otoo_tree_view {
     const double* cell_com;        /* [n_cell][3] */
     const double* cell_mass;       /* [n_cell] */
     const double* cell_quad;       /* [n_cell][6] Qxx Qyy Qzz Qxy Qxz Qyz */
+    const double* cell_b2;         /* [n_cell] B_2 = sum m |x - com|^2 (Eq. B2) */
+    const double* cell_bmax;       /* [n_cell] b_max = max |x - com| */
 } otoo_tree_view;
 
 int otoo_tree_export(const otoo_tree* tree, otoo_tree_view* view);

@@ -32,9 +32,13 @@ class OtooError(RuntimeError):
         self.code = code
 
 
+OTOO_MAC_THETA = 0
+OTOO_MAC_SW = 1
+
+
 class Params(ctypes.Structure):
-    _fields_ = [("theta", f64), ("leaf_size", i32), ("n_crit", i32), ("use_quad", i32), ("pad", i32),
-                ("eps", f64), ("theta_per_group", ctypes.POINTER(f32))]
+    _fields_ = [("theta", f64), ("leaf_size", i32), ("n_crit", i32), ("use_quad", i32), ("mac", i32),
+                ("eps", f64), ("theta_per_group", ctypes.POINTER(f32)), ("delta", f64), ("m_limit", f64)]
 
 
 class Tune(ctypes.Structure):
@@ -89,7 +93,8 @@ class TreeView(ctypes.Structure):
     _fields_ = [("n_part", i64), ("n_cell", i64), ("depth", i32), ("leaf_size", i32),
                 ("root_lo", f64 * 3), ("root_side", f64), ("pos", vp), ("mass", vp), ("perm", vp),
                 ("cell_begin", vp), ("cell_end", vp), ("cell_level", vp), ("cell_nchild", vp),
-                ("cell_child0", vp), ("cell_org", vp), ("cell_com", vp), ("cell_mass", vp), ("cell_quad", vp)]
+                ("cell_child0", vp), ("cell_org", vp), ("cell_com", vp), ("cell_mass", vp), ("cell_quad", vp),
+                ("cell_b2", vp), ("cell_bmax", vp)]
 
 
 class WCell(ctypes.Structure):

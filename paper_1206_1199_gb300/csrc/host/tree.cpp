@@ -99,6 +99,7 @@ struct otoo_tree {
     std::vector<int64_t> c_begin, c_end, c_child0, c_org;
     std::vector<int32_t> c_level, c_nchild;
     std::vector<double> c_com, c_mass, c_quad;     // [3], [1], [6]
+    std::vector<double> c_b2, c_bmax;               // spread about the centre of mass (Eq. B2)
     std::vector<double> c_lo, c_side, c_gc;         // cube lower corner [3], side, centre [3]
 };
 
@@ -138,7 +139,9 @@ int guarded(F&& f)
 
 // Cell moments by direct summation over the cell's particle range (the
 // "direct summation for each cell" variant of Section III-C; it parallelises
-// over cells): mass, centre of mass, traceless quadrupole about it.
+// over cells): mass, centre of mass, traceless quadrupole about it, and the
+// spread the absolute MAC needs: B_2 = sum m |com - x|^2 (Eq. B2) and
+// b_max = max |com - x|.
 void cell_moments(otoo_tree* t, int64_t c)
 {
     const int64_t b = t->c_begin[c], e = t->c_end[c];
@@ -152,10 +155,13 @@ void cell_moments(otoo_tree* t, int64_t c)
     }
     const double cx = sx / m, cy = sy / m, cz = sz / m;
     double q[6] = {0, 0, 0, 0, 0, 0};
+    double b2 = 0, dmax2 = 0;
     for (int64_t i = b; i < e; ++i) {
         const double mi = t->mass[i];
         const double dx = t->pos[3 * i] - cx, dy = t->pos[3 * i + 1] - cy, dz = t->pos[3 * i + 2] - cz;
         const double d2 = dx * dx + dy * dy + dz * dz;
+        b2 += mi * d2;
+        dmax2 = std::max(dmax2, d2);
         q[0] += mi * (3 * dx * dx - d2);
         q[1] += mi * (3 * dy * dy - d2);
         q[2] += mi * (3 * dz * dz - d2);
@@ -168,6 +174,8 @@ void cell_moments(otoo_tree* t, int64_t c)
     t->c_com[3 * c + 1] = cy;
     t->c_com[3 * c + 2] = cz;
     for (int k = 0; k < 6; ++k) t->c_quad[6 * c + k] = q[k];
+    t->c_b2[c] = b2;
+    t->c_bmax[c] = std::sqrt(dmax2);
     // cube geometry on the grid: side h 2^(21-L), lower corner lo + org h
     const double side = t->h * (double)((int64_t)1 << (kLevels - t->c_level[c]));
     t->c_side[c] = side;
@@ -223,6 +231,8 @@ void build_cells(otoo_tree* t)
     t->c_com.resize(3 * nc);
     t->c_mass.resize(nc);
     t->c_quad.resize(6 * nc);
+    t->c_b2.resize(nc);
+    t->c_bmax.resize(nc);
     t->c_lo.resize(3 * nc);
     t->c_side.resize(nc);
     t->c_gc.resize(3 * nc);
@@ -355,6 +365,8 @@ int otoo_tree_export(const otoo_tree* t, otoo_tree_view* v)
     v->cell_com = t->c_com.data();
     v->cell_mass = t->c_mass.data();
     v->cell_quad = t->c_quad.data();
+    v->cell_b2 = t->c_b2.data();
+    v->cell_bmax = t->c_bmax.data();
     return OTOO_OK;
 }
 
@@ -412,6 +424,31 @@ inline bool mac_accept(const otoo_tree* t, int64_t c, const double blo[3], const
     return std::sqrt(d2) > side / theta + std::sqrt(s2);
 }
 
+// Bounding radius of the absolute MAC (Eq. SW_MAC): where the monopole error
+// bound 3 B_2 / (d^2 (d - b_max)^2) equals delta; 2 S_root for cells heavier
+// than m_limit (never accepted, Section III-C); infinite for delta = 0.
+double sw_radius(double b2, double bmax, double m, double delta, double m_limit, double s_root)
+{
+    if (m_limit > 0.0 && m > m_limit) return 2.0 * s_root;
+    if (!(delta > 0.0)) return HUGE_VAL;
+    const double h = 0.5 * bmax;
+    return h + std::sqrt(h * h + std::sqrt(3.0 * b2 / delta));
+}
+
+// Absolute MAC for the box [blo, bhi]: d_min (centre of mass to the box) > r_b.
+inline bool sw_accept(const otoo_tree* t, int64_t c, const double blo[3], const double bhi[3], double rb)
+{
+    const double* com = &t->c_com[3 * c];
+    double d2 = 0;
+    for (int a = 0; a < 3; ++a) {
+        double d = 0;
+        if (blo[a] - com[a] > d) d = blo[a] - com[a];
+        if (com[a] - bhi[a] > d) d = com[a] - bhi[a];
+        d2 += d * d;
+    }
+    return std::sqrt(d2) > rb;
+}
+
 // Sources of the force step: particles in tree order, then cells (centre of
 // mass, mass) and their quadrupoles (zeros for monopole cells).
 void fill_sources(const otoo_tree* t, int use_quad, otoo_src* src, otoo_quad* quad)
@@ -466,6 +503,9 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
     OTOO_REQUIRE(p->eps > 0.0 && std::isfinite(p->eps), OTOO_EINVAL, "eps must be > 0");
     OTOO_REQUIRE(p->n_crit >= 1 && p->n_crit <= kMaxGroup, OTOO_EINVAL, "n_crit out of [1, %d]", kMaxGroup);
     OTOO_REQUIRE(p->theta >= 0.0 && std::isfinite(p->theta), OTOO_EINVAL, "theta must be finite and >= 0");
+    OTOO_REQUIRE(p->mac == OTOO_MAC_THETA || p->mac == OTOO_MAC_SW, OTOO_EINVAL, "unknown mac %d", p->mac);
+    OTOO_REQUIRE(p->mac != OTOO_MAC_SW || (p->delta >= 0.0 && std::isfinite(p->delta) && std::isfinite(p->m_limit)),
+                 OTOO_EINVAL, "delta must be finite and >= 0, m_limit finite");
     OTOO_REQUIRE(t->n <= INT32_MAX / 2, OTOO_EINVAL, "too many particles for 32-bit list indices");
     return guarded([&]() -> int {
         std::vector<GroupRange> gr;
@@ -484,6 +524,14 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
         L->use_quad = p->use_quad ? 1 : 0;
         L->eps = p->eps;
         L->groups.resize(G);
+        const bool sw = p->mac == OTOO_MAC_SW;
+        std::vector<double> rb;
+        if (sw) {
+            rb.resize(nc);
+#pragma omp parallel for schedule(static)
+            for (int64_t c = 0; c < nc; ++c)
+                rb[c] = sw_radius(t->c_b2[c], t->c_bmax[c], t->c_mass[c], p->delta, p->m_limit, t->S);
+        }
         // the walk: one shared list per group (Barnes 1990, Section III-D),
         // entries buffered per thread, then placed in group order
         const int nthr = omp_get_max_threads();
@@ -505,7 +553,7 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
                         blo[a] = std::min(blo[a], t->pos[3 * i + a]);
                         bhi[a] = std::max(bhi[a], t->pos[3 * i + a]);
                     }
-                const double theta = p->theta_per_group ? (double)p->theta_per_group[g] : p->theta;
+                const double theta = sw ? 0.0 : p->theta_per_group ? (double)p->theta_per_group[g] : p->theta;
                 const int64_t start = (int64_t)buf.size();
                 parts.clear();
                 stack.clear();
@@ -514,7 +562,7 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
                 while (!stack.empty()) {
                     const int64_t c = stack.back();
                     stack.pop_back();
-                    if (mac_accept(t, c, blo, bhi, theta)) {
+                    if (sw ? sw_accept(t, c, blo, bhi, rb[c]) : mac_accept(t, c, blo, bhi, theta)) {
                         buf.push_back((int32_t)(n + c));
                         ++ncell;
                     } else if (t->c_nchild[c] == 0) {

@@ -13,13 +13,16 @@ import numpy as np
 from . import _lib as L
 
 
-def _params(theta, leaf_size, n_crit, use_quad, eps, theta_per_group=None):
+def _params(theta, leaf_size, n_crit, use_quad, eps, theta_per_group=None, mac="theta", delta=0.0, m_limit=0.0):
     p = L.Params()
     p.theta = float(theta)
     p.leaf_size = int(leaf_size)
     p.n_crit = int(n_crit)
     p.use_quad = int(bool(use_quad))
+    p.mac = {"theta": L.OTOO_MAC_THETA, "sw": L.OTOO_MAC_SW}[mac]
     p.eps = float(eps)
+    p.delta = float(delta)
+    p.m_limit = float(m_limit)
     if theta_per_group is not None:
         p.theta_per_group = theta_per_group.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     return p
@@ -54,10 +57,14 @@ class Tree:
                     end=L.view(v.cell_end, np.int64, (nc,)), level=L.view(v.cell_level, np.int32, (nc,)),
                     nchild=L.view(v.cell_nchild, np.int32, (nc,)), child0=L.view(v.cell_child0, np.int64, (nc,)),
                     org=L.view(v.cell_org, np.int64, (nc, 3)), com=L.view(v.cell_com, np.float64, (nc, 3)),
-                    cmass=L.view(v.cell_mass, np.float64, (nc,)), quad=L.view(v.cell_quad, np.float64, (nc, 6)))
+                    cmass=L.view(v.cell_mass, np.float64, (nc,)), quad=L.view(v.cell_quad, np.float64, (nc, 6)),
+                    b2=L.view(v.cell_b2, np.float64, (nc,)), bmax=L.view(v.cell_bmax, np.float64, (nc,)),
+                    tree=self)  # the views borrow the tree's memory: keep it alive
 
-    def lists(self, theta, n_crit, eps, use_quad=True, theta_per_group=None):
-        return Lists.make(self, theta, n_crit, eps, use_quad, theta_per_group)
+    def lists(self, theta, n_crit, eps, use_quad=True, theta_per_group=None, mac="theta", delta=0.0, m_limit=0.0):
+        """Groups and lists; mac = "theta" (opening angle) or "sw" (absolute
+        MAC with accuracy delta and mass limit m_limit)."""
+        return Lists.make(self, theta, n_crit, eps, use_quad, theta_per_group, mac, delta, m_limit)
 
 
 class Lists:
@@ -74,11 +81,12 @@ class Lists:
         self.interactions, self.cell_interactions = v.interactions, v.cell_interactions
 
     @classmethod
-    def make(cls, tree, theta, n_crit, eps, use_quad=True, theta_per_group=None):
+    def make(cls, tree, theta, n_crit, eps, use_quad=True, theta_per_group=None, mac="theta", delta=0.0,
+             m_limit=0.0):
         tpg = None
         if theta_per_group is not None:
             tpg = np.ascontiguousarray(theta_per_group, dtype=np.float32)
-        p = _params(theta, tree.leaf_size, n_crit, use_quad, eps, tpg)
+        p = _params(theta, tree.leaf_size, n_crit, use_quad, eps, tpg, mac, delta, m_limit)
         h = ctypes.c_void_p()
         L.call("otoo_make_groups_and_lists", tree._h, ctypes.byref(p), ctypes.byref(h))
         return cls(h, keep=(tree,))

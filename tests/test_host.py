@@ -85,11 +85,26 @@ def test_tree_invariants(model, n, leaf):
             assert np.all(lev[kids] == lev[c] + 1)
 
 
+def test_cell_spread_matches_oracle():
+    # B_2 (Eq. B2) and b_max of every cell against the oracle's own sum over
+    # the cell's particles
+    pos, mass = ic.hernquist(6000, 33)
+    t = S.Tree(pos, mass, 8)
+    e = t.export()
+    for c in range(0, e["n_cell"], 7):
+        p = e["pos"][e["begin"][c]:e["end"][c]]
+        m = e["mass"][e["begin"][c]:e["end"][c]].astype(np.float64)
+        b2, bmax, _ = oracle.sw_radius(p, m, 1.0)
+        assert e["b2"][c] == pytest.approx(b2, rel=1e-12, abs=1e-300)
+        assert e["bmax"][c] == pytest.approx(bmax, rel=1e-12, abs=1e-300)
+
+
 def test_hilbert_order_is_spatially_local():
     # consecutive particles in tree order are close (Hilbert keys): the mean
     # step is far below that of a random order
     pos, mass = ic.uniform_sphere(20000, 22)
-    e = S.Tree(pos, mass, 8).export()
+    t = S.Tree(pos, mass, 8)
+    e = t.export()
     step = np.linalg.norm(np.diff(e["pos"], axis=0), axis=1).mean()
     rnd = np.linalg.norm(np.diff(pos, axis=0), axis=1).mean()
     assert step < 0.1 * rnd
@@ -147,6 +162,31 @@ def test_walk_decisions_match_oracle(model, n, theta, ncrit, leaf):
     # an accept/open decision may flip only at an exact FP64 tie (none expected here)
     assert len(diff) == 0, diff[:5]
     assert lists.interactions == r["interactions"] * 0 + sum(c * (nc + npt) for c, nc, npt in mine.values())
+
+
+@pytest.mark.parametrize("model,n,delta,m_limit,ncrit", [("plummer", 8000, 1e-2, 0.05, 64),
+                                                        ("plummer", 8000, 1e-4, 0.0, 32),
+                                                        ("hernquist", 20000, 1e-3, 0.02, 128),
+                                                        ("uniform", 6000, 3e-3, 0.05, 16)])
+def test_sw_walk_decisions_match_oracle(model, n, delta, m_limit, ncrit):
+    pos, mass = ic.make(model, n, 27)
+    t = S.Tree(pos, mass, 8)
+    lists = t.lists(0.0, ncrit, 0.01, True, mac="sw", delta=delta, m_limit=m_limit)
+    r = oracle.Tree(pos, mass, 8, ncrit).eval(0.0, 0.01, True, group_stride=10 ** 9, mac="sw", delta=delta,
+                                              m_limit=m_limit)
+    g = lists.groups
+    perm = lists.perm
+    keys = np.array([perm[a:a + c].min() for a, c in zip(g["first"], g["count"])])
+    mine = {k: (c, nc, npt) for k, c, nc, npt in zip(keys, g["count"], g["n_cell"], g["n_part"])}
+    theirs = {k: (c, nc, npt) for k, c, nc, npt in zip(r["key"], r["count"], r["n_cell"], r["n_part"])}
+    assert mine == theirs
+    assert np.all(g["theta"] == 0)
+    # no accepted cell is heavier than the mass limit
+    if m_limit > 0:
+        e = t.export()
+        lst = lists.list
+        cells = lst[lst >= lists.n_part] - lists.n_part
+        assert e["cmass"][cells].max() <= m_limit
 
 
 def test_per_group_theta_override():
@@ -240,6 +280,16 @@ def test_invalid_inputs_return_einval():
         assert e.value.code == L.OTOO_EINVAL
     with pytest.raises(L.OtooError):
         L.call("otoo_build_tree", None, None, 0, None, None)
+    for delta in (-1.0, np.inf, np.nan):
+        with pytest.raises(L.OtooError) as e:
+            t.lists(0.0, 64, 0.1, mac="sw", delta=delta)
+        assert e.value.code == L.OTOO_EINVAL
+    p = S._params(0.5, 8, 64, True, 0.1)
+    p.mac = 7
+    h = __import__("ctypes").c_void_p()
+    with pytest.raises(L.OtooError) as e:
+        L.call("otoo_make_groups_and_lists", t._h, __import__("ctypes").byref(p), __import__("ctypes").byref(h))
+    assert e.value.code == L.OTOO_EINVAL
 
 
 def test_features_are_finite_and_consistent():
