@@ -367,15 +367,18 @@ typedef struct otoo_wcell {
     float s;                       /* |com - cube centre| (FP64, as the host test computes it) rounded */
     int32_t child0, nchild;        /* children [child0, child0 + nchild), nchild = 0 for a leaf */
     int32_t begin, end;            /* tree-order particle range */
-    int32_t pad;
+    float rb;                      /* OTOO_MAC_SW: bounding radius r_b rounded (infinite when
+                                      delta = 0); 0 for the opening angle */
 } otoo_wcell;
 
-/* FP64 geometry of cell k (80 bytes): what the exact test reads. */
+/* FP64 geometry of cell k (96 bytes): what the exact test reads. */
 typedef struct otoo_wcell64 {
     double lo[3];                  /* cube lower corner */
     double side;                   /* cube side */
     double com[3];                 /* centre of mass */
     double gc[3];                  /* cube centre */
+    double rb;                     /* OTOO_MAC_SW: r_b as the host walk computes it; else 0 */
+    double pad;
 } otoo_wcell64;
 
 /* Groups of otoo_make_groups_and_lists (maximal cells with at most n_crit
@@ -391,15 +394,20 @@ int otoo_find_groups(const otoo_tree* tree, int32_t n_crit, int32_t* first, int3
    the caller allocated (any may be NULL to skip it): src [n_part + n_cell]
    (particles in tree order, then cells: centre of mass, mass) and quad
    [n_cell] exactly as otoo_make_groups_and_lists stores them (zeros when
-   use_quad = 0); cell [n_cell] and cell64 [n_cell] walk records. */
-int otoo_tree_device_arrays(const otoo_tree* tree, int32_t use_quad, otoo_src* src, otoo_quad* quad,
-                            otoo_wcell* cell, otoo_wcell64* cell64);
+   use_quad = 0); cell [n_cell] and cell64 [n_cell] walk records.  params
+   (may be NULL: opening angle) selects the acceptance rule the records are
+   for; with OTOO_MAC_SW the records carry r_b for params->delta and
+   params->m_limit. */
+int otoo_tree_device_arrays(const otoo_tree* tree, int32_t use_quad, const otoo_params* params, otoo_src* src,
+                            otoo_quad* quad, otoo_wcell* cell, otoo_wcell64* cell64);
 
 /* Device view of one walk (all pointers device, caller-owned). */
 typedef struct otoo_dev_walk {
     int64_t n_part, n_cell;        /* the tree's particles and cells */
     int32_t n_groups;
     int32_t exact;                 /* 1 = every acceptance test in FP64 (no FP32 filter) */
+    int32_t mac;                   /* OTOO_MAC_THETA, or OTOO_MAC_SW (records made for it) */
+    int32_t pad;
     double theta;                  /* opening angle when theta_per_group is NULL (>= 0) */
     double eps2;                   /* softening^2, copied into every group record */
     const otoo_src* src;           /* [n_part + n_cell]: particle positions (tree order) */

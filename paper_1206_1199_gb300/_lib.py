@@ -99,20 +99,21 @@ class TreeView(ctypes.Structure):
 
 class WCell(ctypes.Structure):
     _fields_ = [("com_hi", f32 * 3), ("com_lo", f32 * 3), ("e", f32 * 3), ("side", f32), ("s", f32),
-                ("child0", i32), ("nchild", i32), ("begin", i32), ("end", i32), ("pad", i32)]
+                ("child0", i32), ("nchild", i32), ("begin", i32), ("end", i32), ("rb", f32)]
 
 
 class WCell64(ctypes.Structure):
-    _fields_ = [("lo", f64 * 3), ("side", f64), ("com", f64 * 3), ("gc", f64 * 3)]
+    _fields_ = [("lo", f64 * 3), ("side", f64), ("com", f64 * 3), ("gc", f64 * 3), ("rb", f64), ("pad", f64)]
 
 
 class DevWalk(ctypes.Structure):
-    _fields_ = [("n_part", i64), ("n_cell", i64), ("n_groups", i32), ("exact", i32), ("theta", f64),
+    _fields_ = [("n_part", i64), ("n_cell", i64), ("n_groups", i32), ("exact", i32), ("mac", i32), ("pad", i32),
+                ("theta", f64),
                 ("eps2", f64), ("src", vp), ("cell", vp), ("cell64", vp), ("group_first", vp),
                 ("group_count", vp), ("theta_per_group", vp), ("counter", vp), ("totals", vp)]
 
 
-for _s, _n in ((Src, 32), (Quad, 32), (Group, 64), (Item, 32), (Split, 16), (WCell, 64), (WCell64, 80)):
+for _s, _n in ((Src, 32), (Quad, 32), (Group, 64), (Item, 32), (Split, 16), (WCell, 64), (WCell64, 96)):
     assert ctypes.sizeof(_s) == _n, (_s, ctypes.sizeof(_s))
 
 # name -> (argtypes); every function returns int unless listed in _VOID
@@ -143,7 +144,7 @@ _SIGS = {
     "otoo_mlp_to_bf16": [vp, vp, i32, vp],
     "otoo_select_theta": [vp, vp, vp, i32, i64, f32, vp, f32, vp, vp],
     "otoo_find_groups": [vp, i32, vp, vp, i64, ctypes.POINTER(i64)],
-    "otoo_tree_device_arrays": [vp, i32, vp, vp, vp, vp],
+    "otoo_tree_device_arrays": [vp, i32, ctypes.POINTER(Params), vp, vp, vp, vp],
     "otoo_walk_totals_len": [i64],
     "otoo_walk_count": [ctypes.POINTER(DevWalk), vp, vp],
     "otoo_walk_fill": [ctypes.POINTER(DevWalk), vp, vp, i64, vp],

@@ -47,7 +47,7 @@ constexpr uint32_t kWalkBadGroup = 16u;   // a group range failed its check
 
 struct WalkArgs {
     int64_t n_part, n_cell;
-    int32_t n_groups, exact;
+    int32_t n_groups, exact, mac, pad;
     double theta, eps2;
     const otoo_src* src;
     const otoo_wcell* cell;
@@ -146,6 +146,51 @@ __device__ __forceinline__ void ld256(const void* p, float v[8])
         : "l"(p));
 }
 
+// The absolute MAC of the host walk (Eq. SW_MAC): d_min > r_b, FP64,
+// operation for operation.
+__device__ bool sw_exact(const otoo_wcell64* __restrict__ c64, int k, const double blo[3], const double bhi[3])
+{
+    const otoo_wcell64 c = c64[k];
+    double d2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double d = 0.0;
+        const double t0 = __dsub_rn(blo[a], c.com[a]);
+        if (t0 > d) d = t0;
+        const double t1 = __dsub_rn(c.com[a], bhi[a]);
+        if (t1 > d) d = t1;
+        d2 = __dadd_rn(d2, __dmul_rn(d, d));
+    }
+    return __dsqrt_rn(d2) > c.rb;
+}
+
+// FP32 filter of the absolute MAC with the same bound as mac_filter: the
+// squared distance against r_b^2 decides when they differ by more than
+// 2^-16 K^2 (K now includes r_b, rounded once from the host's FP64 value).
+__device__ __forceinline__ int mac_filter_sw(const otoo_wcell& w, const BoxF& g)
+{
+    const float rb = w.rb;
+    if (!(rb <= 3.0e38f)) return 0;  // infinite r_b (delta = 0): nothing is accepted
+    float u[3], au = 0.f, A = g.A;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        u[a] = __fadd_rn(__fsub_rn(w.com_hi[a], g.c32[a]), __fsub_rn(w.com_lo[a], g.cl32[a]));
+        au += fabsf(u[a]);
+        A += fabsf(w.com_hi[a]);
+    }
+    const float K = au + g.B + rb + A * 0x1p-24f;
+    float d2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d = fmaxf(0.f, fmaxf(g.bl[a] - u[a], u[a] - g.bh[a]));
+        d2 = fmaf(d, d, d2);
+    }
+    const float rb2 = rb * rb, m = K * K * 0x1p-16f;
+    if (d2 > rb2 + m) return 1;
+    if (d2 < rb2 - m) return 0;
+    return -1;
+}
+
 __device__ __forceinline__ otoo_wcell load_wcell(const otoo_wcell* __restrict__ cell, int k)
 {
     float v[16];
@@ -161,7 +206,7 @@ __device__ __forceinline__ otoo_wcell load_wcell(const otoo_wcell* __restrict__ 
     w.nchild = __float_as_int(v[12]);
     w.begin = __float_as_int(v[13]);
     w.end = __float_as_int(v[14]);
-    w.pad = 0;
+    w.rb = v[15];
     return w;
 }
 
@@ -277,8 +322,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
             bf.B += fmaxf(fabsf(bf.bl[k]), fabsf(bf.bh[k]));
             bf.A += fabsf(bf.c32[k]);
         }
-        const double theta = a.tpg ? (double)a.tpg[g] : a.theta;
-        const bool open_all = !(theta > 0.0);
+        const bool sw = a.mac == OTOO_MAC_SW;
+        const double theta = sw ? 0.0 : a.tpg ? (double)a.tpg[g] : a.theta;
+        const bool open_all = !sw && !(theta > 0.0);
         // 1/theta within 2^-23 (the filter's margins allow 2^-21)
         const float invth = open_all ? 0.f : __frcp_rn(__double2float_rn(theta));
         int64_t off_c = 0, off_p = 0;
@@ -362,7 +408,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
                          pb >= 0 && pb <= pe && (int64_t)pe <= a.n_part;
                     if (ok) {
                         int dec = 0;
-                        if (!open_all) {
+                        if (sw) {
+                            dec = a.exact ? -1 : mac_filter_sw(w, bf);
+                            if (dec < 0) dec = sw_exact(a.cell64, node, blo, bhi) ? 1 : 0;
+                        } else if (!open_all) {
                             dec = a.exact ? -1 : mac_filter(w, bf, invth);
                             if (dec < 0) dec = mac_exact(a.cell64, node, blo, bhi, theta) ? 1 : 0;
                         }
@@ -695,6 +744,7 @@ int check_walk(const otoo_dev_walk* w)
     OTOO_REQUIRE(w->n_groups >= 1, OTOO_EINVAL, "walk: n_groups < 1");
     OTOO_REQUIRE(w->eps2 > 0.0, OTOO_EINVAL, "walk: eps2 must be > 0");
     OTOO_REQUIRE(w->theta >= 0.0 && w->theta < 1e300, OTOO_EINVAL, "walk: theta must be finite and >= 0");
+    OTOO_REQUIRE(w->mac == OTOO_MAC_THETA || w->mac == OTOO_MAC_SW, OTOO_EINVAL, "walk: unknown mac %d", w->mac);
     return OTOO_OK;
 }
 
@@ -705,6 +755,8 @@ WalkArgs walk_args(const otoo_dev_walk* w)
     a.n_cell = w->n_cell;
     a.n_groups = w->n_groups;
     a.exact = w->exact ? 1 : 0;
+    a.mac = w->mac;
+    a.pad = 0;
     a.theta = w->theta;
     a.eps2 = w->eps2;
     a.src = w->src;

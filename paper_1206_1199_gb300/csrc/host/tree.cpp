@@ -670,10 +670,14 @@ int otoo_find_groups(const otoo_tree* t, int32_t n_crit, int32_t* first, int32_t
 // offset from the cube's lower corner, side, and the centre-of-mass offset s
 // computed with the host test's FP64 operations) and the FP64 geometry the
 // exact test reads.
-int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, otoo_src* src, otoo_quad* quad,
-                            otoo_wcell* cell, otoo_wcell64* cell64)
+int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, const otoo_params* p, otoo_src* src,
+                            otoo_quad* quad, otoo_wcell* cell, otoo_wcell64* cell64)
 {
     OTOO_REQUIRE(t, OTOO_EINVAL, "otoo_tree_device_arrays: NULL tree");
+    const bool sw = p && p->mac == OTOO_MAC_SW;
+    OTOO_REQUIRE(!p || p->mac == OTOO_MAC_THETA || sw, OTOO_EINVAL, "unknown mac %d", p ? p->mac : 0);
+    OTOO_REQUIRE(!sw || (p->delta >= 0.0 && std::isfinite(p->delta) && std::isfinite(p->m_limit)), OTOO_EINVAL,
+                 "delta must be finite and >= 0, m_limit finite");
     OTOO_REQUIRE(t->n <= INT32_MAX / 2 && (int64_t)t->cells.size() <= INT32_MAX / 2, OTOO_EINVAL,
                  "otoo_tree_device_arrays: tree too large for 32-bit indices");
     return guarded([&]() -> int {
@@ -700,7 +704,8 @@ int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, otoo_src* src,
                 w.child0 = w.nchild > 0 ? (int32_t)t->c_child0[c] : 0;
                 w.begin = (int32_t)t->c_begin[c];
                 w.end = (int32_t)t->c_end[c];
-                w.pad = 0;
+                w.rb = sw ? (float)sw_radius(t->c_b2[c], t->c_bmax[c], t->c_mass[c], p->delta, p->m_limit, t->S)
+                          : 0.f;
             }
         }
         if (cell64) {
@@ -713,6 +718,8 @@ int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, otoo_src* src,
                     w.gc[a] = t->c_gc[3 * c + a];
                 }
                 w.side = t->c_side[c];
+                w.rb = sw ? sw_radius(t->c_b2[c], t->c_bmax[c], t->c_mass[c], p->delta, p->m_limit, t->S) : 0.0;
+                w.pad = 0.0;
             }
         }
         return OTOO_OK;

@@ -296,7 +296,7 @@ class DeviceTree:
     (otoo_tree_device_arrays), the group ranges (otoo_find_groups) and the
     tree-to-caller permutation."""
 
-    def __init__(self, tree, n_crit, use_quad=True, device="cuda"):
+    def __init__(self, tree, n_crit, use_quad=True, device="cuda", mac="theta", delta=0.0, m_limit=0.0):
         v = L.TreeView()
         L.call("otoo_tree_export", tree._h, ctypes.byref(v))
         n, nc = int(v.n_part), int(v.n_cell)
@@ -304,8 +304,10 @@ class DeviceTree:
         quad = np.empty(nc, np.dtype(L.Quad))
         cell = np.empty(nc, np.dtype(L.WCell))
         cell64 = np.empty(nc, np.dtype(L.WCell64))
-        L.call("otoo_tree_device_arrays", tree._h, int(bool(use_quad)), src.ctypes.data, quad.ctypes.data,
-               cell.ctypes.data, cell64.ctypes.data)
+        p = _params(0.0, tree.leaf_size, n_crit, use_quad, 1.0, None, mac, delta, m_limit)
+        L.call("otoo_tree_device_arrays", tree._h, int(bool(use_quad)), ctypes.byref(p), src.ctypes.data,
+               quad.ctypes.data, cell.ctypes.data, cell64.ctypes.data)
+        self.mac = p.mac
         G = ctypes.c_int64()
         L.call("otoo_find_groups", tree._h, int(n_crit), None, None, 0, ctypes.byref(G))
         first = np.empty(G.value, np.int32)
@@ -354,6 +356,7 @@ class DeviceLists:
             b["tpg"].copy_(torch.from_numpy(tpg))
         w = L.DevWalk()
         w.n_part, w.n_cell, w.n_groups, w.exact = dtree.n_part, dtree.n_cell, G, int(bool(exact))
+        w.mac = dtree.mac
         w.theta, w.eps2 = float(theta), float(eps) * float(eps)
         tb = dtree.bufs
         w.src, w.cell, w.cell64 = tb["src"].data_ptr(), tb["cell"].data_ptr(), tb["cell64"].data_ptr()

@@ -69,6 +69,35 @@ def test_device_walk_matches_host_lists(torch, model, n, theta, ncrit, leaf, qua
     np.testing.assert_array_equal(dt.walk(theta, 0.01).list, dl.list)
 
 
+@pytest.mark.parametrize("model,n,delta,m_limit,ncrit", [("plummer", 20000, 1e-2, 0.05, 64),
+                                                        ("hernquist", 30000, 1e-4, 0.0, 32),
+                                                        ("plummer", 3000, 0.0, 0.0, 64)])
+def test_device_walk_sw_matches_host_lists(torch, model, n, delta, m_limit, ncrit):
+    pos, mass = ic.make(model, n, 46)
+    t = S.Tree(pos, mass, 8)
+    hl = t.lists(0.0, ncrit, 0.01, True, mac="sw", delta=delta, m_limit=m_limit)
+    dt = S.DeviceTree(t, ncrit, True, mac="sw", delta=delta, m_limit=m_limit)
+    dl = dt.walk(0.0, 0.01)
+    compare_lists(hl, dl)
+    de = dt.walk(0.0, 0.01, exact=True)
+    np.testing.assert_array_equal(de.list, dl.list)
+    if delta == 0.0:
+        assert dl.interactions == n * n
+
+
+@pytest.mark.parametrize("delta", [1e-2, 1e-3])
+def test_sw_lists_force_matches_oracle(torch, delta):
+    pos, mass = ic.plummer(1 << 14, 47)
+    t = S.Tree(pos, mass, 8)
+    hl = t.lists(0.0, 64, 1e-3, True, mac="sw", delta=delta, m_limit=0.05)
+    dev = S.DeviceSystem.upload(hl, hl.plan(L.default_tune(64)), "cuda")
+    a64, p64 = (x.cpu().numpy() for x in S.force(dev, precision=L.OTOO_FP64))
+    r = oracle.Tree(pos, mass, 8, 64).eval(0.0, 1e-3, use_quad=True, mac="sw", delta=delta, m_limit=0.05)
+    rel = np.linalg.norm(a64 - r["acc"], axis=1) / np.linalg.norm(r["acc"], axis=1)
+    assert rel.max() <= 1e-6
+    assert (np.abs(p64 - r["pot"]) / np.abs(r["pot"])).max() <= 1e-6
+
+
 def test_device_walk_theta_zero_and_per_group(torch):
     pos, mass = ic.plummer(3000, 42)
     t = S.Tree(pos, mass, 8)

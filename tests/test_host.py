@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(L.Src) == 32 and ctypes.sizeof(L.Quad) == 32 and ctypes.sizeof(L.Group) == 64
     assert ctypes.sizeof(L.Item) == 32 and ctypes.sizeof(L.Split) == 16
-    assert ctypes.sizeof(L.WCell) == 64 and ctypes.sizeof(L.WCell64) == 80
+    assert ctypes.sizeof(L.WCell) == 64 and ctypes.sizeof(L.WCell64) == 96
 
 
 def tree_and_lists(pos, mass, theta=0.5, n_crit=64, eps=0.01, quad=True, leaf=8):
@@ -311,16 +311,34 @@ def test_features_are_finite_and_consistent():
     assert np.all(f0[:, 3] == 0) and np.all(f0[:, 1] == np.float32(3.0)) and np.all(f0[:, 4] == np.float32(-12.0))
 
 
-def device_arrays(t, use_quad):
+def device_arrays(t, use_quad, mac="theta", delta=0.0, m_limit=0.0):
     e = t.export()
     n, nc = e["n_part"], e["n_cell"]
     src = np.empty(n + nc, np.dtype(L.Src))
     quad = np.empty(nc, np.dtype(L.Quad))
     cell = np.empty(nc, np.dtype(L.WCell))
     cell64 = np.empty(nc, np.dtype(L.WCell64))
-    L.call("otoo_tree_device_arrays", t._h, int(use_quad), src.ctypes.data, quad.ctypes.data, cell.ctypes.data,
-           cell64.ctypes.data)
+    p = S._params(0.0, 8, 64, use_quad, 1.0, None, mac, delta, m_limit)
+    L.call("otoo_tree_device_arrays", t._h, int(use_quad), ctypes.byref(p), src.ctypes.data, quad.ctypes.data,
+           cell.ctypes.data, cell64.ctypes.data)
     return e, src, quad, cell, cell64
+
+
+def test_sw_walk_records_carry_the_radius():
+    pos, mass = ic.plummer(5000, 34)
+    t = S.Tree(pos, mass, 8)
+    e, _, _, cell, cell64 = device_arrays(t, 1, "sw", 1e-3, 0.05)
+    for c in range(0, e["n_cell"], 5):
+        p = e["pos"][e["begin"][c]:e["end"][c]]
+        m = e["mass"][e["begin"][c]:e["end"][c]].astype(np.float64)
+        rb = oracle.sw_radius(p, m, 1e-3, 0.05, e["root_side"])[2]
+        assert cell64["rb"][c] == pytest.approx(rb, rel=1e-12)
+        assert cell["rb"][c] == np.float32(cell64["rb"][c])
+    assert np.all(cell64["rb"][e["cmass"] > 0.05] == 2 * e["root_side"])
+    _, _, _, c0, c64 = device_arrays(t, 1, "sw", 0.0, 0.0)
+    assert np.all(np.isinf(c64["rb"])) and np.all(np.isinf(c0["rb"]))
+    _, _, _, c0, c64 = device_arrays(t, 1)
+    assert np.all(c64["rb"] == 0) and np.all(c0["rb"] == 0)
 
 
 def find_groups(t, n_crit):
@@ -415,6 +433,57 @@ def filter_accept(blo, bhi, cell, theta):
     out[sep & (d2 < thr2 - m)] = 0
     out[ovl] = 0
     return out
+
+
+def exact_accept_sw(blo, bhi, cell64):
+    com = cell64["com"]
+    d = np.maximum(np.maximum(blo - com, 0.0), com - bhi)
+    d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    return np.sqrt(d2) > cell64["rb"]
+
+
+def filter_accept_sw(blo, bhi, cell):
+    """FP32 filter of the device walk's absolute MAC, restated in numpy."""
+    f = np.float32
+    c = (blo + bhi) * 0.5
+    c32 = c.astype(f)
+    cl32 = (c - c32.astype(np.float64)).astype(f)
+    bl = (blo - c).astype(f)
+    bh = (bhi - c).astype(f)
+    B = np.maximum(np.abs(bl), np.abs(bh)).sum(dtype=f)
+    A = np.abs(c32).sum(dtype=f) + np.abs(cell["com_hi"]).sum(1, dtype=f)
+    u = (cell["com_hi"] - c32) + (cell["com_lo"] - cl32)
+    rb = cell["rb"]
+    K = np.abs(u).sum(1, dtype=f) + B + rb + A * f(2.0 ** -24)
+    d = np.maximum(f(0), np.maximum(bl - u, u - bh))
+    d2 = (d * d).sum(1, dtype=f)
+    m = K * K * f(2.0 ** -16)
+    out = np.full(len(cell), -1, np.int8)
+    with np.errstate(invalid="ignore"):
+        out[d2 > rb * rb + m] = 1
+        out[d2 < rb * rb - m] = 0
+    out[np.isinf(rb)] = 0
+    return out
+
+
+@pytest.mark.parametrize("model,delta,m_limit", [("plummer", 1e-2, 0.05), ("hernquist", 1e-4, 0.0),
+                                                 ("plummer", 0.0, 0.0)])
+def test_fp32_sw_filter_never_contradicts_fp64(model, delta, m_limit):
+    pos, mass = ic.make(model, 6000, 35)
+    t = S.Tree(pos, mass, 8)
+    e, _, _, cell, cell64 = device_arrays(t, 1, "sw", delta, m_limit)
+    first, count = find_groups(t, 32)
+    undecided = total = 0
+    for gi in range(0, len(first), 3):
+        p = e["pos"][first[gi]:first[gi] + count[gi]]
+        blo, bhi = p.min(0), p.max(0)
+        ex = exact_accept_sw(blo, bhi, cell64)
+        fl = filter_accept_sw(blo, bhi, cell)
+        dec = fl >= 0
+        np.testing.assert_array_equal(fl[dec] == 1, ex[dec])
+        undecided += int((~dec).sum())
+        total += len(fl)
+    assert undecided <= 0.01 * total
 
 
 @pytest.mark.parametrize("model,n,theta", [("plummer", 6000, 0.5), ("hernquist", 6000, 0.75),
