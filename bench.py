@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the batched 64-system step and the learned-angle comparison")
     ap.add_argument("--skip-walk", action="store_true", help="skip the device-walk step")
+    ap.add_argument("--skip-sw", action="store_true", help="skip the absolute-MAC (delta) sweep")
     return ap.parse_args()
 
 
@@ -292,6 +293,8 @@ def run_ours(args):
     if rank == 0 and not args.skip_walk:
         line["device_walk"] = guarded_extra(run_device_walk, args, dev_name, tree, w, tune, lists, a32, stream,
                                             t2 - t1, t3 - t2)
+    if rank == 0 and not args.skip_sw and errors is not None:
+        line["sw_sweep"] = guarded_extra(run_sw_sweep, args, dev_name, tree, w, tune, stream, sub, ad)
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_seconds)
     if rank == 0 and not args.skip_extras and args.workload == "hernquist8m":
@@ -365,6 +368,56 @@ def run_device_walk(args, dev_name, tree, w, tune, lists, a32, stream, host_walk
             "group_counts_equal_host": same, "n_list": int(dl.n_list),
             "interactions_equal_host": bool(dl.interactions == lists.interactions),
             "items": int(dp.n_items), "fp32_vs_host_lists_acc_rms": rms, "fp32_vs_host_lists_acc_max": mx}
+
+
+def run_sw_sweep(args, dev_name, tree, w, tune, stream, sub, ad):
+    """The paper's accuracy control (Section II-B, Eq. SW_MAC): the absolute
+    MAC over a range of delta with m_limit = 0.05 of the total mass, walked
+    on the device; per delta the list size, the FP32 force-step time and the
+    error against the FP64 direct sum on the error targets, and the slope of
+    the cost against delta (the paper's model: delta^-3/4 for small delta)."""
+    import torch
+
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import system as S
+    m_limit = 0.05 * float(tree.export()["mass"].astype(np.float64).sum())
+    rows = []
+    n = tree.n
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
+    pot = torch.empty(n, dtype=torch.float64, device=dev_name)
+    for delta in (1e-1, 1e-2, 1e-3, 1e-4, 1e-5):
+        dt = S.DeviceTree(tree, w["n_crit"], w["use_quad"], dev_name, mac="sw", delta=delta, m_limit=m_limit)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        try:
+            dl = dt.walk(0.0, w["eps"], stream=stream, max_entries=int(2.5e9))
+        except ValueError as e:
+            rows.append({"delta": delta, "skipped": str(e)})
+            break
+        e1.record(stream)
+        step = S.DeviceStep(dl, dl.plan(tune, stream=stream))
+        S.force(step, acc, pot, L.OTOO_FP32K, tune, stream=stream)
+        torch.cuda.synchronize()
+        walk_ms = e0.elapsed_time(e1)
+        k = 3
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k):
+            S.force(step, acc, pot, L.OTOO_FP32K, tune, stream=stream, check=False)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms = f0.elapsed_time(f1) / k
+        rms, mx = rel_err(acc.cpu().numpy()[sub], ad)
+        rows.append({"delta": delta, "interactions": int(dl.interactions), "cell_interactions":
+                     int(dl.cell_interactions), "force_ms": ms, "walk_ms": walk_ms, "acc_rms": rms, "acc_max": mx})
+        del step, dl, dt
+        torch.cuda.empty_cache()
+        if ms > 2000:
+            break
+    done = [r for r in rows if "interactions" in r]
+    slopes = [math.log(b["interactions"] / a["interactions"]) / math.log(b["delta"] / a["delta"])
+              for a, b in zip(done, done[1:])]
+    return {"m_limit": m_limit, "rows": rows, "cost_slopes": slopes, "error_targets": int(len(sub))}
 
 
 def run_batch(args, dev_name):

@@ -328,17 +328,19 @@ class DeviceTree:
     def h2d_bytes(self):
         return sum(b.numel() for b in self.bufs.values() if b is not None)
 
-    def walk(self, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None):
+    def walk(self, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None, max_entries=None):
         """otoo_walk_count + otoo_walk_fill: groups and lists on the device.
         With a BufferPool the buffers of the previous walk are reused (and
-        overwritten)."""
-        return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool)
+        overwritten).  max_entries: raise ValueError instead of allocating a
+        longer list."""
+        return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool, max_entries)
 
 
 class DeviceLists:
     """Groups and lists made by the device walk (device buffers)."""
 
-    def __init__(self, dtree, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None):
+    def __init__(self, dtree, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None,
+                 max_entries=None):
         import torch
         dev = dtree.device
         G = dtree.n_groups
@@ -369,6 +371,8 @@ class DeviceLists:
         L.call("otoo_walk_count", ctypes.byref(w), b["groups"].data_ptr(), st)
         tot = b["totals"][:3].tolist()
         self.n_list, self.interactions, self.cell_interactions = (int(x) for x in tot)
+        if max_entries is not None and self.n_list > max_entries:
+            raise ValueError("walk: %d list entries exceed max_entries %d" % (self.n_list, max_entries))
         b["list"] = alloc("list", self.n_list, torch.int32)
         L.call("otoo_walk_fill", ctypes.byref(w), b["groups"].data_ptr(), b["list"].data_ptr(), self.n_list, st)
         L.call("otoo_walk_check_status", ctypes.byref(w), st)
