@@ -463,6 +463,52 @@ int otoo_plan_fill(const otoo_group* groups, int32_t n_groups, const otoo_tune* 
                    const int64_t* plan_totals, otoo_item* items, int64_t items_capacity, otoo_split* splits,
                    int64_t splits_capacity, uint32_t* counter, void* stream);
 
+/* ---- the tree built on the device ------------------------------------------------
+   Section III-B (root cube, keys, sort, cells) and III-C (cell properties) on
+   the GPU, writing the device walk's and the force step's inputs in place.
+   The root cube, grid coordinates, Hilbert keys, the stable (key, index)
+   sort and the cell cubes use the host build's operations, so the particle
+   order, the cells (as particle ranges with their levels), their cubes and
+   the groups equal otoo_build_tree's; cells are numbered level by level
+   (children consecutive), and the moments (mass, centre of mass,
+   quadrupole, B_2, b_max) are combined bottom-up, equal to the host's direct
+   sums to rounding. */
+typedef struct otoo_devtree {
+    /* in */
+    int64_t n_part;                /* particles (>= 1) */
+    int64_t cap_cell;              /* capacity of the cell arrays below */
+    int32_t leaf_size, n_crit;     /* as in otoo_params */
+    int32_t use_quad, mac;         /* quadrupoles stored or zero; OTOO_MAC_THETA / OTOO_MAC_SW */
+    double delta, m_limit;         /* OTOO_MAC_SW: the walk records' r_b */
+    /* out (host values) */
+    int64_t n_cell, n_groups;      /* n_cell = -1 when cap_cell was too small */
+    int32_t depth, pad;
+    double root_lo[3], root_side;
+    /* device arrays, caller-owned */
+    otoo_src* src;                 /* [n_part + cap_cell]: particles in tree order, then cells */
+    otoo_quad* quad;               /* [cap_cell] */
+    otoo_wcell* cell;              /* [cap_cell] walk records */
+    otoo_wcell64* cell64;          /* [cap_cell] */
+    int32_t* group_first;          /* [n_part] */
+    int32_t* group_count;          /* [n_part] */
+    int64_t* perm;                 /* [n_part] caller index of each tree particle */
+    int32_t* cell_level;           /* [cap_cell] level of each cell (0 = root) */
+    uint32_t* status;              /* scratch, >= 2 uint32 */
+} otoo_devtree;
+
+/* Bytes of device scratch otoo_devtree_build needs. */
+int64_t otoo_devtree_scratch_bytes(int64_t n_part, int64_t cap_cell);
+
+/* Builds the tree of pos (device [n_part][3] FP64, caller order) and mass
+   (device [n_part] FP32 > 0) on stream and fills tree's device arrays and
+   out fields; synchronises stream once per tree level (the host reads each
+   level's cell count).  Errors: OTOO_EINVAL (sizes, NULL pointers, scratch
+   too small, a non-finite position or a mass <= 0), OTOO_ENOMEM (more
+   cells than cap_cell: n_cell = -1; call again with a larger capacity),
+   OTOO_ECUDA. */
+int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* tree, void* scratch,
+                       int64_t scratch_bytes, void* stream);
+
 /* ---- learned opening angle (multilayer perceptron 6-32-32-1) ---------------- */
 
 #define OTOO_MLP_IN  6

@@ -113,6 +113,14 @@ class DevWalk(ctypes.Structure):
                 ("group_count", vp), ("theta_per_group", vp), ("counter", vp), ("totals", vp)]
 
 
+class DevTree(ctypes.Structure):
+    _fields_ = [("n_part", i64), ("cap_cell", i64), ("leaf_size", i32), ("n_crit", i32), ("use_quad", i32),
+                ("mac", i32), ("delta", f64), ("m_limit", f64), ("n_cell", i64), ("n_groups", i64), ("depth", i32),
+                ("pad", i32), ("root_lo", f64 * 3), ("root_side", f64), ("src", vp), ("quad", vp), ("cell", vp),
+                ("cell64", vp), ("group_first", vp), ("group_count", vp), ("perm", vp), ("cell_level", vp),
+                ("status", vp)]
+
+
 for _s, _n in ((Src, 32), (Quad, 32), (Group, 64), (Item, 32), (Split, 16), (WCell, 64), (WCell64, 96)):
     assert ctypes.sizeof(_s) == _n, (_s, ctypes.sizeof(_s))
 
@@ -152,10 +160,12 @@ _SIGS = {
     "otoo_plan_scratch_ints": [i64],
     "otoo_plan_count": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp],
     "otoo_plan_fill": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp, i64, vp, i64, vp, vp],
+    "otoo_devtree_scratch_bytes": [i64, i64],
+    "otoo_devtree_build": [vp, vp, ctypes.POINTER(DevTree), vp, i64, vp],
     "otoo_last_error": [],
 }
 _RET_I64 = {"otoo_mlp_scratch_floats", "otoo_force_static_capacity", "otoo_direct_chunks", "otoo_walk_totals_len",
-            "otoo_plan_scratch_ints"}
+            "otoo_plan_scratch_ints", "otoo_devtree_scratch_bytes"}
 _VOID = {"otoo_tree_free", "otoo_lists_free", "otoo_plan_free"}
 _OPTIONAL = set()
 

@@ -17,7 +17,7 @@ LIB = os.path.join(PKG, "libotoo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["host/tree.cpp"]
 CUDA_HDR = ["cuda/force_warp.cuh", "cuda/force_warp2.cuh"]
-CUDA_SRC = ["cuda/force.cu", "cuda/mlp.cu", "cuda/direct.cu", "cuda/walk.cu"]
+CUDA_SRC = ["cuda/force.cu", "cuda/mlp.cu", "cuda/direct.cu", "cuda/walk.cu", "cuda/tree_build.cu"]
 
 
 def _nvcc():
@@ -34,6 +34,7 @@ def _run(cmd):
 
 def sources():
     return [os.path.join(CSRC, s) for s in HOST_SRC + CUDA_SRC + CUDA_HDR] + [os.path.join(CSRC, "common.h"),
+                                                                   os.path.join(CSRC, "treegeom.h"),
                                                                    os.path.join(INCLUDE, "otoo.h")]
 
 

@@ -1,0 +1,831 @@
+// The octree built on the device (Section III-B: root cube, keys, sort,
+// cells; Section III-C: cell properties), producing the inputs of the device
+// walk and the force step directly in device memory.
+//
+// The root cube, the grid coordinates, the Hilbert keys and the cube of every
+// cell are computed with the host build's operations (treegeom.h), and the
+// sort is stable on (key, caller index), so the particle order, the cells (as
+// (level, first particle, last particle) ranges), their cubes and the groups
+// are the host build's.  Cells are numbered level by level (the host numbers
+// them in expansion order); children stay consecutive.  Moments are summed
+// bottom-up (children combined by the parallel-axis rule), so they equal the
+// host's direct sums to rounding.
+//
+// Kernels
+//   k_bbox / k_bbox_final   min/max of the positions (order-preserving integer
+//                           keys: exact), then the root cube.
+//   k_keys                  grid coordinates and Hilbert key per particle.
+//   k_rs_hist / k_rs_scatter  stable LSD radix sort of (key, index), 8 bits
+//                           per pass: per-block digit counts, a scan of the
+//                           counts (digit-major), a scatter that ranks equal
+//                           digits in input order (warp match + per-warp
+//                           running counts).
+//   k_permute               particles in tree order (sources, permutation,
+//                           grid coordinates).
+//   k_expand_count / k_expand_write  one level of cells from the previous one:
+//                           a cell with more than leaf_size particles (above
+//                           the last grid level) splits into the runs of its
+//                           particles' next key digit, found by binary search.
+//   k_moments               bottom-up, one level per launch: leaves sum their
+//                           particles, parents combine their children.
+//   k_bmax                  largest distance of a cell's particles from its
+//                           centre of mass (chunks of particles, atomic max).
+//   k_records               sources, quadrupoles and walk records of the cells.
+//   k_group_flags           first particle of every group (maximal cells with
+//                           at most n_crit particles; larger leaves in chunks).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "../common.h"
+#include "../treegeom.h"
+
+using namespace otoo;
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRsThreads = 256;                 // radix sort: threads per block
+constexpr int kRsItems = 8;                     // keys per thread
+constexpr int kRsTile = kRsThreads * kRsItems;  // keys per block
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kBmaxChunk = 2048;                // particles per b_max work item
+
+// status bits
+constexpr uint32_t kTreeBadInput = 1u;   // a non-finite position or a mass <= 0
+
+struct Geom {
+    double lo[3], S, h, scale;
+};
+
+__device__ __forceinline__ long long dkey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dval(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL)); }
+
+// ---- bounding box ------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_bbox(const double* __restrict__ pos, const float* __restrict__ mass, int64_t n,
+                                              long long* __restrict__ part, uint32_t* __restrict__ status)
+{
+    long long lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = 0x7fffffffffffffffLL, hi[a] = -lo[a] - 1;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            const double x = pos[3 * i + a];
+            bad |= !isfinite(x);
+            const long long k = dkey(x);
+            lo[a] = k < lo[a] ? k : lo[a];
+            hi[a] = k > hi[a] ? k : hi[a];
+        }
+        const float m = mass[i];
+        bad |= !(m > 0.0f) || !isfinite(m);
+    }
+    if (bad) atomicOr(status, kTreeBadInput);
+    __shared__ long long s[6][8];
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long t0 = __shfl_xor_sync(kFull, lo[a], o), t1 = __shfl_xor_sync(kFull, hi[a], o);
+            lo[a] = t0 < lo[a] ? t0 : lo[a];
+            hi[a] = t1 > hi[a] ? t1 : hi[a];
+        }
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) s[a][w] = lo[a], s[3 + a][w] = hi[a];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        long long v = s[threadIdx.x][0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            const long long t = s[threadIdx.x][k];
+            v = threadIdx.x < 3 ? (t < v ? t : v) : (t > v ? t : v);
+        }
+        part[6 * blockIdx.x + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_bbox_final(const long long* __restrict__ part, int nb, Geom* __restrict__ g)
+{
+    if (threadIdx.x != 0) return;
+    long long lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = part[a], hi[a] = part[3 + a];
+    for (int b = 1; b < nb; ++b)
+        for (int a = 0; a < 3; ++a) {
+            const long long l = part[6 * b + a], h = part[6 * b + 3 + a];
+            lo[a] = l < lo[a] ? l : lo[a];
+            hi[a] = h > hi[a] ? h : hi[a];
+        }
+    double mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) mn[a] = dval(lo[a]), mx[a] = dval(hi[a]);
+    root_cube(mn, mx, g->lo, &g->S, &g->h);
+    g->scale = ddiv(kGrid, g->S);
+}
+
+// ---- keys ---------------------------------------------------------------------
+
+__global__ void k_keys(const double* __restrict__ pos, int64_t n, const Geom* __restrict__ g,
+                       uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t x = quantize(pos[3 * i], g->lo[0], g->scale);
+    const uint32_t y = quantize(pos[3 * i + 1], g->lo[1], g->scale);
+    const uint32_t z = quantize(pos[3 * i + 2], g->lo[2], g->scale);
+    keys[i] = hilbert_key(x, y, z);
+    vals[i] = (uint32_t)i;
+}
+
+// ---- stable LSD radix sort ----------------------------------------------------
+// Block b sorts nothing itself: it counts the digits of its tile (hist,
+// digit-major: hist[d * nblk + b]); an exclusive scan of hist gives each
+// (digit, block) its output start; the scatter places each key after all
+// keys of smaller digit and after the keys of equal digit that precede it in
+// the input (earlier blocks, earlier warps of the block, earlier rounds and
+// lower lanes of the warp), which keeps the sort stable.
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                                                         int32_t* __restrict__ hist, int nblk)
+{
+    __shared__ int32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int k = 0; k < kRsItems; ++k) {
+        const int64_t i = base + (int64_t)k * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(int)((keys[i] >> shift) & 255u)], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __restrict__ kin,
+                                                            const uint32_t* __restrict__ vin, int64_t n, int shift,
+                                                            const int32_t* __restrict__ offs, int nblk,
+                                                            uint64_t* __restrict__ kout, uint32_t* __restrict__ vout)
+{
+    __shared__ int32_t wcount[kRsWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int d = lane; d < 256; d += 32) wcount[w][d] = 0;
+    __syncwarp();
+    // warp w owns the contiguous run [base, base + 32 kRsItems) of the tile
+    const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)w * 32 * kRsItems;
+    uint64_t key[kRsItems];
+    uint32_t val[kRsItems];
+    int dig[kRsItems];
+#pragma unroll
+    for (int r = 0; r < kRsItems; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool ok = i < n;
+        key[r] = ok ? kin[i] : 0;
+        val[r] = ok ? vin[i] : 0;
+        dig[r] = ok ? (int)((key[r] >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(kFull, dig[r]);
+        if (ok && (peers & lt) == 0) wcount[w][dig[r]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over the warps of the block, per digit, plus the
+    // block's start in the global order of that digit
+    for (int d = threadIdx.x; d < 256; d += kRsThreads) {
+        int32_t run = offs[(int64_t)d * nblk + blockIdx.x];
+        for (int k = 0; k < kRsWarps; ++k) {
+            const int32_t c = wcount[k][d];
+            wcount[k][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRsItems; ++r) {
+        const unsigned peers = __match_any_sync(kFull, dig[r]);
+        const bool ok = dig[r] < 256;
+        int32_t pos = 0;
+        if (ok) pos = wcount[w][dig[r]] + __popc(peers & lt);
+        __syncwarp();
+        if (ok && (peers & lt) == 0) wcount[w][dig[r]] += __popc(peers);
+        __syncwarp();
+        if (ok) {
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// ---- tree order ------------------------------------------------------------------
+
+__global__ void k_permute(const double* __restrict__ pos, const float* __restrict__ mass,
+                          const uint32_t* __restrict__ order, int64_t n, const Geom* __restrict__ g,
+                          otoo_src* __restrict__ src, int64_t* __restrict__ perm, int32_t* __restrict__ gq)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t i = order[k];
+    otoo_src s;
+    s.x = pos[3 * i];
+    s.y = pos[3 * i + 1];
+    s.z = pos[3 * i + 2];
+    s.m = mass[i];
+    s.pad = 0;
+    src[k] = s;
+    perm[k] = i;
+    gq[3 * k] = (int32_t)quantize(s.x, g->lo[0], g->scale);
+    gq[3 * k + 1] = (int32_t)quantize(s.y, g->lo[1], g->scale);
+    gq[3 * k + 2] = (int32_t)quantize(s.z, g->lo[2], g->scale);
+}
+
+// ---- cells, one level at a time ---------------------------------------------------
+
+struct Cells {
+    int32_t* begin;
+    int32_t* end;
+    int32_t* level;
+    int32_t* parent;
+    int32_t* child0;
+    int32_t* nchild;
+};
+
+// Thread (c, d): the start of the run of next-level digit >= d inside cell
+// c = lo + t / 8 (a split cell's keys are sorted and share the cell's prefix,
+// so its next digit does not decrease along the cell).  cnt[c - lo] = number
+// of non-empty runs (children); starts go to dig[(c - lo) * 8 + d].
+__global__ void k_expand_count(int32_t lo, int32_t hi, int L, int leaf_size, const uint64_t* __restrict__ keys,
+                               Cells c, int32_t* __restrict__ dig, int32_t* __restrict__ cnt)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t cell = lo + (int32_t)(t >> 3);
+    const int d = (int)(t & 7);
+    const bool in = cell < hi;
+    int32_t b = 0, e = 0;
+    bool split = false;
+    if (in) {
+        b = c.begin[cell];
+        e = c.end[cell];
+        split = e - b > leaf_size && L < kLevels;
+    }
+    int32_t start = e;
+    if (split) {
+        const int shift = 3 * (kLevels - 1 - L);
+        int32_t l = b, r = e;  // first index in [b, e) with digit >= d
+        while (l < r) {
+            const int32_t m = l + ((r - l) >> 1);
+            if ((int)((keys[m] >> shift) & 7u) < d)
+                l = m + 1;
+            else
+                r = m;
+        }
+        start = l;
+    }
+    // run d is [start_d, start_{d+1}), start_8 = e
+    const int32_t next = __shfl_down_sync(kFull, start, 1, 8);
+    const int32_t nxt = d == 7 ? e : next;
+    const bool nonempty = split && start < nxt;
+    const unsigned m = __ballot_sync(kFull, nonempty);
+    if (in) {
+        dig[(int64_t)(cell - lo) * 8 + d] = start;
+        if (d == 0) cnt[cell - lo] = __popc((m >> (threadIdx.x & 24)) & 0xffu);
+    }
+}
+
+__global__ void k_expand_write(int32_t lo, int32_t hi, int L, int32_t next_base, Cells c,
+                               const int32_t* __restrict__ dig, const int32_t* __restrict__ coff,
+                               int64_t cap)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t cell = lo + (int32_t)(t >> 3);
+    const int d = (int)(t & 7);
+    const bool in = cell < hi;
+    int32_t start = 0, e = 0;
+    if (in) {
+        start = dig[(int64_t)(cell - lo) * 8 + d];
+        e = c.end[cell];
+    }
+    const int32_t next = __shfl_down_sync(kFull, start, 1, 8);
+    const int32_t nxt = d == 7 ? e : next;
+    const bool nonempty = in && start < nxt;  // a cell that does not split has start = end for every digit
+    const unsigned m = __ballot_sync(kFull, nonempty);
+    const unsigned mine = (m >> (threadIdx.x & 24)) & 0xffu;
+    if (!in) return;
+    const int32_t first = next_base + coff[cell - lo];
+    if (d == 0) {
+        c.child0[cell] = mine ? first : 0;
+        c.nchild[cell] = __popc(mine);
+    }
+    if (nonempty) {
+        const int64_t k = (int64_t)first + __popc(mine & ((1u << d) - 1u));
+        if (k < cap) {
+            c.begin[k] = start;
+            c.end[k] = nxt;
+            c.level[k] = L + 1;
+            c.parent[k] = cell;
+        }
+    }
+}
+
+// ---- moments ------------------------------------------------------------------------
+
+struct Moments {
+    double* m;      // [cap]
+    double* com;    // [cap][3]
+    double* q;      // [cap][6] Qxx Qyy Qzz Qxy Qxz Qyz
+    double* b2;     // [cap]
+    unsigned long long* dmax2;  // [cap] bits of the largest squared distance
+};
+
+// Cells [lo, hi) of one level: a leaf sums its particles (mass and mass-
+// weighted position, then the second moments about the centre of mass); a
+// parent combines its children, shifting each child's moments to the
+// parent's centre of mass: Q += m_c (3 d d^T - |d|^2 I), B_2 += m_c |d|^2,
+// d = com_c - com.
+__global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ src, Cells c, Moments mo)
+{
+    const int32_t cell = lo + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (cell >= hi) return;
+    double m = 0, s[3] = {0, 0, 0}, q[6] = {0, 0, 0, 0, 0, 0}, b2 = 0, com[3];
+    const int32_t nch = c.nchild[cell];
+    if (nch == 0) {
+        const int32_t b = c.begin[cell], e = c.end[cell];
+        for (int32_t i = b; i < e; ++i) {
+            const otoo_src p = src[i];
+            const double mi = p.m;
+            m += mi;
+            s[0] += mi * p.x;
+            s[1] += mi * p.y;
+            s[2] += mi * p.z;
+        }
+        for (int a = 0; a < 3; ++a) com[a] = s[a] / m;
+        for (int32_t i = b; i < e; ++i) {
+            const otoo_src p = src[i];
+            const double mi = p.m;
+            const double dx = p.x - com[0], dy = p.y - com[1], dz = p.z - com[2];
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            b2 += mi * d2;
+            q[0] += mi * (3 * dx * dx - d2);
+            q[1] += mi * (3 * dy * dy - d2);
+            q[2] += mi * (3 * dz * dz - d2);
+            q[3] += mi * 3 * dx * dy;
+            q[4] += mi * 3 * dx * dz;
+            q[5] += mi * 3 * dy * dz;
+        }
+    } else {
+        const int32_t c0 = c.child0[cell];
+        for (int32_t k = c0; k < c0 + nch; ++k) {
+            const double mk = mo.m[k];
+            m += mk;
+            for (int a = 0; a < 3; ++a) s[a] += mk * mo.com[3 * k + a];
+        }
+        for (int a = 0; a < 3; ++a) com[a] = s[a] / m;
+        for (int32_t k = c0; k < c0 + nch; ++k) {
+            const double mk = mo.m[k];
+            const double dx = mo.com[3 * k] - com[0], dy = mo.com[3 * k + 1] - com[1], dz = mo.com[3 * k + 2] - com[2];
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            b2 += mo.b2[k] + mk * d2;
+            q[0] += mo.q[6 * k] + mk * (3 * dx * dx - d2);
+            q[1] += mo.q[6 * k + 1] + mk * (3 * dy * dy - d2);
+            q[2] += mo.q[6 * k + 2] + mk * (3 * dz * dz - d2);
+            q[3] += mo.q[6 * k + 3] + mk * 3 * dx * dy;
+            q[4] += mo.q[6 * k + 4] + mk * 3 * dx * dz;
+            q[5] += mo.q[6 * k + 5] + mk * 3 * dy * dz;
+        }
+    }
+    mo.m[cell] = m;
+    for (int a = 0; a < 3; ++a) mo.com[3 * cell + a] = com[a];
+    for (int k = 0; k < 6; ++k) mo.q[6 * cell + k] = q[k];
+    mo.b2[cell] = b2;
+    mo.dmax2[cell] = 0ull;
+}
+
+// Work item = (cell, chunk of kBmaxChunk particles); item_off: exclusive
+// prefix over cells of their chunk counts.  One warp per item; the chunk's
+// largest squared distance goes to the cell by an atomic max on its bits
+// (non-negative doubles order like their bit patterns).
+__global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restrict__ item_off,
+                       const otoo_src* __restrict__ src, Cells c, Moments mo)
+{
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_items) return;
+    int32_t l = 0, r = n_cell;  // last cell with item_off <= w
+    while (r - l > 1) {
+        const int32_t m = l + ((r - l) >> 1);
+        if (item_off[m] <= w)
+            l = m;
+        else
+            r = m;
+    }
+    const int32_t cell = l;
+    const int64_t chunk = w - item_off[cell];
+    const int32_t b = c.begin[cell], e = c.end[cell];
+    const int64_t i0 = b + chunk * kBmaxChunk;
+    const int64_t i1 = i0 + kBmaxChunk < e ? i0 + kBmaxChunk : e;
+    const double cx = mo.com[3 * cell], cy = mo.com[3 * cell + 1], cz = mo.com[3 * cell + 2];
+    double d2max = 0;
+    for (int64_t i = i0 + lane; i < i1; i += 32) {
+        const otoo_src p = src[i];
+        const double dx = cx - p.x, dy = cy - p.y, dz = cz - p.z;
+        d2max = fmax(d2max, dx * dx + dy * dy + dz * dz);
+    }
+    for (int o = 16; o > 0; o >>= 1) d2max = fmax(d2max, __shfl_xor_sync(kFull, d2max, o));
+    if (lane == 0) atomicMax(mo.dmax2 + cell, (unsigned long long)__double_as_longlong(d2max));
+}
+
+__global__ void k_chunks(int32_t n_cell, Cells c, int32_t* __restrict__ nchunk)
+{
+    const int32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= n_cell) return;
+    const int32_t cnt = c.end[cell] - c.begin[cell];
+    nchunk[cell] = (cnt + kBmaxChunk - 1) / kBmaxChunk;
+}
+
+// ---- records and groups ----------------------------------------------------------
+
+struct RecArgs {
+    int64_t n_part;
+    int32_t n_cell, use_quad, mac, n_crit;
+    double delta, m_limit;
+};
+
+__global__ void k_records(RecArgs ra, const Geom* __restrict__ g, Cells c, Moments mo, const int32_t* __restrict__ gq,
+                          otoo_src* __restrict__ src, otoo_quad* __restrict__ quad, otoo_wcell* __restrict__ wc,
+                          otoo_wcell64* __restrict__ wc64, int32_t* __restrict__ level_out)
+{
+    const int32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= ra.n_cell) return;
+    const int L = c.level[cell];
+    const int32_t b = c.begin[cell];
+    const int sh = kLevels - L;
+    const double side = cube_side(g->h, L);
+    double lo[3], gc[3], com[3];
+    for (int a = 0; a < 3; ++a) {
+        const int64_t gcoord = gq[3 * (int64_t)b + a];
+        const int64_t org = sh >= kLevels ? 0 : (gcoord >> sh) << sh;
+        lo[a] = cube_lo(g->lo[a], org, g->h);
+        gc[a] = cube_centre(lo[a], side);
+        com[a] = mo.com[3 * cell + a];
+    }
+    const double m = mo.m[cell];
+    otoo_src s;
+    s.x = com[0];
+    s.y = com[1];
+    s.z = com[2];
+    s.m = (float)m;
+    s.pad = 0;
+    src[ra.n_part + cell] = s;
+    otoo_quad qd;
+    const bool u = ra.use_quad != 0;
+    qd.xx = u ? (float)mo.q[6 * cell] : 0.f;
+    qd.yy = u ? (float)mo.q[6 * cell + 1] : 0.f;
+    qd.zz = u ? (float)mo.q[6 * cell + 2] : 0.f;
+    qd.xy = u ? (float)mo.q[6 * cell + 3] : 0.f;
+    qd.xz = u ? (float)mo.q[6 * cell + 4] : 0.f;
+    qd.yz = u ? (float)mo.q[6 * cell + 5] : 0.f;
+    qd.pad0 = qd.pad1 = 0.f;
+    quad[cell] = qd;
+    const bool sw = ra.mac == OTOO_MAC_SW;
+    const double bmax = __dsqrt_rn(__longlong_as_double((long long)mo.dmax2[cell]));
+    const double rb = sw ? sw_radius(mo.b2[cell], bmax, m, ra.delta, ra.m_limit, g->S) : 0.0;
+    otoo_wcell w;
+    wcell_geometry(com, lo, gc, side, &w);
+    w.nchild = c.nchild[cell];
+    w.child0 = w.nchild > 0 ? c.child0[cell] : 0;
+    w.begin = b;
+    w.end = c.end[cell];
+    w.rb = (float)rb;
+    wc[cell] = w;
+    otoo_wcell64 w64;
+    for (int a = 0; a < 3; ++a) w64.lo[a] = lo[a], w64.com[a] = com[a], w64.gc[a] = gc[a];
+    w64.side = side;
+    w64.rb = rb;
+    w64.pad = 0.0;
+    wc64[cell] = w64;
+    level_out[cell] = L;
+}
+
+// A group starts at the first particle of each maximal cell with at most
+// n_crit particles, and every n_crit particles inside a leaf that holds more.
+__global__ void k_group_flags(RecArgs ra, Cells c, int32_t* __restrict__ flag)
+{
+    const int32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= ra.n_cell) return;
+    const int32_t b = c.begin[cell], e = c.end[cell], p = c.parent[cell];
+    const int32_t cnt = e - b;
+    const bool parent_big = p < 0 || c.end[p] - c.begin[p] > ra.n_crit;
+    if (!parent_big) return;
+    if (cnt <= ra.n_crit) {
+        flag[b] = 1;
+    } else if (c.nchild[cell] == 0) {
+        for (int32_t k = b; k < e; k += ra.n_crit) flag[k] = 1;
+    }
+}
+
+__global__ void k_group_write(int64_t n, const int32_t* __restrict__ flag, const int32_t* __restrict__ gidx,
+                              int32_t* __restrict__ first)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n && flag[k]) first[gidx[k]] = (int32_t)k;
+}
+
+__global__ void k_group_count(int64_t n, int32_t G, const int32_t* __restrict__ first, int32_t* __restrict__ count)
+{
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    count[g] = (g + 1 < G ? first[g + 1] : (int32_t)n) - first[g];
+}
+
+// ---- scans (exclusive, in place, int32) --------------------------------------------
+
+constexpr int kScanThreads = 1024;
+
+__device__ int64_t block_excl_scan64(int64_t v, int64_t* ws, int64_t* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const int64_t w = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+        int64_t wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += t;
+        }
+        ws[lane] = wi - w;
+        if (lane == 31) ws[32] = wi;
+    }
+    __syncthreads();
+    const int64_t r = ws[wid] + inc - v;
+    *total = ws[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int32_t* __restrict__ a, int64_t n,
+                                                             int64_t* __restrict__ bsum)
+{
+    __shared__ int64_t ws[33];
+    const int64_t i = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+    int64_t tot;
+    block_excl_scan64(i < n ? a[i] : 0, ws, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int64_t* __restrict__ bsum, int64_t nblk,
+                                                            int64_t* __restrict__ total)
+{
+    __shared__ int64_t ws[33];
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nblk; b0 += kScanThreads) {
+        const int64_t i = b0 + threadIdx.x;
+        int64_t tot;
+        const int64_t e = block_excl_scan64(i < nblk ? bsum[i] : 0, ws, &tot);
+        if (i < nblk) bsum[i] = carry + e;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(int32_t* __restrict__ a, int64_t n,
+                                                              const int64_t* __restrict__ bsum)
+{
+    __shared__ int64_t ws[33];
+    const int64_t i = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+    int64_t tot;
+    const int64_t e = block_excl_scan64(i < n ? a[i] : 0, ws, &tot) + bsum[blockIdx.x];
+    if (i < n) a[i] = (int32_t)e;
+}
+
+#define CUDA_TRY(expr)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess) return set_error(OTOO_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));  \
+    } while (0)
+
+// exclusive scan of a[0, n) in place; the total to *total (device)
+int scan32(int32_t* a, int64_t n, int64_t* bsum, int64_t* total, cudaStream_t s)
+{
+    const int64_t nblk = (n + kScanThreads - 1) / kScanThreads;
+    if (nblk == 0) {
+        CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
+        return OTOO_OK;
+    }
+    k_scan_sums<<<(unsigned)nblk, kScanThreads, 0, s>>>(a, n, bsum);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nblk, total);
+    k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, s>>>(a, n, bsum);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+// Scratch layout (byte offsets, each part 256-byte aligned).
+struct Layout {
+    size_t keys0, keys1, vals0, vals1, hist, bsum, part, geom, gq, cells[6], mom_m, mom_com, mom_q, mom_b2,
+        mom_dmax, dig, cnt, flag, tot, total;
+};
+
+size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout(int64_t n, int64_t cap)
+{
+    Layout l;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += up(bytes);
+        return at;
+    };
+    const int64_t nblk = (n + kRsTile - 1) / kRsTile;
+    const int64_t big = n > cap ? n : cap;
+    l.keys0 = take(8 * n);
+    l.keys1 = take(8 * n);
+    l.vals0 = take(4 * n);
+    l.vals1 = take(4 * n);
+    l.hist = take(4 * 256 * nblk);
+    l.bsum = take(8 * ((256 * nblk + 8 * big) / kScanThreads + 8));
+    l.part = take(8 * 6 * 1024);
+    l.geom = take(sizeof(Geom));
+    l.gq = take(12 * n);
+    for (int k = 0; k < 6; ++k) l.cells[k] = take(4 * cap);
+    l.mom_m = take(8 * cap);
+    l.mom_com = take(24 * cap);
+    l.mom_q = take(48 * cap);
+    l.mom_b2 = take(8 * cap);
+    l.mom_dmax = take(8 * cap);
+    l.dig = take(32 * cap);
+    l.cnt = take(4 * (big + 1));
+    l.flag = take(4 * (n + 1));
+    l.tot = take(64);
+    l.total = o;
+    return l;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t otoo_devtree_scratch_bytes(int64_t n_part, int64_t cap_cell)
+{
+    if (n_part < 1 || cap_cell < 1) return 0;
+    return (int64_t)layout(n_part, cap_cell).total;
+}
+
+int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, void* scratch, int64_t scratch_bytes,
+                       void* stream)
+{
+    OTOO_REQUIRE(pos && mass && t && scratch, OTOO_EINVAL, "otoo_devtree_build: NULL pointer");
+    const int64_t n = t->n_part, cap = t->cap_cell;
+    OTOO_REQUIRE(n >= 1 && n <= INT32_MAX / 2 && cap >= 1 && n + cap <= INT32_MAX, OTOO_EINVAL,
+                 "otoo_devtree_build: n_part / cap_cell out of range");
+    OTOO_REQUIRE(t->leaf_size >= 1 && t->n_crit >= 1 && t->n_crit <= kMaxGroup, OTOO_EINVAL,
+                 "otoo_devtree_build: leaf_size < 1 or n_crit outside [1, %d]", kMaxGroup);
+    OTOO_REQUIRE(t->mac == OTOO_MAC_THETA || t->mac == OTOO_MAC_SW, OTOO_EINVAL, "unknown mac %d", t->mac);
+    OTOO_REQUIRE(t->mac != OTOO_MAC_SW || (t->delta >= 0.0 && std::isfinite(t->delta) && std::isfinite(t->m_limit)),
+                 OTOO_EINVAL, "delta must be finite and >= 0, m_limit finite");
+    OTOO_REQUIRE(t->src && t->quad && t->cell && t->cell64 && t->group_first && t->group_count && t->perm &&
+                     t->cell_level && t->status,
+                 OTOO_EINVAL, "otoo_devtree_build: NULL output array");
+    const Layout ly = layout(n, cap);
+    OTOO_REQUIRE(scratch_bytes >= (int64_t)ly.total, OTOO_EINVAL, "otoo_devtree_build: scratch too small (%lld < %lld)",
+                 (long long)scratch_bytes, (long long)ly.total);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(scratch);
+    uint64_t* keys[2] = {reinterpret_cast<uint64_t*>(base + ly.keys0), reinterpret_cast<uint64_t*>(base + ly.keys1)};
+    uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(base + ly.vals0), reinterpret_cast<uint32_t*>(base + ly.vals1)};
+    int32_t* hist = reinterpret_cast<int32_t*>(base + ly.hist);
+    int64_t* bsum = reinterpret_cast<int64_t*>(base + ly.bsum);
+    long long* part = reinterpret_cast<long long*>(base + ly.part);
+    Geom* geom = reinterpret_cast<Geom*>(base + ly.geom);
+    int32_t* gq = reinterpret_cast<int32_t*>(base + ly.gq);
+    Cells c;
+    c.begin = reinterpret_cast<int32_t*>(base + ly.cells[0]);
+    c.end = reinterpret_cast<int32_t*>(base + ly.cells[1]);
+    c.level = reinterpret_cast<int32_t*>(base + ly.cells[2]);
+    c.parent = reinterpret_cast<int32_t*>(base + ly.cells[3]);
+    c.child0 = reinterpret_cast<int32_t*>(base + ly.cells[4]);
+    c.nchild = reinterpret_cast<int32_t*>(base + ly.cells[5]);
+    Moments mo;
+    mo.m = reinterpret_cast<double*>(base + ly.mom_m);
+    mo.com = reinterpret_cast<double*>(base + ly.mom_com);
+    mo.q = reinterpret_cast<double*>(base + ly.mom_q);
+    mo.b2 = reinterpret_cast<double*>(base + ly.mom_b2);
+    mo.dmax2 = reinterpret_cast<unsigned long long*>(base + ly.mom_dmax);
+    int32_t* dig = reinterpret_cast<int32_t*>(base + ly.dig);
+    int32_t* cnt = reinterpret_cast<int32_t*>(base + ly.cnt);
+    int32_t* flag = reinterpret_cast<int32_t*>(base + ly.flag);
+    int64_t* tot = reinterpret_cast<int64_t*>(base + ly.tot);
+    uint32_t* status = t->status;
+
+    // root cube, keys, sort
+    CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(uint32_t), s));
+    const int nbb = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    k_bbox<<<nbb, 256, 0, s>>>(pos, mass, n, part, status);
+    k_bbox_final<<<1, 32, 0, s>>>(part, nbb, geom);
+    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, geom, keys[0], vals[0]);
+    CUDA_TRY(cudaGetLastError());
+    const int nblk = (int)((n + kRsTile - 1) / kRsTile);
+    int cur = 0;
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_rs_hist<<<nblk, kRsThreads, 0, s>>>(keys[cur], n, shift, hist, nblk);
+        const int r = scan32(hist, (int64_t)256 * nblk, bsum, tot, s);
+        if (r) return r;
+        k_rs_scatter<<<nblk, kRsThreads, 0, s>>>(keys[cur], vals[cur], n, shift, hist, nblk, keys[cur ^ 1],
+                                                 vals[cur ^ 1]);
+        CUDA_TRY(cudaGetLastError());
+        cur ^= 1;
+    }
+    k_permute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, mass, vals[cur], n, geom, t->src, t->perm, gq);
+    CUDA_TRY(cudaGetLastError());
+    uint32_t st = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    Geom hg;
+    CUDA_TRY(cudaMemcpyAsync(&hg, geom, sizeof(hg), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (st & kTreeBadInput) return set_error(OTOO_EINVAL, "otoo_devtree_build: non-finite position or mass <= 0");
+    const uint64_t* skeys = keys[cur];
+
+    // cells, level by level (the host reads each level's size)
+    const int32_t root[6] = {0, (int32_t)n, 0, -1, 0, 0};
+    for (int k = 0; k < 6; ++k) {
+        int32_t* arr = k == 0 ? c.begin : k == 1 ? c.end : k == 2 ? c.level : k == 3 ? c.parent : k == 4 ? c.child0 : c.nchild;
+        CUDA_TRY(cudaMemcpyAsync(arr, &root[k], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    std::vector<int32_t> lev_lo{0, 1};
+    int depth = 0;
+    for (int L = 0; L <= kLevels; ++L) {
+        const int32_t lo = lev_lo[L], hi = lev_lo[L + 1];
+        const int64_t nc = hi - lo;
+        if (nc == 0) break;
+        depth = L;
+        const int64_t threads = 8 * nc;
+        const unsigned grid = (unsigned)((threads + 255) / 256);
+        k_expand_count<<<grid, 256, 0, s>>>(lo, hi, L, t->leaf_size, skeys, c, dig, cnt);
+        const int r = scan32(cnt, nc, bsum, tot, s);
+        if (r) return r;
+        int64_t nnext = 0;
+        CUDA_TRY(cudaMemcpyAsync(&nnext, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if ((int64_t)hi + nnext > cap) {
+            t->n_cell = -1;
+            return set_error(OTOO_ENOMEM, "otoo_devtree_build: more than cap_cell = %lld cells", (long long)cap);
+        }
+        k_expand_write<<<grid, 256, 0, s>>>(lo, hi, L, hi, c, dig, cnt, cap);
+        CUDA_TRY(cudaGetLastError());
+        lev_lo.push_back(hi + (int32_t)nnext);
+    }
+    const int32_t n_cell = lev_lo.back();
+
+    // moments, deepest level first
+    for (int L = depth; L >= 0; --L) {
+        const int32_t lo = lev_lo[L], hi = lev_lo[L + 1];
+        if (hi > lo) k_moments<<<(unsigned)((hi - lo + 127) / 128), 128, 0, s>>>(lo, hi, t->src, c, mo);
+    }
+    CUDA_TRY(cudaGetLastError());
+    if (t->mac == OTOO_MAC_SW) {
+        k_chunks<<<(unsigned)((n_cell + 255) / 256), 256, 0, s>>>(n_cell, c, cnt);
+        const int r = scan32(cnt, n_cell, bsum, tot, s);
+        if (r) return r;
+        int64_t n_items = 0;
+        CUDA_TRY(cudaMemcpyAsync(&n_items, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (n_items > 0)
+            k_bmax<<<(unsigned)((n_items * 32 + 255) / 256), 256, 0, s>>>(n_items, n_cell, cnt, t->src, c, mo);
+        CUDA_TRY(cudaGetLastError());
+    }
+    RecArgs ra;
+    ra.n_part = n;
+    ra.n_cell = n_cell;
+    ra.use_quad = t->use_quad ? 1 : 0;
+    ra.mac = t->mac;
+    ra.n_crit = t->n_crit;
+    ra.delta = t->delta;
+    ra.m_limit = t->m_limit;
+    k_records<<<(unsigned)((n_cell + 127) / 128), 128, 0, s>>>(ra, geom, c, mo, gq, t->src, t->quad, t->cell,
+                                                               t->cell64, t->cell_level);
+    // groups
+    CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t) * (size_t)n, s));
+    k_group_flags<<<(unsigned)((n_cell + 255) / 256), 256, 0, s>>>(ra, c, flag);
+    CUDA_TRY(cudaMemcpyAsync(cnt, flag, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    const int r = scan32(cnt, n, bsum, tot, s);
+    if (r) return r;
+    k_group_write<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, flag, cnt, t->group_first);
+    int64_t G = 0;
+    CUDA_TRY(cudaMemcpyAsync(&G, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    k_group_count<<<(unsigned)((G + 255) / 256), 256, 0, s>>>(n, (int32_t)G, t->group_first, t->group_count);
+    CUDA_TRY(cudaGetLastError());
+    t->n_cell = n_cell;
+    t->n_groups = G;
+    t->depth = depth;
+    for (int a = 0; a < 3; ++a) t->root_lo[a] = hg.lo[a];
+    t->root_side = hg.S;
+    return OTOO_OK;
+}
+
+}  // extern "C"

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../common.h"
+#include "../treegeom.h"
 
 namespace otoo {
 
@@ -35,43 +36,6 @@ int set_error(int code, const char* fmt, ...)
 }
 
 namespace {
-
-constexpr int kLevels = 21;                 // 2^21 grid cells per axis, 63-bit keys
-constexpr double kGrid = 2097152.0;         // 2^21
-
-// Hilbert index of a point on the 2^21 grid: Skilling's transpose method
-// (J. Skilling, "Programming the Hilbert curve", AIP Conf. Proc. 707, 2004):
-// undo the excess rotations/reflections level by level, Gray-encode, then
-// interleave the transposed bits from the top level down.  The top 3L bits
-// name the level-L cube that holds the point, so a sort by key keeps every
-// cell contiguous (the property the paper's Morton-to-Hilbert step keeps).
-uint64_t hilbert_key(uint32_t x0, uint32_t x1, uint32_t x2)
-{
-    uint32_t X[3] = {x0, x1, x2};
-    const uint32_t M = 1u << (kLevels - 1);
-    for (uint32_t Q = M; Q > 1; Q >>= 1) {
-        const uint32_t P = Q - 1;
-        for (int i = 0; i < 3; ++i) {
-            if (X[i] & Q) {
-                X[0] ^= P;
-            } else {
-                const uint32_t t = (X[0] ^ X[i]) & P;
-                X[0] ^= t;
-                X[i] ^= t;
-            }
-        }
-    }
-    X[1] ^= X[0];
-    X[2] ^= X[1];
-    uint32_t t = 0;
-    for (uint32_t Q = M; Q > 1; Q >>= 1)
-        if (X[2] & Q) t ^= Q - 1;
-    for (int i = 0; i < 3; ++i) X[i] ^= t;
-    uint64_t key = 0;
-    for (int b = kLevels - 1; b >= 0; --b)
-        for (int i = 0; i < 3; ++i) key = (key << 1) | ((X[i] >> b) & 1u);
-    return key;
-}
 
 struct Cell {
     int64_t begin, end;     // tree-order particle range
@@ -177,11 +141,11 @@ void cell_moments(otoo_tree* t, int64_t c)
     t->c_b2[c] = b2;
     t->c_bmax[c] = std::sqrt(dmax2);
     // cube geometry on the grid: side h 2^(21-L), lower corner lo + org h
-    const double side = t->h * (double)((int64_t)1 << (kLevels - t->c_level[c]));
+    const double side = cube_side(t->h, t->c_level[c]);
     t->c_side[c] = side;
     for (int a = 0; a < 3; ++a) {
-        t->c_lo[3 * c + a] = t->lo[a] + (double)t->c_org[3 * c + a] * t->h;
-        t->c_gc[3 * c + a] = t->c_lo[3 * c + a] + 0.5 * side;
+        t->c_lo[3 * c + a] = cube_lo(t->lo[a], t->c_org[3 * c + a], t->h);
+        t->c_gc[3 * c + a] = cube_centre(t->c_lo[3 * c + a], side);
     }
 }
 
@@ -297,12 +261,7 @@ int otoo_build_tree(const double* pos, const float* mass, int64_t n, const otoo_
                 mx[a] = std::max(mx[a], lmx[a]);
             }
         }
-        double ext = 0;
-        for (int a = 0; a < 3; ++a) ext = std::max(ext, mx[a] - mn[a]);
-        t->S = ext * (1.0 + 1e-12);
-        if (!(t->S > 0.0)) t->S = 1.0;
-        for (int a = 0; a < 3; ++a) t->lo[a] = (mn[a] + mx[a]) * 0.5 - 0.5 * t->S;
-        t->h = t->S / kGrid;
+        root_cube(mn, mx, t->lo, &t->S, &t->h);
         const double scale = kGrid / t->S;
         // step 2: quantise and key
         std::vector<std::pair<uint64_t, int64_t>> kv(n);
@@ -311,10 +270,7 @@ int otoo_build_tree(const double* pos, const float* mass, int64_t n, const otoo_
         for (int64_t i = 0; i < n; ++i) {
             uint32_t g[3];
             for (int a = 0; a < 3; ++a) {
-                double q = std::floor((pos[3 * i + a] - t->lo[a]) * scale);
-                if (q < 0.0) q = 0.0;
-                if (q > kGrid - 1.0) q = kGrid - 1.0;
-                g[a] = (uint32_t)q;
+                g[a] = quantize(pos[3 * i + a], t->lo[a], scale);
                 gq0[3 * i + a] = (int32_t)g[a];
             }
             kv[i] = {hilbert_key(g[0], g[1], g[2]), i};
@@ -422,17 +378,6 @@ inline bool mac_accept(const otoo_tree* t, int64_t c, const double blo[3], const
         s2 += e * e;
     }
     return std::sqrt(d2) > side / theta + std::sqrt(s2);
-}
-
-// Bounding radius of the absolute MAC (Eq. SW_MAC): where the monopole error
-// bound 3 B_2 / (d^2 (d - b_max)^2) equals delta; 2 S_root for cells heavier
-// than m_limit (never accepted, Section III-C); infinite for delta = 0.
-double sw_radius(double b2, double bmax, double m, double delta, double m_limit, double s_root)
-{
-    if (m_limit > 0.0 && m > m_limit) return 2.0 * s_root;
-    if (!(delta > 0.0)) return HUGE_VAL;
-    const double h = 0.5 * bmax;
-    return h + std::sqrt(h * h + std::sqrt(3.0 * b2 / delta));
 }
 
 // Absolute MAC for the box [blo, bhi]: d_min (centre of mass to the box) > r_b.
@@ -687,19 +632,7 @@ int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, const otoo_par
 #pragma omp parallel for schedule(static)
             for (int64_t c = 0; c < nc; ++c) {
                 otoo_wcell& w = cell[c];
-                const double* com = &t->c_com[3 * c];
-                const double* lo = &t->c_lo[3 * c];
-                const double* gc = &t->c_gc[3 * c];
-                double s2 = 0;
-                for (int a = 0; a < 3; ++a) {
-                    w.com_hi[a] = (float)com[a];
-                    w.com_lo[a] = (float)(com[a] - (double)w.com_hi[a]);
-                    w.e[a] = (float)(com[a] - lo[a]);
-                    const double e = com[a] - gc[a];
-                    s2 += e * e;
-                }
-                w.side = (float)t->c_side[c];
-                w.s = (float)std::sqrt(s2);
+                wcell_geometry(&t->c_com[3 * c], &t->c_lo[3 * c], &t->c_gc[3 * c], t->c_side[c], &w);
                 w.nchild = t->c_nchild[c];
                 w.child0 = w.nchild > 0 ? (int32_t)t->c_child0[c] : 0;
                 w.begin = (int32_t)t->c_begin[c];

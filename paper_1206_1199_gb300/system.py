@@ -325,6 +325,67 @@ class DeviceTree:
                          first=_to_dev(first, device), count=_to_dev(count, device), perm=_to_dev(perm, device))
         self._tree = tree
 
+    @classmethod
+    def build(cls, pos, mass, leaf_size, n_crit, use_quad=True, device="cuda", mac="theta", delta=0.0, m_limit=0.0,
+              cap_cell=None, stream=None):
+        """The tree built on the device (otoo_devtree_build) from positions
+        [n][3] FP64 and masses [n] FP32 (numpy arrays or device tensors,
+        caller order); the cell capacity grows until the tree fits."""
+        import torch
+        self = cls.__new__(cls)
+        if torch.is_tensor(pos):
+            pos_d = pos.to(device=device, dtype=torch.float64).contiguous()
+        else:
+            pos_d = torch.from_numpy(np.ascontiguousarray(pos, dtype=np.float64)).to(device)
+        if torch.is_tensor(mass):
+            mass_d = mass.to(device=device, dtype=torch.float32).contiguous()
+        else:
+            mass_d = torch.from_numpy(np.ascontiguousarray(mass, dtype=np.float32)).to(device)
+        n = int(pos_d.shape[0])
+        cap = int(cap_cell) if cap_cell else max(1024, n)
+        st = _stream(stream, device)
+        u8, i32, i64 = torch.uint8, torch.int32, torch.int64
+        while True:
+            b = dict(src=torch.empty((n + cap) * 32, dtype=u8, device=device),
+                     quad=torch.empty(cap * 32, dtype=u8, device=device),
+                     cell=torch.empty(cap * 64, dtype=u8, device=device),
+                     cell64=torch.empty(cap * 96, dtype=u8, device=device),
+                     first=torch.empty(n, dtype=i32, device=device), count=torch.empty(n, dtype=i32, device=device),
+                     perm=torch.empty(n, dtype=i64, device=device), level=torch.empty(cap, dtype=i32, device=device),
+                     status=torch.zeros(2, dtype=i32, device=device))
+            t = L.DevTree()
+            t.n_part, t.cap_cell, t.leaf_size, t.n_crit = n, cap, int(leaf_size), int(n_crit)
+            t.use_quad, t.mac = int(bool(use_quad)), {"theta": L.OTOO_MAC_THETA, "sw": L.OTOO_MAC_SW}[mac]
+            t.delta, t.m_limit = float(delta), float(m_limit)
+            t.src, t.quad, t.cell, t.cell64 = (b[k].data_ptr() for k in ("src", "quad", "cell", "cell64"))
+            t.group_first, t.group_count, t.perm = b["first"].data_ptr(), b["count"].data_ptr(), b["perm"].data_ptr()
+            t.cell_level, t.status = b["level"].data_ptr(), b["status"].data_ptr()
+            nbytes = int(L.load().otoo_devtree_scratch_bytes(n, cap))
+            scratch = torch.empty(nbytes, dtype=u8, device=device)
+            try:
+                L.call("otoo_devtree_build", pos_d.data_ptr(), mass_d.data_ptr(), ctypes.byref(t), scratch.data_ptr(),
+                       nbytes, st)
+                break
+            except L.OtooError as e:
+                if e.code != L.OTOO_ENOMEM:
+                    raise
+                cap *= 2
+        del scratch
+        nc, G = int(t.n_cell), int(t.n_groups)
+        self.n_part, self.n_cell, self.n_groups = n, nc, G
+        self.n_src = n + nc
+        self.use_quad = bool(use_quad)
+        self.n_crit = int(n_crit)
+        self.device = device
+        self.mac = t.mac
+        self.depth = int(t.depth)
+        self.root_lo, self.root_side = np.array(t.root_lo), float(t.root_side)
+        self.bufs = dict(src=b["src"][:(n + nc) * 32], quad=b["quad"][:nc * 32] if use_quad else None,
+                         cell=b["cell"][:nc * 64], cell64=b["cell64"][:nc * 96], first=b["first"][:G],
+                         count=b["count"][:G], perm=b["perm"], level=b["level"][:nc])
+        self._tree = None
+        return self
+
     def h2d_bytes(self):
         return sum(b.numel() for b in self.bufs.values() if b is not None)
 
