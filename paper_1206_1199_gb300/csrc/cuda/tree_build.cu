@@ -55,6 +55,7 @@ constexpr int kBmaxChunk = 2048;                // particles per b_max work item
 
 // status bits
 constexpr uint32_t kTreeBadInput = 1u;   // a non-finite position or a mass <= 0
+constexpr uint32_t kTreeBadSort = 2u;    // the sorted order indexed outside the particles
 
 struct Geom {
     double lo[3], S, h, scale;
@@ -221,11 +222,16 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __res
 
 __global__ void k_permute(const double* __restrict__ pos, const float* __restrict__ mass,
                           const uint32_t* __restrict__ order, int64_t n, const Geom* __restrict__ g,
-                          otoo_src* __restrict__ src, int64_t* __restrict__ perm, int32_t* __restrict__ gq)
+                          otoo_src* __restrict__ src, int64_t* __restrict__ perm, int32_t* __restrict__ gq,
+                          uint32_t* __restrict__ status)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t i = order[k];
+    if (i >= n) {  // the sort is a permutation; this only guards the reads
+        atomicOr(status, kTreeBadSort);
+        return;
+    }
     otoo_src s;
     s.x = pos[3 * i];
     s.y = pos[3 * i + 1];
@@ -740,7 +746,8 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
         CUDA_TRY(cudaGetLastError());
         cur ^= 1;
     }
-    k_permute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, mass, vals[cur], n, geom, t->src, t->perm, gq);
+    k_permute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, mass, vals[cur], n, geom, t->src, t->perm, gq,
+                                                          status);
     CUDA_TRY(cudaGetLastError());
     uint32_t st = 0;
     CUDA_TRY(cudaMemcpyAsync(&st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -748,6 +755,7 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
     CUDA_TRY(cudaMemcpyAsync(&hg, geom, sizeof(hg), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (st & kTreeBadInput) return set_error(OTOO_EINVAL, "otoo_devtree_build: non-finite position or mass <= 0");
+    if (st & kTreeBadSort) return set_error(OTOO_EDEVICE, "otoo_devtree_build: sort produced an invalid order");
     const uint64_t* skeys = keys[cur];
 
     // cells, level by level (the host reads each level's size)
