@@ -82,8 +82,9 @@ def check_tree(pos, mass, leaf, ncrit, use_quad=True, mac="theta", delta=0.0, m_
     assert np.all(np.abs(d64["com"] - com) <= 1e-13 * (side[:, None] + np.abs(com)))
     if use_quad:
         # FP32 copies of quadrupoles summed in another order: a few FP32
-        # ulps of the cell's second-moment scale (3 B_2 bounds every entry)
-        scale = np.abs(e["quad"][m]).max(1) + 3 * e["b2"][m] + 1e-300
+        # ulps of the cell's second-moment scale (3 B_2 bounds every entry),
+        # and FP64 rounding of offsets from the centre of mass (m side^2)
+        scale = np.abs(e["quad"][m]).max(1) + 3 * e["b2"][m] + 1e-6 * e["cmass"][m] * side ** 2
         qd = np.stack([d["quad"][k] for k in ("xx", "yy", "zz", "xy", "xz", "yz")], 1).astype(np.float64)
         assert np.all(np.abs(qd - e["quad"][m]) <= 1e-6 * scale[:, None])
     if mac == "sw":
