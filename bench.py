@@ -48,6 +48,7 @@ def parse():
                     help="skip the batched 64-system step and the learned-angle comparison")
     ap.add_argument("--skip-walk", action="store_true", help="skip the device-walk step")
     ap.add_argument("--skip-sw", action="store_true", help="skip the absolute-MAC (delta) sweep")
+    ap.add_argument("--skip-step", action="store_true", help="skip the whole step on the device")
     return ap.parse_args()
 
 
@@ -293,6 +294,9 @@ def run_ours(args):
     if rank == 0 and not args.skip_walk:
         line["device_walk"] = guarded_extra(run_device_walk, args, dev_name, tree, w, tune, lists, a32, stream,
                                             t2 - t1, t3 - t2)
+    if rank == 0 and not args.skip_step:
+        line["device_step"] = guarded_extra(run_device_step, args, dev_name, pos, mass, w, tune, tree, lists, a32,
+                                            stream, t1 - t0)
     if rank == 0 and not args.skip_sw and errors is not None:
         line["sw_sweep"] = guarded_extra(run_sw_sweep, args, dev_name, tree, w, tune, stream, sub, ad)
     if rank == 0 and not args.skip_cpu:
@@ -368,6 +372,76 @@ def run_device_walk(args, dev_name, tree, w, tune, lists, a32, stream, host_walk
             "group_counts_equal_host": same, "n_list": int(dl.n_list),
             "interactions_equal_host": bool(dl.interactions == lists.interactions),
             "items": int(dp.n_items), "fp32_vs_host_lists_acc_rms": rms, "fp32_vs_host_lists_acc_max": mx}
+
+
+def run_device_step(args, dev_name, pos, mass, w, tune, tree, lists, a32, stream, host_tree_s):
+    """The whole step on the device, from host positions to host
+    accelerations: copy positions and masses in (pinned memory), build the
+    tree (otoo_devtree_build), walk, plan, force, copy accelerations and
+    potentials out.  Timed per step by the host clock (the tree build and
+    the walk read a few sizes back); CUDA events split the device time.
+    Checked against the host build: cell count, groups, per-group entry
+    counts, FP32 accelerations."""
+    import torch
+
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import system as S
+    n = len(pos)
+    pos_h = torch.from_numpy(np.ascontiguousarray(pos, np.float64)).pin_memory()
+    mass_h = torch.from_numpy(np.ascontiguousarray(mass, np.float32)).pin_memory()
+    pos_d = torch.empty_like(pos_h, device=dev_name)
+    mass_d = torch.empty_like(mass_h, device=dev_name)
+    acc_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    pot_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
+    pot = torch.empty(n, dtype=torch.float64, device=dev_name)
+    pool = S.BufferPool(dev_name)
+    cap = [max(1024, n // 2)]
+
+    def one():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record(stream)
+        pos_d.copy_(pos_h, non_blocking=True)
+        mass_d.copy_(mass_h, non_blocking=True)
+        ev[1].record(stream)
+        dt = S.DeviceTree.build(pos_d, mass_d, w["leaf_size"], w["n_crit"], w["use_quad"], dev_name,
+                                cap_cell=cap[0], stream=stream)
+        cap[0] = max(cap[0], dt.n_cell)
+        ev[2].record(stream)
+        dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool)
+        ev[3].record(stream)
+        dp = dl.plan(tune, stream=stream)
+        S.force(S.DeviceStep(dl, dp), acc, pot, L.OTOO_FP32K, tune, stream=stream, check=False)
+        ev[4].record(stream)
+        acc_h.copy_(acc, non_blocking=True)
+        pot_h.copy_(pot, non_blocking=True)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+        return dt, dl, ev
+
+    for _ in range(2):
+        one()
+    k = max(3, min(args.steps, 8))
+    times, walls = [], []
+    for _ in range(k):
+        t0 = time.perf_counter()
+        dt, dl, ev = one()
+        walls.append(time.perf_counter() - t0)
+        times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(5)])
+    med = np.median(np.array(times), axis=0)
+    wall = float(np.median(walls))
+    hg, gd = lists.groups, dl.groups
+    same_groups = bool(np.array_equal(gd["first"], hg["first"]) and np.array_equal(gd["count"], hg["count"]))
+    same_counts = float(np.mean((gd["n_cell"] == hg["n_cell"]) & (gd["n_part"] == hg["n_part"])))
+    rms, mx = rel_err(acc_h.numpy(), a32)
+    return {"step_wall_ms": wall * 1e3, "steps": k, "h2d_ms": float(med[0]), "tree_ms": float(med[1]),
+            "walk_ms": float(med[2]), "plan_force_ms": float(med[3]), "d2h_ms": float(med[4]),
+            "value": dl.interactions / wall, "unit": "interactions/s",
+            "h2d_bytes_per_step": int(n * 28), "d2h_bytes_per_step": int(n * 32),
+            "host_tree_ms": host_tree_s * 1e3, "n_cell": int(dt.n_cell),
+            "n_cell_equal_host": bool(dt.n_cell == tree.export()["n_cell"]), "groups_equal_host": same_groups,
+            "group_counts_equal_fraction": same_counts, "interactions": int(dl.interactions),
+            "fp32_vs_host_path_acc_rms": rms, "fp32_vs_host_path_acc_max": mx}
 
 
 def run_sw_sweep(args, dev_name, tree, w, tune, stream, sub, ad):
