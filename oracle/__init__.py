@@ -12,6 +12,10 @@ with the GPU path (the two sides read the same seeded inputs and nothing else).
                   and the force over each group's walk (Sections II, III-B,
                   III-C, III-D), monopole or quadrupole cells.
 * ``sw_radius``   B_2 (Eq. B2), b_max and r_b (Eq. SW_MAC) of one particle set.
+* ``sph_kernel`` / ``sph_density``  the SPH kernel W and the density
+                  rho_i = sum_j m_j W(|x_i - x_j|, h_j) (Eq. SPH_SUM) by direct
+                  summation; ``Tree.sph_density`` through the group walk with
+                  the bounding radius of Eq. SPH_RAD.
 * ``cell_moments`` / ``cell_field``  the multipole of one particle set and
                   its field at a point.
 * ``errors``      relative force error statistics against a reference.
@@ -73,6 +77,12 @@ def _load():
         lib.oracle_tree_eval.restype = ctypes.c_int
         lib.oracle_sw_radius.argtypes = [_dp, _dp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
         lib.oracle_sw_radius.restype = ctypes.c_int
+        lib.oracle_sph_kernel.argtypes = [ctypes.c_double, ctypes.c_double, _dp]
+        lib.oracle_sph_kernel.restype = ctypes.c_int
+        lib.oracle_sph_density_direct.argtypes = [_i64, _dp, _dp, _dp, _i64, _lp, _dp]
+        lib.oracle_sph_density_direct.restype = ctypes.c_int
+        lib.oracle_tree_sph_density.argtypes = [ctypes.c_void_p, _dp, _dp, _lp, _lp, _lp]
+        lib.oracle_tree_sph_density.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -125,6 +135,29 @@ def sw_radius(pos, mass, delta, m_limit=0.0, s_root=1.0):
                             _d(out)) != 0:
         raise ValueError("empty cell")
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def sph_kernel(r, h):
+    """W(r, h) of the SPH sums (M4 cubic spline, support radius h)."""
+    lib = _load()
+    w = np.zeros(1)
+    if lib.oracle_sph_kernel(float(r), float(h), _d(w)) != 0:
+        raise ValueError("bad r or h")
+    return float(w[0])
+
+
+def sph_density(pos, mass, h, targets=None):
+    """rho_i = sum_j m_j W(|x_i - x_j|, h_j) by direct summation."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    n = pos.shape[0]
+    tgt = np.arange(n, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    rho = np.zeros(tgt.shape[0])
+    if lib.oracle_sph_density_direct(n, _d(pos), _d(mass), _d(h), tgt.shape[0], _l(tgt), _d(rho)) != 0:
+        raise ValueError("oracle_sph_density_direct: bad arguments")
+    return rho
 
 
 def cell_field(x, m, com, q, use_quad, eps):
@@ -187,6 +220,23 @@ class Tree:
             raise ValueError("oracle_tree_eval failed (%d)" % rc)
         return dict(acc=acc, pot=pot, key=key, count=cnt, n_cell=ncell, n_part=npart,
                     mass=gmass, interactions=int(inter[0]))
+
+
+def _tree_sph_density(self, h):
+    """Density through the group walk (Eq. SPH_RAD); returns dict with rho
+    (caller order), per-group key / n_part and the pair count."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    assert h.shape == (self.n,)
+    rho = np.full(self.n, np.nan)
+    key = np.zeros(self.n_groups, np.int64)
+    npart = np.zeros(self.n_groups, np.int64)
+    pairs = np.zeros(1, np.int64)
+    if self._lib.oracle_tree_sph_density(self._h, _d(h), _d(rho), _l(key), _l(npart), _l(pairs)) != 0:
+        raise ValueError("oracle_tree_sph_density failed")
+    return dict(rho=rho, key=key, n_part=npart, pairs=int(pairs[0]))
+
+
+Tree.sph_density = _tree_sph_density
 
 
 def errors(acc, pot, acc_ref, pot_ref):

@@ -28,6 +28,16 @@
  *                      particle entries.
  *   oracle_sw_radius   B_2, b_max and the bounding radius r_b of one particle
  *                      set (Eq. B2, Eq. SW_MAC).
+ *   oracle_sph_*       SPH sums (Section II, "Bounding Radius for SPH"): the
+ *                      density rho_i = sum_j m_j W(|x_i - x_j|, h_j) (Eq.
+ *                      SPH_SUM with A = m) by direct summation and by the
+ *                      group walk with the bounding radius r_SPH of Eq.
+ *                      SPH_RAD (cells whose sphere misses the group box are
+ *                      skipped; particles of the other leaves are summed).
+ *                      Readings: the M4 cubic spline with support radius h
+ *                      (the paper: W is bell-shaped and vanishes beyond h),
+ *                      scatter form (each source's own h_j, as r_SPH uses
+ *                      it), the source itself included.
  *
  * Everything is written for a reader to check by eye: no blocking, no fusion,
  * summation in plain loops.  Compile with -ffp-contract=off so that no FMA
@@ -40,6 +50,7 @@
 
 #define ORACLE_LEVELS 21                 /* 2^21 grid cells per axis (63-bit keys) */
 #define ORACLE_GRID   2097152.0          /* 2^21 */
+#define ORACLE_PI     3.14159265358979323846
 
 /* ------------------------------------------------------------------------- */
 /* C1: direct sum (reading of Section II: particle-particle interaction).     */
@@ -84,6 +95,51 @@ int oracle_direct(int64_t n_src, const double* pos, const double* mass,
         acc[3 * t + 1] = a[1];
         acc[3 * t + 2] = a[2];
         pot[t] = p;
+    }
+    return 0;
+}
+
+/* M4 cubic spline with support radius h, normalised to unit volume in 3D:
+   W = 8 / (pi h^3) * w(q), q = r / h,
+   w = 1 - 6 q^2 + 6 q^3 for q <= 1/2, 2 (1 - q)^3 for 1/2 < q < 1, 0 beyond. */
+static double sph_w(double r, double h)
+{
+    double q = r / h;
+    double w;
+    if (q <= 0.5)
+        w = 1.0 - 6.0 * q * q + 6.0 * q * q * q;
+    else if (q < 1.0)
+        w = 2.0 * (1.0 - q) * (1.0 - q) * (1.0 - q);
+    else
+        w = 0.0;
+    return 8.0 / (ORACLE_PI * h * h * h) * w;
+}
+
+int oracle_sph_kernel(double r, double h, double* w)
+{
+    if (!(h > 0.0) || r < 0.0) return -1;
+    *w = sph_w(r, h);
+    return 0;
+}
+
+/* rho[t] = sum over all sources j of m_j W(|x_i - x_j|, h_j), i = tgt[t]
+   (the source i itself included). */
+int oracle_sph_density_direct(int64_t n, const double* pos, const double* mass, const double* h, int64_t n_tgt,
+                              const int64_t* tgt, double* rho)
+{
+    if (n <= 0 || n_tgt < 0) return -1;
+    for (int64_t j = 0; j < n; ++j)
+        if (!(h[j] > 0.0)) return -1;
+    int64_t t;
+#pragma omp parallel for schedule(static)
+    for (t = 0; t < n_tgt; ++t) {
+        int64_t i = tgt[t];
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double dx = pos[3 * j] - pos[3 * i], dy = pos[3 * j + 1] - pos[3 * i + 1], dz = pos[3 * j + 2] - pos[3 * i + 2];
+            s += mass[j] * sph_w(sqrt(dx * dx + dy * dy + dz * dz), h[j]);
+        }
+        rho[t] = s;
     }
     return 0;
 }
@@ -250,6 +306,7 @@ typedef struct Node {
     struct Node* child[8];     /* children in octant order, NULL where empty */
     double m, com[3], q[6];
     double b2, bmax;           /* spread about the centre of mass (Eq. B2) */
+    double rsph;               /* SPH bounding radius (Eq. SPH_RAD), set per call */
     double cube_lo[3], side, gc[3];   /* geometry for the MAC */
 } Node;
 
@@ -653,5 +710,101 @@ int oracle_tree_eval(const void* handle, double theta, const double* theta_by_ke
         free(ent.part);
     }
     if (interactions) *interactions = total;
+    return err ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* SPH sums through the tree (Section II, Bounding Radius for SPH).          */
+/* ------------------------------------------------------------------------- */
+
+/* r_SPH = max over the cell's particles of |com - x_j| + h_j (Eq. SPH_RAD). */
+static void set_rsph(const OracleTree* t, Node* c, const double* h)
+{
+    double r = 0.0;
+    for (int64_t k = c->begin; k < c->end; ++k) {
+        int64_t j = t->idx[k];
+        double dx = c->com[0] - t->pos[3 * j], dy = c->com[1] - t->pos[3 * j + 1], dz = c->com[2] - t->pos[3 * j + 2];
+        double v = sqrt(dx * dx + dy * dy + dz * dz) + h[j];
+        if (v > r) r = v;
+    }
+    c->rsph = r;
+    for (int k = 0; k < c->n_child; ++k) set_rsph(t, c->child[k], h);
+}
+
+/* The SPH walk: a cell whose sphere (centre of mass, r_SPH) lies farther
+   than r_SPH from the group box holds no neighbour of any group particle and
+   is skipped; other cells open; leaves give their particles. */
+static int sph_walk(const OracleTree* t, const Node* c, const double blo[3], const double bhi[3], Entries* e)
+{
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double d = 0.0;
+        if (blo[a] - c->com[a] > d) d = blo[a] - c->com[a];
+        if (c->com[a] - bhi[a] > d) d = c->com[a] - bhi[a];
+        d2 += d * d;
+    }
+    if (sqrt(d2) > c->rsph) return 0;
+    if (c->n_child == 0) {
+        for (int64_t k = c->begin; k < c->end; ++k)
+            if (push_part(e, t->idx[k])) return -1;
+        return 0;
+    }
+    for (int k = 0; k < c->n_child; ++k)
+        if (sph_walk(t, c->child[k], blo, bhi, e)) return -1;
+    return 0;
+}
+
+/* Density of every particle through the tree's groups (caller order, rho
+   [n]); per-group statistics g_key (lowest particle index), g_npart
+   (particle entries); *pairs = sum over groups of count * entries. */
+int oracle_tree_sph_density(void* handle, const double* h, double* rho, int64_t* g_key, int64_t* g_npart,
+                            int64_t* pairs)
+{
+    OracleTree* t = (OracleTree*)handle;
+    if (!t) return -1;
+    for (int64_t j = 0; j < t->n; ++j)
+        if (!(h[j] > 0.0)) return -1;
+    set_rsph(t, t->root, h);
+    int64_t total = 0;
+    int err = 0;
+    int64_t g;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total) reduction(| : err)
+    for (g = 0; g < t->n_groups; ++g) {
+        int64_t b = t->grp_begin[g], e_ = t->grp_end[g];
+        double blo[3], bhi[3];
+        int64_t key = t->idx[b];
+        for (int a = 0; a < 3; ++a) blo[a] = bhi[a] = t->pos[3 * t->idx[b] + a];
+        for (int64_t k = b; k < e_; ++k) {
+            int64_t i = t->idx[k];
+            if (i < key) key = i;
+            for (int a = 0; a < 3; ++a) {
+                if (t->pos[3 * i + a] < blo[a]) blo[a] = t->pos[3 * i + a];
+                if (t->pos[3 * i + a] > bhi[a]) bhi[a] = t->pos[3 * i + a];
+            }
+        }
+        Entries ent;
+        memset(&ent, 0, sizeof(ent));
+        if (sph_walk(t, t->root, blo, bhi, &ent)) {
+            err |= 1;
+            free(ent.part);
+            continue;
+        }
+        if (g_key) g_key[g] = key;
+        if (g_npart) g_npart[g] = ent.n_part;
+        total += (e_ - b) * ent.n_part;
+        for (int64_t k = b; k < e_; ++k) {
+            int64_t i = t->idx[k];
+            double s = 0.0;
+            for (int64_t q = 0; q < ent.n_part; ++q) {
+                int64_t j = ent.part[q];
+                double dx = t->pos[3 * j] - t->pos[3 * i], dy = t->pos[3 * j + 1] - t->pos[3 * i + 1],
+                       dz = t->pos[3 * j + 2] - t->pos[3 * i + 2];
+                s += t->mass[j] * sph_w(sqrt(dx * dx + dy * dy + dz * dz), h[j]);
+            }
+            rho[i] = s;
+        }
+        free(ent.part);
+    }
+    if (pairs) *pairs = total;
     return err ? -2 : 0;
 }

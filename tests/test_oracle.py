@@ -284,6 +284,58 @@ def test_sw_tree_error_bound_and_cost():
     np.testing.assert_allclose(r["acc"], a2, rtol=1e-10, atol=1e-12)
 
 
+# ---- SPH sums (Section II, Bounding Radius for SPH; Eq. SPH_SUM, SPH_RAD) ----
+
+
+def test_sph_kernel_shape_and_normalisation():
+    integrate = pytest.importorskip("scipy.integrate")
+    for h in (0.3, 1.0, 2.5):
+        c = 8.0 / (math.pi * h ** 3)
+        assert oracle.sph_kernel(0.0, h) == pytest.approx(c, rel=1e-15)
+        assert oracle.sph_kernel(h / 2, h) == pytest.approx(c / 4, rel=1e-15)
+        assert oracle.sph_kernel(h, h) == 0.0 and oracle.sph_kernel(1.5 * h, h) == 0.0
+        # unit volume integral; value and slope continuous at q = 1/2
+        vol = integrate.quad(lambda r: 4 * math.pi * r * r * oracle.sph_kernel(r, h), 0, h, points=[h / 2])[0]
+        assert vol == pytest.approx(1.0, abs=1e-10)
+        e = 1e-7 * h
+        left = (oracle.sph_kernel(h / 2 - e, h) - oracle.sph_kernel(h / 2 - 2 * e, h)) / e
+        right = (oracle.sph_kernel(h / 2 + 2 * e, h) - oracle.sph_kernel(h / 2 + e, h)) / e
+        assert left == pytest.approx(right, rel=1e-4)
+        assert left == pytest.approx(c * -1.5 / h, rel=1e-4)
+
+
+def test_sph_density_closed_forms():
+    # two particles: rho_1 = m_1 W(0, h_1) + m_2 W(d, h_2) (scatter form)
+    pos = np.array([[0.0, 0.0, 0.0], [0.3, 0.4, 0.0]])
+    m = np.array([2.0, 3.0])
+    h = np.array([0.2, 0.8])
+    rho = oracle.sph_density(pos, m, h)
+    assert rho[0] == pytest.approx(2.0 * oracle.sph_kernel(0, 0.2) + 3.0 * oracle.sph_kernel(0.5, 0.8), rel=1e-15)
+    assert rho[1] == pytest.approx(3.0 * oracle.sph_kernel(0, 0.8), rel=1e-15)   # 0.5 > h_1 = 0.2
+    # a cubic lattice of unit masses with spacing a: rho = 1 / a^3 inside
+    k, a = 16, 1.0 / 16
+    g = (np.arange(k) + 0.5) * a
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    inner = np.nonzero(np.all(np.abs(pos - 0.5) < 0.2, axis=1))[0]
+    for f in (2.0, 2.5, 3.0):
+        rho = oracle.sph_density(pos, np.ones(len(pos)), np.full(len(pos), f * a), targets=inner)
+        assert np.all(np.abs(rho * a ** 3 - 1.0) < 5e-3)
+
+
+@pytest.mark.parametrize("model,n,leaf,ncrit", [("plummer", 4000, 8, 32), ("hernquist", 5000, 1, 64)])
+def test_sph_tree_density_is_the_direct_sum(model, n, leaf, ncrit):
+    """The walk only skips cells that hold no neighbour (Eq. SPH_RAD), so the
+    tree density is the direct sum up to summation order, from far fewer
+    pairs."""
+    pos, mass = ic.make(model, n, 36)
+    mass = mass.astype(np.float64)
+    h = 0.02 + 0.3 * np.random.default_rng(1).random(n) * np.minimum(1.0, np.linalg.norm(pos, axis=1))
+    r = oracle.Tree(pos, mass, leaf, ncrit).sph_density(h)
+    d = oracle.sph_density(pos, mass, h)
+    np.testing.assert_allclose(r["rho"], d, rtol=1e-12, atol=0)
+    assert r["pairs"] < 0.2 * n * n
+
+
 from oracle import mlp as omlp  # noqa: E402
 
 
