@@ -56,13 +56,14 @@ extern "C" {
 /* acceptance rule of the walk (otoo_params.mac) */
 #define OTOO_MAC_THETA 0  /* opening angle theta (group MAC of Barnes 1990, Section III-D) */
 #define OTOO_MAC_SW    1  /* Salmon-Warren absolute MAC, Section II-B Eq. SW_MAC */
+#define OTOO_MAC_SPH   2  /* SPH neighbours (Section II, Eq. SPH_RAD): lists of particles only */
 
 typedef struct otoo_params {
     double theta;                  /* opening angle; 0 = open every cell (direct sum) */
     int32_t leaf_size;             /* max particles per tree leaf (>= 1) */
     int32_t n_crit;                /* max particles per group (>= 1, <= 1024) */
     int32_t use_quad;              /* 1 = cells carry a quadrupole */
-    int32_t mac;                   /* OTOO_MAC_THETA or OTOO_MAC_SW */
+    int32_t mac;                   /* OTOO_MAC_THETA, OTOO_MAC_SW or OTOO_MAC_SPH */
     double eps;                    /* Plummer softening length (> 0) */
     const float* theta_per_group;  /* host, NULL = fixed theta; else one angle per group
                                       in the group order of a previous call on the
@@ -71,6 +72,8 @@ typedef struct otoo_params {
                                       G = 1); 0 = accept no cell */
     double m_limit;                /* OTOO_MAC_SW: cells heavier than this are never
                                       accepted (Section III-C); <= 0 = no limit */
+    const float* h_sph;            /* OTOO_MAC_SPH: host, one neighbour radius h > 0 per
+                                      particle, caller order */
 } otoo_params;
 
 typedef struct otoo_tune {
@@ -202,8 +205,11 @@ int otoo_build_tree(const double* pos, const float* mass, int64_t n,
    d_min > r_b = b_max / 2 + sqrt(b_max^2 / 4 + sqrt(3 B_2 / delta)) (Eq.
    SW_MAC; B_2 = sum m |x - com|^2, Eq. B2; b_max = max |x - com|), with r_b
    = 2 S_root for cells heavier than m_limit (S_root: root cube side), and
-   the group records carry theta = 0.  Rejected leaves contribute their
-   particles.  Errors: OTOO_EINVAL (eps <= 0, n_crit < 1 or > 1024, theta < 0,
+   the group records carry theta = 0.  With OTOO_MAC_SPH a cell whose
+   r_SPH = max_j (|x_j - com| + h_j) (Eq. SPH_RAD) is smaller than d_min is
+   skipped (it holds no neighbour of any group particle) instead of entered,
+   so the lists hold particles only (n_cell = 0).  Rejected leaves contribute
+   their particles.  Errors: OTOO_EINVAL (eps <= 0, n_crit < 1 or > 1024, theta < 0,
    unknown mac, delta < 0 or not finite), OTOO_ENOMEM. */
 int otoo_make_groups_and_lists(const otoo_tree* tree, const otoo_params* params,
                                otoo_lists** out);
@@ -368,7 +374,8 @@ typedef struct otoo_wcell {
     int32_t child0, nchild;        /* children [child0, child0 + nchild), nchild = 0 for a leaf */
     int32_t begin, end;            /* tree-order particle range */
     float rb;                      /* OTOO_MAC_SW: bounding radius r_b rounded (infinite when
-                                      delta = 0); 0 for the opening angle */
+                                      delta = 0); OTOO_MAC_SPH: r_SPH rounded; 0 for the
+                                      opening angle */
 } otoo_wcell;
 
 /* FP64 geometry of cell k (96 bytes): what the exact test reads. */
@@ -377,7 +384,8 @@ typedef struct otoo_wcell64 {
     double side;                   /* cube side */
     double com[3];                 /* centre of mass */
     double gc[3];                  /* cube centre */
-    double rb;                     /* OTOO_MAC_SW: r_b as the host walk computes it; else 0 */
+    double rb;                     /* OTOO_MAC_SW / OTOO_MAC_SPH: r_b or r_SPH as the host walk
+                                      computes it; else 0 */
     double pad;
 } otoo_wcell64;
 
@@ -397,7 +405,7 @@ int otoo_find_groups(const otoo_tree* tree, int32_t n_crit, int32_t* first, int3
    use_quad = 0); cell [n_cell] and cell64 [n_cell] walk records.  params
    (may be NULL: opening angle) selects the acceptance rule the records are
    for; with OTOO_MAC_SW the records carry r_b for params->delta and
-   params->m_limit. */
+   params->m_limit, with OTOO_MAC_SPH r_SPH for params->h_sph. */
 int otoo_tree_device_arrays(const otoo_tree* tree, int32_t use_quad, const otoo_params* params, otoo_src* src,
                             otoo_quad* quad, otoo_wcell* cell, otoo_wcell64* cell64);
 
@@ -406,7 +414,8 @@ typedef struct otoo_dev_walk {
     int64_t n_part, n_cell;        /* the tree's particles and cells */
     int32_t n_groups;
     int32_t exact;                 /* 1 = every acceptance test in FP64 (no FP32 filter) */
-    int32_t mac;                   /* OTOO_MAC_THETA, or OTOO_MAC_SW (records made for it) */
+    int32_t mac;                   /* OTOO_MAC_THETA, OTOO_MAC_SW or OTOO_MAC_SPH (records made
+                                      for it; OTOO_MAC_SPH enters no cell) */
     int32_t pad;
     double theta;                  /* opening angle when theta_per_group is NULL (>= 0) */
     double eps2;                   /* softening^2, copied into every group record */
@@ -478,8 +487,9 @@ typedef struct otoo_devtree {
     int64_t n_part;                /* particles (>= 1) */
     int64_t cap_cell;              /* capacity of the cell arrays below */
     int32_t leaf_size, n_crit;     /* as in otoo_params */
-    int32_t use_quad, mac;         /* quadrupoles stored or zero; OTOO_MAC_THETA / OTOO_MAC_SW */
+    int32_t use_quad, mac;         /* quadrupoles stored or zero; OTOO_MAC_THETA / _SW / _SPH */
     double delta, m_limit;         /* OTOO_MAC_SW: the walk records' r_b */
+    const float* h_sph;            /* OTOO_MAC_SPH: device [n_part], caller order */
     /* out (host values) */
     int64_t n_cell, n_groups;      /* n_cell = -1 when cap_cell was too small */
     int32_t depth, pad;
@@ -508,6 +518,21 @@ int64_t otoo_devtree_scratch_bytes(int64_t n_part, int64_t cap_cell);
    OTOO_ECUDA. */
 int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* tree, void* scratch,
                        int64_t scratch_bytes, void* stream);
+
+/* ---- SPH density (Section II, Bounding Radius for SPH) ---------------------------
+   rho_i = sum_j m_j W(|x_i - x_j|, h_j) (Eq. SPH_SUM with A = m) over lists
+   made with OTOO_MAC_SPH (particles only), W the M4 cubic spline with
+   support radius h: W = 8 / (pi h^3) w(q), q = r / h, w = 1 - 6 q^2 + 6 q^3
+   (q <= 1/2), 2 (1 - q)^3 (1/2 < q < 1), 0 beyond; the source itself
+   included.  sys: as for otoo_force, with a plan made for these lists (the
+   quad, accel-related fields are not read; sys->split serves as scratch for
+   h in tree order); h: device [n_part] neighbour radii, caller order (the
+   order sys->perm maps to); rho: device [n_part] FP64, written at perm[k]
+   (tree order when perm is NULL); tune->iblock in {1, 2, 4} as in the plan.
+   FP32 pair terms relative to the group centre, FP64 sums across 32-entry
+   tiles and list chunks.  Asynchronous on stream; bad items or list indices
+   set the status word (otoo_check_status). */
+int otoo_sph_density(const otoo_dev_system* sys, const float* h, double* rho, const otoo_tune* tune, void* stream);
 
 /* ---- learned opening angle (multilayer perceptron 6-32-32-1) ---------------- */
 

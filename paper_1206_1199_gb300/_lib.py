@@ -34,11 +34,13 @@ class OtooError(RuntimeError):
 
 OTOO_MAC_THETA = 0
 OTOO_MAC_SW = 1
+OTOO_MAC_SPH = 2
 
 
 class Params(ctypes.Structure):
     _fields_ = [("theta", f64), ("leaf_size", i32), ("n_crit", i32), ("use_quad", i32), ("mac", i32),
-                ("eps", f64), ("theta_per_group", ctypes.POINTER(f32)), ("delta", f64), ("m_limit", f64)]
+                ("eps", f64), ("theta_per_group", ctypes.POINTER(f32)), ("delta", f64), ("m_limit", f64),
+                ("h_sph", vp)]
 
 
 class Tune(ctypes.Structure):
@@ -115,7 +117,7 @@ class DevWalk(ctypes.Structure):
 
 class DevTree(ctypes.Structure):
     _fields_ = [("n_part", i64), ("cap_cell", i64), ("leaf_size", i32), ("n_crit", i32), ("use_quad", i32),
-                ("mac", i32), ("delta", f64), ("m_limit", f64), ("n_cell", i64), ("n_groups", i64), ("depth", i32),
+                ("mac", i32), ("delta", f64), ("m_limit", f64), ("h_sph", vp), ("n_cell", i64), ("n_groups", i64), ("depth", i32),
                 ("pad", i32), ("root_lo", f64 * 3), ("root_side", f64), ("src", vp), ("quad", vp), ("cell", vp),
                 ("cell64", vp), ("group_first", vp), ("group_count", vp), ("perm", vp), ("cell_level", vp),
                 ("status", vp)]
@@ -160,6 +162,7 @@ _SIGS = {
     "otoo_plan_scratch_ints": [i64],
     "otoo_plan_count": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp],
     "otoo_plan_fill": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp, i64, vp, i64, vp, vp],
+    "otoo_sph_density": [ctypes.POINTER(DevSystem), vp, vp, ctypes.POINTER(Tune), vp],
     "otoo_devtree_scratch_bytes": [i64, i64],
     "otoo_devtree_build": [vp, vp, ctypes.POINTER(DevTree), vp, i64, vp],
     "otoo_last_error": [],

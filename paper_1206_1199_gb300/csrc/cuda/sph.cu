@@ -1,0 +1,226 @@
+// SPH density on the device (Section II, "Bounding Radius for SPH"):
+// rho_i = sum_j m_j W(|x_i - x_j|, h_j) (Eq. SPH_SUM with A = m) over the
+// particle lists of the SPH walk (Eq. SPH_RAD), which hold every source j
+// whose support can reach a particle of the group.  Readings: the M4 cubic
+// spline with support radius h, the scatter form (each source's own h_j), the
+// source itself included.
+//
+// Kernels
+//   k_h_tree          h in tree order (through the permutation).
+//   k_density<IB>     one work item (group, target chunk, list chunk) per warp
+//                     from an atomic ticket; 32-entry tiles staged in shared
+//                     memory as (x_j - c, m_j 8/(pi h_j^3), 1/h_j) in FP32
+//                     relative to the group centre c; each lane sums IB
+//                     targets, FP32 within a tile, FP64 across tiles.
+//   k_density_merge   FP64 sum of the list chunks of split groups, in chunk
+//                     order.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../common.h"
+
+using namespace otoo;
+
+namespace {
+
+constexpr int kDW = 4;  // warps per CTA
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kBadItem = 1u;   // same status bits as the force step
+constexpr uint32_t kBadIndex = 2u;
+constexpr float kNorm = 2.546479089470325f;  // 8 / pi
+
+__global__ void k_h_tree(const float* __restrict__ h, const int64_t* __restrict__ perm, int64_t n,
+                         float* __restrict__ ht, uint32_t* __restrict__ status)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t i = perm ? perm[k] : k;
+    if (i < 0 || i >= n) {
+        atomicOr(status, kBadIndex);
+        ht[k] = 1.0f;
+        return;
+    }
+    ht[k] = h[i];
+}
+
+// M4 cubic spline shape w(q), q = r / h (zero for q >= 1).
+__device__ __forceinline__ float w_m4(float q)
+{
+    const float a = 1.0f - q;
+    const float inner = fmaf(q * q, fmaf(6.0f, q, -6.0f), 1.0f);
+    return q <= 0.5f ? inner : (q < 1.0f ? 2.0f * a * a * a : 0.0f);
+}
+
+template <int IB>
+__global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const float* __restrict__ ht,
+                                                      double* __restrict__ rho)
+{
+    __shared__ float4 tp[kDW][32];
+    __shared__ float tih[kDW][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t* counter = sys.counter;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(counter, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= sys.n_items) break;
+        const otoo_item it = sys.items[t];
+        bool ok = it.g >= 0 && it.g < sys.n_groups;
+        otoo_group g{};
+        if (ok) {
+            g = sys.groups[it.g];
+            const int64_t len = (int64_t)g.n_cell + g.n_part;
+            ok = it.i0 >= 0 && it.ni >= 1 && it.ni <= 32 * IB && it.i0 + it.ni <= g.count && it.j0 >= 0 &&
+                 it.j0 <= it.j1 && it.j1 <= len && g.list_off >= 0 && g.list_off + len <= sys.n_list &&
+                 g.first >= 0 && (int64_t)g.first + g.count <= sys.n_part &&
+                 (it.slot < 0 || g.count <= sys.n_crit_max);
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(counter + 1, kBadItem);
+            continue;
+        }
+        float xi[IB], yi[IB], zi[IB];
+        double acc[IB];
+#pragma unroll
+        for (int r = 0; r < IB; ++r) {
+            const int k = lane + 32 * r;
+            acc[r] = 0.0;
+            xi[r] = yi[r] = zi[r] = 0.f;
+            if (k < it.ni) {
+                const otoo_src s = sys.src[g.first + it.i0 + k];
+                xi[r] = (float)(s.x - g.cx);
+                yi[r] = (float)(s.y - g.cy);
+                zi[r] = (float)(s.z - g.cz);
+            }
+        }
+        for (int32_t j = it.j0; j < it.j1; j += 32) {
+            const int32_t jj = j + lane;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            float ih = 0.f;
+            if (jj < it.j1) {
+                const int32_t e = sys.list[g.list_off + jj];
+                if (e >= 0 && e < sys.n_part) {
+                    const otoo_src s = sys.src[e];
+                    const float h = ht[e];
+                    ih = 1.0f / h;
+                    p = make_float4((float)(s.x - g.cx), (float)(s.y - g.cy), (float)(s.z - g.cz),
+                                    s.m * kNorm * ih * ih * ih);
+                } else {
+                    atomicOr(counter + 1, kBadIndex);
+                }
+            }
+            tp[w][lane] = p;
+            tih[w][lane] = ih;
+            __syncwarp();
+            const int cnt = it.j1 - j < 32 ? it.j1 - j : 32;
+            float part[IB];
+#pragma unroll
+            for (int r = 0; r < IB; ++r) part[r] = 0.f;
+            for (int q = 0; q < cnt; ++q) {
+                const float4 pj = tp[w][q];
+                const float ihj = tih[w][q];
+#pragma unroll
+                for (int r = 0; r < IB; ++r) {
+                    const float dx = pj.x - xi[r], dy = pj.y - yi[r], dz = pj.z - zi[r];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float qq = r2 > 0.f ? r2 * rsqrtf(r2) * ihj : 0.f;
+                    part[r] = fmaf(pj.w, w_m4(qq), part[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < IB; ++r) acc[r] += (double)part[r];
+            __syncwarp();
+        }
+#pragma unroll
+        for (int r = 0; r < IB; ++r) {
+            const int k = lane + 32 * r;
+            if (k >= it.ni) continue;
+            const int64_t ti = (int64_t)g.first + it.i0 + k;
+            if (it.slot < 0) {
+                rho[sys.perm ? sys.perm[ti] : ti] = acc[r];
+            } else {
+                sys.partial[((int64_t)it.slot * sys.n_crit_max + it.i0 + k) * 4] = acc[r];
+            }
+        }
+    }
+}
+
+__global__ void k_density_merge(otoo_dev_system sys, double* __restrict__ rho)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= sys.n_splits) return;
+    const otoo_split sp = sys.splits[wid];
+    if (sp.g < 0 || sp.g >= sys.n_groups || sp.slot0 < 0 || sp.n_chunks < 1) {
+        if (lane == 0) atomicOr(sys.counter + 1, kBadItem);
+        return;
+    }
+    const otoo_group g = sys.groups[sp.g];
+    if (g.count > sys.n_crit_max) {
+        if (lane == 0) atomicOr(sys.counter + 1, kBadItem);
+        return;
+    }
+    for (int i = lane; i < g.count; i += 32) {
+        double s = 0.0;
+        for (int c = 0; c < sp.n_chunks; ++c) s += sys.partial[((int64_t)(sp.slot0 + c) * sys.n_crit_max + i) * 4];
+        const int64_t ti = (int64_t)g.first + i;
+        rho[sys.perm ? sys.perm[ti] : ti] = s;
+    }
+}
+
+#define CUDA_TRY(expr)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess) return set_error(OTOO_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));  \
+    } while (0)
+
+template <int IB>
+int launch(const otoo_dev_system* sys, const float* ht, double* rho, cudaStream_t s)
+{
+    int dev = 0, sms = 0, occ = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_density<IB>, kDW * 32, 0));
+    if (occ < 1) occ = 1;
+    int64_t blocks = (int64_t)sms * occ;
+    const int64_t need = ((int64_t)sys->n_items + kDW - 1) / kDW;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    k_density<IB><<<(unsigned)blocks, kDW * 32, 0, s>>>(*sys, ht, rho);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int otoo_sph_density(const otoo_dev_system* sys, const float* h, double* rho, const otoo_tune* tune, void* stream)
+{
+    OTOO_REQUIRE(sys && h && rho && tune, OTOO_EINVAL, "otoo_sph_density: NULL argument");
+    OTOO_REQUIRE(sys->src && sys->groups && sys->list && sys->items && sys->counter && sys->split, OTOO_EINVAL,
+                 "otoo_sph_density: NULL device array");
+    OTOO_REQUIRE(sys->n_part >= 1 && sys->n_groups >= 1 && sys->n_items >= 0 && sys->n_crit_max >= 1, OTOO_EINVAL,
+                 "otoo_sph_density: bad sizes");
+    OTOO_REQUIRE(sys->n_splits == 0 || (sys->splits && sys->partial), OTOO_EINVAL,
+                 "otoo_sph_density: split lists need splits and partial");
+    const int ib = tune->iblock;
+    OTOO_REQUIRE(ib == 1 || ib == 2 || ib == 4, OTOO_EINVAL, "otoo_sph_density: iblock must be 1, 2 or 4");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float* ht = static_cast<float*>(sys->split);
+    CUDA_TRY(cudaMemsetAsync(sys->counter, 0, 2 * sizeof(uint32_t), s));
+    k_h_tree<<<(unsigned)((sys->n_part + 255) / 256), 256, 0, s>>>(h, sys->perm, sys->n_part, ht, sys->counter + 1);
+    CUDA_TRY(cudaGetLastError());
+    if (sys->n_items > 0) {
+        const int r = ib == 1 ? launch<1>(sys, ht, rho, s) : ib == 2 ? launch<2>(sys, ht, rho, s) : launch<4>(sys, ht, rho, s);
+        if (r) return r;
+    }
+    if (sys->n_splits > 0) {
+        k_density_merge<<<(unsigned)((sys->n_splits * 32 + 127) / 128), 128, 0, s>>>(*sys, rho);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return OTOO_OK;
+}
+
+}  // extern "C"

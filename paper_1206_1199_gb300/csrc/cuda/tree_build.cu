@@ -410,8 +410,12 @@ __global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ s
 // prefix over cells of their chunk counts.  One warp per item; the chunk's
 // largest squared distance goes to the cell by an atomic max on its bits
 // (non-negative doubles order like their bit patterns).
+// With h (caller order, through perm) the same pass gives the SPH radius
+// instead: the largest |com - x_j| + h_j (Eq. SPH_RAD), kept as the bits of
+// that non-negative value (not squared).
 __global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restrict__ item_off,
-                       const otoo_src* __restrict__ src, Cells c, Moments mo)
+                       const otoo_src* __restrict__ src, Cells c, Moments mo, const float* __restrict__ h,
+                       const int64_t* __restrict__ perm)
 {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -434,7 +438,8 @@ __global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restric
     for (int64_t i = i0 + lane; i < i1; i += 32) {
         const otoo_src p = src[i];
         const double dx = cx - p.x, dy = cy - p.y, dz = cz - p.z;
-        d2max = fmax(d2max, dx * dx + dy * dy + dz * dz);
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        d2max = fmax(d2max, h ? sqrt(d2) + (double)h[perm[i]] : d2);
     }
     for (int o = 16; o > 0; o >>= 1) d2max = fmax(d2max, __shfl_xor_sync(kFull, d2max, o));
     if (lane == 0) atomicMax(mo.dmax2 + cell, (unsigned long long)__double_as_longlong(d2max));
@@ -492,9 +497,10 @@ __global__ void k_records(RecArgs ra, const Geom* __restrict__ g, Cells c, Momen
     qd.yz = u ? (float)mo.q[6 * cell + 5] : 0.f;
     qd.pad0 = qd.pad1 = 0.f;
     quad[cell] = qd;
-    const bool sw = ra.mac == OTOO_MAC_SW;
-    const double bmax = __dsqrt_rn(__longlong_as_double((long long)mo.dmax2[cell]));
-    const double rb = sw ? sw_radius(mo.b2[cell], bmax, m, ra.delta, ra.m_limit, g->S) : 0.0;
+    const double dm = __longlong_as_double((long long)mo.dmax2[cell]);
+    const double rb = ra.mac == OTOO_MAC_SW    ? sw_radius(mo.b2[cell], __dsqrt_rn(dm), m, ra.delta, ra.m_limit, g->S)
+                      : ra.mac == OTOO_MAC_SPH ? dm
+                                               : 0.0;
     otoo_wcell w;
     wcell_geometry(com, lo, gc, side, &w);
     w.nchild = c.nchild[cell];
@@ -691,7 +697,9 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
                  "otoo_devtree_build: n_part / cap_cell out of range");
     OTOO_REQUIRE(t->leaf_size >= 1 && t->n_crit >= 1 && t->n_crit <= kMaxGroup, OTOO_EINVAL,
                  "otoo_devtree_build: leaf_size < 1 or n_crit outside [1, %d]", kMaxGroup);
-    OTOO_REQUIRE(t->mac == OTOO_MAC_THETA || t->mac == OTOO_MAC_SW, OTOO_EINVAL, "unknown mac %d", t->mac);
+    OTOO_REQUIRE(t->mac == OTOO_MAC_THETA || t->mac == OTOO_MAC_SW || t->mac == OTOO_MAC_SPH, OTOO_EINVAL,
+                 "unknown mac %d", t->mac);
+    OTOO_REQUIRE(t->mac != OTOO_MAC_SPH || t->h_sph, OTOO_EINVAL, "OTOO_MAC_SPH needs h_sph");
     OTOO_REQUIRE(t->mac != OTOO_MAC_SW || (t->delta >= 0.0 && std::isfinite(t->delta) && std::isfinite(t->m_limit)),
                  OTOO_EINVAL, "delta must be finite and >= 0, m_limit finite");
     OTOO_REQUIRE(t->src && t->quad && t->cell && t->cell64 && t->group_first && t->group_count && t->perm &&
@@ -795,7 +803,8 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
         if (hi > lo) k_moments<<<(unsigned)((hi - lo + 127) / 128), 128, 0, s>>>(lo, hi, t->src, c, mo);
     }
     CUDA_TRY(cudaGetLastError());
-    if (t->mac == OTOO_MAC_SW) {
+    const bool sph = t->mac == OTOO_MAC_SPH;
+    if (t->mac == OTOO_MAC_SW || sph) {
         k_chunks<<<(unsigned)((n_cell + 255) / 256), 256, 0, s>>>(n_cell, c, cnt);
         const int r = scan32(cnt, n_cell, bsum, tot, s);
         if (r) return r;
@@ -803,7 +812,8 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
         CUDA_TRY(cudaMemcpyAsync(&n_items, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         if (n_items > 0)
-            k_bmax<<<(unsigned)((n_items * 32 + 255) / 256), 256, 0, s>>>(n_items, n_cell, cnt, t->src, c, mo);
+            k_bmax<<<(unsigned)((n_items * 32 + 255) / 256), 256, 0, s>>>(n_items, n_cell, cnt, t->src, c, mo,
+                                                                          sph ? t->h_sph : nullptr, t->perm);
         CUDA_TRY(cudaGetLastError());
     }
     RecArgs ra;

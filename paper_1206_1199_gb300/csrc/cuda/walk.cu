@@ -322,7 +322,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
             bf.B += fmaxf(fabsf(bf.bl[k]), fabsf(bf.bh[k]));
             bf.A += fabsf(bf.c32[k]);
         }
-        const bool sw = a.mac == OTOO_MAC_SW;
+        // the absolute MAC and the SPH radius share the test d_min > r_b; an
+        // SPH walk drops the cells that pass it (no neighbour inside)
+        const bool sw = a.mac == OTOO_MAC_SW || a.mac == OTOO_MAC_SPH;
+        const bool drop = a.mac == OTOO_MAC_SPH;
         const double theta = sw ? 0.0 : a.tpg ? (double)a.tpg[g] : a.theta;
         const bool open_all = !sw && !(theta > 0.0);
         // 1/theta within 2^-23 (the filter's margins allow 2^-21)
@@ -421,8 +424,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
                 if (!ok) atomicOr(status, kWalkBadRecord);
             }
             // accepted cells
-            const unsigned am = __ballot_sync(kFull, kind == 1);
-            if (kFill && kind == 1) {
+            const unsigned am = __ballot_sync(kFull, kind == 1 && !drop);
+            if (kFill && kind == 1 && !drop) {
                 const int32_t r = ncell + __popc(am & lt);
                 if (r < want_c) list[off_c + r] = (int32_t)(a.n_part + node);
             }
@@ -744,7 +747,8 @@ int check_walk(const otoo_dev_walk* w)
     OTOO_REQUIRE(w->n_groups >= 1, OTOO_EINVAL, "walk: n_groups < 1");
     OTOO_REQUIRE(w->eps2 > 0.0, OTOO_EINVAL, "walk: eps2 must be > 0");
     OTOO_REQUIRE(w->theta >= 0.0 && w->theta < 1e300, OTOO_EINVAL, "walk: theta must be finite and >= 0");
-    OTOO_REQUIRE(w->mac == OTOO_MAC_THETA || w->mac == OTOO_MAC_SW, OTOO_EINVAL, "walk: unknown mac %d", w->mac);
+    OTOO_REQUIRE(w->mac == OTOO_MAC_THETA || w->mac == OTOO_MAC_SW || w->mac == OTOO_MAC_SPH, OTOO_EINVAL,
+                 "walk: unknown mac %d", w->mac);
     return OTOO_OK;
 }
 

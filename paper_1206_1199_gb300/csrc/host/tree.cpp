@@ -394,6 +394,33 @@ inline bool sw_accept(const otoo_tree* t, int64_t c, const double blo[3], const 
     return std::sqrt(d2) > rb;
 }
 
+// SPH bounding radius of every cell (Eq. SPH_RAD): the largest |com - x_j| +
+// h_j over the cell's particles (h in caller order).
+void sph_radii(const otoo_tree* t, const float* h, std::vector<double>& rb)
+{
+    const int64_t nc = (int64_t)t->cells.size();
+    rb.resize(nc);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t c = 0; c < nc; ++c) {
+        const double* com = &t->c_com[3 * c];
+        double r = 0;
+        for (int64_t j = t->c_begin[c]; j < t->c_end[c]; ++j) {
+            const double dx = com[0] - t->pos[3 * j], dy = com[1] - t->pos[3 * j + 1], dz = com[2] - t->pos[3 * j + 2];
+            const double v = std::sqrt(dx * dx + dy * dy + dz * dz) + (double)h[t->perm[j]];
+            if (v > r) r = v;
+        }
+        rb[c] = r;
+    }
+}
+
+bool valid_h(const float* h, int64_t n)
+{
+    if (!h) return false;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(h[i] > 0.0f) || !std::isfinite(h[i])) return false;
+    return true;
+}
+
 // Sources of the force step: particles in tree order, then cells (centre of
 // mass, mass) and their quadrupoles (zeros for monopole cells).
 void fill_sources(const otoo_tree* t, int use_quad, otoo_src* src, otoo_quad* quad)
@@ -448,7 +475,10 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
     OTOO_REQUIRE(p->eps > 0.0 && std::isfinite(p->eps), OTOO_EINVAL, "eps must be > 0");
     OTOO_REQUIRE(p->n_crit >= 1 && p->n_crit <= kMaxGroup, OTOO_EINVAL, "n_crit out of [1, %d]", kMaxGroup);
     OTOO_REQUIRE(p->theta >= 0.0 && std::isfinite(p->theta), OTOO_EINVAL, "theta must be finite and >= 0");
-    OTOO_REQUIRE(p->mac == OTOO_MAC_THETA || p->mac == OTOO_MAC_SW, OTOO_EINVAL, "unknown mac %d", p->mac);
+    OTOO_REQUIRE(p->mac == OTOO_MAC_THETA || p->mac == OTOO_MAC_SW || p->mac == OTOO_MAC_SPH, OTOO_EINVAL,
+                 "unknown mac %d", p->mac);
+    OTOO_REQUIRE(p->mac != OTOO_MAC_SPH || valid_h(p->h_sph, t->n), OTOO_EINVAL,
+                 "OTOO_MAC_SPH needs h_sph > 0 and finite for every particle");
     OTOO_REQUIRE(p->mac != OTOO_MAC_SW || (p->delta >= 0.0 && std::isfinite(p->delta) && std::isfinite(p->m_limit)),
                  OTOO_EINVAL, "delta must be finite and >= 0, m_limit finite");
     OTOO_REQUIRE(t->n <= INT32_MAX / 2, OTOO_EINVAL, "too many particles for 32-bit list indices");
@@ -469,13 +499,15 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
         L->use_quad = p->use_quad ? 1 : 0;
         L->eps = p->eps;
         L->groups.resize(G);
-        const bool sw = p->mac == OTOO_MAC_SW;
+        const bool sw = p->mac == OTOO_MAC_SW, sph = p->mac == OTOO_MAC_SPH;
         std::vector<double> rb;
         if (sw) {
             rb.resize(nc);
 #pragma omp parallel for schedule(static)
             for (int64_t c = 0; c < nc; ++c)
                 rb[c] = sw_radius(t->c_b2[c], t->c_bmax[c], t->c_mass[c], p->delta, p->m_limit, t->S);
+        } else if (sph) {
+            sph_radii(t, p->h_sph, rb);
         }
         // the walk: one shared list per group (Barnes 1990, Section III-D),
         // entries buffered per thread, then placed in group order
@@ -498,7 +530,7 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
                         blo[a] = std::min(blo[a], t->pos[3 * i + a]);
                         bhi[a] = std::max(bhi[a], t->pos[3 * i + a]);
                     }
-                const double theta = sw ? 0.0 : p->theta_per_group ? (double)p->theta_per_group[g] : p->theta;
+                const double theta = (sw || sph) ? 0.0 : p->theta_per_group ? (double)p->theta_per_group[g] : p->theta;
                 const int64_t start = (int64_t)buf.size();
                 parts.clear();
                 stack.clear();
@@ -507,7 +539,16 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
                 while (!stack.empty()) {
                     const int64_t c = stack.back();
                     stack.pop_back();
-                    if (sw ? sw_accept(t, c, blo, bhi, rb[c]) : mac_accept(t, c, blo, bhi, theta)) {
+                    if (sph) {
+                        // no neighbour of the group in c: skip it (Eq. SPH_RAD)
+                        if (sw_accept(t, c, blo, bhi, rb[c])) continue;
+                        if (t->c_nchild[c] == 0) {
+                            for (int64_t i = t->c_begin[c]; i < t->c_end[c]; ++i) parts.push_back((int32_t)i);
+                        } else {
+                            const int64_t c0 = t->c_child0[c];
+                            for (int k = t->c_nchild[c] - 1; k >= 0; --k) stack.push_back(c0 + k);
+                        }
+                    } else if (sw ? sw_accept(t, c, blo, bhi, rb[c]) : mac_accept(t, c, blo, bhi, theta)) {
                         buf.push_back((int32_t)(n + c));
                         ++ncell;
                     } else if (t->c_nchild[c] == 0) {
@@ -619,8 +660,9 @@ int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, const otoo_par
                             otoo_quad* quad, otoo_wcell* cell, otoo_wcell64* cell64)
 {
     OTOO_REQUIRE(t, OTOO_EINVAL, "otoo_tree_device_arrays: NULL tree");
-    const bool sw = p && p->mac == OTOO_MAC_SW;
-    OTOO_REQUIRE(!p || p->mac == OTOO_MAC_THETA || sw, OTOO_EINVAL, "unknown mac %d", p ? p->mac : 0);
+    const bool sw = p && p->mac == OTOO_MAC_SW, sph = p && p->mac == OTOO_MAC_SPH;
+    OTOO_REQUIRE(!p || p->mac == OTOO_MAC_THETA || sw || sph, OTOO_EINVAL, "unknown mac %d", p ? p->mac : 0);
+    OTOO_REQUIRE(!sph || valid_h(p->h_sph, t->n), OTOO_EINVAL, "OTOO_MAC_SPH needs h_sph > 0 for every particle");
     OTOO_REQUIRE(!sw || (p->delta >= 0.0 && std::isfinite(p->delta) && std::isfinite(p->m_limit)), OTOO_EINVAL,
                  "delta must be finite and >= 0, m_limit finite");
     OTOO_REQUIRE(t->n <= INT32_MAX / 2 && (int64_t)t->cells.size() <= INT32_MAX / 2, OTOO_EINVAL,
@@ -628,6 +670,14 @@ int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, const otoo_par
     return guarded([&]() -> int {
         fill_sources(t, use_quad, src, quad);
         const int64_t nc = (int64_t)t->cells.size();
+        std::vector<double> rb(nc, 0.0);
+        if (sw) {
+#pragma omp parallel for schedule(static)
+            for (int64_t c = 0; c < nc; ++c)
+                rb[c] = sw_radius(t->c_b2[c], t->c_bmax[c], t->c_mass[c], p->delta, p->m_limit, t->S);
+        } else if (sph) {
+            sph_radii(t, p->h_sph, rb);
+        }
         if (cell) {
 #pragma omp parallel for schedule(static)
             for (int64_t c = 0; c < nc; ++c) {
@@ -637,8 +687,7 @@ int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, const otoo_par
                 w.child0 = w.nchild > 0 ? (int32_t)t->c_child0[c] : 0;
                 w.begin = (int32_t)t->c_begin[c];
                 w.end = (int32_t)t->c_end[c];
-                w.rb = sw ? (float)sw_radius(t->c_b2[c], t->c_bmax[c], t->c_mass[c], p->delta, p->m_limit, t->S)
-                          : 0.f;
+                w.rb = (float)rb[c];
             }
         }
         if (cell64) {
@@ -651,7 +700,7 @@ int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, const otoo_par
                     w.gc[a] = t->c_gc[3 * c + a];
                 }
                 w.side = t->c_side[c];
-                w.rb = sw ? sw_radius(t->c_b2[c], t->c_bmax[c], t->c_mass[c], p->delta, p->m_limit, t->S) : 0.0;
+                w.rb = rb[c];
                 w.pad = 0.0;
             }
         }

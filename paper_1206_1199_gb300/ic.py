@@ -223,6 +223,24 @@ WORKLOADS = {
 }
 
 
+def sph_radii(pos, mass, n_ngb=64, model="plummer", a=1.0):
+    """Neighbour radii for the SPH density stage: h_j encloses about n_ngb
+    particles at the model's analytic density, (4 pi / 3) h^3 rho(r_j) / m_j
+    = n_ngb, with rho(r) = 3 M / (4 pi a^3) (1 + r^2/a^2)^(-5/2) for a
+    Plummer sphere and M a / (2 pi r (r + a)^3) for a Hernquist halo (M = 1).
+    FP32, caller order."""
+    r = np.linalg.norm(np.asarray(pos, np.float64), axis=1)
+    if model == "plummer":
+        rho = 3.0 / (4.0 * math.pi * a ** 3) * (1.0 + (r / a) ** 2) ** -2.5
+    elif model == "hernquist":
+        rr = np.maximum(r, 1e-6 * a)
+        rho = a / (2.0 * math.pi * rr * (rr + a) ** 3)
+    else:
+        raise ValueError(model)
+    h = (3.0 * n_ngb * np.asarray(mass, np.float64) / (4.0 * math.pi * rho)) ** (1.0 / 3.0)
+    return h.astype(np.float32)
+
+
 def make(model, n, seed, **kw):
     """Positions and masses of a named model."""
     if model == "plummer":

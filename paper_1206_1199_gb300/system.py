@@ -13,13 +13,22 @@ import numpy as np
 from . import _lib as L
 
 
-def _params(theta, leaf_size, n_crit, use_quad, eps, theta_per_group=None, mac="theta", delta=0.0, m_limit=0.0):
+MAC_KINDS = {"theta": L.OTOO_MAC_THETA, "sw": L.OTOO_MAC_SW, "sph": L.OTOO_MAC_SPH}
+
+
+def _params(theta, leaf_size, n_crit, use_quad, eps, theta_per_group=None, mac="theta", delta=0.0, m_limit=0.0,
+            h_sph=None):
+    """otoo_params; h_sph (OTOO_MAC_SPH) must be a float32 numpy array kept
+    alive by the caller for the call."""
     p = L.Params()
     p.theta = float(theta)
     p.leaf_size = int(leaf_size)
     p.n_crit = int(n_crit)
     p.use_quad = int(bool(use_quad))
-    p.mac = {"theta": L.OTOO_MAC_THETA, "sw": L.OTOO_MAC_SW}[mac]
+    p.mac = MAC_KINDS[mac]
+    if h_sph is not None:
+        assert h_sph.dtype == np.float32 and h_sph.flags.c_contiguous
+        p.h_sph = h_sph.ctypes.data
     p.eps = float(eps)
     p.delta = float(delta)
     p.m_limit = float(m_limit)
@@ -61,10 +70,12 @@ class Tree:
                     b2=L.view(v.cell_b2, np.float64, (nc,)), bmax=L.view(v.cell_bmax, np.float64, (nc,)),
                     tree=self)  # the views borrow the tree's memory: keep it alive
 
-    def lists(self, theta, n_crit, eps, use_quad=True, theta_per_group=None, mac="theta", delta=0.0, m_limit=0.0):
-        """Groups and lists; mac = "theta" (opening angle) or "sw" (absolute
-        MAC with accuracy delta and mass limit m_limit)."""
-        return Lists.make(self, theta, n_crit, eps, use_quad, theta_per_group, mac, delta, m_limit)
+    def lists(self, theta, n_crit, eps, use_quad=True, theta_per_group=None, mac="theta", delta=0.0, m_limit=0.0,
+              h_sph=None):
+        """Groups and lists; mac = "theta" (opening angle), "sw" (absolute
+        MAC with accuracy delta and mass limit m_limit) or "sph" (neighbour
+        lists for the radii h_sph, caller order)."""
+        return Lists.make(self, theta, n_crit, eps, use_quad, theta_per_group, mac, delta, m_limit, h_sph)
 
 
 class Lists:
@@ -82,11 +93,12 @@ class Lists:
 
     @classmethod
     def make(cls, tree, theta, n_crit, eps, use_quad=True, theta_per_group=None, mac="theta", delta=0.0,
-             m_limit=0.0):
+             m_limit=0.0, h_sph=None):
         tpg = None
         if theta_per_group is not None:
             tpg = np.ascontiguousarray(theta_per_group, dtype=np.float32)
-        p = _params(theta, tree.leaf_size, n_crit, use_quad, eps, tpg, mac, delta, m_limit)
+        hs = None if h_sph is None else np.ascontiguousarray(h_sph, dtype=np.float32)
+        p = _params(theta, tree.leaf_size, n_crit, use_quad, eps, tpg, mac, delta, m_limit, hs)
         h = ctypes.c_void_p()
         L.call("otoo_make_groups_and_lists", tree._h, ctypes.byref(p), ctypes.byref(h))
         return cls(h, keep=(tree,))
@@ -235,6 +247,28 @@ def force(dev, accel=None, pot=None, precision=L.OTOO_FP32K, tune=None, stream=N
     return accel, pot
 
 
+def sph_density(dev, h, rho=None, tune=None, stream=None, check=True):
+    """otoo_sph_density on a DeviceSystem or DeviceStep made from SPH lists:
+    h = neighbour radii (caller order; numpy array or device tensor);
+    returns rho [n] FP64 (caller order)."""
+    import torch
+    n = dev.n_part
+    device = dev.bufs["src"].device
+    if torch.is_tensor(h):
+        hd = h.to(device=device, dtype=torch.float32).contiguous()
+    else:
+        hd = torch.from_numpy(np.ascontiguousarray(h, dtype=np.float32)).to(device)
+    if rho is None:
+        rho = torch.empty(n, dtype=torch.float64, device=device)
+    tune = tune if tune is not None else dev.tune
+    st = stream if stream is not None else torch.cuda.current_stream(device)
+    L.call("otoo_sph_density", ctypes.byref(dev.struct), hd.data_ptr(), rho.data_ptr(), ctypes.byref(tune),
+           ctypes.c_void_p(st.cuda_stream))
+    if check:
+        L.call("otoo_check_status", ctypes.byref(dev.struct), ctypes.c_void_p(st.cuda_stream))
+    return rho
+
+
 def force_host(lists, plan, precision=L.OTOO_FP32K, tune=None, stream=None, accel=None, pot=None, view=None):
     """otoo_force_host: host arrays in, host arrays out (caller order)."""
     import torch
@@ -296,7 +330,7 @@ class DeviceTree:
     (otoo_tree_device_arrays), the group ranges (otoo_find_groups) and the
     tree-to-caller permutation."""
 
-    def __init__(self, tree, n_crit, use_quad=True, device="cuda", mac="theta", delta=0.0, m_limit=0.0):
+    def __init__(self, tree, n_crit, use_quad=True, device="cuda", mac="theta", delta=0.0, m_limit=0.0, h_sph=None):
         v = L.TreeView()
         L.call("otoo_tree_export", tree._h, ctypes.byref(v))
         n, nc = int(v.n_part), int(v.n_cell)
@@ -304,7 +338,8 @@ class DeviceTree:
         quad = np.empty(nc, np.dtype(L.Quad))
         cell = np.empty(nc, np.dtype(L.WCell))
         cell64 = np.empty(nc, np.dtype(L.WCell64))
-        p = _params(0.0, tree.leaf_size, n_crit, use_quad, 1.0, None, mac, delta, m_limit)
+        hs = None if h_sph is None else np.ascontiguousarray(h_sph, dtype=np.float32)
+        p = _params(0.0, tree.leaf_size, n_crit, use_quad, 1.0, None, mac, delta, m_limit, hs)
         L.call("otoo_tree_device_arrays", tree._h, int(bool(use_quad)), ctypes.byref(p), src.ctypes.data,
                quad.ctypes.data, cell.ctypes.data, cell64.ctypes.data)
         self.mac = p.mac
@@ -327,7 +362,7 @@ class DeviceTree:
 
     @classmethod
     def build(cls, pos, mass, leaf_size, n_crit, use_quad=True, device="cuda", mac="theta", delta=0.0, m_limit=0.0,
-              cap_cell=None, stream=None):
+              cap_cell=None, stream=None, h_sph=None):
         """The tree built on the device (otoo_devtree_build) from positions
         [n][3] FP64 and masses [n] FP32 (numpy arrays or device tensors,
         caller order); the cell capacity grows until the tree fits."""
@@ -342,6 +377,10 @@ class DeviceTree:
         else:
             mass_d = torch.from_numpy(np.ascontiguousarray(mass, dtype=np.float32)).to(device)
         n = int(pos_d.shape[0])
+        h_d = None
+        if h_sph is not None:
+            h_d = (h_sph.to(device=device, dtype=torch.float32).contiguous() if torch.is_tensor(h_sph)
+                   else torch.from_numpy(np.ascontiguousarray(h_sph, dtype=np.float32)).to(device))
         cap = int(cap_cell) if cap_cell else max(1024, n)
         st = _stream(stream, device)
         u8, i32, i64 = torch.uint8, torch.int32, torch.int64
@@ -355,8 +394,9 @@ class DeviceTree:
                      status=torch.zeros(2, dtype=i32, device=device))
             t = L.DevTree()
             t.n_part, t.cap_cell, t.leaf_size, t.n_crit = n, cap, int(leaf_size), int(n_crit)
-            t.use_quad, t.mac = int(bool(use_quad)), {"theta": L.OTOO_MAC_THETA, "sw": L.OTOO_MAC_SW}[mac]
+            t.use_quad, t.mac = int(bool(use_quad)), MAC_KINDS[mac]
             t.delta, t.m_limit = float(delta), float(m_limit)
+            t.h_sph = h_d.data_ptr() if h_d is not None else None
             t.src, t.quad, t.cell, t.cell64 = (b[k].data_ptr() for k in ("src", "quad", "cell", "cell64"))
             t.group_first, t.group_count, t.perm = b["first"].data_ptr(), b["count"].data_ptr(), b["perm"].data_ptr()
             t.cell_level, t.status = b["level"].data_ptr(), b["status"].data_ptr()

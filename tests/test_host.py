@@ -189,6 +189,25 @@ def test_sw_walk_decisions_match_oracle(model, n, delta, m_limit, ncrit):
         assert e["cmass"][cells].max() <= m_limit
 
 
+@pytest.mark.parametrize("model,n,ncrit,n_ngb", [("plummer", 8000, 64, 32), ("hernquist", 12000, 32, 64)])
+def test_sph_walk_matches_oracle(model, n, ncrit, n_ngb):
+    pos, mass = ic.make(model, n, 37)
+    h = ic.sph_radii(pos, mass, n_ngb, model)
+    t = S.Tree(pos, mass, 8)
+    lists = t.lists(0.0, ncrit, 1.0, False, mac="sph", h_sph=h)
+    r = oracle.Tree(pos, mass, 8, ncrit).sph_density(h.astype(np.float64))
+    g = lists.groups
+    assert np.all(g["n_cell"] == 0)
+    perm = lists.perm
+    keys = np.array([perm[a:a + c].min() for a, c in zip(g["first"], g["count"])])
+    assert dict(zip(keys, g["n_part"])) == dict(zip(r["key"], r["n_part"]))
+    assert lists.interactions == r["pairs"]
+    with pytest.raises(L.OtooError):
+        bad = h.copy()
+        bad[3] = 0.0
+        t.lists(0.0, ncrit, 1.0, False, mac="sph", h_sph=bad)
+
+
 def test_per_group_theta_override():
     pos, mass = ic.plummer(8000, 26)
     t, base = tree_and_lists(pos, mass, 0.5, 64)
