@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--skip-walk", action="store_true", help="skip the device-walk step")
     ap.add_argument("--skip-sw", action="store_true", help="skip the absolute-MAC (delta) sweep")
     ap.add_argument("--skip-step", action="store_true", help="skip the whole step on the device")
+    ap.add_argument("--skip-sph", action="store_true", help="skip the SPH density stage")
     return ap.parse_args()
 
 
@@ -297,6 +298,8 @@ def run_ours(args):
     if rank == 0 and not args.skip_step:
         line["device_step"] = guarded_extra(run_device_step, args, dev_name, pos, mass, w, tune, tree, lists, a32,
                                             stream, t1 - t0)
+    if rank == 0 and not args.skip_sph:
+        line["sph_density"] = guarded_extra(run_sph, args, dev_name, pos, mass, w, stream)
     if rank == 0 and not args.skip_sw and errors is not None:
         line["sw_sweep"] = guarded_extra(run_sw_sweep, args, dev_name, tree, w, tune, stream, sub, ad)
     if rank == 0 and not args.skip_cpu:
@@ -442,6 +445,53 @@ def run_device_step(args, dev_name, pos, mass, w, tune, tree, lists, a32, stream
             "n_cell_equal_host": bool(dt.n_cell == tree.export()["n_cell"]), "groups_equal_host": same_groups,
             "group_counts_equal_fraction": same_counts, "interactions": int(dl.interactions),
             "fp32_vs_host_path_acc_rms": rms, "fp32_vs_host_path_acc_max": mx}
+
+
+def run_sph(args, dev_name, pos, mass, w, stream):
+    """The SPH density stage (Section II, Eq. SPH_SUM, Eq. SPH_RAD) on the
+    same particles, all on the device: tree with r_SPH records, SPH walk,
+    plan, density kernel; neighbour radii enclosing about 64 particles at
+    the model's analytic density.  Checked against the FP64 direct sum on
+    256 targets."""
+    import torch
+
+    import oracle
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import ic
+    from paper_1206_1199_gb300 import system as S
+    h = ic.sph_radii(pos, mass, 64, w["model"])
+    n = len(pos)
+    tune = L.default_tune(w["n_crit"])
+    tune.iblock = 4 if w["n_crit"] > 64 else 2
+    rho = torch.empty(n, dtype=torch.float64, device=dev_name)
+    h_d = torch.from_numpy(h).to(dev_name)
+
+    def one():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        dt = S.DeviceTree.build(pos, mass, w["leaf_size"], w["n_crit"], False, dev_name, mac="sph", h_sph=h_d,
+                                cap_cell=n // 2, stream=stream)
+        ev[1].record(stream)
+        dl = dt.walk(0.0, 1.0, stream=stream)
+        ev[2].record(stream)
+        S.sph_density(S.DeviceStep(dl, dl.plan(tune, stream=stream)), h_d, rho, tune, stream=stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        return dl, ev
+
+    one()
+    times = []
+    for _ in range(3):
+        dl, ev = one()
+        times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+    med = np.median(np.array(times), axis=0)
+    sub = ic.subsample(n, 256, 17)
+    ref = oracle.sph_density(pos, mass, h.astype(np.float64), targets=sub)
+    err = np.abs(rho.cpu().numpy()[sub] - ref) / ref
+    return {"tree_ms": float(med[0]), "walk_ms": float(med[1]), "plan_density_ms": float(med[2]),
+            "pairs": int(dl.interactions), "pairs_per_s": dl.interactions / (med[2] * 1e-3),
+            "mean_list": dl.interactions / n, "n_ngb": 64, "targets": 256, "rel_err_max": float(err.max()),
+            "rel_err_rms": float(np.sqrt(np.mean(err * err)))}
 
 
 def run_sw_sweep(args, dev_name, tree, w, tune, stream, sub, ad):
