@@ -427,8 +427,9 @@ typedef struct otoo_dev_walk {
     const float* theta_per_group;  /* [n_groups] or NULL; a negative angle skips the group */
     uint32_t* counter;             /* scratch, >= 4 uint32: work ticket, status */
     int64_t* totals;               /* >= otoo_walk_totals_len(n_groups) int64: [0] list
-                                      entries, [1] interactions, [2] cell interactions
-                                      (written by otoo_walk_count), then scratch */
+                                      entries, [1] interactions, [2] cell interactions,
+                                      [3] largest n_cell, [4] largest n_part, [5] groups
+                                      beyond their slots (otoo_walk_single), then scratch */
 } otoo_dev_walk;
 
 /* Length of otoo_dev_walk.totals for n_groups groups. */
@@ -449,6 +450,21 @@ int otoo_walk_count(const otoo_dev_walk* walk, otoo_group* groups, void* stream)
    otoo_walk_check_status). */
 int otoo_walk_fill(const otoo_dev_walk* walk, const otoo_group* groups, int32_t* list, int64_t capacity,
                    void* stream);
+
+/* The walk in one pass (the steady state of a time loop, where the list
+   sizes of the previous step bound the next): like otoo_walk_count, and each
+   group's entries go to fixed slots, cells to cell_pool[g * cell_cap ...],
+   particles to part_pool[g * part_cap ...] (device pools of n_groups slots);
+   totals[5] counts the groups with more entries than their slots (their
+   entries are cut, their counts and offsets stay exact: follow with
+   otoo_walk_fill instead of otoo_walk_compact).  otoo_walk_compact then
+   copies the slots into the list at the offsets (nothing when totals[5] > 0
+   or the list is shorter than totals[0]: status set). */
+int otoo_walk_single(const otoo_dev_walk* walk, otoo_group* groups, int32_t* cell_pool, int64_t cell_cap,
+                     int32_t* part_pool, int64_t part_cap, void* stream);
+int otoo_walk_compact(const otoo_dev_walk* walk, const otoo_group* groups, const int32_t* cell_pool,
+                      int64_t cell_cap, const int32_t* part_pool, int64_t part_cap, int32_t* list,
+                      int64_t capacity, void* stream);
 
 /* Reads the walk's status word after a sync: OTOO_EDEVICE when a record
    failed its bounds check, a group's stack overflowed, the two passes

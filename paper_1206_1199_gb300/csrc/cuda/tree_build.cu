@@ -110,17 +110,37 @@ __global__ void __launch_bounds__(256) k_bbox(const double* __restrict__ pos, co
     }
 }
 
-__global__ void k_bbox_final(const long long* __restrict__ part, int nb, Geom* __restrict__ g)
+// One block of 256 threads: each thread folds a stride of the block
+// partials, then the warps and the block reduce; thread 0 sets the cube.
+__global__ void __launch_bounds__(256) k_bbox_final(const long long* __restrict__ part, int nb, Geom* __restrict__ g)
 {
-    if (threadIdx.x != 0) return;
     long long lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) lo[a] = part[a], hi[a] = part[3 + a];
-    for (int b = 1; b < nb; ++b)
+    for (int a = 0; a < 3; ++a) lo[a] = 0x7fffffffffffffffLL, hi[a] = -lo[a] - 1;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
         for (int a = 0; a < 3; ++a) {
             const long long l = part[6 * b + a], h = part[6 * b + 3 + a];
             lo[a] = l < lo[a] ? l : lo[a];
             hi[a] = h > hi[a] ? h : hi[a];
         }
+    __shared__ long long s[6][8];
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long t0 = __shfl_xor_sync(kFull, lo[a], o), t1 = __shfl_xor_sync(kFull, hi[a], o);
+            lo[a] = t0 < lo[a] ? t0 : lo[a];
+            hi[a] = t1 > hi[a] ? t1 : hi[a];
+        }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) s[a][w] = lo[a], s[3 + a][w] = hi[a];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = s[a][0], hi[a] = s[3 + a][0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            lo[a] = s[a][k] < lo[a] ? s[a][k] : lo[a];
+            hi[a] = s[3 + a][k] > hi[a] ? s[3 + a][k] : hi[a];
+        }
+    }
     double mn[3], mx[3];
     for (int a = 0; a < 3; ++a) mn[a] = dval(lo[a]), mx[a] = dval(hi[a]);
     root_cube(mn, mx, g->lo, &g->S, &g->h);
@@ -740,7 +760,7 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
     CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(uint32_t), s));
     const int nbb = (int)std::min<int64_t>(1024, (n + 255) / 256);
     k_bbox<<<nbb, 256, 0, s>>>(pos, mass, n, part, status);
-    k_bbox_final<<<1, 32, 0, s>>>(part, nbb, geom);
+    k_bbox_final<<<1, 256, 0, s>>>(part, nbb, geom);
     k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, geom, keys[0], vals[0]);
     CUDA_TRY(cudaGetLastError());
     const int nblk = (int)((n + kRsTile - 1) / kRsTile);

@@ -36,6 +36,8 @@ constexpr int kMaxLevels = 22;      // tree levels (root level 0 to the 2^21 gri
 constexpr int kScanThreads = 1024;  // scan kernels: threads per CTA
 constexpr int kScanBlock = 2048;    // elements per scan block
 constexpr int kClasses = 128;       // cost classes of the plan's launch order
+constexpr int kTotals = 6;          // walk totals: entries, interactions, cell interactions,
+                                    // largest n_cell, largest n_part, groups beyond their slots
 constexpr unsigned kFull = 0xffffffffu;
 
 // status bits (counter[1])
@@ -262,10 +264,18 @@ __device__ __forceinline__ uint32_t run(int first, int n) { return (uint32_t)fir
 // 33 + kMaxLevels entries free; otherwise the step takes one cell, which adds
 // at most one entry, and only when it descends a level (a tree has at most
 // kMaxLevels levels below any cell), so the stack never overflows.
-template <bool kFill>
+// kMode 0: count (group records, totals); 1: fill the list at the offsets
+// of pass 0; 2: single pass -- count as pass 0 and write each group's entries
+// into fixed slots of two pools (cells: list = cell pool, capacity = slot
+// size; particles: ppool, pcap), for otoo_walk_compact.
+template <int kMode>
 __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_group* __restrict__ groups,
-                                                          int32_t* __restrict__ list, int64_t capacity)
+                                                          int32_t* __restrict__ list, int64_t capacity,
+                                                          int32_t* __restrict__ ppool, int64_t pcap)
 {
+    constexpr bool kFill = kMode == 1;
+    constexpr bool kCount = kMode != 1;
+    constexpr bool kWrite = kMode != 0;
     __shared__ uint32_t stack_s[kWalkWarps][kStack];
     const int lane = threadIdx.x & 31;
     uint32_t* stk = stack_s[threadIdx.x >> 5];
@@ -284,7 +294,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
         if (first < 0 || count < 1 || count > kMaxGroup || (int64_t)first + count > a.n_part) {
             if (lane == 0) {
                 atomicOr(status, kWalkBadGroup);
-                if (!kFill) {
+                if (kCount) {
                     otoo_group z = {};
                     z.first = first;
                     z.eps2 = a.eps2;
@@ -332,6 +342,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
         const float invth = open_all ? 0.f : __frcp_rn(__double2float_rn(theta));
         int64_t off_c = 0, off_p = 0;
         int32_t want_c = 0, want_p = 0;
+        int32_t* pdst = kMode == 2 ? ppool : list;
+        if (kMode == 2) {
+            off_c = (int64_t)g * capacity;
+            want_c = (int32_t)capacity;
+            off_p = (int64_t)g * pcap;
+            want_p = (int32_t)pcap;
+        }
         if (kFill) {
             const otoo_group gr = groups[g];
             off_c = gr.list_off;
@@ -425,7 +442,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
             }
             // accepted cells
             const unsigned am = __ballot_sync(kFull, kind == 1 && !drop);
-            if (kFill && kind == 1 && !drop) {
+            if (kWrite && kind == 1 && !drop) {
                 const int32_t r = ncell + __popc(am & lt);
                 if (r < want_c) list[off_c + r] = (int32_t)(a.n_part + node);
             }
@@ -433,10 +450,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
             // particles of rejected leaves
             const int np = kind == 2 ? pe - pb : 0;
             const int pin = warp_incl_scan(np, lane);
-            if (kFill && np > 0) {
+            if (kWrite && np > 0) {
                 const int32_t base = npart + pin - np;
                 for (int k = 0; k < np; ++k)
-                    if (base + k < want_p) list[off_p + base + k] = pb + k;
+                    if (base + k < want_p) pdst[off_p + base + k] = pb + k;
             }
             npart += __shfl_sync(kFull, pin, 31);
             // one run per rejected inner cell, the lowest lane's on top
@@ -447,7 +464,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
             __syncwarp();
         }
         if (failed && lane == 0) atomicOr(status, kWalkOverflow);
-        if (!kFill) {
+        if (kCount) {
             if (lane == 0) {
                 otoo_group r;
                 r.first = first;
@@ -467,11 +484,44 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
                 atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 1), (unsigned long long)(len * count));
                 atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 2),
                           (unsigned long long)((int64_t)ncell * count));
+                atomicMax(reinterpret_cast<unsigned long long*>(a.totals + 3), (unsigned long long)ncell);
+                atomicMax(reinterpret_cast<unsigned long long*>(a.totals + 4), (unsigned long long)npart);
+                if (kMode == 2 && (ncell > want_c || npart > want_p))
+                    atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 5), 1ull);
             }
         } else if (lane == 0 && (ncell != want_c || npart != want_p)) {
             atomicOr(status, kWalkMismatch);
         }
     }
+}
+
+// One warp per group: the group's slots of the two pools (filled by the
+// single pass) copied to its place in the list, cells then particles.
+// Nothing is copied when a group did not fit its slots (totals[5] > 0: the
+// caller runs otoo_walk_fill instead) or when the list is too small.
+__global__ void k_compact(const otoo_group* __restrict__ groups, int32_t G, const int32_t* __restrict__ cpool,
+                          int64_t ccap, const int32_t* __restrict__ ppool, int64_t pcap, int32_t* __restrict__ list,
+                          int64_t capacity, const int64_t* __restrict__ totals, uint32_t* __restrict__ status)
+{
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= G) return;
+    if (totals[5] > 0 || totals[0] > capacity) {
+        if (g == 0 && lane == 0) atomicOr(status, kWalkNoRoom);
+        return;
+    }
+    const otoo_group gr = groups[g];
+    if (gr.n_cell < 0 || gr.n_part < 0 || gr.n_cell > ccap || gr.n_part > pcap || gr.list_off < 0 ||
+        gr.list_off + gr.n_cell + gr.n_part > capacity) {
+        if (lane == 0) atomicOr(status, kWalkNoRoom);
+        return;
+    }
+    const int32_t* cs = cpool + g * ccap;
+    const int32_t* ps = ppool + g * pcap;
+    int32_t* d = list + gr.list_off;
+    for (int k = lane; k < gr.n_cell; k += 32) d[k] = cs[k];
+    d += gr.n_cell;
+    for (int k = lane; k < gr.n_part; k += 32) d[k] = ps[k];
 }
 
 // ---- exclusive prefix sums in index order ---------------------------------
@@ -774,19 +824,20 @@ WalkArgs walk_args(const otoo_dev_walk* w)
     return a;
 }
 
-template <bool kFill>
-int launch_walk(const otoo_dev_walk* w, otoo_group* groups, int32_t* list, int64_t capacity, cudaStream_t s)
+template <int kMode>
+int launch_walk(const otoo_dev_walk* w, otoo_group* groups, int32_t* list, int64_t capacity, cudaStream_t s,
+                int32_t* ppool = nullptr, int64_t pcap = 0)
 {
     int dev = 0, sms = 0, occ = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk<kFill>, kWalkWarps * 32, 0));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk<kMode>, kWalkWarps * 32, 0));
     if (occ < 1) occ = 1;
     int64_t blocks = (int64_t)sms * occ;
     const int64_t need = ((int64_t)w->n_groups + kWalkWarps - 1) / kWalkWarps;
     if (blocks > need) blocks = need;
     CUDA_TRY(cudaMemsetAsync(w->counter, 0, sizeof(uint32_t), s));
-    k_walk<kFill><<<(unsigned)blocks, kWalkWarps * 32, 0, s>>>(walk_args(w), groups, list, capacity);
+    k_walk<kMode><<<(unsigned)blocks, kWalkWarps * 32, 0, s>>>(walk_args(w), groups, list, capacity, ppool, pcap);
     CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }
@@ -795,7 +846,7 @@ int launch_walk(const otoo_dev_walk* w, otoo_group* groups, int32_t* list, int64
 
 extern "C" {
 
-int64_t otoo_walk_totals_len(int64_t n_groups) { return 4 + scan_blocks(n_groups < 0 ? 0 : n_groups) + 1; }
+int64_t otoo_walk_totals_len(int64_t n_groups) { return kTotals + scan_blocks(n_groups < 0 ? 0 : n_groups) + 1; }
 
 int otoo_walk_count(const otoo_dev_walk* w, otoo_group* groups, void* stream)
 {
@@ -804,10 +855,42 @@ int otoo_walk_count(const otoo_dev_walk* w, otoo_group* groups, void* stream)
     OTOO_REQUIRE(groups, OTOO_EINVAL, "otoo_walk_count: groups is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(cudaMemsetAsync(w->counter, 0, 4 * sizeof(uint32_t), s));
-    CUDA_TRY(cudaMemsetAsync(w->totals, 0, 4 * sizeof(int64_t), s));
-    const int r2 = launch_walk<false>(w, groups, nullptr, 0, s);
+    CUDA_TRY(cudaMemsetAsync(w->totals, 0, kTotals * sizeof(int64_t), s));
+    const int r2 = launch_walk<0>(w, groups, nullptr, 0, s);
     if (r2) return r2;
-    CUDA_TRY(excl_scan(GroupLen{groups}, GroupOff{groups}, w->n_groups, w->totals + 4, nullptr, s));
+    CUDA_TRY(excl_scan(GroupLen{groups}, GroupOff{groups}, w->n_groups, w->totals + kTotals, nullptr, s));
+    return OTOO_OK;
+}
+
+int otoo_walk_single(const otoo_dev_walk* w, otoo_group* groups, int32_t* cell_pool, int64_t cell_cap,
+                     int32_t* part_pool, int64_t part_cap, void* stream)
+{
+    const int rc = check_walk(w);
+    if (rc) return rc;
+    OTOO_REQUIRE(groups && cell_pool && part_pool, OTOO_EINVAL, "otoo_walk_single: NULL pointer");
+    OTOO_REQUIRE(cell_cap >= 1 && part_cap >= 1 && cell_cap <= INT32_MAX && part_cap <= INT32_MAX, OTOO_EINVAL,
+                 "otoo_walk_single: slot sizes out of range");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(w->counter, 0, 4 * sizeof(uint32_t), s));
+    CUDA_TRY(cudaMemsetAsync(w->totals, 0, kTotals * sizeof(int64_t), s));
+    const int r2 = launch_walk<2>(w, groups, cell_pool, cell_cap, s, part_pool, part_cap);
+    if (r2) return r2;
+    CUDA_TRY(excl_scan(GroupLen{groups}, GroupOff{groups}, w->n_groups, w->totals + kTotals, nullptr, s));
+    return OTOO_OK;
+}
+
+int otoo_walk_compact(const otoo_dev_walk* w, const otoo_group* groups, const int32_t* cell_pool, int64_t cell_cap,
+                      const int32_t* part_pool, int64_t part_cap, int32_t* list, int64_t capacity, void* stream)
+{
+    const int rc = check_walk(w);
+    if (rc) return rc;
+    OTOO_REQUIRE(groups && cell_pool && part_pool && list, OTOO_EINVAL, "otoo_walk_compact: NULL pointer");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t warps = w->n_groups;
+    k_compact<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(groups, w->n_groups, cell_pool, cell_cap, part_pool,
+                                                                   part_cap, list, capacity, w->totals,
+                                                                   w->counter + 1);
+    CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }
 
@@ -818,7 +901,7 @@ int otoo_walk_fill(const otoo_dev_walk* w, const otoo_group* groups, int32_t* li
     OTOO_REQUIRE(groups && list, OTOO_EINVAL, "otoo_walk_fill: NULL pointer");
     OTOO_REQUIRE(capacity >= 0, OTOO_EINVAL, "otoo_walk_fill: negative capacity");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    return launch_walk<true>(w, const_cast<otoo_group*>(groups), list, capacity, s);
+    return launch_walk<1>(w, const_cast<otoo_group*>(groups), list, capacity, s);
 }
 
 int otoo_walk_check_status(const otoo_dev_walk* w, void* stream)

@@ -307,6 +307,7 @@ class BufferPool:
     def __init__(self, device):
         self.device = device
         self.bufs = {}
+        self.meta = {}
 
     def get(self, name, n, dtype):
         import torch
@@ -429,19 +430,25 @@ class DeviceTree:
     def h2d_bytes(self):
         return sum(b.numel() for b in self.bufs.values() if b is not None)
 
-    def walk(self, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None, max_entries=None):
-        """otoo_walk_count + otoo_walk_fill: groups and lists on the device.
-        With a BufferPool the buffers of the previous walk are reused (and
-        overwritten).  max_entries: raise ValueError instead of allocating a
-        longer list."""
-        return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool, max_entries)
+    def walk(self, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None, max_entries=None,
+             single=True):
+        """Groups and lists on the device.  Without a BufferPool: two passes
+        (otoo_walk_count, otoo_walk_fill).  With one, the buffers of the
+        previous walk are reused (and overwritten), and once a walk has set
+        the slot sizes (1.25 x its largest n_cell / n_part) the walk is one
+        pass (otoo_walk_single + otoo_walk_compact), falling back to
+        otoo_walk_fill when a group outgrows its slots.  max_entries: raise
+        ValueError instead of allocating a longer list."""
+        return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool, max_entries, single)
 
 
 class DeviceLists:
     """Groups and lists made by the device walk (device buffers)."""
 
+    SLOT_BYTES_MAX = 24 << 30  # device memory the one-pass walk's slots may take
+
     def __init__(self, dtree, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None,
-                 max_entries=None):
+                 max_entries=None, single=True):
         import torch
         dev = dtree.device
         G = dtree.n_groups
@@ -469,14 +476,32 @@ class DeviceLists:
         self.struct = w
         self.bufs = b
         st = _stream(stream, dev)
-        L.call("otoo_walk_count", ctypes.byref(w), b["groups"].data_ptr(), st)
-        tot = b["totals"][:3].tolist()
-        self.n_list, self.interactions, self.cell_interactions = (int(x) for x in tot)
+        gp = b["groups"].data_ptr()
+        key = (dtree.n_groups, dtree.mac)
+        slots = pool.meta.get(key) if (pool is not None and single) else None
+        if slots:
+            ccap, pcap = slots
+            cpool = alloc("cpool", G * ccap, torch.int32)
+            ppool = alloc("ppool", G * pcap, torch.int32)
+            L.call("otoo_walk_single", ctypes.byref(w), gp, cpool.data_ptr(), ccap, ppool.data_ptr(), pcap, st)
+        else:
+            L.call("otoo_walk_count", ctypes.byref(w), gp, st)
+        tot = [int(x) for x in b["totals"][:6].tolist()]
+        self.n_list, self.interactions, self.cell_interactions = tot[:3]
+        self.one_pass = bool(slots) and tot[5] == 0
         if max_entries is not None and self.n_list > max_entries:
             raise ValueError("walk: %d list entries exceed max_entries %d" % (self.n_list, max_entries))
         b["list"] = alloc("list", self.n_list, torch.int32)
-        L.call("otoo_walk_fill", ctypes.byref(w), b["groups"].data_ptr(), b["list"].data_ptr(), self.n_list, st)
+        if self.one_pass:
+            L.call("otoo_walk_compact", ctypes.byref(w), gp, cpool.data_ptr(), ccap, ppool.data_ptr(), pcap,
+                   b["list"].data_ptr(), self.n_list, st)
+        else:
+            L.call("otoo_walk_fill", ctypes.byref(w), gp, b["list"].data_ptr(), self.n_list, st)
         L.call("otoo_walk_check_status", ctypes.byref(w), st)
+        if pool is not None and single:
+            ccap, pcap = int(1.25 * tot[3]) + 64, int(1.25 * tot[4]) + 64
+            if 4 * G * (ccap + pcap) <= self.SLOT_BYTES_MAX:
+                pool.meta[key] = (ccap, pcap)
 
     @property
     def groups(self):

@@ -98,6 +98,29 @@ def test_sw_lists_force_matches_oracle(torch, delta):
     assert (np.abs(p64 - r["pot"]) / np.abs(r["pot"])).max() <= 1e-6
 
 
+@pytest.mark.parametrize("mac", ["theta", "sw", "sph"])
+def test_one_pass_walk_equals_two_pass(torch, mac):
+    pos, mass = ic.hernquist(30000, 48)
+    h = ic.sph_radii(pos, mass, 48, "hernquist") if mac == "sph" else None
+    t = S.Tree(pos, mass, 8)
+    dt = S.DeviceTree(t, 64, mac != "sph", mac=mac, delta=1e-3, m_limit=0.05, h_sph=h)
+    two = dt.walk(0.6 if mac == "theta" else 0.0, 0.01)
+    pool = S.BufferPool("cuda")
+    first = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
+    assert not first.one_pass
+    ref_list, ref_groups = two.list, two.groups.view(np.uint8)
+    one = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
+    assert one.one_pass
+    np.testing.assert_array_equal(one.list, ref_list)
+    np.testing.assert_array_equal(one.groups.view(np.uint8), ref_groups)
+    # slots too small: the walk notices and fills the list in a second pass
+    key = (dt.n_groups, dt.mac)
+    pool.meta[key] = (4, 4)
+    small = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
+    assert not small.one_pass
+    np.testing.assert_array_equal(small.list, ref_list)
+
+
 def test_device_walk_theta_zero_and_per_group(torch):
     pos, mass = ic.plummer(3000, 42)
     t = S.Tree(pos, mass, 8)
