@@ -290,7 +290,8 @@ def run_ours(args):
         "errors": errors,
         "e2e": e2e,
         "clocks": clocks,
-        "gpu_launches": args.steps * (1 + (1 if plan.n_splits else 0)),
+        # per FP32 step: the float-pair split, the force kernel, the chunk merge when lists are split
+        "gpu_launches": args.steps * (2 + (1 if plan.n_splits else 0)),
     }
     if rank == 0 and not args.skip_walk:
         line["device_walk"] = guarded_extra(run_device_walk, args, dev_name, tree, w, tune, lists, a32, stream,
@@ -560,7 +561,8 @@ def run_batch(args, dev_name):
     per = [S.Tree(p, m, w["leaf_size"]).lists(w["theta"], w["n_crit"], e, w["use_quad"]) for p, m, e in systems]
     packed = S.Lists.pack(per)
     host_s = time.perf_counter() - t0
-    tune = L.default_tune(w["n_crit"])
+    # the packed kernel with 256-entry tiles, as the autotuner picks for N = 2^23
+    tune = L.Tune(block=128, iblock=2, tile=256, split=16384, ctas_per_sm=0, packed=1)
     dev = S.DeviceSystem.upload(packed, packed.plan(tune), dev_name)
     n = packed.n_part
     acc = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
