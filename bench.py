@@ -28,6 +28,12 @@ sys.path.insert(0, ROOT)
 
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 partitions x 32)
 
+# DRAM bytes of one force-kernel launch (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu capture of k_force_warp2<4,2,8> on the
+# Hernquist N = 2^23 workload: 23.67 GB + 0.671 GB), keyed by the workload,
+# n_crit and tuning it was taken on; other configurations report null.
+CAPTURED_TRAFFIC = {("hernquist8m", 8388608, 128, (128, 2, 256, 16384, 1)): 23.67e9 + 0.671e9}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -282,7 +288,11 @@ def run_ours(args):
                    "host_tree_s": t1 - t0, "host_walk_s": t2 - t1, "host_plan_s": t3 - t2,
                    "parallelism": "replica per rank (weak)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": CAPTURED_TRAFFIC.get((args.workload, n, w["n_crit"],
+                                                      (tune.block, tune.iblock, tune.tile, tune.split, tune.packed))),
+                     "traffic_note": "DRAM bytes per force-kernel launch from one ncu capture of this configuration",
+                     "timing": "achieved uses the CUDA-event time of the whole step (float-pair split 0.26 ms included)",
                      "flops_per_step": flops,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived; no measured FP32 peak)",
                      "flop_convention": "20 per monopole/particle interaction, 60 per quadrupole cell interaction"},
