@@ -306,7 +306,7 @@ int otoo_check_status(const otoo_dev_system* sys, void* stream);
    Such callers include code running under a device-memory budget owned by
    someone else (a host application's pool allocator that already holds the
    GPU's memory, an embedding runtime whose allocator must not be bypassed),
-   and latency-critical loops that must not enter the driver's allocator.
+   and latency-critical loops that must not enter the CUDA runtime's allocator.
    There is no counterpart in the paper; this is a deployment option.
      sys:       as for otoo_force; its partial, counter and split fields are
                 ignored (the array is used instead).

@@ -146,7 +146,7 @@ int oracle_sph_density_direct(int64_t n, const double* pos, const double* mass, 
 
 /* ------------------------------------------------------------------------- */
 /* Cell moments and the cell field (Section II: the cell acts as a virtual    */
-/* particle at its centre of mass; quadrupole is this build's extension).     */
+/* particle at its centre of mass; the quadrupole is an extension).          */
 /* ------------------------------------------------------------------------- */
 
 /*

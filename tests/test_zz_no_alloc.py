@@ -2,7 +2,7 @@
 the C ABI, against the allocating one (otoo_force) on the same device inputs.
 
 Callers that cannot allocate device memory (their GPU memory is owned by
-another allocator, or their loop must not enter the driver's allocator) use
+another allocator, or their loop must not enter the CUDA runtime's allocator) use
 otoo_force_static: its scratch is a library-held device array.  This file is
 collected last so that a failure here leaves every other test already run;
 it also passes on its own in a fresh process."""
