@@ -99,12 +99,16 @@ __device__ bool mac_exact(const otoo_wcell64* __restrict__ c64, int k, const dou
 }
 
 // FP32 filter of the acceptance test: 1 = accept, 0 = reject, -1 = too close
-// to call.  u = com - c from the float pairs; every rounded quantity is
+// to call.  Without kOverlap (opening angles below 1/sqrt(3)) the cube
+// overlap part is left out: a cube that overlaps the box puts its centre of
+// mass within sqrt(3) l of the box, below l / theta + s, so the distance part
+// alone already rejects it.  u = com - c from the float pairs; every rounded quantity is
 // within 2^-20 K of its exact value (K: sum of the magnitudes the test
 // combines, plus 2^-24 of the absolute coordinates for the truncated low
 // words), so a comparison decided by more than 2^-18 K (box overlap) or
 // 2^-16 K^2 (squared distances) is decided the same way by the exact
 // arithmetic and by the host's FP64.
+template <bool kOverlap>
 __device__ __forceinline__ int mac_filter(const otoo_wcell& w, const BoxF& g, float invth)
 {
     float u[3], au = 0.f, A = g.A;
@@ -116,17 +120,19 @@ __device__ __forceinline__ int mac_filter(const otoo_wcell& w, const BoxF& g, fl
     }
     const float thr = __fadd_rn(__fmul_rn(w.side, invth), w.s);
     const float K = au + g.B + thr + w.side + A * 0x1p-24f;
-    const float del = K * 0x1p-18f;
-    bool sep = false, ovl = true;
+    if (kOverlap) {
+        const float del = K * 0x1p-18f;
+        bool sep = false, ovl = true;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float lo = __fsub_rn(u[a], w.e[a]);
-        const float hi = __fadd_rn(lo, w.side);
-        sep = sep || (lo > g.bh[a] + del) || (g.bl[a] > hi + del);
-        ovl = ovl && (lo < g.bh[a] - del) && (g.bl[a] < hi - del);
+        for (int a = 0; a < 3; ++a) {
+            const float lo = __fsub_rn(u[a], w.e[a]);
+            const float hi = __fadd_rn(lo, w.side);
+            sep = sep || (lo > g.bh[a] + del) || (g.bl[a] > hi + del);
+            ovl = ovl && (lo < g.bh[a] - del) && (g.bl[a] < hi - del);
+        }
+        if (ovl) return 0;
+        if (!sep) return -1;
     }
-    if (ovl) return 0;
-    if (!sep) return -1;
     float d2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -338,6 +344,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
         const bool drop = a.mac == OTOO_MAC_SPH;
         const double theta = sw ? 0.0 : a.tpg ? (double)a.tpg[g] : a.theta;
         const bool open_all = !sw && !(theta > 0.0);
+        const bool small_angle = theta < 0.57;  // below 1/sqrt(3) = 0.5774 with room for rounding
         // 1/theta within 2^-23 (the filter's margins allow 2^-21)
         const float invth = open_all ? 0.f : __frcp_rn(__double2float_rn(theta));
         int64_t off_c = 0, off_p = 0;
@@ -432,7 +439,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
                             dec = a.exact ? -1 : mac_filter_sw(w, bf);
                             if (dec < 0) dec = sw_exact(a.cell64, node, blo, bhi) ? 1 : 0;
                         } else if (!open_all) {
-                            dec = a.exact ? -1 : mac_filter(w, bf, invth);
+                            dec = a.exact ? -1 : small_angle ? mac_filter<false>(w, bf, invth) : mac_filter<true>(w, bf, invth);
                             if (dec < 0) dec = mac_exact(a.cell64, node, blo, bhi, theta) ? 1 : 0;
                         }
                         kind = dec ? 1 : (nch == 0 ? 2 : 3);
@@ -448,14 +455,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
             }
             ncell += __popc(am);
             // particles of rejected leaves
-            const int np = kind == 2 ? pe - pb : 0;
-            const int pin = warp_incl_scan(np, lane);
-            if (kWrite && np > 0) {
-                const int32_t base = npart + pin - np;
-                for (int k = 0; k < np; ++k)
-                    if (base + k < want_p) pdst[off_p + base + k] = pb + k;
+            if (__any_sync(kFull, kind == 2)) {
+                const int np = kind == 2 ? pe - pb : 0;
+                const int pin = warp_incl_scan(np, lane);
+                if (kWrite && np > 0) {
+                    const int32_t base = npart + pin - np;
+                    for (int k = 0; k < np; ++k)
+                        if (base + k < want_p) pdst[off_p + base + k] = pb + k;
+                }
+                npart += __shfl_sync(kFull, pin, 31);
             }
-            npart += __shfl_sync(kFull, pin, 31);
             // one run per rejected inner cell, the lowest lane's on top
             const unsigned om = __ballot_sync(kFull, kind == 3);
             const int no = __popc(om);

@@ -441,8 +441,13 @@ def filter_accept(blo, bhi, cell, theta):
     dl = K * f(2.0 ** -18)
     lo = u - cell["e"]
     hi = lo + side[:, None]
-    sep = np.any((lo > bh + dl[:, None]) | (bl > hi + dl[:, None]), axis=1)
-    ovl = np.all((lo < bh - dl[:, None]) & (bl < hi - dl[:, None]), axis=1)
+    if theta < 0.57:
+        # below 1/sqrt(3) the device leaves the overlap part out
+        sep = np.ones(len(cell), bool)
+        ovl = np.zeros(len(cell), bool)
+    else:
+        sep = np.any((lo > bh + dl[:, None]) | (bl > hi + dl[:, None]), axis=1)
+        ovl = np.all((lo < bh - dl[:, None]) & (bl < hi - dl[:, None]), axis=1)
     d = np.maximum(f(0), np.maximum(bl - u, u - bh))
     d2 = (d * d).sum(1, dtype=f)
     thr2 = thr * thr
@@ -506,7 +511,8 @@ def test_fp32_sw_filter_never_contradicts_fp64(model, delta, m_limit):
 
 
 @pytest.mark.parametrize("model,n,theta", [("plummer", 6000, 0.5), ("hernquist", 6000, 0.75),
-                                           ("lattice", 4096, 0.5), ("lattice", 4096, 1.0)])
+                                           ("lattice", 4096, 0.5), ("lattice", 4096, 1.0),
+                                           ("hernquist", 6000, 0.3), ("plummer", 6000, 0.5773)])
 def test_fp32_filter_never_contradicts_fp64(model, n, theta):
     """Wherever the FP32 filter decides, the FP64 test decides the same; the
     undecided share stays small.  The lattice puts many cells exactly on the
