@@ -10,8 +10,12 @@
 //   k_density<IB>     one work item (group, target chunk, list chunk) per warp
 //                     from an atomic ticket; 32-entry tiles staged in shared
 //                     memory as (x_j - c, m_j 8/(pi h_j^3), 1/h_j) in FP32
-//                     relative to the group centre c; each lane sums IB
-//                     targets, FP32 within a tile, FP64 across tiles.
+//                     relative to the group centre c, keeping only entries
+//                     within (1 + 2^-10) h_j of the item's own target box (the
+//                     others have W = 0 at every target; the walk's lists are
+//                     cut at cell level and hold about 12 times more entries
+//                     than neighbours); each lane sums IB targets, FP32
+//                     within a tile, FP64 across tiles.
 //   k_density_merge   FP64 sum of the list chunks of split groups, in chunk
 //                     order.
 #include <cuda_runtime.h>
@@ -82,6 +86,7 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
         }
         float xi[IB], yi[IB], zi[IB];
         double acc[IB];
+        float blo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, bhi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
 #pragma unroll
         for (int r = 0; r < IB; ++r) {
             const int k = lane + 32 * r;
@@ -92,12 +97,24 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
                 xi[r] = (float)(s.x - g.cx);
                 yi[r] = (float)(s.y - g.cy);
                 zi[r] = (float)(s.z - g.cz);
+                blo[0] = fminf(blo[0], xi[r]), bhi[0] = fmaxf(bhi[0], xi[r]);
+                blo[1] = fminf(blo[1], yi[r]), bhi[1] = fmaxf(bhi[1], yi[r]);
+                blo[2] = fminf(blo[2], zi[r]), bhi[2] = fmaxf(bhi[2], zi[r]);
             }
         }
+        // the box of this item's targets (the same FP32 values the pairs use)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                blo[a] = fminf(blo[a], __shfl_xor_sync(kFull, blo[a], o));
+                bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(kFull, bhi[a], o));
+            }
         for (int32_t j = it.j0; j < it.j1; j += 32) {
             const int32_t jj = j + lane;
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
             float ih = 0.f;
+            bool keep = false;
             if (jj < it.j1) {
                 const int32_t e = sys.list[g.list_off + jj];
                 if (e >= 0 && e < sys.n_part) {
@@ -106,14 +123,24 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
                     ih = 1.0f / h;
                     p = make_float4((float)(s.x - g.cx), (float)(s.y - g.cy), (float)(s.z - g.cz),
                                     s.m * kNorm * ih * ih * ih);
+                    // distance from the entry to the target box against its support
+                    const float dx = fmaxf(0.f, fmaxf(blo[0] - p.x, p.x - bhi[0]));
+                    const float dy = fmaxf(0.f, fmaxf(blo[1] - p.y, p.y - bhi[1]));
+                    const float dz = fmaxf(0.f, fmaxf(blo[2] - p.z, p.z - bhi[2]));
+                    const float hm = h * (1.0f + 0x1p-10f);
+                    keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < hm * hm;
                 } else {
                     atomicOr(counter + 1, kBadIndex);
                 }
             }
-            tp[w][lane] = p;
-            tih[w][lane] = ih;
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int slot = __popc(km & ((1u << lane) - 1u));
+                tp[w][slot] = p;
+                tih[w][slot] = ih;
+            }
             __syncwarp();
-            const int cnt = it.j1 - j < 32 ? it.j1 - j : 32;
+            const int cnt = __popc(km);
             float part[IB];
 #pragma unroll
             for (int r = 0; r < IB; ++r) part[r] = 0.f;
