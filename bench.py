@@ -245,10 +245,10 @@ def run_ours(args):
     # accuracy against the FP64 direct sum on a seeded subsample
     errors = None
     if rank == 0 and args.err_targets > 0:
-        import oracle
         from paper_1206_1199_gb300 import ic
         sub = ic.subsample(n, args.err_targets, 7)
-        ad, pd = oracle.direct(pos, mass, w["eps"], targets=sub)
+        # the library's FP64 direct sum on the device (checked against the oracle in the tests)
+        ad, pd = S.direct_sum(pos, mass, w["eps"], sub, dev_name)
         rms, mx = rel_err(a32[sub], ad)
         errors = {"targets": int(sub.shape[0]), "fp32k_acc_rms": rms, "fp32k_acc_max": mx,
                   "fp32k_pot_rms": float(np.sqrt(np.mean(((p32[sub] - pd) / pd) ** 2)))}
@@ -467,7 +467,6 @@ def run_sph(args, dev_name, pos, mass, w, stream):
     against the FP64 direct sum on 256 targets."""
     import torch
 
-    import oracle
     from paper_1206_1199_gb300 import _lib as L
     from paper_1206_1199_gb300 import ic
     from paper_1206_1199_gb300 import system as S
@@ -500,7 +499,7 @@ def run_sph(args, dev_name, pos, mass, w, stream):
         times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
     med = np.median(np.array(times), axis=0)
     sub = ic.subsample(n, 256, 17)
-    ref = oracle.sph_density(pos, mass, h.astype(np.float64), targets=sub)
+    ref = S.sph_direct(pos, mass, h, sub, dev_name)  # FP64 brute force on the device, checked in the tests
     err = np.abs(rho.cpu().numpy()[sub] - ref) / ref
     return {"tree_ms": float(med[0]), "walk_ms": float(med[1]), "plan_density_ms": float(med[2]),
             "pairs": int(dl.interactions), "pairs_per_s": dl.interactions / (med[2] * 1e-3),

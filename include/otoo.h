@@ -550,6 +550,14 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* tree,
    set the status word (otoo_check_status). */
 int otoo_sph_density(const otoo_dev_system* sys, const float* h, double* rho, const otoo_tune* tune, void* stream);
 
+/* FP64 brute-force density for chosen targets, the reference of the checks:
+   rho[t] = sum over all j < n of m_j W(|x_i - x_j|, h_j), i = targets[t]
+   (index into src and h, which are in the same order).  Device arrays: src
+   [n] (particles only), h [n], targets [n_tgt] int64, rho [n_tgt] FP64,
+   status one uint32 (bit 2: a target index out of range).  Asynchronous. */
+int otoo_sph_direct(const otoo_src* src, const float* h, int64_t n, const int64_t* targets, int64_t n_tgt,
+                    double* rho, uint32_t* status, void* stream);
+
 /* ---- learned opening angle (multilayer perceptron 6-32-32-1) ---------------- */
 
 #define OTOO_MLP_IN  6

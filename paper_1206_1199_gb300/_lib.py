@@ -165,6 +165,7 @@ _SIGS = {
     "otoo_plan_count": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp],
     "otoo_plan_fill": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp, i64, vp, i64, vp, vp],
     "otoo_sph_density": [ctypes.POINTER(DevSystem), vp, vp, ctypes.POINTER(Tune), vp],
+    "otoo_sph_direct": [vp, vp, i64, vp, i64, vp, vp, vp],
     "otoo_devtree_scratch_bytes": [i64, i64],
     "otoo_devtree_build": [vp, vp, ctypes.POINTER(DevTree), vp, i64, vp],
     "otoo_last_error": [],

@@ -18,6 +18,9 @@
 //                     within a tile, FP64 across tiles.
 //   k_density_merge   FP64 sum of the list chunks of split groups, in chunk
 //                     order.
+//   k_sph_direct      FP64 brute force over all sources for chosen targets
+//                     (the reference of the checks): one thread per target,
+//                     sources staged through shared memory.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -196,6 +199,54 @@ __global__ void k_density_merge(otoo_dev_system sys, double* __restrict__ rho)
     }
 }
 
+// FP64 kernel value (same spline as the pairs above, in FP64).
+__device__ __forceinline__ double w_m4_64(double r, double h)
+{
+    const double q = r / h;
+    const double a = 1.0 - q;
+    const double w = q <= 0.5 ? 1.0 - 6.0 * q * q + 6.0 * q * q * q : (q < 1.0 ? 2.0 * a * a * a : 0.0);
+    return 8.0 / (3.141592653589793 * h * h * h) * w;
+}
+
+__global__ void __launch_bounds__(128) k_sph_direct(const otoo_src* __restrict__ src, const float* __restrict__ h,
+                                                    int64_t n, const int64_t* __restrict__ tgt, int64_t n_tgt,
+                                                    double* __restrict__ rho, uint32_t* __restrict__ status)
+{
+    __shared__ double4 s[128];
+    __shared__ double sh[128];
+    const int64_t t = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    int64_t i = -1;
+    double xi = 0, yi = 0, zi = 0;
+    if (t < n_tgt) {
+        i = tgt[t];
+        if (i < 0 || i >= n) {
+            atomicOr(status, kBadIndex);
+            i = -1;
+        } else {
+            xi = src[i].x, yi = src[i].y, zi = src[i].z;
+        }
+    }
+    double sum = 0.0;
+    for (int64_t b = 0; b < n; b += 128) {
+        const int64_t j = b + threadIdx.x;
+        if (j < n) {
+            const otoo_src q = src[j];
+            s[threadIdx.x] = make_double4(q.x, q.y, q.z, (double)q.m);
+            sh[threadIdx.x] = (double)h[j];
+        }
+        __syncthreads();
+        const int cnt = n - b < 128 ? (int)(n - b) : 128;
+        for (int k = 0; k < cnt; ++k) {
+            const double4 q = s[k];
+            const double dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r < sh[k]) sum += q.w * w_m4_64(r, sh[k]);
+        }
+        __syncthreads();
+    }
+    if (t < n_tgt) rho[t] = sum;
+}
+
 #define CUDA_TRY(expr)                                                                                 \
     do {                                                                                               \
         cudaError_t e_ = (expr);                                                                       \
@@ -247,6 +298,18 @@ int otoo_sph_density(const otoo_dev_system* sys, const float* h, double* rho, co
         k_density_merge<<<(unsigned)((sys->n_splits * 32 + 127) / 128), 128, 0, s>>>(*sys, rho);
         CUDA_TRY(cudaGetLastError());
     }
+    return OTOO_OK;
+}
+
+int otoo_sph_direct(const otoo_src* src, const float* h, int64_t n, const int64_t* targets, int64_t n_tgt, double* rho,
+                    uint32_t* status, void* stream)
+{
+    OTOO_REQUIRE(src && h && targets && rho && status, OTOO_EINVAL, "otoo_sph_direct: NULL pointer");
+    OTOO_REQUIRE(n >= 1 && n_tgt >= 1 && n_tgt <= ((int64_t)1 << 31), OTOO_EINVAL, "otoo_sph_direct: bad sizes");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+    k_sph_direct<<<(unsigned)((n_tgt + 127) / 128), 128, 0, s>>>(src, h, n, targets, n_tgt, rho, status);
+    CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }
 

@@ -269,6 +269,52 @@ def sph_density(dev, h, rho=None, tune=None, stream=None, check=True):
     return rho
 
 
+def _particle_sources(pos, mass, device):
+    import torch
+    src = np.zeros(len(pos), dtype=np.dtype(L.Src))
+    p = np.asarray(pos, np.float64)
+    src["x"], src["y"], src["z"] = p[:, 0], p[:, 1], p[:, 2]
+    src["m"] = np.asarray(mass, np.float32)
+    return torch.from_numpy(src.view(np.uint8).reshape(-1).copy()).to(device)
+
+
+def direct_sum(pos, mass, eps, targets, device="cuda"):
+    """FP64 direct sum on the device (otoo_direct) for the given particle
+    indices (caller order): returns (acc [k][3], pot [k]) as numpy."""
+    import torch
+    src = _particle_sources(pos, mass, device)
+    t = torch.from_numpy(np.ascontiguousarray(targets, np.int64)).to(device)
+    n, nt = len(pos), int(t.shape[0])
+    nch = int(L.load().otoo_direct_chunks(n, nt))
+    scratch = torch.empty(4 * nch * nt, dtype=torch.float64, device=device)
+    acc = torch.empty((nt, 3), dtype=torch.float64, device=device)
+    pot = torch.empty(nt, dtype=torch.float64, device=device)
+    status = torch.zeros(1, dtype=torch.int32, device=device)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.call("otoo_direct", src.data_ptr(), n, t.data_ptr(), nt, float(eps) ** 2, acc.data_ptr(), pot.data_ptr(),
+           scratch.data_ptr(), status.data_ptr(), st)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0, "otoo_direct: target index out of range"
+    return acc.cpu().numpy(), pot.cpu().numpy()
+
+
+def sph_direct(pos, mass, h, targets, device="cuda"):
+    """FP64 brute-force SPH density on the device (otoo_sph_direct) for the
+    given particle indices (caller order)."""
+    import torch
+    src = _particle_sources(pos, mass, device)
+    hd = torch.from_numpy(np.ascontiguousarray(h, np.float32)).to(device)
+    t = torch.from_numpy(np.ascontiguousarray(targets, np.int64)).to(device)
+    rho = torch.empty(int(t.shape[0]), dtype=torch.float64, device=device)
+    status = torch.zeros(1, dtype=torch.int32, device=device)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.call("otoo_sph_direct", src.data_ptr(), hd.data_ptr(), len(pos), t.data_ptr(), int(t.shape[0]),
+           rho.data_ptr(), status.data_ptr(), st)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0, "otoo_sph_direct: target index out of range"
+    return rho.cpu().numpy()
+
+
 def force_host(lists, plan, precision=L.OTOO_FP32K, tune=None, stream=None, accel=None, pot=None, view=None):
     """otoo_force_host: host arrays in, host arrays out (caller order)."""
     import torch

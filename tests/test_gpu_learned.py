@@ -7,6 +7,7 @@ import pytest
 import oracle
 from paper_1206_1199_gb300 import _lib as L
 from paper_1206_1199_gb300 import ic
+from paper_1206_1199_gb300 import system as S
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +77,12 @@ def test_learned_angles_gain_over_fixed_angle(LR):
     assert 0.2e-3 < res["learned"]["rms"] < 3e-3
     assert abs(res["fixed_equal_rms"]["rms"] - res["learned"]["rms"]) < 0.25 * res["learned"]["rms"]
     assert res["gain_interactions"] > 1.0, res
+
+
+def test_direct_sum_helper_matches_oracle(LR):
+    pos, mass = ic.plummer(5000, 12)
+    tgt = ic.subsample(5000, 200, 3)
+    a, p = S.direct_sum(pos, mass, 0.01, tgt)
+    ar, pr = oracle.direct(pos, mass, 0.01, targets=tgt)
+    np.testing.assert_allclose(a, ar, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(p, pr, rtol=1e-12)

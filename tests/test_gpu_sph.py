@@ -94,3 +94,12 @@ def test_density_whole_device_pipeline(torch, model):
     t = S.Tree(pos, mass, 8)
     hl = t.lists(0.0, 64, 1.0, False, mac="sph", h_sph=h)
     assert abs(dl.interactions - hl.interactions) <= 1e-4 * hl.interactions
+
+
+def test_device_brute_force_matches_oracle(torch):
+    pos, mass = ic.hernquist(6000, 65)
+    h = ic.sph_radii(pos, mass, 64, "hernquist")
+    tgt = ic.subsample(6000, 300, 2)
+    rho = S.sph_direct(pos, mass, h, tgt)
+    ref = oracle.sph_density(pos, mass, h.astype(np.float64), targets=tgt)
+    np.testing.assert_allclose(rho, ref, rtol=1e-12)
