@@ -34,7 +34,7 @@ def _run(cmd):
 
 def sources():
     return [os.path.join(CSRC, s) for s in HOST_SRC + CUDA_SRC + CUDA_HDR] + [os.path.join(CSRC, "common.h"),
-                                                                   os.path.join(CSRC, "treegeom.h"),
+                                                                   os.path.join(CSRC, "treegeom.h"), os.path.join(CSRC, "plan_chunks.h"),
                                                                    os.path.join(INCLUDE, "otoo.h")]
 
 

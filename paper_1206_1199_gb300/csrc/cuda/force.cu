@@ -196,6 +196,25 @@ __global__ void k_split(const otoo_src* __restrict__ src, float4* __restrict__ o
                                  __double2float_rn(z - (double)hz), 0.f);
 }
 
+// Merges the compensated sums (S, C) of a warp's nsub lane subsets into the
+// js == 0 lanes: subset js + d is added into subset js for d = 1, 2, 4, ...
+// while js is a multiple of 2d (a fixed pairwise order, so the result does not
+// depend on timing).  Lane islot + js * P holds subset js of target slot
+// islot; every lane of the warp takes part in the shuffles.
+__device__ __forceinline__ void merge_subsets(float& S, float& C, int js, int nsub, int P)
+{
+    for (int d = 1; d < nsub; d *= 2) {
+        const float so = __shfl_down_sync(kFull, S, d * P);
+        const float co = __shfl_down_sync(kFull, C, d * P);
+        if ((js & (2 * d - 1)) == 0 && js + d < nsub) {
+            const float y = __fsub_rn(__fsub_rn(so, co), C);
+            const float tt = __fadd_rn(S, y);
+            C = __fsub_rn(__fsub_rn(tt, S), y);
+            S = tt;
+        }
+    }
+}
+
 #include "force_warp.cuh"
 #include "force_warp2.cuh"
 

@@ -20,7 +20,7 @@
 //
 // Sums: a lane accumulates pairs in plain FP32 over a tile and adds the tile
 // sum to its Kahan-compensated running sum; the lane subsets are merged with
-// a compensated FP32 sum in subset order and converted to FP64 once.
+// a compensated FP32 sum in a fixed pairwise order and converted to FP64 once.
 
 // Resident warps per SM asked of the register allocator (more warps hide the
 // latency of the staged loads).
@@ -148,9 +148,10 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
                 for (int u = 0; u < 2; ++u) {
                     if (!any[u]) continue;
                     const int k = lane + 32 * (e0 + u);
-                    const float4 a = real[u] ? make_float4((h[u].x - cx) + l[u].x, (h[u].y - cy) + l[u].y,
-                                                           (h[u].z - cz) + l[u].z, h[u].w)
-                                             : zero4;
+                    // padding and rejected entries loaded as zeros: mass (and
+                    // quadrupole) 0, so they add exactly nothing
+                    const float4 a = make_float4((h[u].x - cx) + l[u].x, (h[u].y - cy) + l[u].y,
+                                                 (h[u].z - cz) + l[u].z, h[u].w);
                     if (cq) {
                         rec[3 * k] = a;
                         rec[3 * k + 1] = qa[u];
@@ -216,22 +217,15 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
             __syncwarp();
         }
 
-        // merge the lane subsets into the js == 0 lanes, in subset order, with
-        // a compensated FP32 sum; one conversion to FP64 per output value
+        // merge the lane subsets into the js == 0 lanes (pairwise, in a fixed
+        // order) with a compensated FP32 sum; one conversion to FP64 per output
 #pragma unroll
         for (int k = 0; k < IB; ++k) {
             double a[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 float S = acc[k].s[c], C = acc[k].c[c];
-                for (int j = 1; j < nsub; ++j) {
-                    const float so = __shfl_sync(kFull, acc[k].s[c], islot + j * P);
-                    const float co = __shfl_sync(kFull, acc[k].c[c], islot + j * P);
-                    const float y = __fsub_rn(__fsub_rn(so, co), C);
-                    const float tt = __fadd_rn(S, y);
-                    C = __fsub_rn(__fsub_rn(tt, S), y);
-                    S = tt;
-                }
+                merge_subsets(S, C, js, nsub, P);
                 a[c] = (double)S - (double)C;
             }
             const int i = islot + k * P;

@@ -243,10 +243,12 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
                 float x[2], y[2], z[2], w[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    x[h] = real[h] ? (hh[h].x - cx) + ll[h].x : 0.f;
-                    y[h] = real[h] ? (hh[h].y - cy) + ll[h].y : 0.f;
-                    z[h] = real[h] ? (hh[h].z - cz) + ll[h].z : 0.f;
-                    w[h] = real[h] ? hh[h].w : 0.f;
+                    // padding and rejected entries loaded as zeros: mass (and
+                    // quadrupole) 0, so they add exactly nothing
+                    x[h] = (hh[h].x - cx) + ll[h].x;
+                    y[h] = (hh[h].y - cy) + ll[h].y;
+                    z[h] = (hh[h].z - cz) + ll[h].z;
+                    w[h] = hh[h].w;
                 }
                 if (cq) {
                     float4* r = rec + 5 * m;
@@ -312,22 +314,15 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
             __syncwarp();
         }
 
-        // merge the lane subsets into the js == 0 lanes, in subset order, with
-        // a compensated FP32 sum; one conversion to FP64 per output value
+        // merge the lane subsets into the js == 0 lanes (pairwise, in a fixed
+        // order) with a compensated FP32 sum; one conversion to FP64 per output
 #pragma unroll
         for (int k = 0; k < IB; ++k) {
             double a[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 float S = acc[k].s[c], C = acc[k].c[c];
-                for (int j = 1; j < nsub; ++j) {
-                    const float so = __shfl_sync(kFull, acc[k].s[c], islot + j * P);
-                    const float co = __shfl_sync(kFull, acc[k].c[c], islot + j * P);
-                    const float y = __fsub_rn(__fsub_rn(so, co), C);
-                    const float tt = __fadd_rn(S, y);
-                    C = __fsub_rn(__fsub_rn(tt, S), y);
-                    S = tt;
-                }
+                merge_subsets(S, C, js, nsub, P);
                 a[c] = (double)S - (double)C;
             }
             a[3] = -a[3];  // the potential was summed with the opposite sign

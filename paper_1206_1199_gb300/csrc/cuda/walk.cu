@@ -23,8 +23,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "../common.h"
+#include "../plan_chunks.h"
 
 using namespace otoo;
 
@@ -680,17 +682,7 @@ PlanScratch plan_layout(int32_t* base, int64_t G)
     return p;
 }
 
-// The host plan's cost of one item on a warp (steps through the list in
-// lockstep plus staging and a fixed cost); exact in FP64 (integers and
-// halves far below 2^53), so the choice below matches the host's.
-__device__ __forceinline__ double item_cost(int32_t ni, int64_t len, int32_t ib)
-{
-    const int32_t P = (ni + ib - 1) / ib;
-    const int32_t nsub = 32 / P;
-    return (double)((len + nsub - 1) / nsub) * ib * 36.0 + 0.5 * (double)len + 300.0;
-}
-
-__global__ void k_plan_count(const otoo_group* __restrict__ groups, int32_t G, int32_t ib, int32_t split,
+__global__ void k_plan_count(const otoo_group* __restrict__ groups, int32_t G, const ChunkTable tab, int32_t split,
                              PlanScratch p, int64_t* __restrict__ totals)
 {
     const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -699,21 +691,13 @@ __global__ void k_plan_count(const otoo_group* __restrict__ groups, int32_t G, i
     atomicMax(reinterpret_cast<unsigned long long*>(totals + 3), (unsigned long long)(gr.count > 1 ? gr.count : 1));
     const int64_t len = (int64_t)gr.n_cell + gr.n_part;
     int32_t nic = 0, nch = 0, cls = 0;
-    if (len > 0 && gr.count > 0) {
-        const int32_t imax = 32 * ib;
-        nic = (gr.count + imax - 1) / imax;
-        double best = 0;
-        int32_t bestc = nic;
-        const int32_t cmax = gr.count < nic + 3 ? gr.count : nic + 3;
-        for (int32_t c = nic; c <= cmax; ++c) {
-            const int32_t big = (gr.count + c - 1) / c;
-            const double cost = c * item_cost(big, len, ib);
-            if (c == nic || cost < best) best = cost, bestc = c;
-        }
-        nic = bestc;
+    if (len > 0 && gr.count > 0 && gr.count <= kMaxGroup) {
+        // the host plan's particle chunks (plan_chunks.h)
+        int32_t big = 0;
+        nic = chunk_count(tab, gr.count, &big);
         nch = (int32_t)((len + split - 1) / split);
-        // cost class: 4 * log2 of the first item's ni * (j1 - j0), in quarter octaves
-        const int64_t c0 = (int64_t)((gr.count + nic - 1) / nic) * ((len + nch - 1) / nch);
+        // cost class: 4 * log2 of the largest item's ni * (j1 - j0), in quarter octaves
+        const int64_t c0 = (int64_t)big * ((len + nch - 1) / nch);
         const int msb = 63 - __clzll((long long)c0);
         const int frac = msb >= 2 ? (int)((c0 >> (msb - 2)) & 3) : (int)((c0 << (2 - msb)) & 3);
         cls = 4 * msb + frac;
@@ -742,7 +726,7 @@ __global__ void k_plan_cursor(PlanScratch p)
     }
 }
 
-__global__ void k_plan_fill(const otoo_group* __restrict__ groups, int32_t G, PlanScratch p,
+__global__ void k_plan_fill(const otoo_group* __restrict__ groups, int32_t G, const ChunkTable tab, PlanScratch p,
                             otoo_item* __restrict__ items, int64_t items_cap, otoo_split* __restrict__ splits,
                             int64_t splits_cap, uint32_t* __restrict__ status)
 {
@@ -771,21 +755,22 @@ __global__ void k_plan_fill(const otoo_group* __restrict__ groups, int32_t G, Pl
         s.pad = 0;
         splits[si] = s;
     }
-    int32_t k = pos;
-    for (int32_t ic = 0; ic < nic; ++ic) {
-        const int32_t i0 = (int32_t)((int64_t)gr.count * ic / nic);
-        const int32_t i1 = (int32_t)((int64_t)gr.count * (ic + 1) / nic);
+    int32_t k = pos, i0 = 0;
+    for (int32_t rest = gr.count; rest > 0;) {
+        const int32_t ni = tab.last[rest];
         for (int32_t q = 0; q < nch; ++q) {
             otoo_item it;
             it.g = g;
             it.i0 = i0;
-            it.ni = i1 - i0;
+            it.ni = ni;
             it.j0 = (int32_t)(len * q / nch);
             it.j1 = (int32_t)(len * (q + 1) / nch);
             it.slot = nch > 1 ? slot0 + q : -1;
             it.pad0 = it.pad1 = 0;
             items[k++] = it;
         }
+        i0 += ni;
+        rest -= ni;
     }
 }
 
@@ -794,6 +779,22 @@ __global__ void k_plan_fill(const otoo_group* __restrict__ groups, int32_t G, Pl
         cudaError_t e_ = (expr);                                                                       \
         if (e_ != cudaSuccess) return set_error(OTOO_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));  \
     } while (0)
+
+// The particle-chunk table of the plan for ib targets per lane, built once
+// per process for each ib in {1, 2, 4} (others each call).
+const ChunkTable& chunk_table(int32_t ib)
+{
+    static ChunkTable tabs[3];
+    static std::once_flag once[3];
+    const int k = ib == 1 ? 0 : ib == 2 ? 1 : ib == 4 ? 2 : -1;
+    if (k < 0) {
+        thread_local ChunkTable t;
+        chunk_table_build(ib, t);
+        return t;
+    }
+    std::call_once(once[k], [&] { chunk_table_build(ib, tabs[k]); });
+    return tabs[k];
+}
 
 int check_walk(const otoo_dev_walk* w)
 {
@@ -945,7 +946,8 @@ int otoo_plan_count(const otoo_group* groups, int32_t n_groups, const otoo_tune*
     PlanScratch p = plan_layout(plan_scratch, n_groups);
     CUDA_TRY(cudaMemsetAsync(plan_totals, 0, 4 * sizeof(int64_t), s));
     CUDA_TRY(cudaMemsetAsync(p.hist, 0, kClasses * sizeof(int32_t), s));
-    k_plan_count<<<(n_groups + 255) / 256, 256, 0, s>>>(groups, n_groups, ib, tune->split, p, plan_totals);
+    k_plan_count<<<(n_groups + 255) / 256, 256, 0, s>>>(groups, n_groups, chunk_table(ib), tune->split, p,
+                                                         plan_totals);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(excl_scan(I32In{p.slot0}, I32Out{p.slot0}, n_groups, p.bsum, nullptr, s));
     CUDA_TRY(excl_scan(I32In{p.sidx}, I32Out{p.sidx}, n_groups, p.bsum, nullptr, s));
@@ -964,9 +966,10 @@ int otoo_plan_fill(const otoo_group* groups, int32_t n_groups, const otoo_tune* 
     OTOO_REQUIRE(splits || splits_capacity == 0, OTOO_EINVAL, "otoo_plan_fill: splits is NULL");
     OTOO_REQUIRE(n_groups >= 1, OTOO_EINVAL, "otoo_plan_fill: n_groups < 1");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t ib = tune->iblock > 1 ? tune->iblock : 1;
     PlanScratch p = plan_layout(plan_scratch, n_groups);
-    k_plan_fill<<<(n_groups + 255) / 256, 256, 0, s>>>(groups, n_groups, p, items, items_capacity, splits,
-                                                        splits_capacity, counter + 1);
+    k_plan_fill<<<(n_groups + 255) / 256, 256, 0, s>>>(groups, n_groups, chunk_table(ib), p, items, items_capacity,
+                                                        splits, splits_capacity, counter + 1);
     CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }

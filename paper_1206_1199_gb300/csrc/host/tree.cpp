@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../common.h"
+#include "../plan_chunks.h"
 #include "../treegeom.h"
 
 namespace otoo {
@@ -783,8 +784,9 @@ int otoo_default_tune(int32_t n_crit, otoo_tune* tune)
     return OTOO_OK;
 }
 
-// Work items (longest processing time first over chunks of at most `split`
-// entries, chunks of one group balanced in length).
+// Work items (longest processing time first): each group cut into particle
+// chunks that fill a warp's lanes (plan_chunks.h) times list chunks of at most
+// `split` entries, balanced in length.
 int otoo_make_plan(const otoo_lists* L, const otoo_tune* tune, otoo_plan** out)
 {
     OTOO_REQUIRE(out != nullptr, OTOO_EINVAL, "otoo_make_plan: out is NULL");
@@ -795,45 +797,33 @@ int otoo_make_plan(const otoo_lists* L, const otoo_tune* tune, otoo_plan** out)
         otoo_plan* P = new otoo_plan();
         int32_t ncm = 1;
         for (const otoo_group& g : L->groups) ncm = std::max(ncm, g.count);
+        if (ncm > kMaxGroup) {
+            delete P;
+            return set_error(OTOO_EINVAL, "otoo_make_plan: a group holds more than %d particles", kMaxGroup);
+        }
         P->n_crit_max = ncm;
         const int32_t ib = std::max(1, tune->iblock);
-        const int32_t imax = 32 * ib;  // targets per item
-        // Device time of one item on a warp: its lanes step through the list
-        // in lockstep, ceil(len / nsub) steps of ib pairs each (nsub = 32 /
-        // ceil(ni / ib) lane subsets), plus staging and a fixed cost.  A group
-        // is cut into the number of particle chunks that minimises the sum.
-        auto item_cost = [&](int32_t ni, int64_t len) {
-            const int32_t P = (ni + ib - 1) / ib;
-            const int32_t nsub = 32 / P;
-            return (double)((len + nsub - 1) / nsub) * ib * 36.0 + 0.5 * (double)len + 300.0;
-        };
+        // particle chunks of each group: the cut of plan_chunks.h (warp-filling
+        // item sizes), the same on the device plan
+        ChunkTable tab;
+        chunk_table_build(ib, tab);
         int64_t slot = 0;
         for (size_t g = 0; g < L->groups.size(); ++g) {
             const otoo_group& og = L->groups[g];
             const int64_t len = (int64_t)og.n_cell + og.n_part;
             if (len == 0) continue;  // skipped group
-            int32_t nic = (og.count + imax - 1) / imax;
-            {
-                double best = 0;
-                int32_t bestc = nic;
-                for (int32_t c = nic; c <= std::min<int32_t>(og.count, nic + 3); ++c) {
-                    const int32_t big = (og.count + c - 1) / c;
-                    const double cost = c * item_cost(big, len);
-                    if (c == nic || cost < best) best = cost, bestc = c;
-                }
-                nic = bestc;
-            }
             const int64_t nch = (len + tune->split - 1) / tune->split;
             if (nch > 1) P->splits.push_back({(int32_t)g, (int32_t)slot, (int32_t)nch, 0});
-            for (int32_t ic = 0; ic < nic; ++ic) {
-                // balanced particle chunks
-                const int32_t i0 = (int32_t)((int64_t)og.count * ic / nic);
-                const int32_t i1 = (int32_t)((int64_t)og.count * (ic + 1) / nic);
+            int32_t i0 = 0;
+            for (int32_t rest = og.count; rest > 0;) {
+                const int32_t ni = tab.last[rest];
                 for (int64_t k = 0; k < nch; ++k) {
                     const int64_t j0 = len * k / nch, j1 = len * (k + 1) / nch;
-                    P->items.push_back({(int32_t)g, i0, i1 - i0, (int32_t)j0, (int32_t)j1,
+                    P->items.push_back({(int32_t)g, i0, ni, (int32_t)j0, (int32_t)j1,
                                         nch > 1 ? (int32_t)(slot + k) : -1, 0, 0});
                 }
+                i0 += ni;
+                rest -= ni;
             }
             if (nch > 1) slot += nch;
         }

@@ -286,6 +286,53 @@ def test_plan_covers_every_list_once(split):
         assert p.partial_doubles == sp["n_chunks"].sum() * 4 * p.n_crit_max
 
 
+def _chunk_cut(n, ib):
+    """Restatement of the plan's particle-chunk rule: the cut of n targets
+    into items that minimises the summed modelled warp time (pair steps of
+    36 per target, 4 per staged entry of a 4096-entry list, 600 per item, 40
+    per round of the pairwise subset merge), ties to the smaller last chunk."""
+    def cost(s):
+        nsub = 32 // ((s + ib - 1) // ib)
+        return (4096 + nsub - 1) // nsub * ib * 36 + 4 * 4096 + 600 + (nsub - 1).bit_length() * 40
+    best, last = [0], [0]
+    for m in range(1, n + 1):
+        c = [(best[m - s] + cost(s), s) for s in range(1, min(m, 32 * ib) + 1)]
+        b = min(c)
+        best.append(b[0])
+        last.append(b[1])
+    out = []
+    while n:
+        out.append(last[n])
+        n -= last[n]
+    return out
+
+
+@pytest.mark.parametrize("ib", [1, 2, 4])
+def test_plan_particle_chunks_follow_the_cut(ib):
+    # the items of a group have the sizes of the cost-minimising cut, first
+    # chunk at i0 = 0; a group of 26 at ib = 2 is cut 10 + 16 (5 lanes x 6
+    # subsets and 8 lanes x 4 subsets: 31 of 32 lanes busy against 26 lanes
+    # for one item of 13 x 2)
+    assert _chunk_cut(26, 2) == [10, 16] and _chunk_cut(64, 2) == [64] and _chunk_cut(128, 2) == [64, 64]
+    pos, mass = ic.plummer(20000, 29)
+    _, lists = tree_and_lists(pos, mass, 0.5, 128)
+    tune = L.default_tune(128)
+    tune.iblock, tune.split = ib, 100000
+    plan = lists.plan(tune)  # the items view borrows the plan's memory
+    it = plan.items
+    g = lists.groups
+    per = {}
+    for r in it:
+        per.setdefault(int(r["g"]), []).append((int(r["i0"]), int(r["ni"])))
+    memo = {}
+    for gi, segs in per.items():
+        n = int(g["count"][gi])
+        if n not in memo:
+            memo[n] = _chunk_cut(n, ib)
+        assert [ni for _, ni in sorted(segs)] == memo[n], (gi, n, sorted(segs))
+    assert sum(int(r["ni"]) for r in it) == int(g["count"].sum())
+
+
 def test_invalid_inputs_return_einval():
     pos, mass = ic.plummer(100, 28)
     for bad_pos, bad_mass in ((pos * np.nan, mass), (pos, mass * 0), (pos, -mass)):
