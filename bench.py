@@ -31,9 +31,9 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 partitions x 32)
 
 # DRAM bytes of one force-kernel launch (dram__bytes_read.sum +
 # dram__bytes_write.sum, one ncu capture of k_force_warp2<4,2,8> on the
-# Hernquist N = 2^23 workload: 23.61 GB + 0.671 GB), keyed by the workload,
+# Hernquist N = 2^23 workload: 27.36 GB + 0.673 GB), keyed by the workload,
 # n_crit and tuning it was taken on; other configurations report null.
-CAPTURED_TRAFFIC = {("hernquist8m", 8388608, 128, (128, 2, 256, 16384, 1)): 23.61e9 + 0.671e9}
+CAPTURED_TRAFFIC = {("hernquist8m", 8388608, 128, (128, 2, 256, 8192, 1)): 27.36e9 + 0.6726e9}
 
 
 def parse():
@@ -256,10 +256,24 @@ def run_ours(args):
             rms64, mx64 = rel_err(a64[sub], ad)
             errors.update({"fp64_acc_rms": rms64, "fp64_acc_max": mx64})
 
-    # end to end through the C ABI from pinned host buffers
-    e2e = None
+    # end to end through the C ABI from pinned host buffers: the user's time
+    # step (positions in, tree, walk, plan and force on the device,
+    # accelerations out) and the force step on lists built by the host
+    # (groups, lists and work items copied in)
+    e2e = e2e_lists = step = None
+    if not args.skip_step:
+        step = guarded_extra(run_device_step, args, dev_name, pos, mass, w, tune, tree, lists, a32, stream, t1 - t0,
+                             world)
     if not args.skip_e2e:
-        e2e = run_e2e(args, lists, plan, tune, stream, world)
+        e2e_lists = run_e2e(args, lists, plan, tune, stream, world)
+    if step is not None and "error" not in step:
+        e2e = {"value": step["value"], "unit": "interactions/s", "ms_per_step": step["step_wall_ms"],
+               "h2d_bytes_per_step": step["h2d_bytes_per_step"], "d2h_bytes_per_step": step["d2h_bytes_per_step"],
+               "steps": step["steps"],
+               "path": "pinned host positions and masses in; tree, walk, plan and force on the device; "
+                       "accelerations and potentials out (interactions equal to the host walk's)"}
+    elif e2e_lists is not None:
+        e2e = dict(e2e_lists, path="host-built groups, lists and work items copied in; force; results out")
 
     flops = 20.0 * mono_inter + (60.0 if lists.use_quad else 20.0) * cell_inter
     props = torch.cuda.get_device_properties(local)
@@ -300,6 +314,7 @@ def run_ours(args):
         "fp64_form": fp64,
         "errors": errors,
         "e2e": e2e,
+        "e2e_host_lists": e2e_lists,
         "clocks": clocks,
         # per FP32 step: the float-pair split, the force kernel, the chunk merge when lists are split
         "gpu_launches": args.steps * (2 + (1 if plan.n_splits else 0)),
@@ -307,9 +322,8 @@ def run_ours(args):
     if rank == 0 and not args.skip_walk:
         line["device_walk"] = guarded_extra(run_device_walk, args, dev_name, tree, w, tune, lists, a32, stream,
                                             t2 - t1, t3 - t2)
-    if rank == 0 and not args.skip_step:
-        line["device_step"] = guarded_extra(run_device_step, args, dev_name, pos, mass, w, tune, tree, lists, a32,
-                                            stream, t1 - t0)
+    if rank == 0 and step is not None:
+        line["device_step"] = step
     if rank == 0 and not args.skip_sph:
         line["sph_density"] = guarded_extra(run_sph, args, dev_name, pos, mass, w, stream)
     if rank == 0 and not args.skip_sw and errors is not None:
@@ -389,7 +403,7 @@ def run_device_walk(args, dev_name, tree, w, tune, lists, a32, stream, host_walk
             "items": int(dp.n_items), "fp32_vs_host_lists_acc_rms": rms, "fp32_vs_host_lists_acc_max": mx}
 
 
-def run_device_step(args, dev_name, pos, mass, w, tune, tree, lists, a32, stream, host_tree_s):
+def run_device_step(args, dev_name, pos, mass, w, tune, tree, lists, a32, stream, host_tree_s, world=1):
     """The whole step on the device, from host positions to host
     accelerations: copy positions and masses in (pinned memory), build the
     tree (otoo_devtree_build), walk, plan, force, copy accelerations and
@@ -444,14 +458,14 @@ def run_device_step(args, dev_name, pos, mass, w, tune, tree, lists, a32, stream
         walls.append(time.perf_counter() - t0)
         times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(5)])
     med = np.median(np.array(times), axis=0)
-    wall = float(np.median(walls))
+    wall = max_over_ranks(float(np.median(walls)), dev_name)  # the slowest rank's step
     hg, gd = lists.groups, dl.groups
     same_groups = bool(np.array_equal(gd["first"], hg["first"]) and np.array_equal(gd["count"], hg["count"]))
     same_counts = float(np.mean((gd["n_cell"] == hg["n_cell"]) & (gd["n_part"] == hg["n_part"])))
     rms, mx = rel_err(acc_h.numpy(), a32)
     return {"step_wall_ms": wall * 1e3, "steps": k, "h2d_ms": float(med[0]), "tree_ms": float(med[1]),
             "walk_ms": float(med[2]), "plan_force_ms": float(med[3]), "d2h_ms": float(med[4]),
-            "value": dl.interactions / wall, "unit": "interactions/s",
+            "value": world * dl.interactions / wall, "unit": "interactions/s",
             "h2d_bytes_per_step": int(n * 28), "d2h_bytes_per_step": int(n * 32),
             "host_tree_ms": host_tree_s * 1e3, "n_cell": int(dt.n_cell),
             "n_cell_equal_host": bool(dt.n_cell == tree.export()["n_cell"]), "groups_equal_host": same_groups,
