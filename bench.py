@@ -331,6 +331,7 @@ def run_ours(args):
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_seconds)
     if rank == 0 and not args.skip_extras and args.workload == "hernquist8m":
+        line["paper_workloads"] = guarded_extra(run_paper_workloads, args, dev_name, tune, stream)
         line["batch64"] = guarded_extra(run_batch, args, dev_name)
         line["learned_merger4m"] = guarded_extra(run_learned, args, dev_name)
     if rank == 0:
@@ -569,6 +570,64 @@ def run_sw_sweep(args, dev_name, tree, w, tune, stream, sub, ad):
     slopes = [math.log(b["interactions"] / a["interactions"]) / math.log(b["delta"] / a["delta"])
               for a, b in zip(done, done[1:])]
     return {"m_limit": m_limit, "rows": rows, "cost_slopes": slopes, "error_targets": int(len(sub))}
+
+
+# The paper's own gravity benchmark (Section IV-A): N = 8M Plummer model and
+# uniform sphere, absolute MAC with delta = 0.01 and m_limit = 0.05, monopole
+# cells, tree leaves of 16; its OpenCL kernel time per step on one Tesla
+# M2090 (walk and force fused on the GPU, single precision).
+PAPER_WORKLOADS = (("plummer", 1 << 23, 2.08, "1x Tesla M2090 (2012), OpenCL, walk and force fused"),
+                   ("uniform", 8000 * 1024, 1.52, "1x Tesla M2090 (2012), OpenCL, walk and force fused"))
+
+
+def run_paper_workloads(args, dev_name, tune, stream):
+    """The paper's gravity benchmark configurations, for context beside its
+    published kernel times: device tree (leaf size 16), device walk with the
+    absolute MAC (delta 0.01, m_limit 0.05), plan and FP32 force (monopole
+    cells, eps 1e-3: the paper gives no softening); errors against the FP64
+    direct sum on 256 targets."""
+    import torch
+
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import ic
+    from paper_1206_1199_gb300 import system as S
+    out = []
+    eps = 1e-3
+    for model, n, paper_s, paper_hw in PAPER_WORKLOADS:
+        pos, mass = ic.make(model, n, ic.BASE_SEED + 6)
+        pos_d = torch.from_numpy(np.ascontiguousarray(pos)).to(dev_name)
+        mass_d = torch.from_numpy(np.ascontiguousarray(mass)).to(dev_name)
+        acc = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
+        pot = torch.empty(n, dtype=torch.float64, device=dev_name)
+
+        def one():
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            dt = S.DeviceTree.build(pos_d, mass_d, 16, 128, False, dev_name, mac="sw", delta=0.01, m_limit=0.05,
+                                    stream=stream)
+            ev[1].record(stream)
+            dl = dt.walk(0.0, eps, stream=stream)
+            ev[2].record(stream)
+            S.force(S.DeviceStep(dl, dl.plan(tune, stream=stream)), acc, pot, L.OTOO_FP32K, tune, stream=stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            return dl, [ev[i].elapsed_time(ev[i + 1]) for i in range(3)]
+
+        one()
+        runs = [one() for _ in range(3)]
+        dl = runs[-1][0]
+        med = np.median(np.array([r[1] for r in runs]), axis=0)
+        sub = ic.subsample(n, 256, 11)
+        ad, _ = S.direct_sum(pos, mass, eps, sub, dev_name)
+        rms, mx = rel_err(acc.cpu().numpy()[sub], ad)
+        out.append({"model": model, "n": n, "interactions": int(dl.interactions), "tree_ms": float(med[0]),
+                    "walk_ms": float(med[1]), "plan_force_ms": float(med[2]),
+                    "gravity_ms": float(med[1] + med[2]), "acc_rms": rms, "acc_max": mx, "error_targets": 256,
+                    "paper_kernel_s": paper_s, "paper_hardware": paper_hw})
+        del dl, runs
+        torch.cuda.empty_cache()
+    return {"mac": "absolute, delta 0.01, m_limit 0.05", "cells": "monopole", "leaf_size": 16, "n_crit": 128,
+            "eps": eps, "rows": out}
 
 
 def run_batch(args, dev_name):

@@ -33,6 +33,14 @@ using namespace otoo;
 namespace {
 
 constexpr int kWalkWarps = 8;       // warps per CTA
+#ifndef OTOO_WALK_HALVES
+#define OTOO_WALK_HALVES 2
+#endif
+constexpr int kWalkHalves = OTOO_WALK_HALVES;  // cells per lane per walk step
+#ifndef OTOO_WALK_MIN_BLOCKS
+#define OTOO_WALK_MIN_BLOCKS 3  // resident CTAs per SM asked of the register allocator (85 registers)
+#endif
+constexpr int kWide = 32 * kWalkHalves;         // cells per walk step at most
 constexpr int kStack = 512;         // stack entries (runs of sibling cells) per warp
 constexpr int kMaxLevels = 22;      // tree levels (root level 0 to the 2^21 grid level)
 constexpr int kScanThreads = 1024;  // scan kernels: threads per CTA
@@ -265,19 +273,20 @@ constexpr uint32_t kRunMask = (1u << kRunShift) - 1u;
 __device__ __forceinline__ uint32_t run(int first, int n) { return (uint32_t)first | ((uint32_t)(n - 1) << kRunShift); }
 
 // One warp per group (atomic ticket).  The stack holds runs of sibling
-// cells; each step takes up to 32 cells from the top runs (the last run may
-// be split, its rest goes back), tests them, emits accepted cells and
-// rejected leaves' particles and pushes one run per rejected inner cell (its
-// children).  A 32-cell step adds at most 32 entries and runs only with
-// 33 + kMaxLevels entries free; otherwise the step takes one cell, which adds
-// at most one entry, and only when it descends a level (a tree has at most
-// kMaxLevels levels below any cell), so the stack never overflows.
+// cells; each step takes up to kWide = 32 kWalkHalves cells from the top runs
+// (the last run may be split, its rest goes back; lane j tests the cells at
+// positions j, j + 32, ...), emits accepted cells and rejected leaves'
+// particles in position order and pushes one run per rejected inner cell (its
+// children).  A kWide-cell step adds at most kWide entries and runs only with
+// kWide + 1 + kMaxLevels entries free; otherwise the step takes one cell,
+// which adds at most one entry, and only when it descends a level (a tree has
+// at most kMaxLevels levels below any cell), so the stack never overflows.
 // kMode 0: count (group records, totals); 1: fill the list at the offsets
 // of pass 0; 2: single pass -- count as pass 0 and write each group's entries
 // into fixed slots of two pools (cells: list = cell pool, capacity = slot
 // size; particles: ppool, pcap), for otoo_walk_compact.
 template <int kMode>
-__global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_group* __restrict__ groups,
+__global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(WalkArgs a, otoo_group* __restrict__ groups,
                                                           int32_t* __restrict__ list, int64_t capacity,
                                                           int32_t* __restrict__ ppool, int64_t pcap)
 {
@@ -383,7 +392,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
                 failed = true;
                 break;
             }
-            const int wcap = sp + 33 + kMaxLevels <= kStack ? 32 : 1;
+            const int wcap = sp + kWide + 1 + kMaxLevels <= kStack ? kWide : 1;
             // the top runs: lane l reads the l-th entry from the top
             const int nr = sp < 32 ? sp : 32;
             uint32_t e = 0;
@@ -401,7 +410,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
             const unsigned cutm = __ballot_sync(kFull, cut);
             const int in_whole = __shfl_sync(kFull, rinc, nwhole > 0 ? nwhole - 1 : 0);
             const int W = cutm ? wcap : (nwhole > 0 ? in_whole : 0);
-            const unsigned starts = __reduce_or_sync(kFull, (whole || cut) ? (1u << rstart) : 0u);
+            // start positions of the taken runs, 32 positions per mask word
+            unsigned starts[kWalkHalves];
+#pragma unroll
+            for (int h = 0; h < kWalkHalves; ++h)
+                starts[h] = __reduce_or_sync(kFull, (whole || cut) && rstart >= 32 * h && rstart < 32 * h + 32
+                                                        ? (1u << (rstart - 32 * h))
+                                                        : 0u);
             // the run that continues after the cut goes back on the stack first
             sp -= nwhole + (cutm ? 1 : 0);
             if (cut) {
@@ -414,64 +429,86 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 4) k_walk(WalkArgs a, otoo_gr
                 failed = true;
                 break;
             }
-            // lane j < W takes the cell at position j of the taken runs
-            int node = -1;
-            {
-                const int r = __popc(starts & ((2u << lane) - 1u)) - 1;
+            // lane j takes the cells at positions j, j + 32, ... of the taken
+            // runs; position q lies in the run whose start is the last one <= q
+            int kind[kWalkHalves], c0[kWalkHalves], nch[kWalkHalves], pb[kWalkHalves], pe[kWalkHalves];
+            int node[kWalkHalves];
+#pragma unroll
+            for (int h = 0; h < kWalkHalves; ++h) {
+                int r = -1;
+#pragma unroll
+                for (int k = 0; k <= h; ++k)
+                    r += __popc(starts[k] & (k < h ? 0xffffffffu : (2u << lane) - 1u));
                 const uint32_t er = __shfl_sync(kFull, e, r < 0 ? 0 : r);
                 const int sr = __shfl_sync(kFull, rstart, r < 0 ? 0 : r);
-                if (lane < W) node = (int)(er & kRunMask) + (lane - sr);
+                const int q = lane + 32 * h;
+                node[h] = q < W ? (int)(er & kRunMask) + (q - sr) : -1;
+                kind[h] = 0;  // 1 accept, 2 leaf, 3 open
+                c0[h] = nch[h] = pb[h] = pe[h] = 0;
             }
             __syncwarp();
-            int kind = 0;  // 1 accept, 2 leaf, 3 open
-            int c0 = 0, nch = 0, pb = 0, pe = 0;
-            if (lane < W) {
-                bool ok = node >= 0 && node < a.n_cell;
+#pragma unroll
+            for (int h = 0; h < kWalkHalves; ++h) {
+                if (lane + 32 * h >= W) continue;
+                const int nd = node[h];
+                bool ok = nd >= 0 && nd < a.n_cell;
                 if (ok) {
-                    const otoo_wcell w = load_wcell(a.cell, node);
-                    nch = w.nchild;
-                    c0 = w.child0;
-                    pb = w.begin;
-                    pe = w.end;
-                    ok = nch >= 0 && nch <= 8 && (nch == 0 || (c0 > node && (int64_t)c0 + nch <= a.n_cell)) &&
-                         pb >= 0 && pb <= pe && (int64_t)pe <= a.n_part;
+                    const otoo_wcell w = load_wcell(a.cell, nd);
+                    nch[h] = w.nchild;
+                    c0[h] = w.child0;
+                    pb[h] = w.begin;
+                    pe[h] = w.end;
+                    ok = nch[h] >= 0 && nch[h] <= 8 &&
+                         (nch[h] == 0 || (c0[h] > nd && (int64_t)c0[h] + nch[h] <= a.n_cell)) && pb[h] >= 0 &&
+                         pb[h] <= pe[h] && (int64_t)pe[h] <= a.n_part;
                     if (ok) {
                         int dec = 0;
                         if (sw) {
                             dec = a.exact ? -1 : mac_filter_sw(w, bf);
-                            if (dec < 0) dec = sw_exact(a.cell64, node, blo, bhi) ? 1 : 0;
+                            if (dec < 0) dec = sw_exact(a.cell64, nd, blo, bhi) ? 1 : 0;
                         } else if (!open_all) {
-                            dec = a.exact ? -1 : small_angle ? mac_filter<false>(w, bf, invth) : mac_filter<true>(w, bf, invth);
-                            if (dec < 0) dec = mac_exact(a.cell64, node, blo, bhi, theta) ? 1 : 0;
+                            dec = a.exact ? -1
+                                  : small_angle ? mac_filter<false>(w, bf, invth)
+                                                : mac_filter<true>(w, bf, invth);
+                            if (dec < 0) dec = mac_exact(a.cell64, nd, blo, bhi, theta) ? 1 : 0;
                         }
-                        kind = dec ? 1 : (nch == 0 ? 2 : 3);
+                        kind[h] = dec ? 1 : (nch[h] == 0 ? 2 : 3);
                     }
                 }
                 if (!ok) atomicOr(status, kWalkBadRecord);
             }
-            // accepted cells
-            const unsigned am = __ballot_sync(kFull, kind == 1 && !drop);
-            if (kWrite && kind == 1 && !drop) {
-                const int32_t r = ncell + __popc(am & lt);
-                if (r < want_c) list[off_c + r] = (int32_t)(a.n_part + node);
+            // accepted cells, in position order
+#pragma unroll
+            for (int h = 0; h < kWalkHalves; ++h) {
+                const unsigned am = __ballot_sync(kFull, kind[h] == 1 && !drop);
+                if (kWrite && kind[h] == 1 && !drop) {
+                    const int32_t r = ncell + __popc(am & lt);
+                    if (r < want_c) list[off_c + r] = (int32_t)(a.n_part + node[h]);
+                }
+                ncell += __popc(am);
             }
-            ncell += __popc(am);
-            // particles of rejected leaves
-            if (__any_sync(kFull, kind == 2)) {
-                const int np = kind == 2 ? pe - pb : 0;
+            // particles of rejected leaves, in position order
+#pragma unroll
+            for (int h = 0; h < kWalkHalves; ++h) {
+                if (!__any_sync(kFull, kind[h] == 2)) continue;
+                const int np = kind[h] == 2 ? pe[h] - pb[h] : 0;
                 const int pin = warp_incl_scan(np, lane);
                 if (kWrite && np > 0) {
                     const int32_t base = npart + pin - np;
                     for (int k = 0; k < np; ++k)
-                        if (base + k < want_p) pdst[off_p + base + k] = pb + k;
+                        if (base + k < want_p) pdst[off_p + base + k] = pb[h] + k;
                 }
                 npart += __shfl_sync(kFull, pin, 31);
             }
-            // one run per rejected inner cell, the lowest lane's on top
-            const unsigned om = __ballot_sync(kFull, kind == 3);
-            const int no = __popc(om);
-            if (kind == 3) stk[sp + no - 1 - __popc(om & lt)] = run(c0, nch);
-            sp += no;
+            // one run per rejected inner cell, the lowest position's on top:
+            // the last positions are pushed first
+#pragma unroll
+            for (int h = kWalkHalves - 1; h >= 0; --h) {
+                const unsigned om = __ballot_sync(kFull, kind[h] == 3);
+                const int no = __popc(om);
+                if (kind[h] == 3) stk[sp + no - 1 - __popc(om & lt)] = run(c0[h], nch[h]);
+                sp += no;
+            }
             __syncwarp();
         }
         if (failed && lane == 0) atomicOr(status, kWalkOverflow);
