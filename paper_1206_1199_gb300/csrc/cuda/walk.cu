@@ -354,8 +354,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
         const bool sw = a.mac == OTOO_MAC_SW || a.mac == OTOO_MAC_SPH;
         const bool drop = a.mac == OTOO_MAC_SPH;
         const double theta = sw ? 0.0 : a.tpg ? (double)a.tpg[g] : a.theta;
-        const bool open_all = !sw && !(theta > 0.0);
-        const bool small_angle = theta < 0.57;  // below 1/sqrt(3) = 0.5774 with room for rounding
+        // the per-group choices as bits of an integer, taken through an opaque
+        // move: the compiler must not re-derive them from theta inside the
+        // walk loop, where FP64 compares would occupy GB300's narrow FP64 pipe
+        int fl = (!sw && !(theta > 0.0) ? 1 : 0) | (theta < 0.57 ? 2 : 0);  // 0.57 < 1/sqrt(3) = 0.5774
+        asm volatile("mov.b32 %0, %0;" : "+r"(fl));
+        const bool open_all = (fl & 1) != 0;
+        const bool small_angle = (fl & 2) != 0;
         // 1/theta within 2^-23 (the filter's margins allow 2^-21)
         const float invth = open_all ? 0.f : __frcp_rn(__double2float_rn(theta));
         int64_t off_c = 0, off_p = 0;
