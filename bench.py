@@ -331,6 +331,7 @@ def run_ours(args):
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_seconds)
     if rank == 0 and not args.skip_extras and args.workload == "hernquist8m":
+        line["fused_walk_force"] = guarded_extra(run_fused, args, dev_name, pos, mass, w, tune, stream)
         line["paper_workloads"] = guarded_extra(run_paper_workloads, args, dev_name, tune, stream)
         line["batch64"] = guarded_extra(run_batch, args, dev_name)
         line["learned_merger4m"] = guarded_extra(run_learned, args, dev_name)
@@ -570,6 +571,62 @@ def run_sw_sweep(args, dev_name, tree, w, tune, stream, sub, ad):
     slopes = [math.log(b["interactions"] / a["interactions"]) / math.log(b["delta"] / a["delta"])
               for a, b in zip(done, done[1:])]
     return {"m_limit": m_limit, "rows": rows, "cost_slopes": slopes, "error_targets": int(len(sub))}
+
+
+def run_fused(args, dev_name, pos, mass, w, tune, stream):
+    """The walk fused with the force (otoo_walk_force: one warp per group
+    walks and evaluates, no list in memory) against the split device step
+    (one-pass walk into lists, plan, packed force) on the same device tree,
+    for n_crit 64 (2 targets per lane) and 128 (4 per lane); errors against
+    the FP64 direct sum on 256 targets."""
+    import torch
+
+    from paper_1206_1199_gb300 import _lib as L
+    from paper_1206_1199_gb300 import ic
+    from paper_1206_1199_gb300 import system as S
+    n = len(pos)
+    pos_d = torch.from_numpy(np.ascontiguousarray(pos)).to(dev_name)
+    mass_d = torch.from_numpy(np.ascontiguousarray(mass)).to(dev_name)
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
+    pot = torch.empty(n, dtype=torch.float64, device=dev_name)
+    sub = ic.subsample(n, 256, 13)
+    ad, _ = S.direct_sum(pos, mass, w["eps"], sub, dev_name)
+    rows = []
+
+    def timed(fn, k=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    for nc, ib in ((64, 2), (128, 4)):
+        dt = S.DeviceTree.build(pos_d, mass_d, w["leaf_size"], nc, w["use_quad"], dev_name, stream=stream)
+        fs = dt.fused(w["theta"], w["eps"], ib)
+        fused_ms = timed(lambda: fs(acc, pot, stream=stream, check=False))
+        fs(acc, pot, stream=stream)
+        rms, mx = rel_err(acc.cpu().numpy()[sub], ad)
+        nl, inter, cinter = fs.totals()
+        t = L.Tune(block=128, iblock=2, tile=256, split=8192, ctas_per_sm=0, packed=1)
+        pool = S.BufferPool(dev_name)
+        dt.walk(w["theta"], w["eps"], stream=stream, pool=pool)
+
+        def split_step():
+            dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool)
+            S.force(S.DeviceStep(dl, dl.plan(t, stream=stream)), acc, pot, L.OTOO_FP32K, t, stream=stream,
+                    check=False)
+
+        split_ms = timed(split_step)
+        rows.append({"n_crit": nc, "iblock": ib, "interactions": int(inter), "cell_interactions": int(cinter),
+                     "fused_ms": fused_ms, "split_walk_plan_force_ms": split_ms,
+                     "fused_interactions_per_s": inter / (fused_ms * 1e-3), "acc_rms": rms, "acc_max": mx})
+        del dt, fs, pool
+        torch.cuda.empty_cache()
+    return {"rows": rows, "error_targets": 256}
 
 
 # The paper's own gravity benchmark (Section IV-A): N = 8M Plummer model and

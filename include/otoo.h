@@ -466,6 +466,29 @@ int otoo_walk_compact(const otoo_dev_walk* walk, const otoo_group* groups, const
                       int64_t cell_cap, const int32_t* part_pool, int64_t part_cap, int32_t* list,
                       int64_t capacity, void* stream);
 
+/* The walk fused with the FP32 force (Section III-D: the paper's GPU kernel
+   walks the tree for each group of particles and evaluates the interactions
+   it finds, with no interaction list in memory).  One warp per group walks as
+   otoo_walk_count does (same acceptance decisions) and evaluates each tile of
+   accepted cells or leaf particles as soon as it is complete, with the pair
+   arithmetic of otoo_force's packed FP32 form (centre-relative FP32 pairs,
+   per-tile Kahan sums, FP64 outputs).
+   walk: as for otoo_walk_count (OTOO_MAC_THETA or OTOO_MAC_SW; every group at
+   most 32 * iblock particles, larger groups get no output and set the status
+   word).  quad: device, [n_cell] quadrupoles as otoo_tree_device_arrays
+   writes them, or NULL for monopole cells.  perm: device, [n_part] tree ->
+   caller order (NULL: tree order).  split: device scratch, 8 * (n_part +
+   n_cell) floats (the per-step float pairs of the positions).  iblock:
+   targets per lane, 1, 2 or 4.  accel: device, [n_part][3]; pot: device,
+   [n_part] (groups skipped by a negative per-group angle are not written).
+   totals[0..4] as otoo_walk_count: list entries, interactions, cell
+   interactions, largest n_cell and n_part.  Asynchronous on stream; errors
+   of the walk or a group too large for iblock are reported by
+   otoo_walk_check_status.  Errors: OTOO_EINVAL (arguments, OTOO_MAC_SPH),
+   OTOO_ECUDA. */
+int otoo_walk_force(const otoo_dev_walk* walk, const otoo_quad* quad, const int64_t* perm, float* split,
+                    int32_t iblock, double* accel, double* pot, void* stream);
+
 /* Reads the walk's status word after a sync: OTOO_EDEVICE when a record
    failed its bounds check, a group's stack overflowed, the two passes
    disagreed, or the list did not fit. */

@@ -159,6 +159,7 @@ _SIGS = {
     "otoo_walk_count": [ctypes.POINTER(DevWalk), vp, vp],
     "otoo_walk_fill": [ctypes.POINTER(DevWalk), vp, vp, i64, vp],
     "otoo_walk_check_status": [ctypes.POINTER(DevWalk), vp],
+    "otoo_walk_force": [ctypes.POINTER(DevWalk), vp, vp, vp, i32, vp, vp, vp],
     "otoo_walk_single": [ctypes.POINTER(DevWalk), vp, vp, i64, vp, i64, vp],
     "otoo_walk_compact": [ctypes.POINTER(DevWalk), vp, vp, i64, vp, i64, vp, i64, vp],
     "otoo_plan_scratch_ints": [i64],

@@ -14,6 +14,11 @@ int set_error(int code, const char* fmt, ...);
 // Largest group the device kernels accept (threads * particles per thread).
 constexpr int kMaxGroup = 1024;
 
+// Enqueues the float-pair split of the FP32 form on a CUDA stream: out[2 s] =
+// (x, y, z rounded to FP32, m), out[2 s + 1] = (the rounding remainders, 0)
+// for the n sources (force.cu).  Returns OTOO_OK or OTOO_ECUDA.
+int enqueue_split(const otoo_src* src, float* out, int64_t n, void* stream);
+
 }  // namespace otoo
 
 #define OTOO_REQUIRE(cond, code, ...)                      \

@@ -35,100 +35,11 @@ using namespace otoo;
 
 namespace {
 
-template <typename R> struct V4;
-template <> struct __align__(16) V4<float> { float x, y, z, w; };
-template <> struct __align__(32) V4<double> { double x, y, z, w; };
-template <typename R> struct V2;
-template <> struct __align__(8) V2<float> { float x, y; };
-template <> struct __align__(16) V2<double> { double x, y; };
-
-// FP32 reciprocal square root: the hardware approximation (PTX
-// rsqrt.approx.ftz.f32, relative error about 2^-23); the argument r^2 + eps^2
-// is never subnormal for eps > 0, so flushing subnormals changes nothing.
-__device__ __forceinline__ float rsqrt_r(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
-
 // Status bits written to counter[1].
 constexpr uint32_t kBadItem = 1u;
 constexpr uint32_t kBadIndex = 2u;
-constexpr unsigned kFull = 0xffffffffu;
 
-// Running sum of one target particle: FP32 with Kahan compensation c (the sum
-// is s - c), FP64 plain.
-template <typename R> struct Acc {
-    R s[4], c[4];
-    __device__ __forceinline__ void zero()
-    {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s[k] = c[k] = R(0);
-    }
-    __device__ __forceinline__ void add(const R p[4]);
-    __device__ __forceinline__ double value(int k) const;
-};
-template <> __device__ __forceinline__ void Acc<float>::add(const float p[4])
-{
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float y = __fsub_rn(p[k], c[k]);
-        const float t = __fadd_rn(s[k], y);
-        c[k] = __fsub_rn(__fsub_rn(t, s[k]), y);
-        s[k] = t;
-    }
-}
-template <> __device__ __forceinline__ double Acc<float>::value(int k) const { return (double)s[k] - (double)c[k]; }
-template <> __device__ __forceinline__ void Acc<double>::add(const double p[4])
-{
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s[k] += p[k];
-}
-template <> __device__ __forceinline__ double Acc<double>::value(int k) const { return s[k]; }
-
-// Monopole pair (also a particle entry): r = x_j - x_i,
-// a += m r / (r^2 + eps^2)^(3/2), phi -= m / (r^2 + eps^2)^(1/2).
-template <typename R>
-__device__ __forceinline__ void pair_mono(const V4<R>& s, R xi, R yi, R zi, R eps2, R p[4])
-{
-    const R rx = s.x - xi, ry = s.y - yi, rz = s.z - zi;
-    const R r2 = fma(rx, rx, fma(ry, ry, fma(rz, rz, eps2)));
-    const R q = rsqrt_r(r2);
-    const R mq = s.w * q;
-    const R mq3 = mq * (q * q);
-    p[3] -= mq;
-    p[0] = fma(mq3, rx, p[0]);
-    p[1] = fma(mq3, ry, p[1]);
-    p[2] = fma(mq3, rz, p[2]);
-}
-
-// Quadrupole cell: with q = (r^2 + eps^2)^(-1/2),
-// phi -= m q + (1/2) (r.Q.r) q^5,  a += (m q^3 + (5/2) (r.Q.r) q^7) r - q^5 Q r.
-template <typename R>
-__device__ __forceinline__ void pair_quad(const V4<R>& s, const V4<R>& qa, const V2<R>& qb, R xi, R yi, R zi,
-                                          R eps2, R p[4])
-{
-    const R rx = s.x - xi, ry = s.y - yi, rz = s.z - zi;
-    const R r2 = fma(rx, rx, fma(ry, ry, fma(rz, rz, eps2)));
-    const R q = rsqrt_r(r2);
-    const R q2 = q * q;
-    const R mq = s.w * q;
-    const R mq3 = mq * q2;
-    // qa = (xx, yy, zz, xy), qb = (xz, yz)
-    const R qr0 = fma(qa.x, rx, fma(qa.w, ry, qb.x * rz));
-    const R qr1 = fma(qa.w, rx, fma(qa.y, ry, qb.y * rz));
-    const R qr2 = fma(qb.x, rx, fma(qb.y, ry, qa.z * rz));
-    const R rqr = fma(rx, qr0, fma(ry, qr1, rz * qr2));
-    const R q5 = q * (q2 * q2);
-    const R t = rqr * q5;
-    p[3] -= fma(R(0.5), t, mq);
-    const R cr = fma(R(2.5) * t, q2, mq3);
-    p[0] = fma(cr, rx, fma(-q5, qr0, p[0]));
-    p[1] = fma(cr, ry, fma(-q5, qr1, p[1]));
-    p[2] = fma(cr, rz, fma(-q5, qr2, p[2]));
-}
+#include "pair.cuh"
 
 __device__ __forceinline__ void load_src(const otoo_src* src, int64_t idx, double& x, double& y, double& z, float& m)
 {
@@ -194,25 +105,6 @@ __global__ void k_split(const otoo_src* __restrict__ src, float4* __restrict__ o
     out[2 * s] = make_float4(hx, hy, hz, m);
     out[2 * s + 1] = make_float4(__double2float_rn(x - (double)hx), __double2float_rn(y - (double)hy),
                                  __double2float_rn(z - (double)hz), 0.f);
-}
-
-// Merges the compensated sums (S, C) of a warp's nsub lane subsets into the
-// js == 0 lanes: subset js + d is added into subset js for d = 1, 2, 4, ...
-// while js is a multiple of 2d (a fixed pairwise order, so the result does not
-// depend on timing).  Lane islot + js * P holds subset js of target slot
-// islot; every lane of the warp takes part in the shuffles.
-__device__ __forceinline__ void merge_subsets(float& S, float& C, int js, int nsub, int P)
-{
-    for (int d = 1; d < nsub; d *= 2) {
-        const float so = __shfl_down_sync(kFull, S, d * P);
-        const float co = __shfl_down_sync(kFull, C, d * P);
-        if ((js & (2 * d - 1)) == 0 && js + d < nsub) {
-            const float y = __fsub_rn(__fsub_rn(so, co), C);
-            const float tt = __fadd_rn(S, y);
-            C = __fsub_rn(__fsub_rn(tt, S), y);
-            S = tt;
-        }
-    }
 }
 
 #include "force_warp.cuh"
@@ -440,6 +332,19 @@ int check_tune(const otoo_tune* t)
     } while (0)
 
 // Records the launches of one force step on stream s.
+}  // namespace
+
+int otoo::enqueue_split(const otoo_src* src, float* out, int64_t n, void* stream)
+{
+    if (n <= 0) return OTOO_OK;
+    const int64_t nb = (n + 255) / 256;
+    k_split<<<(unsigned)nb, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(src, reinterpret_cast<float4*>(out), n);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+namespace {
+
 int enqueue_force(const otoo_dev_system* sys, double* accel, double* pot, int precision, const otoo_tune* t,
                   cudaStream_t s)
 {

@@ -16,88 +16,7 @@
 // needs no negation: with n = -Q r and u = r.n = -(r.Q.r),
 //   phi -= m q - (1/2) u q^5,  a += (m q^3 - (5/2) u q^7) r + q^5 n.
 // The potential is accumulated as a positive sum and negated at the end.
-
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 f2pack(float lo, float hi)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2unpack(f2 v, float& lo, float& hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2 f2add(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 f2mul(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2 f2rsqrt(f2 a)
-{
-    float lo, hi;
-    f2unpack(a, lo, hi);
-    return f2pack(rsqrt_r(lo), rsqrt_r(hi));
-}
-
-// Accumulator of one target over packed entry pairs: A[0..2] acceleration,
-// A[3] the positive potential sum.
-struct Acc2 {
-    f2 v[4];
-};
-
-// Two particle entries (or monopole cells) against one target; nx = -x_i
-// broadcast.
-__device__ __forceinline__ void pair_mono2(f2 sx, f2 sy, f2 sz, f2 m, f2 nx, f2 ny, f2 nz, f2 e2, Acc2& A)
-{
-    const f2 rx = f2add(sx, nx), ry = f2add(sy, ny), rz = f2add(sz, nz);
-    const f2 r2 = f2fma(rx, rx, f2fma(ry, ry, f2fma(rz, rz, e2)));
-    const f2 q = f2rsqrt(r2);
-    const f2 mq = f2mul(m, q);
-    const f2 mq3 = f2mul(mq, f2mul(q, q));
-    A.v[3] = f2add(A.v[3], mq);
-    A.v[0] = f2fma(mq3, rx, A.v[0]);
-    A.v[1] = f2fma(mq3, ry, A.v[1]);
-    A.v[2] = f2fma(mq3, rz, A.v[2]);
-}
-
-// Two quadrupole cells against one target (the fields of -Q as above);
-// mhalf = (-1/2, -1/2), m5half = (-5/2, -5/2).
-__device__ __forceinline__ void pair_quad2(f2 sx, f2 sy, f2 sz, f2 m, f2 nqxx, f2 nqyy, f2 nqzz, f2 nqxy, f2 nqxz,
-                                           f2 nqyz, f2 nx, f2 ny, f2 nz, f2 e2, f2 mhalf, f2 m5half, Acc2& A)
-{
-    const f2 rx = f2add(sx, nx), ry = f2add(sy, ny), rz = f2add(sz, nz);
-    const f2 r2 = f2fma(rx, rx, f2fma(ry, ry, f2fma(rz, rz, e2)));
-    const f2 q = f2rsqrt(r2);
-    const f2 q2 = f2mul(q, q);
-    const f2 mq = f2mul(m, q);
-    const f2 mq3 = f2mul(mq, q2);
-    const f2 n0 = f2fma(nqxx, rx, f2fma(nqxy, ry, f2mul(nqxz, rz)));
-    const f2 n1 = f2fma(nqxy, rx, f2fma(nqyy, ry, f2mul(nqyz, rz)));
-    const f2 n2 = f2fma(nqxz, rx, f2fma(nqyz, ry, f2mul(nqzz, rz)));
-    const f2 u = f2fma(rx, n0, f2fma(ry, n1, f2mul(rz, n2)));
-    const f2 q5 = f2mul(q, f2mul(q2, q2));
-    const f2 tu = f2mul(u, q5);
-    A.v[3] = f2add(A.v[3], f2fma(mhalf, tu, mq));
-    const f2 cr = f2fma(f2mul(m5half, tu), q2, mq3);
-    A.v[0] = f2fma(cr, rx, f2fma(q5, n0, A.v[0]));
-    A.v[1] = f2fma(cr, ry, f2fma(q5, n1, A.v[1]));
-    A.v[2] = f2fma(cr, rz, f2fma(q5, n2, A.v[2]));
-}
+// The packed arithmetic (f2 operations, pair_mono2, pair_quad2) is in pair.cuh.
 
 // Packed operands take register pairs: fewer resident warps than the scalar
 // kernel, each with twice the independent FP32 work per instruction.

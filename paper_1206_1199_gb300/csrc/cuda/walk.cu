@@ -48,7 +48,8 @@ constexpr int kScanBlock = 2048;    // elements per scan block
 constexpr int kClasses = 128;       // cost classes of the plan's launch order
 constexpr int kTotals = 6;          // walk totals: entries, interactions, cell interactions,
                                     // largest n_cell, largest n_part, groups beyond their slots
-constexpr unsigned kFull = 0xffffffffu;
+
+#include "pair.cuh"
 
 // status bits (counter[1])
 constexpr uint32_t kWalkBadRecord = 1u;   // a cell record failed its bounds check
@@ -272,15 +273,183 @@ constexpr uint32_t kRunShift = 28;
 constexpr uint32_t kRunMask = (1u << kRunShift) - 1u;
 __device__ __forceinline__ uint32_t run(int first, int n) { return (uint32_t)first | ((uint32_t)(n - 1) << kRunShift); }
 
+// Geometry and acceptance rule of one group's walk.
+struct GroupWalk {
+    double blo[3], bhi[3], c[3];  // the particles' box (exact) and its centre
+    BoxF bf;
+    double theta;                 // opening angle of this group (0 for the absolute MAC / SPH)
+    float invth;                  // 1 / theta rounded to FP32
+    bool sw;                      // absolute MAC or SPH radius: accept when d_min > r_b
+    bool drop;                    // SPH: accepted cells enter no list
+    bool open_all;                // opening angle 0: nothing is accepted
+    bool small_angle;             // theta < 1/sqrt(3): the filter skips the cube-overlap part
+};
+
+// The box of particles [first, first + count) (min/max on order-preserving
+// integer keys, exact), its FP32 form for the filter, and the group's rule.
+__device__ __forceinline__ void group_walk_setup(const WalkArgs& a, int g, int32_t first, int32_t count, int lane,
+                                                 GroupWalk& w)
+{
+    long long klo[3], khi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) klo[k] = 0x7fffffffffffffffLL, khi[k] = -klo[k] - 1;
+    for (int i = lane; i < count; i += 32) {
+        const double2* ps = reinterpret_cast<const double2*>(a.src + first + i);
+        const double2 xy = __ldg(ps), zm = __ldg(ps + 1);
+        const long long kx = dkey(xy.x), ky = dkey(xy.y), kz = dkey(zm.x);
+        klo[0] = kx < klo[0] ? kx : klo[0], khi[0] = kx > khi[0] ? kx : khi[0];
+        klo[1] = ky < klo[1] ? ky : klo[1], khi[1] = ky > khi[1] ? ky : khi[1];
+        klo[2] = kz < klo[2] ? kz : klo[2], khi[2] = kz > khi[2] ? kz : khi[2];
+    }
+    w.bf.B = 0.f;
+    w.bf.A = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        w.blo[k] = dval(warp_min(klo[k]));
+        w.bhi[k] = dval(warp_max(khi[k]));
+        w.c[k] = __dmul_rn(__dadd_rn(w.blo[k], w.bhi[k]), 0.5);
+        w.bf.c32[k] = __double2float_rn(w.c[k]);
+        w.bf.cl32[k] = __double2float_rn(__dsub_rn(w.c[k], (double)w.bf.c32[k]));
+        w.bf.bl[k] = __double2float_rn(__dsub_rn(w.blo[k], w.c[k]));
+        w.bf.bh[k] = __double2float_rn(__dsub_rn(w.bhi[k], w.c[k]));
+        w.bf.B += fmaxf(fabsf(w.bf.bl[k]), fabsf(w.bf.bh[k]));
+        w.bf.A += fabsf(w.bf.c32[k]);
+    }
+    // the absolute MAC and the SPH radius share the test d_min > r_b; an
+    // SPH walk drops the cells that pass it (no neighbour inside)
+    w.sw = a.mac == OTOO_MAC_SW || a.mac == OTOO_MAC_SPH;
+    w.drop = a.mac == OTOO_MAC_SPH;
+    w.theta = w.sw ? 0.0 : a.tpg ? (double)a.tpg[g] : a.theta;
+    // the per-group choices as bits of an integer, taken through an opaque
+    // move: the compiler must not re-derive them from theta inside the
+    // walk loop, where FP64 compares would occupy GB300's narrow FP64 pipe
+    int fl = (!w.sw && !(w.theta > 0.0) ? 1 : 0) | (w.theta < 0.57 ? 2 : 0);  // 0.57 < 1/sqrt(3) = 0.5774
+    asm volatile("mov.b32 %0, %0;" : "+r"(fl));
+    w.open_all = (fl & 1) != 0;
+    w.small_angle = (fl & 2) != 0;
+    // 1/theta within 2^-23 (the filter's margins allow 2^-21)
+    w.invth = w.open_all ? 0.f : __frcp_rn(__double2float_rn(w.theta));
+}
+
+// The cells one walk step took and their decisions: lane j holds positions
+// j + 32 h of the taken runs; kind 1 accept, 2 rejected leaf, 3 open, 0 none.
+struct StepCells {
+    int node[kWalkHalves], kind[kWalkHalves], c0[kWalkHalves], nch[kWalkHalves], pb[kWalkHalves],
+        pe[kWalkHalves];
+};
+
+// Takes up to kWide cells from the top runs of the stack (the last run may be
+// split, its rest goes back) and tests them.  False when the stack or the
+// cell budget ran out (the walk stops).
+__device__ __forceinline__ bool walk_take(const WalkArgs& a, const GroupWalk& w, uint32_t* stk, int& sp,
+                                          int64_t& budget, int lane, StepCells& sc, uint32_t* status)
+{
+    if (sp + 2 > kStack) return false;
+    const int wcap = sp + kWide + 1 + kMaxLevels <= kStack ? kWide : 1;
+    // the top runs: lane l reads the l-th entry from the top
+    const int nr = sp < 32 ? sp : 32;
+    uint32_t e = 0;
+    int rn = 0;
+    if (lane < nr) {
+        e = stk[sp - 1 - lane];
+        rn = (int)(e >> kRunShift) + 1;
+    }
+    const int rinc = warp_incl_scan(rn, lane);
+    const int rstart = rinc - rn;
+    // runs wholly taken, and a run cut at wcap
+    const bool whole = lane < nr && rinc <= wcap;
+    const bool cut = lane < nr && rstart < wcap && rinc > wcap;
+    const int nwhole = __popc(__ballot_sync(kFull, whole));
+    const unsigned cutm = __ballot_sync(kFull, cut);
+    const int in_whole = __shfl_sync(kFull, rinc, nwhole > 0 ? nwhole - 1 : 0);
+    const int W = cutm ? wcap : (nwhole > 0 ? in_whole : 0);
+    // start positions of the taken runs, 32 positions per mask word
+    unsigned starts[kWalkHalves];
+#pragma unroll
+    for (int h = 0; h < kWalkHalves; ++h)
+        starts[h] = __reduce_or_sync(kFull, (whole || cut) && rstart >= 32 * h && rstart < 32 * h + 32
+                                                ? (1u << (rstart - 32 * h))
+                                                : 0u);
+    // the run that continues after the cut goes back on the stack first
+    sp -= nwhole + (cutm ? 1 : 0);
+    if (cut) {
+        const int taken = wcap - rstart;
+        stk[sp] = run((int)(e & kRunMask) + taken, rn - taken);
+    }
+    sp += cutm ? 1 : 0;
+    budget -= W;
+    if (budget < 0) return false;
+    // lane j takes the cells at positions j, j + 32, ... of the taken
+    // runs; position q lies in the run whose start is the last one <= q
+#pragma unroll
+    for (int h = 0; h < kWalkHalves; ++h) {
+        int r = -1;
+#pragma unroll
+        for (int k = 0; k <= h; ++k) r += __popc(starts[k] & (k < h ? 0xffffffffu : (2u << lane) - 1u));
+        const uint32_t er = __shfl_sync(kFull, e, r < 0 ? 0 : r);
+        const int sr = __shfl_sync(kFull, rstart, r < 0 ? 0 : r);
+        const int q = lane + 32 * h;
+        sc.node[h] = q < W ? (int)(er & kRunMask) + (q - sr) : -1;
+        sc.kind[h] = 0;
+        sc.c0[h] = sc.nch[h] = sc.pb[h] = sc.pe[h] = 0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < kWalkHalves; ++h) {
+        if (lane + 32 * h >= W) continue;
+        const int nd = sc.node[h];
+        bool ok = nd >= 0 && nd < a.n_cell;
+        if (ok) {
+            const otoo_wcell c = load_wcell(a.cell, nd);
+            sc.nch[h] = c.nchild;
+            sc.c0[h] = c.child0;
+            sc.pb[h] = c.begin;
+            sc.pe[h] = c.end;
+            ok = sc.nch[h] >= 0 && sc.nch[h] <= 8 &&
+                 (sc.nch[h] == 0 || (sc.c0[h] > nd && (int64_t)sc.c0[h] + sc.nch[h] <= a.n_cell)) &&
+                 sc.pb[h] >= 0 && sc.pb[h] <= sc.pe[h] && (int64_t)sc.pe[h] <= a.n_part;
+            if (ok) {
+                int dec = 0;
+                if (w.sw) {
+                    dec = a.exact ? -1 : mac_filter_sw(c, w.bf);
+                    if (dec < 0) dec = sw_exact(a.cell64, nd, w.blo, w.bhi) ? 1 : 0;
+                } else if (!w.open_all) {
+                    dec = a.exact ? -1
+                          : w.small_angle ? mac_filter<false>(c, w.bf, w.invth)
+                                          : mac_filter<true>(c, w.bf, w.invth);
+                    if (dec < 0) dec = mac_exact(a.cell64, nd, w.blo, w.bhi, w.theta) ? 1 : 0;
+                }
+                sc.kind[h] = dec ? 1 : (sc.nch[h] == 0 ? 2 : 3);
+            }
+        }
+        if (!ok) atomicOr(status, kWalkBadRecord);
+    }
+    return true;
+}
+
+// One run per rejected inner cell of the step, the lowest position's on top:
+// the last positions are pushed first.
+__device__ __forceinline__ void walk_push(uint32_t* stk, int& sp, const StepCells& sc, unsigned lt)
+{
+#pragma unroll
+    for (int h = kWalkHalves - 1; h >= 0; --h) {
+        const unsigned om = __ballot_sync(kFull, sc.kind[h] == 3);
+        const int no = __popc(om);
+        if (sc.kind[h] == 3) stk[sp + no - 1 - __popc(om & lt)] = run(sc.c0[h], sc.nch[h]);
+        sp += no;
+    }
+    __syncwarp();
+}
+
 // One warp per group (atomic ticket).  The stack holds runs of sibling
 // cells; each step takes up to kWide = 32 kWalkHalves cells from the top runs
-// (the last run may be split, its rest goes back; lane j tests the cells at
-// positions j, j + 32, ...), emits accepted cells and rejected leaves'
-// particles in position order and pushes one run per rejected inner cell (its
-// children).  A kWide-cell step adds at most kWide entries and runs only with
-// kWide + 1 + kMaxLevels entries free; otherwise the step takes one cell,
-// which adds at most one entry, and only when it descends a level (a tree has
-// at most kMaxLevels levels below any cell), so the stack never overflows.
+// (walk_take; lane j tests the cells at positions j, j + 32, ...), emits
+// accepted cells and rejected leaves' particles in position order and pushes
+// one run per rejected inner cell (its children, walk_push).  A kWide-cell
+// step adds at most kWide entries and runs only with kWide + 1 + kMaxLevels
+// entries free; otherwise the step takes one cell, which adds at most one
+// entry, and only when it descends a level (a tree has at most kMaxLevels
+// levels below any cell), so the stack never overflows.
 // kMode 0: count (group records, totals); 1: fill the list at the offsets
 // of pass 0; 2: single pass -- count as pass 0 and write each group's entries
 // into fixed slots of two pools (cells: list = cell pool, capacity = slot
@@ -321,48 +490,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
             }
             continue;
         }
-        // the group's box: min/max on order-preserving integer keys (exact)
-        long long klo[3], khi[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) klo[k] = 0x7fffffffffffffffLL, khi[k] = -klo[k] - 1;
-        for (int i = lane; i < count; i += 32) {
-            const double2* ps = reinterpret_cast<const double2*>(a.src + first + i);
-            const double2 xy = __ldg(ps), zm = __ldg(ps + 1);
-            const long long kx = dkey(xy.x), ky = dkey(xy.y), kz = dkey(zm.x);
-            klo[0] = kx < klo[0] ? kx : klo[0], khi[0] = kx > khi[0] ? kx : khi[0];
-            klo[1] = ky < klo[1] ? ky : klo[1], khi[1] = ky > khi[1] ? ky : khi[1];
-            klo[2] = kz < klo[2] ? kz : klo[2], khi[2] = kz > khi[2] ? kz : khi[2];
-        }
-        double blo[3], bhi[3], c[3];
-        BoxF bf;
-        bf.B = 0.f;
-        bf.A = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            blo[k] = dval(warp_min(klo[k]));
-            bhi[k] = dval(warp_max(khi[k]));
-            c[k] = __dmul_rn(__dadd_rn(blo[k], bhi[k]), 0.5);
-            bf.c32[k] = __double2float_rn(c[k]);
-            bf.cl32[k] = __double2float_rn(__dsub_rn(c[k], (double)bf.c32[k]));
-            bf.bl[k] = __double2float_rn(__dsub_rn(blo[k], c[k]));
-            bf.bh[k] = __double2float_rn(__dsub_rn(bhi[k], c[k]));
-            bf.B += fmaxf(fabsf(bf.bl[k]), fabsf(bf.bh[k]));
-            bf.A += fabsf(bf.c32[k]);
-        }
-        // the absolute MAC and the SPH radius share the test d_min > r_b; an
-        // SPH walk drops the cells that pass it (no neighbour inside)
-        const bool sw = a.mac == OTOO_MAC_SW || a.mac == OTOO_MAC_SPH;
-        const bool drop = a.mac == OTOO_MAC_SPH;
-        const double theta = sw ? 0.0 : a.tpg ? (double)a.tpg[g] : a.theta;
-        // the per-group choices as bits of an integer, taken through an opaque
-        // move: the compiler must not re-derive them from theta inside the
-        // walk loop, where FP64 compares would occupy GB300's narrow FP64 pipe
-        int fl = (!sw && !(theta > 0.0) ? 1 : 0) | (theta < 0.57 ? 2 : 0);  // 0.57 < 1/sqrt(3) = 0.5774
-        asm volatile("mov.b32 %0, %0;" : "+r"(fl));
-        const bool open_all = (fl & 1) != 0;
-        const bool small_angle = (fl & 2) != 0;
-        // 1/theta within 2^-23 (the filter's margins allow 2^-21)
-        const float invth = open_all ? 0.f : __frcp_rn(__double2float_rn(theta));
+        GroupWalk w;
+        group_walk_setup(a, g, first, count, lane, w);
         int64_t off_c = 0, off_p = 0;
         int32_t want_c = 0, want_p = 0;
         int32_t* pdst = kMode == 2 ? ppool : list;
@@ -385,7 +514,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
         }
         int32_t ncell = 0, npart = 0;
         int sp = 0;
-        if (theta >= 0.0) {
+        if (w.theta >= 0.0) {
             if (lane == 0) stk[0] = run(0, 1);
             sp = 1;
         }
@@ -393,128 +522,35 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
         int64_t budget = a.n_cell;  // a tree visits each cell at most once
         bool failed = false;
         while (sp > 0) {
-            if (sp + 2 > kStack) {
+            StepCells sc;
+            if (!walk_take(a, w, stk, sp, budget, lane, sc, status)) {
                 failed = true;
                 break;
-            }
-            const int wcap = sp + kWide + 1 + kMaxLevels <= kStack ? kWide : 1;
-            // the top runs: lane l reads the l-th entry from the top
-            const int nr = sp < 32 ? sp : 32;
-            uint32_t e = 0;
-            int rn = 0;
-            if (lane < nr) {
-                e = stk[sp - 1 - lane];
-                rn = (int)(e >> kRunShift) + 1;
-            }
-            const int rinc = warp_incl_scan(rn, lane);
-            const int rstart = rinc - rn;
-            // runs wholly taken, and a run cut at wcap
-            const bool whole = lane < nr && rinc <= wcap;
-            const bool cut = lane < nr && rstart < wcap && rinc > wcap;
-            const int nwhole = __popc(__ballot_sync(kFull, whole));
-            const unsigned cutm = __ballot_sync(kFull, cut);
-            const int in_whole = __shfl_sync(kFull, rinc, nwhole > 0 ? nwhole - 1 : 0);
-            const int W = cutm ? wcap : (nwhole > 0 ? in_whole : 0);
-            // start positions of the taken runs, 32 positions per mask word
-            unsigned starts[kWalkHalves];
-#pragma unroll
-            for (int h = 0; h < kWalkHalves; ++h)
-                starts[h] = __reduce_or_sync(kFull, (whole || cut) && rstart >= 32 * h && rstart < 32 * h + 32
-                                                        ? (1u << (rstart - 32 * h))
-                                                        : 0u);
-            // the run that continues after the cut goes back on the stack first
-            sp -= nwhole + (cutm ? 1 : 0);
-            if (cut) {
-                const int taken = wcap - rstart;
-                stk[sp] = run((int)(e & kRunMask) + taken, rn - taken);
-            }
-            sp += cutm ? 1 : 0;
-            budget -= W;
-            if (budget < 0) {
-                failed = true;
-                break;
-            }
-            // lane j takes the cells at positions j, j + 32, ... of the taken
-            // runs; position q lies in the run whose start is the last one <= q
-            int kind[kWalkHalves], c0[kWalkHalves], nch[kWalkHalves], pb[kWalkHalves], pe[kWalkHalves];
-            int node[kWalkHalves];
-#pragma unroll
-            for (int h = 0; h < kWalkHalves; ++h) {
-                int r = -1;
-#pragma unroll
-                for (int k = 0; k <= h; ++k)
-                    r += __popc(starts[k] & (k < h ? 0xffffffffu : (2u << lane) - 1u));
-                const uint32_t er = __shfl_sync(kFull, e, r < 0 ? 0 : r);
-                const int sr = __shfl_sync(kFull, rstart, r < 0 ? 0 : r);
-                const int q = lane + 32 * h;
-                node[h] = q < W ? (int)(er & kRunMask) + (q - sr) : -1;
-                kind[h] = 0;  // 1 accept, 2 leaf, 3 open
-                c0[h] = nch[h] = pb[h] = pe[h] = 0;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int h = 0; h < kWalkHalves; ++h) {
-                if (lane + 32 * h >= W) continue;
-                const int nd = node[h];
-                bool ok = nd >= 0 && nd < a.n_cell;
-                if (ok) {
-                    const otoo_wcell w = load_wcell(a.cell, nd);
-                    nch[h] = w.nchild;
-                    c0[h] = w.child0;
-                    pb[h] = w.begin;
-                    pe[h] = w.end;
-                    ok = nch[h] >= 0 && nch[h] <= 8 &&
-                         (nch[h] == 0 || (c0[h] > nd && (int64_t)c0[h] + nch[h] <= a.n_cell)) && pb[h] >= 0 &&
-                         pb[h] <= pe[h] && (int64_t)pe[h] <= a.n_part;
-                    if (ok) {
-                        int dec = 0;
-                        if (sw) {
-                            dec = a.exact ? -1 : mac_filter_sw(w, bf);
-                            if (dec < 0) dec = sw_exact(a.cell64, nd, blo, bhi) ? 1 : 0;
-                        } else if (!open_all) {
-                            dec = a.exact ? -1
-                                  : small_angle ? mac_filter<false>(w, bf, invth)
-                                                : mac_filter<true>(w, bf, invth);
-                            if (dec < 0) dec = mac_exact(a.cell64, nd, blo, bhi, theta) ? 1 : 0;
-                        }
-                        kind[h] = dec ? 1 : (nch[h] == 0 ? 2 : 3);
-                    }
-                }
-                if (!ok) atomicOr(status, kWalkBadRecord);
             }
             // accepted cells, in position order
 #pragma unroll
             for (int h = 0; h < kWalkHalves; ++h) {
-                const unsigned am = __ballot_sync(kFull, kind[h] == 1 && !drop);
-                if (kWrite && kind[h] == 1 && !drop) {
+                const unsigned am = __ballot_sync(kFull, sc.kind[h] == 1 && !w.drop);
+                if (kWrite && sc.kind[h] == 1 && !w.drop) {
                     const int32_t r = ncell + __popc(am & lt);
-                    if (r < want_c) list[off_c + r] = (int32_t)(a.n_part + node[h]);
+                    if (r < want_c) list[off_c + r] = (int32_t)(a.n_part + sc.node[h]);
                 }
                 ncell += __popc(am);
             }
             // particles of rejected leaves, in position order
 #pragma unroll
             for (int h = 0; h < kWalkHalves; ++h) {
-                if (!__any_sync(kFull, kind[h] == 2)) continue;
-                const int np = kind[h] == 2 ? pe[h] - pb[h] : 0;
+                if (!__any_sync(kFull, sc.kind[h] == 2)) continue;
+                const int np = sc.kind[h] == 2 ? sc.pe[h] - sc.pb[h] : 0;
                 const int pin = warp_incl_scan(np, lane);
                 if (kWrite && np > 0) {
                     const int32_t base = npart + pin - np;
                     for (int k = 0; k < np; ++k)
-                        if (base + k < want_p) pdst[off_p + base + k] = pb[h] + k;
+                        if (base + k < want_p) pdst[off_p + base + k] = sc.pb[h] + k;
                 }
                 npart += __shfl_sync(kFull, pin, 31);
             }
-            // one run per rejected inner cell, the lowest position's on top:
-            // the last positions are pushed first
-#pragma unroll
-            for (int h = kWalkHalves - 1; h >= 0; --h) {
-                const unsigned om = __ballot_sync(kFull, kind[h] == 3);
-                const int no = __popc(om);
-                if (kind[h] == 3) stk[sp + no - 1 - __popc(om & lt)] = run(c0[h], nch[h]);
-                sp += no;
-            }
-            __syncwarp();
+            walk_push(stk, sp, sc, lt);
         }
         if (failed && lane == 0) atomicOr(status, kWalkOverflow);
         if (kCount) {
@@ -526,10 +562,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
                 r.n_part = npart;
                 r.list_off = 0;
                 r.eps2 = a.eps2;
-                r.cx = c[0];
-                r.cy = c[1];
-                r.cz = c[2];
-                r.theta = (float)theta;
+                r.cx = w.c[0];
+                r.cy = w.c[1];
+                r.cz = w.c[2];
+                r.theta = (float)w.theta;
                 r.sys = 0;
                 groups[g] = r;
                 const int64_t len = (int64_t)ncell + npart;
@@ -544,6 +580,308 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
             }
         } else if (lane == 0 && (ncell != want_c || npart != want_p)) {
             atomicOr(status, kWalkMismatch);
+        }
+    }
+}
+
+
+// ---- the walk fused with the force (the paper's GPU design) ------------------
+// One warp per group walks the tree as k_walk does, but the entries do not go
+// to a list in device memory: accepted cells and the particles of rejected
+// leaves collect in two shared-memory index buffers, and whenever one holds a
+// tile of entries the warp stages the tile as pair records (the layout of
+// k_force_warp2) and evaluates it against the group's particles, IB per lane
+// in lane subsets, with packed FP32 pairs and per-tile Kahan sums.  No list,
+// no plan, no work items: the group is the work item.
+constexpr int kFuseWarps = 4;                 // warps per CTA
+constexpr int kFuseTP = 128;                  // pair records per tile at most
+constexpr int kFusePPL = kFuseTP / 32;        // pair records staged per lane
+constexpr int kFuseBuf = 2 * kFuseTP + kWide; // index buffer: a tile plus one step's cells
+
+struct FuseArgs {
+    const float4* split;    // [2 n_src] float pairs of the sources
+    const otoo_quad* quad;  // [n_cell] or NULL (monopole cells)
+    const int64_t* perm;    // [n_part] tree order -> caller order, or NULL
+    double* accel;          // [n_part][3]
+    double* pot;            // [n_part]
+};
+
+// Stages cnt entries buf[0..cnt) (cells: source n_part + k, else particles)
+// as pair records relative to the group centre c and evaluates them for the
+// lane's IB targets; the tile sums go into the Kahan sums acc.
+template <int IB>
+__device__ __forceinline__ void fuse_tile(const WalkArgs& a, const FuseArgs& f, const int32_t* buf, int cnt, bool cell,
+                                          float4* rec, int lane, int nsub, int js, bool active, float cx, float cy,
+                                          float cz, const f2 nx[IB], const f2 ny[IB], const f2 nz[IB], f2 e2,
+                                          Acc<float> acc[IB], uint32_t* status)
+{
+    const bool cq = cell && f.quad != nullptr;
+    const int npair = (cnt + 1) / 2;
+    const int npair_pad = (npair + nsub - 1) / nsub * nsub;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t n_src = a.n_part + a.n_cell;
+#pragma unroll
+    for (int pp = 0; pp < kFusePPL; ++pp) {
+        const int m = lane + 32 * pp;
+        if (m >= npair_pad) continue;
+        float4 hh[2], ll[2], qa[2], qb[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * m + h;
+            hh[h] = ll[h] = qa[h] = qb[h] = zero4;
+            if (k < cnt) {
+                const int idx = buf[k];
+                const bool good = cell ? (idx >= a.n_part && idx < n_src) : (idx >= 0 && idx < a.n_part);
+                if (good) {
+                    hh[h] = __ldg(f.split + 2 * (int64_t)idx);
+                    ll[h] = __ldg(f.split + 2 * (int64_t)idx + 1);
+                    if (cq) {
+                        const float4* qp = reinterpret_cast<const float4*>(f.quad + (idx - a.n_part));
+                        qa[h] = __ldg(qp);
+                        qb[h] = __ldg(qp + 1);
+                    }
+                } else {
+                    atomicOr(status, kWalkBadRecord);
+                }
+            }
+        }
+        // padding and rejected entries were loaded as zeros: mass (and
+        // quadrupole) 0, so they add exactly nothing
+        float x[2], y[2], z[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            x[h] = (hh[h].x - cx) + ll[h].x;
+            y[h] = (hh[h].y - cy) + ll[h].y;
+            z[h] = (hh[h].z - cz) + ll[h].z;
+        }
+        if (cq) {
+            float4* r = rec + 5 * m;
+            r[0] = make_float4(x[0], x[1], y[0], y[1]);
+            r[1] = make_float4(z[0], z[1], hh[0].w, hh[1].w);
+            // qa = (xx, yy, zz, xy), qb = (xz, yz, -, -), stored negated
+            r[2] = make_float4(-qa[0].x, -qa[1].x, -qa[0].y, -qa[1].y);
+            r[3] = make_float4(-qa[0].z, -qa[1].z, -qa[0].w, -qa[1].w);
+            r[4] = make_float4(-qb[0].x, -qb[1].x, -qb[0].y, -qb[1].y);
+        } else {
+            float4* r = rec + 2 * m;
+            r[0] = make_float4(x[0], x[1], y[0], y[1]);
+            r[1] = make_float4(z[0], z[1], hh[0].w, hh[1].w);
+        }
+    }
+    __syncwarp();
+    if (active) {
+        const f2 mhalf = f2pack(-0.5f, -0.5f), m5half = f2pack(-2.5f, -2.5f), zero2 = f2pack(0.f, 0.f);
+        Acc2 P2[IB];
+#pragma unroll
+        for (int k = 0; k < IB; ++k) P2[k].v[0] = P2[k].v[1] = P2[k].v[2] = P2[k].v[3] = zero2;
+        const int niter = npair_pad / nsub;
+        if (cq) {
+            const float4* __restrict__ r = rec + 5 * js;
+            const int S = 5 * nsub;
+#pragma unroll 2
+            for (int n = 0; n < niter; ++n, r += S) {
+                const float4 v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4];
+                const f2 sx = f2pack(v0.x, v0.y), sy = f2pack(v0.z, v0.w), sz = f2pack(v1.x, v1.y);
+                const f2 sm = f2pack(v1.z, v1.w);
+                const f2 qxx = f2pack(v2.x, v2.y), qyy = f2pack(v2.z, v2.w), qzz = f2pack(v3.x, v3.y);
+                const f2 qxy = f2pack(v3.z, v3.w), qxz = f2pack(v4.x, v4.y), qyz = f2pack(v4.z, v4.w);
+#pragma unroll
+                for (int k = 0; k < IB; ++k)
+                    pair_quad2(sx, sy, sz, sm, qxx, qyy, qzz, qxy, qxz, qyz, nx[k], ny[k], nz[k], e2, mhalf, m5half,
+                               P2[k]);
+            }
+        } else {
+            const float4* __restrict__ r = rec + 2 * js;
+            const int S = 2 * nsub;
+#pragma unroll 3
+            for (int n = 0; n < niter; ++n, r += S) {
+                const float4 v0 = r[0], v1 = r[1];
+                const f2 sx = f2pack(v0.x, v0.y), sy = f2pack(v0.z, v0.w), sz = f2pack(v1.x, v1.y);
+                const f2 sm = f2pack(v1.z, v1.w);
+#pragma unroll
+                for (int k = 0; k < IB; ++k) pair_mono2(sx, sy, sz, sm, nx[k], ny[k], nz[k], e2, P2[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            float t4[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float lo, hi;
+                f2unpack(P2[k].v[c], lo, hi);
+                t4[c] = lo + hi;
+            }
+            acc[k].add(t4);
+        }
+    }
+    __syncwarp();
+}
+
+// Drops the first `used` entries of buf (n in total; n - used < used).
+__device__ __forceinline__ void fuse_shift(int32_t* buf, int n, int used, int lane)
+{
+    for (int k = lane; k < n - used; k += 32) buf[k] = buf[used + k];
+    __syncwarp();
+}
+
+template <int IB>
+#ifndef OTOO_FUSE_MIN_BLOCKS
+#define OTOO_FUSE_MIN_BLOCKS 1  // resident CTAs per SM asked of the register allocator
+#endif
+__global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_force(WalkArgs a, FuseArgs f)
+{
+    __shared__ uint32_t stack_s[kFuseWarps][kStack];
+    __shared__ int32_t cbuf_s[kFuseWarps][kFuseBuf];
+    __shared__ int32_t pbuf_s[kFuseWarps][kFuseBuf];
+    __shared__ float4 rec_s[kFuseWarps][5 * kFuseTP];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    uint32_t* stk = stack_s[wid];
+    int32_t* cbuf = cbuf_s[wid];
+    int32_t* pbuf = pbuf_s[wid];
+    float4* rec = rec_s[wid];
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t* status = a.counter + 1;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(a.counter, 1u);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= a.n_groups) break;
+        const int32_t first = a.gfirst[g], count = a.gcount[g];
+        if (first < 0 || count < 1 || count > 32 * IB || (int64_t)first + count > a.n_part) {
+            if (lane == 0) atomicOr(status, kWalkBadGroup);
+            continue;
+        }
+        GroupWalk w;
+        group_walk_setup(a, g, first, count, lane, w);
+        if (!(w.theta >= 0.0)) continue;  // a negative per-group angle skips the group
+
+        // the group's particles, IB per lane in nsub lane subsets
+        const int P = (count + IB - 1) / IB;
+        const int nsub = 32 / P;
+        const int islot = lane % P, js = lane / P;
+        const bool active = js < nsub;
+        // entries per evaluated tile: a multiple of 2 nsub
+        const int TE = 2 * ((kFuseTP / nsub) * nsub);
+        const float eps2 = (float)a.eps2;
+        const f2 e2 = f2pack(eps2, eps2);
+        const float cx = __double2float_rn(w.c[0]), cy = __double2float_rn(w.c[1]), cz = __double2float_rn(w.c[2]);
+        f2 nx[IB], ny[IB], nz[IB];
+        Acc<float> acc[IB];
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            const int i = islot + k * P;
+            float x = 0.f, y = 0.f, z = 0.f;
+            if (active && i < count) {
+                const int64_t t = (int64_t)first + i;
+                const float4 h = __ldg(f.split + 2 * t);
+                const float4 l = __ldg(f.split + 2 * t + 1);
+                x = (h.x - cx) + l.x;
+                y = (h.y - cy) + l.y;
+                z = (h.z - cz) + l.z;
+            }
+            nx[k] = f2pack(-x, -x);
+            ny[k] = f2pack(-y, -y);
+            nz[k] = f2pack(-z, -z);
+            acc[k].zero();
+        }
+
+        int32_t ncell = 0, npart = 0;  // entries of the group's (virtual) list
+        int nc = 0, npb = 0;           // entries waiting in the two buffers
+        int sp = 1;
+        if (lane == 0) stk[0] = run(0, 1);
+        __syncwarp();
+        int64_t budget = a.n_cell;
+        bool failed = false;
+        while (sp > 0) {
+            StepCells sc;
+            if (!walk_take(a, w, stk, sp, budget, lane, sc, status)) {
+                failed = true;
+                break;
+            }
+            // accepted cells into the cell buffer, in position order
+#pragma unroll
+            for (int h = 0; h < kWalkHalves; ++h) {
+                const unsigned am = __ballot_sync(kFull, sc.kind[h] == 1);
+                if (sc.kind[h] == 1) cbuf[nc + __popc(am & lt)] = (int32_t)(a.n_part + sc.node[h]);
+                nc += __popc(am);
+                ncell += __popc(am);
+            }
+            __syncwarp();
+            // particles of rejected leaves into the particle buffer, in
+            // position order, a buffer's worth at a time
+#pragma unroll
+            for (int h = 0; h < kWalkHalves; ++h) {
+                if (!__any_sync(kFull, sc.kind[h] == 2)) continue;
+                const int np = sc.kind[h] == 2 ? sc.pe[h] - sc.pb[h] : 0;
+                const int pin = warp_incl_scan(np, lane);
+                const int total = __shfl_sync(kFull, pin, 31);
+                npart += total;
+                for (int done = 0; done < total;) {
+                    const int take = min(kFuseBuf - npb, total - done);
+                    const int lo = max(pin - np, done), hi = min(pin, done + take);
+                    for (int o = lo; o < hi; ++o) pbuf[npb + o - done] = sc.pb[h] + (o - (pin - np));
+                    __syncwarp();
+                    npb += take;
+                    done += take;
+                    while (npb >= TE) {
+                        fuse_tile<IB>(a, f, pbuf, TE, false, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2,
+                                      acc, status);
+                        fuse_shift(pbuf, npb, TE, lane);
+                        npb -= TE;
+                    }
+                }
+            }
+            walk_push(stk, sp, sc, lt);
+            while (nc >= TE) {
+                fuse_tile<IB>(a, f, cbuf, TE, true, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, acc,
+                              status);
+                fuse_shift(cbuf, nc, TE, lane);
+                nc -= TE;
+            }
+        }
+        if (failed) {
+            if (lane == 0) atomicOr(status, kWalkOverflow);
+            continue;
+        }
+        if (nc > 0)
+            fuse_tile<IB>(a, f, cbuf, nc, true, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, acc, status);
+        if (npb > 0)
+            fuse_tile<IB>(a, f, pbuf, npb, false, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, acc,
+                          status);
+
+        // merge the lane subsets, FP64 outputs in caller order; the self pair
+        // (always in the list: a group never accepts a cell overlapping its
+        // box) added exactly -m_i rsqrt(eps^2) in FP32
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            double r[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float S = acc[k].s[c], C = acc[k].c[c];
+                merge_subsets(S, C, js, nsub, P);
+                r[c] = (double)S - (double)C;
+            }
+            r[3] = -r[3];
+            const int i = islot + k * P;
+            if (js == 0 && i < count) {
+                const int64_t t = (int64_t)first + i;
+                const float4 h = __ldg(f.split + 2 * t);
+                r[3] += (double)(h.w * rsqrt_r(eps2));
+                const int64_t o = f.perm ? f.perm[t] : t;
+                f.accel[3 * o] = r[0];
+                f.accel[3 * o + 1] = r[1];
+                f.accel[3 * o + 2] = r[2];
+                f.pot[o] = r[3];
+            }
+        }
+        if (lane == 0) {
+            const int64_t len = (int64_t)ncell + npart;
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.totals), (unsigned long long)len);
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 1), (unsigned long long)(len * count));
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 2), (unsigned long long)((int64_t)ncell * count));
+            atomicMax(reinterpret_cast<unsigned long long*>(a.totals + 3), (unsigned long long)ncell);
+            atomicMax(reinterpret_cast<unsigned long long*>(a.totals + 4), (unsigned long long)npart);
         }
     }
 }
@@ -954,6 +1292,39 @@ int otoo_walk_fill(const otoo_dev_walk* w, const otoo_group* groups, int32_t* li
     OTOO_REQUIRE(capacity >= 0, OTOO_EINVAL, "otoo_walk_fill: negative capacity");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     return launch_walk<1>(w, const_cast<otoo_group*>(groups), list, capacity, s);
+}
+
+int otoo_walk_force(const otoo_dev_walk* w, const otoo_quad* quad, const int64_t* perm, float* split, int32_t iblock,
+                    double* accel, double* pot, void* stream)
+{
+    const int rc = check_walk(w);
+    if (rc) return rc;
+    OTOO_REQUIRE(split && accel && pot, OTOO_EINVAL, "otoo_walk_force: NULL pointer");
+    OTOO_REQUIRE(w->mac != OTOO_MAC_SPH, OTOO_EINVAL, "otoo_walk_force: the SPH walk has no force");
+    OTOO_REQUIRE(iblock == 1 || iblock == 2 || iblock == 4, OTOO_EINVAL, "otoo_walk_force: iblock must be 1, 2 or 4");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(w->counter, 0, 4 * sizeof(uint32_t), s));
+    CUDA_TRY(cudaMemsetAsync(w->totals, 0, kTotals * sizeof(int64_t), s));
+    const int r1 = enqueue_split(w->src, split, w->n_part + w->n_cell, stream);
+    if (r1) return r1;
+    FuseArgs f;
+    f.split = reinterpret_cast<const float4*>(split);
+    f.quad = quad;
+    f.perm = perm;
+    f.accel = accel;
+    f.pot = pot;
+    void (*fn)(WalkArgs, FuseArgs) = iblock == 1 ? k_walk_force<1> : iblock == 2 ? k_walk_force<2> : k_walk_force<4>;
+    int dev = 0, sms = 0, occ = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFuseWarps * 32, 0));
+    if (occ < 1) return set_error(OTOO_EINVAL, "otoo_walk_force: kernel does not fit on an SM");
+    int64_t blocks = (int64_t)sms * occ;
+    const int64_t need = ((int64_t)w->n_groups + kFuseWarps - 1) / kFuseWarps;
+    if (blocks > need) blocks = need;
+    fn<<<(unsigned)blocks, kFuseWarps * 32, 0, s>>>(walk_args(w), f);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
 }
 
 int otoo_walk_check_status(const otoo_dev_walk* w, void* stream)

@@ -476,6 +476,11 @@ class DeviceTree:
     def h2d_bytes(self):
         return sum(b.numel() for b in self.bufs.values() if b is not None)
 
+    def fused(self, theta, eps, iblock=2, theta_per_group=None, pool=None):
+        """The walk fused with the FP32 force (FusedStep); every group at most
+        32 * iblock particles."""
+        return FusedStep(self, theta, eps, iblock, theta_per_group, pool)
+
     def walk(self, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None, max_entries=None,
              single=True):
         """Groups and lists on the device.  Without a BufferPool: two passes
@@ -486,6 +491,55 @@ class DeviceTree:
         otoo_walk_fill when a group outgrows its slots.  max_entries: raise
         ValueError instead of allocating a longer list."""
         return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool, max_entries, single)
+
+
+class FusedStep:
+    """The walk fused with the FP32 force (otoo_walk_force): one warp per
+    group walks the tree and evaluates each tile of its entries as it is
+    found; no list, no plan.  Outputs in caller order."""
+
+    def __init__(self, dtree, theta, eps, iblock=2, theta_per_group=None, pool=None):
+        import torch
+        dev = dtree.device
+        G = dtree.n_groups
+        alloc = _alloc(pool, dev)
+        self.tree = dtree
+        self.iblock = int(iblock)
+        b = dict(counter=alloc("fcounter", 4, torch.int32),
+                 totals=alloc("ftotals", L.load().otoo_walk_totals_len(G), torch.int64),
+                 split=alloc("fsplit", 8 * dtree.n_src, torch.float32))
+        if theta_per_group is not None:
+            tpg = np.ascontiguousarray(theta_per_group, dtype=np.float32)
+            assert tpg.shape == (G,)
+            b["tpg"] = alloc("ftpg", G, torch.float32)
+            b["tpg"].copy_(torch.from_numpy(tpg))
+        w = L.DevWalk()
+        w.n_part, w.n_cell, w.n_groups, w.exact = dtree.n_part, dtree.n_cell, G, 0
+        w.mac = dtree.mac
+        w.theta, w.eps2 = float(theta), float(eps) * float(eps)
+        tb = dtree.bufs
+        w.src, w.cell, w.cell64 = tb["src"].data_ptr(), tb["cell"].data_ptr(), tb["cell64"].data_ptr()
+        w.group_first, w.group_count = tb["first"].data_ptr(), tb["count"].data_ptr()
+        w.theta_per_group = b["tpg"].data_ptr() if "tpg" in b else None
+        w.counter, w.totals = b["counter"].data_ptr(), b["totals"].data_ptr()
+        self.struct = w
+        self.bufs = b
+
+    def __call__(self, accel, pot, stream=None, check=True):
+        """Enqueues one step into accel [n][3] and pot [n] (FP64 device
+        tensors); with check, waits and raises on a device-side error."""
+        st = _stream(stream, self.tree.device)
+        tb = self.tree.bufs
+        quad = tb["quad"].data_ptr() if tb.get("quad") is not None else None
+        L.call("otoo_walk_force", ctypes.byref(self.struct), quad, tb["perm"].data_ptr(),
+               self.bufs["split"].data_ptr(), self.iblock, accel.data_ptr(), pot.data_ptr(), st)
+        if check:
+            L.call("otoo_walk_check_status", ctypes.byref(self.struct), st)
+
+    def totals(self):
+        """(list entries, interactions, cell interactions) of the last step."""
+        t = [int(x) for x in self.bufs["totals"][:3].tolist()]
+        return tuple(t)
 
 
 class DeviceLists:
