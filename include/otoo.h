@@ -91,7 +91,8 @@ typedef struct otoo_tune {
 } otoo_tune;
 
 /* ---- device-side layout (what the host library exports and the caller
-        uploads; every array is 16-byte aligned and tightly packed) ------------ */
+        uploads; every array is 16-byte aligned and tightly packed, quad and the
+        split scratch 32-byte aligned) ----------------------------------------- */
 
 /* A source: a particle (index < n_part) or a cell (index >= n_part).  For a
    cell, (x, y, z) is its centre of mass and m its mass. 32 bytes. */
@@ -142,7 +143,7 @@ typedef struct otoo_dev_system {
     int64_t n_list;                /* entries in list */
     int32_t n_groups, n_items, n_splits, n_crit_max;
     const otoo_src* src;           /* [n_src] */
-    const otoo_quad* quad;         /* [n_src - n_part], NULL = monopole cells */
+    const otoo_quad* quad;         /* [n_src - n_part], NULL = monopole cells; 32-byte aligned */
     const otoo_group* groups;      /* [n_groups] */
     const int32_t* list;           /* CSR source indices */
     const otoo_item* items;        /* [n_items], in launch order */
@@ -150,7 +151,7 @@ typedef struct otoo_dev_system {
     const int64_t* perm;           /* [n_part] output index of each tree particle, NULL = tree order */
     double* partial;               /* scratch, >= otoo_plan_info.partial_doubles doubles */
     uint32_t* counter;             /* scratch, >= 4 uint32 (work ticket and status) */
-    void* split;                   /* scratch for OTOO_FP32K, >= 32 * n_src bytes: each source's
+    void* split;                   /* scratch for OTOO_FP32K, >= 32 * n_src bytes, 32-byte aligned: each source's
                                       position as a float pair (hi = x rounded to FP32,
                                       lo = x - hi rounded) and its mass */
 } otoo_dev_system;

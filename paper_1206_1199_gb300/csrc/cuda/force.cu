@@ -407,6 +407,8 @@ int validate_sys(const otoo_dev_system* sys)
     OTOO_REQUIRE(sys->src && sys->groups && sys->counter && (sys->n_items == 0 || (sys->items && sys->list)),
                  OTOO_EINVAL, "NULL device array");
     OTOO_REQUIRE(sys->n_splits == 0 || (sys->splits && sys->partial), OTOO_EINVAL, "split lists need partial scratch");
+    OTOO_REQUIRE((reinterpret_cast<uintptr_t>(sys->quad) & 31) == 0 && (reinterpret_cast<uintptr_t>(sys->split) & 31) == 0,
+                 OTOO_EINVAL, "quad and split must be 32-byte aligned (one 32-byte load per record)");
     return OTOO_OK;
 }
 

@@ -146,13 +146,9 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
                         const bool good =
                             cell ? (idx >= sys.n_part && idx < sys.n_src) : (idx >= 0 && idx < sys.n_part);
                         if (good) {
-                            hh[h] = __ldg(ff + 2 * (int64_t)idx);
-                            ll[h] = __ldg(ff + 2 * (int64_t)idx + 1);
-                            if (cq) {
-                                const float4* qp = reinterpret_cast<const float4*>(sys.quad + (idx - sys.n_part));
-                                qa[h] = __ldg(qp);
-                                qb[h] = __ldg(qp + 1);
-                            }
+                            // a source's float pair and a cell's quadrupole: one 32-byte load each
+                            ld256x2(ff + 2 * (int64_t)idx, hh[h], ll[h]);
+                            if (cq) ld256x2(reinterpret_cast<const float4*>(sys.quad + (idx - sys.n_part)), qa[h], qb[h]);
                         } else {
                             atomicOr(status, kBadIndex);
                             real[h] = false;

@@ -200,3 +200,12 @@ __device__ __forceinline__ void merge_subsets(float& S, float& C, int js, int ns
     }
 }
 
+
+// One 32-byte sector per load (256-bit vector load, sm_100 and later): the
+// two consecutive float4 at p (32-byte aligned) in one request.
+__device__ __forceinline__ void ld256x2(const float4* p, float4& a, float4& b)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}

@@ -726,7 +726,7 @@ __device__ __forceinline__ void fuse_shift(int32_t* buf, int n, int used, int la
 
 template <int IB>
 #ifndef OTOO_FUSE_MIN_BLOCKS
-#define OTOO_FUSE_MIN_BLOCKS 1  // resident CTAs per SM asked of the register allocator
+#define OTOO_FUSE_MIN_BLOCKS 3  // resident CTAs per SM asked of the register allocator (168 registers)
 #endif
 __global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_force(WalkArgs a, FuseArgs f)
 {
