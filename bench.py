@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--skip-sw", action="store_true", help="skip the absolute-MAC (delta) sweep")
     ap.add_argument("--skip-step", action="store_true", help="skip the whole step on the device")
     ap.add_argument("--skip-sph", action="store_true", help="skip the SPH density stage")
+    ap.add_argument("--fused-only", action="store_true",
+                    help="only the walk fused with the force against the split device step, on this workload")
     return ap.parse_args()
 
 
@@ -860,10 +862,25 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_fused_only(args):
+    """The fused walk + force comparison alone (rank 0, one JSON line)."""
+    import torch
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    w, pos, mass = workload(args, 0)
+    tune, _ = pick_tune(w, args)
+    r = run_fused(args, "cuda:%d" % local, pos, mass, w, tune, torch.cuda.current_stream())
+    print(json.dumps({"workload": args.workload, "n": len(pos), "fused_walk_force": r}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.fused_only:
+        run_fused_only(args)
     else:
         run_ours(args)
 
