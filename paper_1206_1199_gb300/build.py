@@ -25,6 +25,13 @@ def _nvcc():
     return cand
 
 
+def _cuda_home():
+    nv = _nvcc()
+    if os.path.isabs(nv):
+        return os.path.dirname(os.path.dirname(os.path.realpath(nv)))
+    return os.environ.get("CUDA_HOME", "/usr/local/cuda")
+
+
 def _run(cmd):
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
@@ -56,7 +63,7 @@ def build(force=False, verbose=False, ptxas_info=False):
         o = os.path.join(BUILD, os.path.basename(s) + ".o")
         objs.append(o)
         jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-I" + INCLUDE,
-                     "-c", os.path.join(CSRC, s), "-o", o])
+                     "-I" + os.path.join(_cuda_home(), "include"), "-c", os.path.join(CSRC, s), "-o", o])
     for s in CUDA_SRC:
         o = os.path.join(BUILD, os.path.basename(s) + ".o")
         objs.append(o)

@@ -114,6 +114,7 @@ int64_t otoo_direct_chunks(int64_t n_src, int64_t n_tgt)
 int otoo_direct(const otoo_src* src, int64_t n_src, const int64_t* targets, int64_t n_tgt, double eps2, double* accel,
                 double* pot, double* scratch, uint32_t* status, void* stream)
 {
+    otoo::Range range_("otoo_direct");
     OTOO_REQUIRE(src && targets && accel && pot && scratch && status, OTOO_EINVAL, "otoo_direct: NULL pointer");
     OTOO_REQUIRE(n_src >= 1 && n_tgt >= 1 && n_tgt <= ((int64_t)1 << 31), OTOO_EINVAL, "otoo_direct: bad sizes");
     OTOO_REQUIRE(eps2 > 0.0, OTOO_EINVAL, "otoo_direct: eps2 must be > 0");

@@ -419,6 +419,7 @@ extern "C" {
 int otoo_force(const otoo_dev_system* sys, double* accel, double* pot, int32_t precision, const otoo_tune* tune,
                void* stream)
 {
+    otoo::Range range_("otoo_force");
     int rc = validate_sys(sys);
     if (rc) return rc;
     OTOO_REQUIRE(accel && pot, OTOO_EINVAL, "accel/pot is NULL");
@@ -522,6 +523,7 @@ int ensure(int k, size_t bytes)
 extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* pl, double* accel, double* pot,
                                int32_t precision, const otoo_tune* tune, void* stream)
 {
+    otoo::Range range_("otoo_force_host");
     OTOO_REQUIRE(lv && pl && accel && pot, OTOO_EINVAL, "otoo_force_host: NULL argument");
     OTOO_REQUIRE(lv->n_part >= 1 && lv->n_groups >= 1, OTOO_EINVAL, "otoo_force_host: empty input");
     std::lock_guard<std::mutex> lock(g_host_mu);
@@ -625,6 +627,7 @@ extern "C" int64_t otoo_force_static_capacity(void) { return (int64_t)kStaticScr
 extern "C" int otoo_force_static(const otoo_dev_system* sys, int64_t partial_doubles, double* accel, double* pot,
                                  int32_t precision, const otoo_tune* tune, void* stream)
 {
+    otoo::Range range_("otoo_force_static");
     OTOO_REQUIRE(sys, OTOO_EINVAL, "sys is NULL");
     OTOO_REQUIRE(accel && pot, OTOO_EINVAL, "accel/pot is NULL");
     OTOO_REQUIRE(precision == OTOO_FP32K || precision == OTOO_FP64, OTOO_EINVAL, "bad precision %d", precision);

@@ -291,6 +291,7 @@ int otoo_mlp_train_step(float* w, uint16_t* wbf16, float* m, float* v, float* sc
                         const float* target, int64_t n_rows, float lr, float beta1, float beta2, float eps_adam,
                         int32_t t, float* loss, void* stream)
 {
+    otoo::Range range_("otoo_mlp_train_step");
     OTOO_REQUIRE(w && wbf16 && m && v && scratch && x && target, OTOO_EINVAL, "otoo_mlp_train_step: NULL pointer");
     OTOO_REQUIRE(n_rows >= 1 && t >= 1, OTOO_EINVAL, "otoo_mlp_train_step: n_rows and t must be >= 1");
     OTOO_REQUIRE(lr > 0 && beta1 >= 0 && beta1 < 1 && beta2 >= 0 && beta2 < 1 && eps_adam > 0, OTOO_EINVAL,
@@ -320,6 +321,7 @@ int otoo_select_theta(const uint16_t* wbf16, const float* x, const float* theta_
                       int64_t n_groups, float log10_target, const float* log10_target_per_group, float fallback,
                       float* theta_out, void* stream)
 {
+    otoo::Range range_("otoo_select_theta");
     OTOO_REQUIRE(wbf16 && x && theta_grid && theta_out, OTOO_EINVAL, "otoo_select_theta: NULL pointer");
     OTOO_REQUIRE(n_theta >= 1 && n_groups >= 0, OTOO_EINVAL, "otoo_select_theta: bad sizes");
     if (n_groups == 0) return OTOO_OK;

@@ -276,6 +276,7 @@ extern "C" {
 
 int otoo_sph_density(const otoo_dev_system* sys, const float* h, double* rho, const otoo_tune* tune, void* stream)
 {
+    otoo::Range range_("otoo_sph_density");
     OTOO_REQUIRE(sys && h && rho && tune, OTOO_EINVAL, "otoo_sph_density: NULL argument");
     OTOO_REQUIRE(sys->src && sys->groups && sys->list && sys->items && sys->counter && sys->split, OTOO_EINVAL,
                  "otoo_sph_density: NULL device array");

@@ -720,6 +720,7 @@ int64_t otoo_devtree_scratch_bytes(int64_t n_part, int64_t cap_cell)
 int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, void* scratch, int64_t scratch_bytes,
                        void* stream)
 {
+    otoo::Range range_("otoo_devtree_build");
     OTOO_REQUIRE(pos && mass && t && scratch, OTOO_EINVAL, "otoo_devtree_build: NULL pointer");
     const int64_t n = t->n_part, cap = t->cap_cell;
     OTOO_REQUIRE(n >= 1 && n <= INT32_MAX / 2 && cap >= 1 && n + cap <= INT32_MAX, OTOO_EINVAL,

@@ -1240,6 +1240,7 @@ int64_t otoo_walk_totals_len(int64_t n_groups) { return kTotals + scan_blocks(n_
 
 int otoo_walk_count(const otoo_dev_walk* w, otoo_group* groups, void* stream)
 {
+    otoo::Range range_("otoo_walk_count");
     const int rc = check_walk(w);
     if (rc) return rc;
     OTOO_REQUIRE(groups, OTOO_EINVAL, "otoo_walk_count: groups is NULL");
@@ -1255,6 +1256,7 @@ int otoo_walk_count(const otoo_dev_walk* w, otoo_group* groups, void* stream)
 int otoo_walk_single(const otoo_dev_walk* w, otoo_group* groups, int32_t* cell_pool, int64_t cell_cap,
                      int32_t* part_pool, int64_t part_cap, void* stream)
 {
+    otoo::Range range_("otoo_walk_single");
     const int rc = check_walk(w);
     if (rc) return rc;
     OTOO_REQUIRE(groups && cell_pool && part_pool, OTOO_EINVAL, "otoo_walk_single: NULL pointer");
@@ -1272,6 +1274,7 @@ int otoo_walk_single(const otoo_dev_walk* w, otoo_group* groups, int32_t* cell_p
 int otoo_walk_compact(const otoo_dev_walk* w, const otoo_group* groups, const int32_t* cell_pool, int64_t cell_cap,
                       const int32_t* part_pool, int64_t part_cap, int32_t* list, int64_t capacity, void* stream)
 {
+    otoo::Range range_("otoo_walk_compact");
     const int rc = check_walk(w);
     if (rc) return rc;
     OTOO_REQUIRE(groups && cell_pool && part_pool && list, OTOO_EINVAL, "otoo_walk_compact: NULL pointer");
@@ -1286,6 +1289,7 @@ int otoo_walk_compact(const otoo_dev_walk* w, const otoo_group* groups, const in
 
 int otoo_walk_fill(const otoo_dev_walk* w, const otoo_group* groups, int32_t* list, int64_t capacity, void* stream)
 {
+    otoo::Range range_("otoo_walk_fill");
     const int rc = check_walk(w);
     if (rc) return rc;
     OTOO_REQUIRE(groups && list, OTOO_EINVAL, "otoo_walk_fill: NULL pointer");
@@ -1297,6 +1301,7 @@ int otoo_walk_fill(const otoo_dev_walk* w, const otoo_group* groups, int32_t* li
 int otoo_walk_force(const otoo_dev_walk* w, const otoo_quad* quad, const int64_t* perm, float* split, int32_t iblock,
                     double* accel, double* pot, void* stream)
 {
+    otoo::Range range_("otoo_walk_force");
     const int rc = check_walk(w);
     if (rc) return rc;
     OTOO_REQUIRE(split && accel && pot, OTOO_EINVAL, "otoo_walk_force: NULL pointer");
@@ -1351,6 +1356,7 @@ int64_t otoo_plan_scratch_ints(int64_t n_groups)
 int otoo_plan_count(const otoo_group* groups, int32_t n_groups, const otoo_tune* tune, int32_t* plan_scratch,
                     int64_t* plan_totals, void* stream)
 {
+    otoo::Range range_("otoo_plan_count");
     OTOO_REQUIRE(groups && tune && plan_scratch && plan_totals, OTOO_EINVAL, "otoo_plan_count: NULL pointer");
     OTOO_REQUIRE(n_groups >= 1, OTOO_EINVAL, "otoo_plan_count: n_groups < 1");
     OTOO_REQUIRE(tune->split >= 1, OTOO_EINVAL, "split must be >= 1");
@@ -1373,6 +1379,7 @@ int otoo_plan_fill(const otoo_group* groups, int32_t n_groups, const otoo_tune* 
                    const int64_t* plan_totals, otoo_item* items, int64_t items_capacity, otoo_split* splits,
                    int64_t splits_capacity, uint32_t* counter, void* stream)
 {
+    otoo::Range range_("otoo_plan_fill");
     OTOO_REQUIRE(groups && tune && plan_scratch && plan_totals && counter, OTOO_EINVAL,
                  "otoo_plan_fill: NULL pointer");
     OTOO_REQUIRE(items || items_capacity == 0, OTOO_EINVAL, "otoo_plan_fill: items is NULL");

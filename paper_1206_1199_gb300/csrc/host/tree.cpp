@@ -227,6 +227,7 @@ const char* otoo_last_error(void) { return g_last_error.c_str(); }
 int otoo_build_tree(const double* pos, const float* mass, int64_t n, const otoo_params* params,
                     otoo_tree** out)
 {
+    Range range_("otoo_build_tree");
     OTOO_REQUIRE(out != nullptr, OTOO_EINVAL, "otoo_build_tree: out is NULL");
     *out = nullptr;
     OTOO_REQUIRE(pos && mass && params, OTOO_EINVAL, "otoo_build_tree: NULL input");
@@ -470,6 +471,7 @@ extern "C" {
 
 int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_lists** out)
 {
+    Range range_("otoo_make_groups_and_lists");
     OTOO_REQUIRE(out != nullptr, OTOO_EINVAL, "otoo_make_groups_and_lists: out is NULL");
     *out = nullptr;
     OTOO_REQUIRE(t && p, OTOO_EINVAL, "otoo_make_groups_and_lists: NULL argument");
@@ -660,6 +662,7 @@ int otoo_find_groups(const otoo_tree* t, int32_t n_crit, int32_t* first, int32_t
 int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, const otoo_params* p, otoo_src* src,
                             otoo_quad* quad, otoo_wcell* cell, otoo_wcell64* cell64)
 {
+    Range range_("otoo_tree_device_arrays");
     OTOO_REQUIRE(t, OTOO_EINVAL, "otoo_tree_device_arrays: NULL tree");
     const bool sw = p && p->mac == OTOO_MAC_SW, sph = p && p->mac == OTOO_MAC_SPH;
     OTOO_REQUIRE(!p || p->mac == OTOO_MAC_THETA || sw || sph, OTOO_EINVAL, "unknown mac %d", p ? p->mac : 0);
@@ -711,6 +714,7 @@ int otoo_tree_device_arrays(const otoo_tree* t, int32_t use_quad, const otoo_par
 
 int otoo_pack_batch(const otoo_lists* const* per, int32_t n_sys, otoo_lists** out)
 {
+    Range range_("otoo_pack_batch");
     OTOO_REQUIRE(out != nullptr, OTOO_EINVAL, "otoo_pack_batch: out is NULL");
     *out = nullptr;
     OTOO_REQUIRE(per && n_sys >= 1, OTOO_EINVAL, "otoo_pack_batch: need at least one system");
@@ -789,6 +793,7 @@ int otoo_default_tune(int32_t n_crit, otoo_tune* tune)
 // `split` entries, balanced in length.
 int otoo_make_plan(const otoo_lists* L, const otoo_tune* tune, otoo_plan** out)
 {
+    Range range_("otoo_make_plan");
     OTOO_REQUIRE(out != nullptr, OTOO_EINVAL, "otoo_make_plan: out is NULL");
     *out = nullptr;
     OTOO_REQUIRE(L && tune, OTOO_EINVAL, "otoo_make_plan: NULL argument");
@@ -861,6 +866,7 @@ void otoo_plan_free(otoo_plan* P) { delete P; }
 // Features of each group's list for the learned opening angle.
 int otoo_group_features(const otoo_tree* t, const otoo_lists* L, float* feat)
 {
+    Range range_("otoo_group_features");
     OTOO_REQUIRE(t && L && feat, OTOO_EINVAL, "otoo_group_features: NULL argument");
     OTOO_REQUIRE(L->n_sys == 1 && L->n_part == t->n, OTOO_EINVAL, "features need the single-system lists of this tree");
     const int64_t G = (int64_t)L->groups.size();

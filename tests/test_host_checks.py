@@ -18,11 +18,13 @@ def test_host_library_under_address_and_ub_sanitizers(tmp_path):
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("no g++")
+    from paper_1206_1199_gb300 import build
     exe = str(tmp_path / "driver")
     cmd = [gxx, "-std=c++17", "-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined", "-fopenmp",
            "-ffp-contract=off", "-I" + os.path.join(ROOT, "include"),
+           "-I" + os.path.join(build._cuda_home(), "include"),  # NVTX (header-only)
            os.path.join(ROOT, "tests", "host_check", "driver.cpp"),
-           os.path.join(ROOT, "paper_1206_1199_gb300", "csrc", "host", "tree.cpp"), "-o", exe]
+           os.path.join(ROOT, "paper_1206_1199_gb300", "csrc", "host", "tree.cpp"), "-o", exe, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0 and "sanitize" in r.stderr:
         pytest.skip("sanitizer runtime not available: " + r.stderr[-200:])
