@@ -27,7 +27,9 @@ the calls):
 from __future__ import annotations
 
 import ctypes
+import json
 import math
+import os
 import time
 
 import numpy as np
@@ -113,11 +115,23 @@ def relerr(a, ref):
 # ---------------------------------------------------------------------------
 # snapshots
 
-def leapfrog_snapshots(pos, mass, vel, eps, dt, n_snap, every, theta=0.5, n_crit=64, device="cuda", log=None):
+def leapfrog_snapshots(pos, mass, vel, eps, dt, n_snap, every, theta=0.5, n_crit=64, device="cuda", log=None,
+                       resume=None, velocities=None):
     """Kick-drift-kick with the method's FP32 forces at a fixed angle; a
-    snapshot (positions) every `every` steps, the first one at step 0."""
-    x = np.array(pos, np.float64)
-    v = np.array(vel, np.float64)
+    snapshot (positions) every `every` steps, the first one at step 0.
+    resume: (positions, velocities, snapshots so far) of an earlier run's
+    last snapshot (load_snapshots) to continue from instead of pos/vel.
+    velocities: a list that receives the velocity at each snapshot."""
+    if resume is not None:
+        x0, v0, done = resume
+        x = np.array(x0[-1], np.float64)
+        v = np.array(v0[-1], np.float64)
+        snaps = [np.array(a) for a in x0]
+        vels = [np.array(a) for a in v0]
+    else:
+        x = np.array(pos, np.float64)
+        v = np.array(vel, np.float64)
+        snaps, vels = [x.copy()], [v.copy()]
 
     def accel(xx):
         ev = Evaluator(xx, mass, eps, n_crit, device=device)
@@ -126,7 +140,6 @@ def leapfrog_snapshots(pos, mass, vel, eps, dt, n_snap, every, theta=0.5, n_crit
         out[ev.tree.export()["perm"]] = a  # back to caller order
         return out
 
-    snaps = [x.copy()]
     a = accel(x)
     step = 0
     while len(snaps) < n_snap:
@@ -138,9 +151,25 @@ def leapfrog_snapshots(pos, mass, vel, eps, dt, n_snap, every, theta=0.5, n_crit
         step += 1
         if step % every == 0:
             snaps.append(x.copy())
+            vels.append(v.copy())
         if log:
             log("step %d (%.2f s)" % (step, time.perf_counter() - t0))
+    if velocities is not None:
+        velocities[:] = vels
     return snaps
+
+
+def save_snapshots(path, snaps, vels, mass, **meta):
+    """Checkpoint of a snapshot run: positions and velocities at every
+    snapshot (FP64), masses, and the run's parameters (dt, every, eps, ...)."""
+    np.savez(path, pos=np.stack(snaps), vel=np.stack(vels), mass=np.asarray(mass, np.float32),
+             meta=np.array(json.dumps(meta, sort_keys=True)))
+
+
+def load_snapshots(path):
+    """(positions list, velocities list, masses, parameters) of a checkpoint."""
+    d = np.load(path)
+    return list(d["pos"]), list(d["vel"]), d["mass"], json.loads(str(d["meta"]))
 
 
 # ---------------------------------------------------------------------------
@@ -298,7 +327,6 @@ def orbital_period(m_total=1.5, sep=0.05):
 
 def main():
     import argparse
-    import json
     ap = argparse.ArgumentParser(description="train the opening-angle network on method-generated snapshots")
     ap.add_argument("--n", type=int, default=1 << 22)
     ap.add_argument("--snaps", type=int, default=16)
@@ -311,12 +339,25 @@ def main():
     ap.add_argument("--target", type=float, default=1e-3)
     ap.add_argument("--weights", default=None, help="write the trained network here (.npz)")
     ap.add_argument("--summary", default=None, help="write the evaluation here (.json)")
+    ap.add_argument("--checkpoint", default=None,
+                    help="snapshot checkpoint (.npz): continued when it exists and matches the run, written after")
     args = ap.parse_args()
     log = lambda s: print(s, flush=True)  # noqa: E731
     pos, mass, vel = merger_ic(args.n)
     dt = args.dt_frac * orbital_period()
+    meta = dict(n=args.n, dt=dt, every=args.every, eps=args.eps, n_crit=args.n_crit, seed=ic.BASE_SEED + 5)
+    resume = None
+    if args.checkpoint and os.path.exists(args.checkpoint):
+        xs, vs, _, m = load_snapshots(args.checkpoint)
+        if m == json.loads(json.dumps(meta, sort_keys=True)):
+            resume = (xs[:args.snaps + 1], vs[:args.snaps + 1], len(xs))
+            log("checkpoint: %d snapshots loaded" % len(resume[0]))
     t0 = time.perf_counter()
-    snaps = leapfrog_snapshots(pos, mass, vel, args.eps, dt, args.snaps + 1, args.every, n_crit=args.n_crit, log=None)
+    vels = []
+    snaps = leapfrog_snapshots(pos, mass, vel, args.eps, dt, args.snaps + 1, args.every, n_crit=args.n_crit, log=None,
+                               resume=resume, velocities=vels)
+    if args.checkpoint:
+        save_snapshots(args.checkpoint, snaps, vels, mass, **meta)
     t1 = time.perf_counter()
     log("snapshots: %d in %.1f s" % (len(snaps), t1 - t0))
     train_snaps, held_out = snaps[:args.snaps], snaps[args.snaps]
