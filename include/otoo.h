@@ -565,12 +565,13 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* tree,
    support radius h: W = 8 / (pi h^3) w(q), q = r / h, w = 1 - 6 q^2 + 6 q^3
    (q <= 1/2), 2 (1 - q)^3 (1/2 < q < 1), 0 beyond; the source itself
    included.  sys: as for otoo_force, with a plan made for these lists (the
-   quad, accel-related fields are not read; sys->split serves as scratch for
-   h in tree order); h: device [n_part] neighbour radii, caller order (the
+   quad, accel-related fields are not read; sys->split, 32-byte aligned,
+   serves as scratch for 32 bytes per particle: its position as a float pair,
+   m 8/(pi h^3) and 1/h); h: device [n_part] neighbour radii, caller order (the
    order sys->perm maps to); rho: device [n_part] FP64, written at perm[k]
    (tree order when perm is NULL); tune->iblock in {1, 2, 4} as in the plan.
-   FP32 pair terms relative to the group centre, FP64 sums across 32-entry
-   tiles and list chunks.  Asynchronous on stream; bad items or list indices
+   FP32 pair terms relative to the group centre, Kahan-compensated FP32 sums
+   across 32-entry tiles and lane subsets, FP64 sums across list chunks.  Asynchronous on stream; bad items or list indices
    set the status word (otoo_check_status). */
 int otoo_sph_density(const otoo_dev_system* sys, const float* h, double* rho, const otoo_tune* tune, void* stream);
 

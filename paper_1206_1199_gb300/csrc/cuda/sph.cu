@@ -6,16 +6,24 @@
 // source itself included.
 //
 // Kernels
-//   k_h_tree          h in tree order (through the permutation).
+//   k_sph_prep        once per step, per source in tree order: its position
+//                     as a float pair (hi = x rounded to FP32, lo = the
+//                     remainder), m_j 8/(pi h_j^3) and 1/h_j (h through the
+//                     permutation): the step's only FP64 work, as in the
+//                     force step's float-pair split.
 //   k_density<IB>     one work item (group, target chunk, list chunk) per warp
-//                     from an atomic ticket; 32-entry tiles staged in shared
+//                     from an atomic ticket, IB targets per lane in lane
+//                     subsets that share out the kept entries of a tile (as
+//                     the force kernels do); 32-entry tiles staged in shared
 //                     memory as (x_j - c, m_j 8/(pi h_j^3), 1/h_j) in FP32
-//                     relative to the group centre c, keeping only entries
-//                     within (1 + 2^-10) h_j of the item's own target box (the
-//                     others have W = 0 at every target; the walk's lists are
-//                     cut at cell level and hold about 12 times more entries
-//                     than neighbours); each lane sums IB targets, FP32
-//                     within a tile, FP64 across tiles.
+//                     relative to the group centre c ((hi - c) + lo), keeping
+//                     only entries within (1 + 2^-10) h_j of the item's own
+//                     target box (the others have W = 0 at every target; the
+//                     walk's lists are cut at cell level and hold about 12
+//                     times more entries than neighbours); each lane sums IB
+//                     targets, plain FP32 within a tile, Kahan-compensated
+//                     FP32 across tiles and lane subsets (pairwise, in a fixed
+//                     order), FP64 output.
 //   k_density_merge   FP64 sum of the list chunks of split groups, in chunk
 //                     order.
 //   k_sph_direct      FP64 brute force over all sources for chosen targets
@@ -32,23 +40,33 @@ using namespace otoo;
 namespace {
 
 constexpr int kDW = 4;  // warps per CTA
-constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kBadItem = 1u;   // same status bits as the force step
 constexpr uint32_t kBadIndex = 2u;
 constexpr float kNorm = 2.546479089470325f;  // 8 / pi
 
-__global__ void k_h_tree(const float* __restrict__ h, const int64_t* __restrict__ perm, int64_t n,
-                         float* __restrict__ ht, uint32_t* __restrict__ status)
+#include "pair.cuh"
+
+// Per tree-order source k: out[2k] = (hi_x, hi_y, hi_z, m 8/(pi h^3)),
+// out[2k + 1] = (lo_x, lo_y, lo_z, 1/h), h = h[perm[k]].
+__global__ void k_sph_prep(const otoo_src* __restrict__ src, const float* __restrict__ h,
+                           const int64_t* __restrict__ perm, int64_t n, float4* __restrict__ out,
+                           uint32_t* __restrict__ status)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t i = perm ? perm[k] : k;
+    float hk = 1.0f;
     if (i < 0 || i >= n) {
         atomicOr(status, kBadIndex);
-        ht[k] = 1.0f;
-        return;
+    } else {
+        hk = h[i];
     }
-    ht[k] = h[i];
+    const otoo_src s = src[k];
+    const float ih = 1.0f / hk;
+    const float hx = __double2float_rn(s.x), hy = __double2float_rn(s.y), hz = __double2float_rn(s.z);
+    out[2 * k] = make_float4(hx, hy, hz, s.m * kNorm * ih * ih * ih);
+    out[2 * k + 1] = make_float4(__double2float_rn(s.x - (double)hx), __double2float_rn(s.y - (double)hy),
+                                 __double2float_rn(s.z - (double)hz), ih);
 }
 
 // M4 cubic spline shape w(q), q = r / h (zero for q >= 1).
@@ -60,7 +78,7 @@ __device__ __forceinline__ float w_m4(float q)
 }
 
 template <int IB>
-__global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const float* __restrict__ ht,
+__global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const float4* __restrict__ rec,
                                                       double* __restrict__ rho)
 {
     __shared__ float4 tp[kDW][32];
@@ -87,19 +105,27 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
             if (lane == 0) atomicOr(counter + 1, kBadItem);
             continue;
         }
+        // the item's targets, IB per lane in nsub lane subsets of P lanes;
+        // subset js takes every nsub-th kept entry of a tile
+        const int P = (it.ni + IB - 1) / IB;
+        const int nsub = 32 / P;
+        const int islot = lane % P, js = lane / P;
+        const bool active = js < nsub;
+        const float cx = __double2float_rn(g.cx), cy = __double2float_rn(g.cy), cz = __double2float_rn(g.cz);
         float xi[IB], yi[IB], zi[IB];
-        double acc[IB];
+        float as[IB], ac[IB];  // Kahan sum of the lane's share: as - ac
         float blo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, bhi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
 #pragma unroll
         for (int r = 0; r < IB; ++r) {
-            const int k = lane + 32 * r;
-            acc[r] = 0.0;
+            const int k = islot + r * P;
+            as[r] = ac[r] = 0.f;
             xi[r] = yi[r] = zi[r] = 0.f;
-            if (k < it.ni) {
-                const otoo_src s = sys.src[g.first + it.i0 + k];
-                xi[r] = (float)(s.x - g.cx);
-                yi[r] = (float)(s.y - g.cy);
-                zi[r] = (float)(s.z - g.cz);
+            if (active && k < it.ni) {
+                float4 a, b;
+                ld256x2(rec + 2 * ((int64_t)g.first + it.i0 + k), a, b);
+                xi[r] = (a.x - cx) + b.x;
+                yi[r] = (a.y - cy) + b.y;
+                zi[r] = (a.z - cz) + b.z;
                 blo[0] = fminf(blo[0], xi[r]), bhi[0] = fmaxf(bhi[0], xi[r]);
                 blo[1] = fminf(blo[1], yi[r]), bhi[1] = fmaxf(bhi[1], yi[r]);
                 blo[2] = fminf(blo[2], zi[r]), bhi[2] = fmaxf(bhi[2], zi[r]);
@@ -121,17 +147,18 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
             if (jj < it.j1) {
                 const int32_t e = sys.list[g.list_off + jj];
                 if (e >= 0 && e < sys.n_part) {
-                    const otoo_src s = sys.src[e];
-                    const float h = ht[e];
-                    ih = 1.0f / h;
-                    p = make_float4((float)(s.x - g.cx), (float)(s.y - g.cy), (float)(s.z - g.cz),
-                                    s.m * kNorm * ih * ih * ih);
-                    // distance from the entry to the target box against its support
+                    float4 a, b;
+                    ld256x2(rec + 2 * (int64_t)e, a, b);
+                    ih = b.w;
+                    p = make_float4((a.x - cx) + b.x, (a.y - cy) + b.y, (a.z - cz) + b.z, a.w);
+                    // distance from the entry to the target box against its
+                    // support: kept unless d >= (1 + 2^-10) h, where every
+                    // target's q = r / h exceeds 1 even after rounding
                     const float dx = fmaxf(0.f, fmaxf(blo[0] - p.x, p.x - bhi[0]));
                     const float dy = fmaxf(0.f, fmaxf(blo[1] - p.y, p.y - bhi[1]));
                     const float dz = fmaxf(0.f, fmaxf(blo[2] - p.z, p.z - bhi[2]));
-                    const float hm = h * (1.0f + 0x1p-10f);
-                    keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < hm * hm;
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    keep = d2 * ih * ih < (1.0f + 0x1p-10f) * (1.0f + 0x1p-10f);
                 } else {
                     atomicOr(counter + 1, kBadIndex);
                 }
@@ -147,7 +174,7 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
             float part[IB];
 #pragma unroll
             for (int r = 0; r < IB; ++r) part[r] = 0.f;
-            for (int q = 0; q < cnt; ++q) {
+            for (int q = active ? js : cnt; q < cnt; q += nsub) {
                 const float4 pj = tp[w][q];
                 const float ihj = tih[w][q];
 #pragma unroll
@@ -159,13 +186,25 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
                 }
             }
 #pragma unroll
-            for (int r = 0; r < IB; ++r) acc[r] += (double)part[r];
+            for (int r = 0; r < IB; ++r) {
+                const float y = __fsub_rn(part[r], ac[r]);
+                const float tt = __fadd_rn(as[r], y);
+                ac[r] = __fsub_rn(__fsub_rn(tt, as[r]), y);
+                as[r] = tt;
+            }
             __syncwarp();
+        }
+        // merge the lane subsets into js == 0 (pairwise, a fixed order)
+        double acc[IB];
+#pragma unroll
+        for (int r = 0; r < IB; ++r) {
+            merge_subsets(as[r], ac[r], js, nsub, P);
+            acc[r] = (double)as[r] - (double)ac[r];
         }
 #pragma unroll
         for (int r = 0; r < IB; ++r) {
-            const int k = lane + 32 * r;
-            if (k >= it.ni) continue;
+            const int k = islot + r * P;
+            if (js != 0 || k >= it.ni) continue;
             const int64_t ti = (int64_t)g.first + it.i0 + k;
             if (it.slot < 0) {
                 rho[sys.perm ? sys.perm[ti] : ti] = acc[r];
@@ -254,7 +293,7 @@ __global__ void __launch_bounds__(128) k_sph_direct(const otoo_src* __restrict__
     } while (0)
 
 template <int IB>
-int launch(const otoo_dev_system* sys, const float* ht, double* rho, cudaStream_t s)
+int launch(const otoo_dev_system* sys, const float4* rec, double* rho, cudaStream_t s)
 {
     int dev = 0, sms = 0, occ = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -265,7 +304,7 @@ int launch(const otoo_dev_system* sys, const float* ht, double* rho, cudaStream_
     const int64_t need = ((int64_t)sys->n_items + kDW - 1) / kDW;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    k_density<IB><<<(unsigned)blocks, kDW * 32, 0, s>>>(*sys, ht, rho);
+    k_density<IB><<<(unsigned)blocks, kDW * 32, 0, s>>>(*sys, rec, rho);
     CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }
@@ -286,13 +325,16 @@ int otoo_sph_density(const otoo_dev_system* sys, const float* h, double* rho, co
                  "otoo_sph_density: split lists need splits and partial");
     const int ib = tune->iblock;
     OTOO_REQUIRE(ib == 1 || ib == 2 || ib == 4, OTOO_EINVAL, "otoo_sph_density: iblock must be 1, 2 or 4");
+    OTOO_REQUIRE((reinterpret_cast<uintptr_t>(sys->split) & 31) == 0, OTOO_EINVAL,
+                 "otoo_sph_density: the split scratch must be 32-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    float* ht = static_cast<float*>(sys->split);
+    float4* rec = static_cast<float4*>(sys->split);
     CUDA_TRY(cudaMemsetAsync(sys->counter, 0, 2 * sizeof(uint32_t), s));
-    k_h_tree<<<(unsigned)((sys->n_part + 255) / 256), 256, 0, s>>>(h, sys->perm, sys->n_part, ht, sys->counter + 1);
+    k_sph_prep<<<(unsigned)((sys->n_part + 255) / 256), 256, 0, s>>>(sys->src, h, sys->perm, sys->n_part, rec,
+                                                                      sys->counter + 1);
     CUDA_TRY(cudaGetLastError());
     if (sys->n_items > 0) {
-        const int r = ib == 1 ? launch<1>(sys, ht, rho, s) : ib == 2 ? launch<2>(sys, ht, rho, s) : launch<4>(sys, ht, rho, s);
+        const int r = ib == 1 ? launch<1>(sys, rec, rho, s) : ib == 2 ? launch<2>(sys, rec, rho, s) : launch<4>(sys, rec, rho, s);
         if (r) return r;
     }
     if (sys->n_splits > 0) {
