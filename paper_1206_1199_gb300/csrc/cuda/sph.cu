@@ -20,7 +20,8 @@
 //                     only entries within (1 + 2^-10) h_j of the item's own
 //                     target box (the others have W = 0 at every target; the
 //                     walk's lists are cut at cell level and hold about 12
-//                     times more entries than neighbours); each lane sums IB
+//                     times more entries than neighbours); kept entries wait
+//                     in shared memory until 32 are there; each lane sums IB
 //                     targets, plain FP32 within a tile, Kahan-compensated
 //                     FP32 across tiles and lane subsets (pairwise, in a fixed
 //                     order), FP64 output.
@@ -81,8 +82,8 @@ template <int IB>
 __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const float4* __restrict__ rec,
                                                       double* __restrict__ rho)
 {
-    __shared__ float4 tp[kDW][32];
-    __shared__ float tih[kDW][32];
+    __shared__ float4 tp[kDW][64];  // kept entries waiting: up to 31 plus a tile's 32
+    __shared__ float tih[kDW][64];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t* counter = sys.counter;
     for (;;) {
@@ -139,6 +140,33 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
                 blo[a] = fminf(blo[a], __shfl_xor_sync(kFull, blo[a], o));
                 bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(kFull, bhi[a], o));
             }
+        // evaluates the first cnt waiting entries for the lane's targets and
+        // adds the batch into the Kahan sums
+        auto batch = [&](int cnt) {
+            float part[IB];
+#pragma unroll
+            for (int r = 0; r < IB; ++r) part[r] = 0.f;
+            for (int q = active ? js : cnt; q < cnt; q += nsub) {
+                const float4 pj = tp[w][q];
+                const float ihj = tih[w][q];
+#pragma unroll
+                for (int r = 0; r < IB; ++r) {
+                    const float dx = pj.x - xi[r], dy = pj.y - yi[r], dz = pj.z - zi[r];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float qq = r2 > 0.f ? r2 * rsqrtf(r2) * ihj : 0.f;
+                    part[r] = fmaf(pj.w, w_m4(qq), part[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < IB; ++r) {
+                const float y = __fsub_rn(part[r], ac[r]);
+                const float tt = __fadd_rn(as[r], y);
+                ac[r] = __fsub_rn(__fsub_rn(tt, as[r]), y);
+                as[r] = tt;
+            }
+            __syncwarp();
+        };
+        int nk = 0;  // kept entries waiting in tp / tih
         for (int32_t j = it.j0; j < it.j1; j += 32) {
             const int32_t jj = j + lane;
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -165,35 +193,23 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
             }
             const unsigned km = __ballot_sync(kFull, keep);
             if (keep) {
-                const int slot = __popc(km & ((1u << lane) - 1u));
+                const int slot = nk + __popc(km & ((1u << lane) - 1u));
                 tp[w][slot] = p;
                 tih[w][slot] = ih;
             }
+            nk += __popc(km);
             __syncwarp();
-            const int cnt = __popc(km);
-            float part[IB];
-#pragma unroll
-            for (int r = 0; r < IB; ++r) part[r] = 0.f;
-            for (int q = active ? js : cnt; q < cnt; q += nsub) {
-                const float4 pj = tp[w][q];
-                const float ihj = tih[w][q];
-#pragma unroll
-                for (int r = 0; r < IB; ++r) {
-                    const float dx = pj.x - xi[r], dy = pj.y - yi[r], dz = pj.z - zi[r];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float qq = r2 > 0.f ? r2 * rsqrtf(r2) * ihj : 0.f;
-                    part[r] = fmaf(pj.w, w_m4(qq), part[r]);
+            if (nk >= 32) {  // a full batch: evaluate it, move the rest to the front
+                batch(32);
+                if (lane < nk - 32) {
+                    tp[w][lane] = tp[w][32 + lane];
+                    tih[w][lane] = tih[w][32 + lane];
                 }
+                nk -= 32;
+                __syncwarp();
             }
-#pragma unroll
-            for (int r = 0; r < IB; ++r) {
-                const float y = __fsub_rn(part[r], ac[r]);
-                const float tt = __fadd_rn(as[r], y);
-                ac[r] = __fsub_rn(__fsub_rn(tt, as[r]), y);
-                as[r] = tt;
-            }
-            __syncwarp();
         }
+        if (nk > 0) batch(nk);
         // merge the lane subsets into js == 0 (pairwise, a fixed order)
         double acc[IB];
 #pragma unroll
