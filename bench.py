@@ -820,15 +820,18 @@ def cpu_baseline(w, pos, mass, seconds, tree=None):
     `seconds`; the oracle's own tree build is not timed."""
     t = tree if tree is not None else oracle_tree(w, pos, mass)
     stride = max(1, t.n_groups // 2048)
-    t0 = time.perf_counter()
-    r = t.eval(w["theta"], w["eps"], w["use_quad"], group_stride=stride)
-    dt = time.perf_counter() - t0
-    rate = r["interactions"] / max(dt, 1e-9)
-    full_estimate = r["interactions"] * stride
-    stride = max(1, int(math.ceil(full_estimate / max(rate * seconds, 1.0))))
-    t0 = time.perf_counter()
-    r = t.eval(w["theta"], w["eps"], w["use_quad"], group_stride=stride)
-    dt = time.perf_counter() - t0
+    # a small probe, then samples sized from the last measured rate until one
+    # takes at least 60% of the time asked for (a cold first probe
+    # underestimates the rate)
+    for attempt in range(3):
+        t0 = time.perf_counter()
+        r = t.eval(w["theta"], w["eps"], w["use_quad"], group_stride=stride)
+        dt = time.perf_counter() - t0
+        if attempt > 0 and (dt >= 0.6 * seconds or stride == 1):
+            break
+        rate = r["interactions"] / max(dt, 1e-9)
+        full_estimate = r["interactions"] * stride
+        stride = max(1, int(math.ceil(full_estimate / max(rate * seconds, 1.0))))
     return {"value": r["interactions"] / dt, "unit": "interactions/s", "cores": cores(), "kind": "oracle",
             "sample": "FP64 oracle tree force (walk + evaluation) for every %d-th of %d groups "
                       "(%d interactions, %.1f s); oracle tree build not timed" % (stride, t.n_groups,
