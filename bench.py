@@ -644,7 +644,9 @@ def run_paper_workloads(args, dev_name, tune, stream):
     published kernel times: device tree (leaf size 16), device walk with the
     absolute MAC (delta 0.01, m_limit 0.05), plan and FP32 force (monopole
     cells, eps 1e-3: the paper gives no softening); errors against the FP64
-    direct sum on 256 targets."""
+    direct sum on 256 targets.  On the uniform sphere also the delta sweep of
+    the paper's Figs. 4 and 5 (walk + force time and mean error against
+    delta, their slopes between successive deltas)."""
     import torch
 
     from paper_1206_1199_gb300 import _lib as L
@@ -652,17 +654,15 @@ def run_paper_workloads(args, dev_name, tune, stream):
     from paper_1206_1199_gb300 import system as S
     out = []
     eps = 1e-3
-    for model, n, paper_s, paper_hw in PAPER_WORKLOADS:
-        pos, mass = ic.make(model, n, ic.BASE_SEED + 6)
-        pos_d = torch.from_numpy(np.ascontiguousarray(pos)).to(dev_name)
-        mass_d = torch.from_numpy(np.ascontiguousarray(mass)).to(dev_name)
+
+    def measure(pos_d, mass_d, n, delta, sub, ad):
         acc = torch.empty((n, 3), dtype=torch.float64, device=dev_name)
         pot = torch.empty(n, dtype=torch.float64, device=dev_name)
 
         def one():
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record(stream)
-            dt = S.DeviceTree.build(pos_d, mass_d, 16, 128, False, dev_name, mac="sw", delta=0.01, m_limit=0.05,
+            dt = S.DeviceTree.build(pos_d, mass_d, 16, 128, False, dev_name, mac="sw", delta=delta, m_limit=0.05,
                                     stream=stream)
             ev[1].record(stream)
             dl = dt.walk(0.0, eps, stream=stream)
@@ -676,17 +676,36 @@ def run_paper_workloads(args, dev_name, tune, stream):
         runs = [one() for _ in range(3)]
         dl = runs[-1][0]
         med = np.median(np.array([r[1] for r in runs]), axis=0)
+        d = np.linalg.norm(acc.cpu().numpy()[sub] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        row = {"delta": delta, "interactions": int(dl.interactions), "tree_ms": float(med[0]),
+               "walk_ms": float(med[1]), "plan_force_ms": float(med[2]), "gravity_ms": float(med[1] + med[2]),
+               "acc_mean": float(d.mean()), "acc_rms": float(np.sqrt(np.mean(d * d))), "acc_max": float(d.max())}
+        del dl, runs, acc, pot
+        torch.cuda.empty_cache()
+        return row
+
+    sweep = None
+    for model, n, paper_s, paper_hw in PAPER_WORKLOADS:
+        pos, mass = ic.make(model, n, ic.BASE_SEED + 6)
+        pos_d = torch.from_numpy(np.ascontiguousarray(pos)).to(dev_name)
+        mass_d = torch.from_numpy(np.ascontiguousarray(mass)).to(dev_name)
         sub = ic.subsample(n, 256, 11)
         ad, _ = S.direct_sum(pos, mass, eps, sub, dev_name)
-        rms, mx = rel_err(acc.cpu().numpy()[sub], ad)
-        out.append({"model": model, "n": n, "interactions": int(dl.interactions), "tree_ms": float(med[0]),
-                    "walk_ms": float(med[1]), "plan_force_ms": float(med[2]),
-                    "gravity_ms": float(med[1] + med[2]), "acc_rms": rms, "acc_max": mx, "error_targets": 256,
-                    "paper_kernel_s": paper_s, "paper_hardware": paper_hw})
-        del dl, runs
+        row = measure(pos_d, mass_d, n, 0.01, sub, ad)
+        row.update(model=model, n=n, error_targets=256, paper_kernel_s=paper_s, paper_hardware=paper_hw)
+        out.append(row)
+        if model == "uniform":
+            rows = [measure(pos_d, mass_d, n, dlt, sub, ad) for dlt in (1e-1, 3e-2, 1e-2, 3e-3, 1e-3)]
+            lg = lambda a, b, k: math.log(b[k] / a[k]) / math.log(b["delta"] / a["delta"])  # noqa: E731
+            sweep = {"rows": rows,
+                     "time_slopes": [lg(a, b, "gravity_ms") for a, b in zip(rows, rows[1:])],
+                     "mean_error_slopes": [lg(a, b, "acc_mean") for a, b in zip(rows, rows[1:])],
+                     "paper": "time ~ delta^-3/4 (Section II-B, Fig. 4); mean error ~ delta^0.25 at small delta "
+                              "(Fig. 5)"}
+        del pos_d, mass_d
         torch.cuda.empty_cache()
     return {"mac": "absolute, delta 0.01, m_limit 0.05", "cells": "monopole", "leaf_size": 16, "n_crit": 128,
-            "eps": eps, "rows": out}
+            "eps": eps, "rows": out, "uniform_delta_sweep": sweep}
 
 
 def run_batch(args, dev_name):
