@@ -82,8 +82,10 @@ struct BoxF {
 
 // The acceptance test of the host walk, operation for operation in FP64
 // (no contraction: every operation is an explicitly rounded intrinsic).
-__device__ bool mac_exact(const otoo_wcell64* __restrict__ c64, int k, const double blo[3], const double bhi[3],
-                          double theta)
+// Called for the few tests the FP32 filter cannot decide, so kept out of line
+// (a smaller walk loop for the instruction cache).
+__device__ __noinline__ bool mac_exact(const otoo_wcell64* __restrict__ c64, int k, const double blo[3],
+                                       const double bhi[3], double theta)
 {
     if (!(theta > 0.0)) return false;
     const otoo_wcell64 c = c64[k];
@@ -166,8 +168,9 @@ __device__ __forceinline__ void ld256(const void* p, float v[8])
 }
 
 // The absolute MAC of the host walk (Eq. SW_MAC): d_min > r_b, FP64,
-// operation for operation.
-__device__ bool sw_exact(const otoo_wcell64* __restrict__ c64, int k, const double blo[3], const double bhi[3])
+// operation for operation (out of line, as mac_exact).
+__device__ __noinline__ bool sw_exact(const otoo_wcell64* __restrict__ c64, int k, const double blo[3],
+                                      const double bhi[3])
 {
     const otoo_wcell64 c = c64[k];
     double d2 = 0.0;
@@ -675,10 +678,12 @@ __device__ __forceinline__ void fuse_tile(const WalkArgs& a, const FuseArgs& f, 
 #pragma unroll
         for (int k = 0; k < IB; ++k) P2[k].v[0] = P2[k].v[1] = P2[k].v[2] = P2[k].v[3] = zero2;
         const int niter = npair_pad / nsub;
+        // loops not unrolled: the walk and the evaluation alternate in one
+        // warp and must fit the instruction cache together
         if (cq) {
             const float4* __restrict__ r = rec + 5 * js;
             const int S = 5 * nsub;
-#pragma unroll 2
+#pragma unroll 1
             for (int n = 0; n < niter; ++n, r += S) {
                 const float4 v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4];
                 const f2 sx = f2pack(v0.x, v0.y), sy = f2pack(v0.z, v0.w), sz = f2pack(v1.x, v1.y);
@@ -693,7 +698,7 @@ __device__ __forceinline__ void fuse_tile(const WalkArgs& a, const FuseArgs& f, 
         } else {
             const float4* __restrict__ r = rec + 2 * js;
             const int S = 2 * nsub;
-#pragma unroll 3
+#pragma unroll 1
             for (int n = 0; n < niter; ++n, r += S) {
                 const float4 v0 = r[0], v1 = r[1];
                 const f2 sx = f2pack(v0.x, v0.y), sy = f2pack(v0.z, v0.w), sz = f2pack(v1.x, v1.y);
