@@ -26,8 +26,9 @@
 //                           a cell with more than leaf_size particles (above
 //                           the last grid level) splits into the runs of its
 //                           particles' next key digit, found by binary search.
-//   k_moments               bottom-up, one level per launch: leaves sum their
-//                           particles, parents combine their children.
+//   k_moments               leaves sum their particles (all leaves in one
+//                           launch), then parents combine their children, one
+//                           level per launch, deepest first.
 //   k_bmax                  largest distance of a cell's particles from its
 //                           centre of mass (chunks of particles, atomic max).
 //   k_records               sources, quadrupoles and walk records of the cells.
@@ -363,17 +364,18 @@ struct Moments {
     unsigned long long* dmax2;  // [cap] bits of the largest squared distance
 };
 
-// Cells [lo, hi) of one level: a leaf sums its particles (mass and mass-
-// weighted position, then the second moments about the centre of mass); a
-// parent combines its children, shifting each child's moments to the
-// parent's centre of mass: Q += m_c (3 d d^T - |d|^2 I), B_2 += m_c |d|^2,
-// d = com_c - com.
-__global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ src, Cells c, Moments mo)
+// Cells [lo, hi): a leaf sums its particles (mass and mass-weighted
+// position, then the second moments about the centre of mass); a parent
+// combines its children, shifting each child's moments to the parent's
+// centre of mass: Q += m_c (3 d d^T - |d|^2 I), B_2 += m_c |d|^2, d = com_c -
+// com.  mode 1: leaves only; 2: parents only (their children done); else all.
+__global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ src, Cells c, Moments mo, int mode)
 {
     const int32_t cell = lo + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (cell >= hi) return;
     double m = 0, s[3] = {0, 0, 0}, q[6] = {0, 0, 0, 0, 0, 0}, b2 = 0, com[3];
     const int32_t nch = c.nchild[cell];
+    if ((mode == 1 && nch != 0) || (mode == 2 && nch == 0)) return;
     if (nch == 0) {
         const int32_t b = c.begin[cell], e = c.end[cell];
         for (int32_t i = b; i < e; ++i) {
@@ -827,10 +829,12 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
     }
     const int32_t n_cell = lev_lo.back();
 
-    // moments, deepest level first
+    // moments: every leaf in one launch, then the parents level by level,
+    // deepest first
+    k_moments<<<(unsigned)((n_cell + 127) / 128), 128, 0, s>>>(0, n_cell, t->src, c, mo, 1);
     for (int L = depth; L >= 0; --L) {
         const int32_t lo = lev_lo[L], hi = lev_lo[L + 1];
-        if (hi > lo) k_moments<<<(unsigned)((hi - lo + 127) / 128), 128, 0, s>>>(lo, hi, t->src, c, mo);
+        if (hi > lo) k_moments<<<(unsigned)((hi - lo + 127) / 128), 128, 0, s>>>(lo, hi, t->src, c, mo, 2);
     }
     CUDA_TRY(cudaGetLastError());
     const bool sph = t->mac == OTOO_MAC_SPH;
