@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--err-targets", type=int, default=512)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the batched 64-system step and the learned-angle comparison")
     ap.add_argument("--skip-walk", action="store_true", help="skip the device-walk step")
