@@ -864,7 +864,8 @@ def run_reference(args):
     w, pos, mass = workload(args, 0)
     pick_tune(w, args)  # the same n_crit as the GPU arm
     steps = []
-    per = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    # about two minutes for the whole run, at most --cpu-seconds per step
+    per = min(args.cpu_seconds, max(2.0, 120.0 / max(1, args.steps + args.warmup)))
     tree = oracle_tree(w, pos, mass)
     for k in range(args.warmup + args.steps):
         cb = cpu_baseline(w, pos, mass, per, tree)
