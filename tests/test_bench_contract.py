@@ -1,10 +1,13 @@
-"""The benchmark's reference arm (the FP64 CPU oracle on a bounded sample of
-the workload) prints one JSON line with the keys the benchmark contract
-names; run here on a small particle count so it needs no GPU."""
+"""The benchmark prints one JSON line with the keys of its contract: the
+reference arm (the FP64 CPU oracle on a bounded sample of the workload, no
+GPU needed) and, on a GPU, this library's arm (roofline, CPU baseline, end to
+end, clocks, launch count), both run on a small particle count."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -26,3 +29,28 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "groups" in cb["sample"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+@pytest.mark.gpu
+def test_gpu_arm_prints_one_contract_line():
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--n", "65536", "--steps", "3", "--warmup", "3",
+           "--err-targets", "64", "--cpu-seconds", "0.5", "--skip-extras", "--skip-walk", "--skip-sw", "--skip-step",
+           "--skip-sph"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches"):
+        assert k in d, k
+    assert d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3 and d["value"] > 0
+    assert d["config"]["workload"] == "hernquist8m" and d["config"]["n"] == 65536
+    rf = d["roofline"]
+    assert rf["bound"] == "alu" and rf["unit"] == "TFLOP/s" and 0 < rf["frac"] < 1.2
+    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-9
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    e2e = d["e2e"]
+    assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] == 65536 * 32
+    assert d["gpu_launches"] >= 2 * d["steps"]
+    assert d["errors"]["fp32k_acc_rms"] < 2e-3
