@@ -220,12 +220,18 @@ int otoo_make_groups_and_lists(const otoo_tree* tree, const otoo_params* params,
    indices are rebased.  The inputs stay owned by the caller. */
 int otoo_pack_batch(const otoo_lists* const* per_sys, int32_t n_sys, otoo_lists** out);
 
-/* Work items for otoo_force: groups with more than 32 * tune->iblock
-   particles are cut into particle chunks of at most that many, lists longer
-   than tune->split entries into chunks of at most tune->split entries (of
-   balanced length); items are ordered by decreasing cost ni * (j1 - j0)
-   (longest processing time first).  Groups with an empty list (a negative
-   per-group angle) get no item. */
+/* Work items for otoo_force: every group is cut into particle chunks of at
+   most 32 * tune->iblock particles whose sizes fill a warp's lanes (a fixed
+   table per iblock, the cut of each group size that minimises a modelled
+   warp time: pair steps of ceil(ni / iblock) lanes in 32 / that many lane
+   subsets, staging of the list once per chunk, a fixed cost per item, the
+   subset merge; e.g. 26 particles at iblock 2 become chunks of 10 and 16),
+   lists longer than tune->split entries into chunks of at most tune->split
+   entries (of balanced length); items are ordered by decreasing cost ni *
+   (j1 - j0) (longest processing time first).  Groups with an empty list (a
+   negative per-group angle) get no item.  The device plan (otoo_plan_count,
+   otoo_plan_fill) makes the same items.  Errors: OTOO_EINVAL (a group of
+   more than 1024 particles), OTOO_ENOMEM. */
 int otoo_make_plan(const otoo_lists* lists, const otoo_tune* tune, otoo_plan** out);
 
 /* Host arrays of a tree (pointers owned by the tree handle); cells are
