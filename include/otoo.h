@@ -527,7 +527,9 @@ int otoo_plan_fill(const otoo_group* groups, int32_t n_groups, const otoo_tune* 
    the groups equal otoo_build_tree's; cells are numbered level by level
    (children consecutive), and the moments (mass, centre of mass,
    quadrupole, B_2, b_max) are combined bottom-up, equal to the host's direct
-   sums to rounding. */
+   sums to rounding.  The SPH radius of a cell (OTOO_MAC_SPH) is an FP32
+   upper bound on the host's: larger by at most about 2^-20 relative plus
+   the FP32 rounding of the positions, never smaller. */
 typedef struct otoo_devtree {
     /* in */
     int64_t n_part;                /* particles (>= 1) */
@@ -552,16 +554,16 @@ typedef struct otoo_devtree {
     uint32_t* status;              /* scratch, >= 2 uint32 */
 } otoo_devtree;
 
-/* Bytes of device scratch otoo_devtree_build needs. */
+/* Bytes of device scratch otoo_devtree_build needs (16-byte aligned). */
 int64_t otoo_devtree_scratch_bytes(int64_t n_part, int64_t cap_cell);
 
 /* Builds the tree of pos (device [n_part][3] FP64, caller order) and mass
    (device [n_part] FP32 > 0) on stream and fills tree's device arrays and
    out fields; synchronises stream once per tree level (the host reads each
    level's cell count).  Errors: OTOO_EINVAL (sizes, NULL pointers, scratch
-   too small, a non-finite position or a mass <= 0), OTOO_ENOMEM (more
-   cells than cap_cell: n_cell = -1; call again with a larger capacity),
-   OTOO_ECUDA. */
+   too small or not 16-byte aligned, a non-finite position or a mass <= 0),
+   OTOO_ENOMEM (more cells than cap_cell: n_cell = -1; call again with a
+   larger capacity), OTOO_ECUDA. */
 int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* tree, void* scratch,
                        int64_t scratch_bytes, void* stream);
 

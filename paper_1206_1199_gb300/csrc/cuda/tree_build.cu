@@ -30,7 +30,8 @@
 //                           launch), then parents combine their children, one
 //                           level per launch, deepest first.
 //   k_bmax                  largest distance of a cell's particles from its
-//                           centre of mass (chunks of particles, atomic max).
+//                           centre of mass, or the SPH radius bound (chunks of
+//                           particles, atomic max).
 //   k_records               sources, quadrupoles and walk records of the cells.
 //   k_group_flags           first particle of every group (maximal cells with
 //                           at most n_crit particles; larger leaves in chunks).
@@ -361,7 +362,8 @@ struct Moments {
     double* com;    // [cap][3]
     double* q;      // [cap][6] Qxx Qyy Qzz Qxy Qxz Qyz
     double* b2;     // [cap]
-    unsigned long long* dmax2;  // [cap] bits of the largest squared distance
+    unsigned long long* dmax2;  // [cap] bits of the largest squared distance (FP64), or of
+                                //   the SPH radius (FP32, zero-extended)
 };
 
 // Cells [lo, hi): a leaf sums its particles (mass and mass-weighted
@@ -428,60 +430,101 @@ __global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ s
     mo.dmax2[cell] = 0ull;
 }
 
-// Work item = (cell, chunk of kBmaxChunk particles); item_off: exclusive
-// prefix over cells of their chunk counts.  One warp per item; the chunk's
-// largest squared distance goes to the cell by an atomic max on its bits
-// (non-negative doubles order like their bit patterns).
-// With h (caller order, through perm) the same pass gives the SPH radius
-// instead: the largest |com - x_j| + h_j (Eq. SPH_RAD), kept as the bits of
-// that non-negative value (not squared).  The distance is taken in FP32 from
-// the FP64 offset and the sum rounded up by 2^-20 relative (FP32 square root
-// and sum err by a few 2^-24): the radius can only be larger than the exact
-// one, so a cell may keep particles that contribute W = 0 but never loses a
-// neighbour.
-__global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restrict__ item_off,
-                       const otoo_src* __restrict__ src, Cells c, Moments mo, const float* __restrict__ h,
-                       const int64_t* __restrict__ perm)
+// Work items, one warp each: warp w < n_cell takes the first kBmaxChunk
+// particles of cell w; warp n_cell + k takes extra chunk k of the cells that
+// hold more (extra_off: exclusive prefix over cells of their chunk counts
+// minus one, so only those few warps search it).  The chunk's largest value
+// goes to the cell by an atomic max on its bits (non-negative floating-point
+// values order like their bit patterns).
+//
+// Without pk (absolute MAC) the value is the squared distance from the
+// centre of mass in FP64, as the host computes it; dmax2 holds double bits.
+// With pk (SPH) it is an upper bound on the cell's SPH radius, the largest
+// |com - x_j| + h_j (Eq. SPH_RAD), in FP32 throughout; dmax2 holds the float
+// bits, zero-extended.  pk[j] = (x_j, y_j, z_j rounded to FP32, h_j) in tree
+// order, cf[cell] = (com rounded to FP32, e_c).  Rounding a value v to FP32
+// moves it by at most 2^-24 |v| per coordinate, so |com - x_j| <= |com~ - x~_j|
+// + e_c + e_j with e = 2^-23 (|x~| + |y~| + |z~|) (twice the bound, which
+// also covers rounding in e itself); the FP32 distance, square root and sums
+// err by a few 2^-24 relative, covered by rounding the total up by 2^-20.  The
+// radius can therefore only be larger than the exact one: a cell may keep
+// particles that contribute W = 0 but never loses a neighbour.
+__global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restrict__ extra_off,
+                       const otoo_src* __restrict__ src, const float4* __restrict__ pk,
+                       const float4* __restrict__ cf, Cells c, Moments mo)
 {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n_items) return;
-    int32_t l = 0, r = n_cell;  // last cell with item_off <= w
-    while (r - l > 1) {
-        const int32_t m = l + ((r - l) >> 1);
-        if (item_off[m] <= w)
-            l = m;
-        else
-            r = m;
+    int32_t cell;
+    int64_t chunk;
+    if (w < n_cell) {
+        cell = (int32_t)w;
+        chunk = 0;
+    } else {
+        const int64_t k = w - n_cell;
+        int32_t l = 0, r = n_cell;  // last cell with extra_off <= k
+        while (r - l > 1) {
+            const int32_t m = l + ((r - l) >> 1);
+            if (extra_off[m] <= k)
+                l = m;
+            else
+                r = m;
+        }
+        cell = l;
+        chunk = 1 + k - extra_off[cell];
     }
-    const int32_t cell = l;
-    const int64_t chunk = w - item_off[cell];
     const int32_t b = c.begin[cell], e = c.end[cell];
     const int64_t i0 = b + chunk * kBmaxChunk;
     const int64_t i1 = i0 + kBmaxChunk < e ? i0 + kBmaxChunk : e;
+    if (pk) {
+        const float4 cc = cf[cell];
+        float vmax = 0.f;
+        for (int64_t i = i0 + lane; i < i1; i += 32) {
+            const float4 p = pk[i];
+            const float dx = cc.x - p.x, dy = cc.y - p.y, dz = cc.z - p.z;
+            const float ej = 0x1p-23f * (fabsf(p.x) + fabsf(p.y) + fabsf(p.z));
+            vmax = fmaxf(vmax, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + (p.w + ej));
+        }
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(kFull, vmax, o));
+        if (lane == 0)
+            atomicMax(mo.dmax2 + cell, (unsigned long long)__float_as_uint((vmax + cc.w) * (1.0f + 0x1p-20f)));
+        return;
+    }
     const double cx = mo.com[3 * cell], cy = mo.com[3 * cell + 1], cz = mo.com[3 * cell + 2];
     double d2max = 0;
     for (int64_t i = i0 + lane; i < i1; i += 32) {
         const otoo_src p = src[i];
         const double dx = cx - p.x, dy = cy - p.y, dz = cz - p.z;
-        if (h) {
-            const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-            const float v = (sqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz))) + h[perm[i]]) * (1.0f + 0x1p-20f);
-            d2max = fmax(d2max, (double)v);
-        } else {
-            d2max = fmax(d2max, dx * dx + dy * dy + dz * dz);
-        }
+        d2max = fmax(d2max, dx * dx + dy * dy + dz * dz);
     }
     for (int o = 16; o > 0; o >>= 1) d2max = fmax(d2max, __shfl_xor_sync(kFull, d2max, o));
     if (lane == 0) atomicMax(mo.dmax2 + cell, (unsigned long long)__double_as_longlong(d2max));
 }
 
-__global__ void k_chunks(int32_t n_cell, Cells c, int32_t* __restrict__ nchunk)
+// Chunks of kBmaxChunk particles beyond the first, per cell; with cf (SPH)
+// also the cell's FP32 centre of mass and its rounding bound e_c (k_bmax).
+__global__ void k_chunks(int32_t n_cell, Cells c, const double* __restrict__ com, int32_t* __restrict__ extra,
+                         float4* __restrict__ cf)
 {
     const int32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= n_cell) return;
     const int32_t cnt = c.end[cell] - c.begin[cell];
-    nchunk[cell] = (cnt + kBmaxChunk - 1) / kBmaxChunk;
+    extra[cell] = (cnt + kBmaxChunk - 1) / kBmaxChunk - 1;
+    if (cf) {
+        const float x = (float)com[3 * cell], y = (float)com[3 * cell + 1], z = (float)com[3 * cell + 2];
+        cf[cell] = make_float4(x, y, z, 0x1p-23f * (fabsf(x) + fabsf(y) + fabsf(z)));
+    }
+}
+
+// Tree-order FP32 positions with each particle's SPH radius (k_bmax).
+__global__ void k_sph_bpack(int64_t n, const otoo_src* __restrict__ src, const float* __restrict__ h,
+                            const int64_t* __restrict__ perm, float4* __restrict__ pk)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const otoo_src p = src[i];
+    pk[i] = make_float4((float)p.x, (float)p.y, (float)p.z, h[perm[i]]);
 }
 
 // ---- records and groups ----------------------------------------------------------
@@ -530,7 +573,7 @@ __global__ void k_records(RecArgs ra, const Geom* __restrict__ g, Cells c, Momen
     quad[cell] = qd;
     const double dm = __longlong_as_double((long long)mo.dmax2[cell]);
     const double rb = ra.mac == OTOO_MAC_SW    ? sw_radius(mo.b2[cell], __dsqrt_rn(dm), m, ra.delta, ra.m_limit, g->S)
-                      : ra.mac == OTOO_MAC_SPH ? dm
+                      : ra.mac == OTOO_MAC_SPH ? (double)__uint_as_float((unsigned)mo.dmax2[cell])
                                                : 0.0;
     otoo_wcell w;
     wcell_geometry(com, lo, gc, side, &w);
@@ -740,6 +783,8 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
     const Layout ly = layout(n, cap);
     OTOO_REQUIRE(scratch_bytes >= (int64_t)ly.total, OTOO_EINVAL, "otoo_devtree_build: scratch too small (%lld < %lld)",
                  (long long)scratch_bytes, (long long)ly.total);
+    OTOO_REQUIRE((reinterpret_cast<uintptr_t>(scratch) & 15) == 0, OTOO_EINVAL,
+                 "otoo_devtree_build: scratch not 16-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char* base = static_cast<char*>(scratch);
     uint64_t* keys[2] = {reinterpret_cast<uint64_t*>(base + ly.keys0), reinterpret_cast<uint64_t*>(base + ly.keys1)};
@@ -839,15 +884,20 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
     CUDA_TRY(cudaGetLastError());
     const bool sph = t->mac == OTOO_MAC_SPH;
     if (t->mac == OTOO_MAC_SW || sph) {
-        k_chunks<<<(unsigned)((n_cell + 255) / 256), 256, 0, s>>>(n_cell, c, cnt);
+        // The sorted keys and the expansion digits are dead once the cells
+        // exist: keys0..keys1 (two adjacent 256-byte-aligned parts of 8 n
+        // bytes) hold the FP32 particles, dig (32 cap bytes) the FP32 centres.
+        float4* pk = sph ? reinterpret_cast<float4*>(base + ly.keys0) : nullptr;
+        float4* cf = sph ? reinterpret_cast<float4*>(dig) : nullptr;
+        k_chunks<<<(unsigned)((n_cell + 255) / 256), 256, 0, s>>>(n_cell, c, mo.com, cnt, cf);
+        if (sph) k_sph_bpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, t->src, t->h_sph, t->perm, pk);
         const int r = scan32(cnt, n_cell, bsum, tot, s);
         if (r) return r;
-        int64_t n_items = 0;
-        CUDA_TRY(cudaMemcpyAsync(&n_items, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        int64_t n_extra = 0;
+        CUDA_TRY(cudaMemcpyAsync(&n_extra, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
-        if (n_items > 0)
-            k_bmax<<<(unsigned)((n_items * 32 + 255) / 256), 256, 0, s>>>(n_items, n_cell, cnt, t->src, c, mo,
-                                                                          sph ? t->h_sph : nullptr, t->perm);
+        const int64_t n_items = n_cell + n_extra;
+        k_bmax<<<(unsigned)((n_items * 32 + 255) / 256), 256, 0, s>>>(n_items, n_cell, cnt, t->src, pk, cf, c, mo);
         CUDA_TRY(cudaGetLastError());
     }
     RecArgs ra;

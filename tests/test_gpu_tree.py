@@ -112,6 +112,31 @@ def test_device_tree_matches_host(torch, model, n, leaf, ncrit):
     check_tree(pos, mass, leaf, ncrit)
 
 
+@pytest.mark.parametrize("model,n,leaf", [("plummer", 20000, 8), ("hernquist", 30000, 8), ("plummer", 5000, 1)])
+def test_device_tree_sph_radius_is_an_upper_bound(torch, model, n, leaf):
+    # The device's SPH radius (Eq. SPH_RAD) is an FP32 bound: never below
+    # the host's FP64 value, and above it by at most 2^-19 relative plus the
+    # FP32 rounding of the centre of mass and the particles and the bounds
+    # added for it (a few 2^-24 of the coordinates' magnitudes; the particles
+    # lie within r_b of the centre)
+    pos, mass = ic.make(model, n, 53)
+    h = ic.sph_radii(pos, mass, 64, model).astype(np.float32)
+    t = S.Tree(pos, mass, leaf)
+    e = t.export()
+    cell = np.empty(e["n_cell"], np.dtype(L.WCell))
+    cell64 = np.empty(e["n_cell"], np.dtype(L.WCell64))
+    p = S._params(0.0, leaf, 64, False, 1.0, None, "sph", h_sph=h)
+    L.call("otoo_tree_device_arrays", t._h, 0, ctypes.byref(p), None, None, cell.ctypes.data, cell64.ctypes.data)
+    dt = S.DeviceTree.build(pos, mass, leaf, 64, False, "cuda", mac="sph", h_sph=h)
+    d = dev_arrays(dt)
+    m = cell_map(e, d)
+    rd, rh = d["cell64"]["rb"], cell64["rb"][m]
+    com1 = np.abs(d["cell64"]["com"]).sum(1)
+    assert np.all(rd >= rh)
+    assert np.all(rd <= rh * (1 + 2.0 ** -19) + 2.0 ** -20 * (com1 + rh))
+    np.testing.assert_array_equal(d["cell"]["rb"], rd.astype(np.float32))
+
+
 def test_device_tree_edge_cases(torch):
     # one particle; coincident particles (a last-level leaf bigger than
     # n_crit and leaf_size); a tiny cell capacity that has to grow
