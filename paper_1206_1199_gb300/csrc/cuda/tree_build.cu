@@ -30,8 +30,9 @@
 //                           launch), then parents combine their children, one
 //                           level per launch, deepest first.
 //   k_bmax                  largest distance of a cell's particles from its
-//                           centre of mass, or the SPH radius bound (chunks of
-//                           particles, atomic max).
+//                           centre of mass (FP64, on the particles an FP32
+//                           bound leaves), or the SPH radius bound (FP32);
+//                           chunks of particles, atomic max.
 //   k_records               sources, quadrupoles and walk records of the cells.
 //   k_group_flags           first particle of every group (maximal cells with
 //                           at most n_crit particles; larger leaves in chunks).
@@ -430,6 +431,16 @@ __global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ s
     mo.dmax2[cell] = 0ull;
 }
 
+// FP32 distance |c~ - x~_j| between a cell's rounded centre of mass c~ and a
+// rounded particle x~_j (k_bmax), and the particle's rounding bound
+// e_j = 2^-23 (|x~| + |y~| + |z~|).
+__device__ __forceinline__ float bmax_dist(const float4 cc, const float4 p, float& ej)
+{
+    const float dx = cc.x - p.x, dy = cc.y - p.y, dz = cc.z - p.z;
+    ej = 0x1p-23f * (fabsf(p.x) + fabsf(p.y) + fabsf(p.z));
+    return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+}
+
 // Work items, one warp each: warp w < n_cell takes the first kBmaxChunk
 // particles of cell w; warp n_cell + k takes extra chunk k of the cells that
 // hold more (extra_off: exclusive prefix over cells of their chunk counts
@@ -437,21 +448,28 @@ __global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ s
 // goes to the cell by an atomic max on its bits (non-negative floating-point
 // values order like their bit patterns).
 //
-// Without pk (absolute MAC) the value is the squared distance from the
-// centre of mass in FP64, as the host computes it; dmax2 holds double bits.
-// With pk (SPH) it is an upper bound on the cell's SPH radius, the largest
+// pk[j] = (x_j, y_j, z_j rounded to FP32, h_j or 0) in tree order,
+// cf[cell] = (com rounded to FP32, e_c).  Rounding a value v to FP32 moves it
+// by at most 2^-24 |v| per coordinate, so |com - x_j| lies within
+// e_c + e_j (twice that bound, which also covers rounding in e itself) of
+// |com~ - x~_j|, and the FP32 distance errs by a few 2^-24 relative, covered
+// by a factor 1 -+ 2^-20.
+//
+// SPH (sph != 0): an upper bound on the cell's SPH radius, the largest
 // |com - x_j| + h_j (Eq. SPH_RAD), in FP32 throughout; dmax2 holds the float
-// bits, zero-extended.  pk[j] = (x_j, y_j, z_j rounded to FP32, h_j) in tree
-// order, cf[cell] = (com rounded to FP32, e_c).  Rounding a value v to FP32
-// moves it by at most 2^-24 |v| per coordinate, so |com - x_j| <= |com~ - x~_j|
-// + e_c + e_j with e = 2^-23 (|x~| + |y~| + |z~|) (twice the bound, which
-// also covers rounding in e itself); the FP32 distance, square root and sums
-// err by a few 2^-24 relative, covered by rounding the total up by 2^-20.  The
-// radius can therefore only be larger than the exact one: a cell may keep
-// particles that contribute W = 0 but never loses a neighbour.
+// bits, zero-extended.  The radius can only be larger than the exact one: a
+// cell may keep particles that contribute W = 0 but never loses a neighbour.
+//
+// Absolute MAC: the largest squared distance in FP64, as the host computes
+// it; dmax2 holds double bits.  A first FP32 pass finds a lower bound L on
+// the chunk's largest distance; the FP64 distance is then taken only for the
+// particles whose FP32 upper bound reaches L.  That set holds every particle
+// whose FP64 value could be the largest (their exact distances lie within
+// 2^-40 or so of the largest, far inside the bounds' margin), so the result
+// is the same bits as the FP64 maximum over all particles.
 __global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restrict__ extra_off,
                        const otoo_src* __restrict__ src, const float4* __restrict__ pk,
-                       const float4* __restrict__ cf, Cells c, Moments mo)
+                       const float4* __restrict__ cf, Cells c, Moments mo, int sph)
 {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -477,33 +495,48 @@ __global__ void k_bmax(int64_t n_items, int32_t n_cell, const int32_t* __restric
     const int32_t b = c.begin[cell], e = c.end[cell];
     const int64_t i0 = b + chunk * kBmaxChunk;
     const int64_t i1 = i0 + kBmaxChunk < e ? i0 + kBmaxChunk : e;
-    if (pk) {
-        const float4 cc = cf[cell];
+    const float4 cc = cf[cell];
+    if (sph) {
         float vmax = 0.f;
         for (int64_t i = i0 + lane; i < i1; i += 32) {
             const float4 p = pk[i];
-            const float dx = cc.x - p.x, dy = cc.y - p.y, dz = cc.z - p.z;
-            const float ej = 0x1p-23f * (fabsf(p.x) + fabsf(p.y) + fabsf(p.z));
-            vmax = fmaxf(vmax, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + (p.w + ej));
+            float ej;
+            const float d = bmax_dist(cc, p, ej);
+            vmax = fmaxf(vmax, d + (p.w + ej));
         }
         for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(kFull, vmax, o));
         if (lane == 0)
             atomicMax(mo.dmax2 + cell, (unsigned long long)__float_as_uint((vmax + cc.w) * (1.0f + 0x1p-20f)));
         return;
     }
-    const double cx = mo.com[3 * cell], cy = mo.com[3 * cell + 1], cz = mo.com[3 * cell + 2];
-    double d2max = 0;
+    float lo = 0.f;
     for (int64_t i = i0 + lane; i < i1; i += 32) {
-        const otoo_src p = src[i];
-        const double dx = cx - p.x, dy = cy - p.y, dz = cz - p.z;
-        d2max = fmax(d2max, dx * dx + dy * dy + dz * dz);
+        float ej;
+        const float d = bmax_dist(cc, pk[i], ej);
+        lo = fmaxf(lo, d * (1.0f - 0x1p-20f) - 2.0f * (ej + cc.w));
     }
-    for (int o = 16; o > 0; o >>= 1) d2max = fmax(d2max, __shfl_xor_sync(kFull, d2max, o));
-    if (lane == 0) atomicMax(mo.dmax2 + cell, (unsigned long long)__double_as_longlong(d2max));
+    for (int o = 16; o > 0; o >>= 1) lo = fmaxf(lo, __shfl_xor_sync(kFull, lo, o));
+    const double cx = mo.com[3 * cell], cy = mo.com[3 * cell + 1], cz = mo.com[3 * cell + 2];
+    unsigned long long d2max = 0;
+    for (int64_t i = i0 + lane; i < i1; i += 32) {
+        float ej;
+        const float d = bmax_dist(cc, pk[i], ej);
+        if (!((d + 2.0f * (ej + cc.w)) * (1.0f + 0x1p-20f) < lo)) {  // NaN bounds count as candidates
+            const otoo_src p = src[i];
+            const double dx = cx - p.x, dy = cy - p.y, dz = cz - p.z;
+            const unsigned long long v = (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz);
+            d2max = v > d2max ? v : d2max;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(kFull, d2max, o);
+        d2max = v > d2max ? v : d2max;
+    }
+    if (lane == 0) atomicMax(mo.dmax2 + cell, d2max);
 }
 
-// Chunks of kBmaxChunk particles beyond the first, per cell; with cf (SPH)
-// also the cell's FP32 centre of mass and its rounding bound e_c (k_bmax).
+// Chunks of kBmaxChunk particles beyond the first, per cell, and the cell's
+// FP32 centre of mass with its rounding bound e_c (k_bmax).
 __global__ void k_chunks(int32_t n_cell, Cells c, const double* __restrict__ com, int32_t* __restrict__ extra,
                          float4* __restrict__ cf)
 {
@@ -511,20 +544,19 @@ __global__ void k_chunks(int32_t n_cell, Cells c, const double* __restrict__ com
     if (cell >= n_cell) return;
     const int32_t cnt = c.end[cell] - c.begin[cell];
     extra[cell] = (cnt + kBmaxChunk - 1) / kBmaxChunk - 1;
-    if (cf) {
-        const float x = (float)com[3 * cell], y = (float)com[3 * cell + 1], z = (float)com[3 * cell + 2];
-        cf[cell] = make_float4(x, y, z, 0x1p-23f * (fabsf(x) + fabsf(y) + fabsf(z)));
-    }
+    const float x = (float)com[3 * cell], y = (float)com[3 * cell + 1], z = (float)com[3 * cell + 2];
+    cf[cell] = make_float4(x, y, z, 0x1p-23f * (fabsf(x) + fabsf(y) + fabsf(z)));
 }
 
-// Tree-order FP32 positions with each particle's SPH radius (k_bmax).
-__global__ void k_sph_bpack(int64_t n, const otoo_src* __restrict__ src, const float* __restrict__ h,
-                            const int64_t* __restrict__ perm, float4* __restrict__ pk)
+// Tree-order FP32 positions with each particle's SPH radius, or 0 without h
+// (k_bmax).
+__global__ void k_bpack(int64_t n, const otoo_src* __restrict__ src, const float* __restrict__ h,
+                        const int64_t* __restrict__ perm, float4* __restrict__ pk)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const otoo_src p = src[i];
-    pk[i] = make_float4((float)p.x, (float)p.y, (float)p.z, h[perm[i]]);
+    pk[i] = make_float4((float)p.x, (float)p.y, (float)p.z, h ? h[perm[i]] : 0.0f);
 }
 
 // ---- records and groups ----------------------------------------------------------
@@ -887,17 +919,18 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
         // The sorted keys and the expansion digits are dead once the cells
         // exist: keys0..keys1 (two adjacent 256-byte-aligned parts of 8 n
         // bytes) hold the FP32 particles, dig (32 cap bytes) the FP32 centres.
-        float4* pk = sph ? reinterpret_cast<float4*>(base + ly.keys0) : nullptr;
-        float4* cf = sph ? reinterpret_cast<float4*>(dig) : nullptr;
+        float4* pk = reinterpret_cast<float4*>(base + ly.keys0);
+        float4* cf = reinterpret_cast<float4*>(dig);
         k_chunks<<<(unsigned)((n_cell + 255) / 256), 256, 0, s>>>(n_cell, c, mo.com, cnt, cf);
-        if (sph) k_sph_bpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, t->src, t->h_sph, t->perm, pk);
+        k_bpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, t->src, sph ? t->h_sph : nullptr, t->perm, pk);
         const int r = scan32(cnt, n_cell, bsum, tot, s);
         if (r) return r;
         int64_t n_extra = 0;
         CUDA_TRY(cudaMemcpyAsync(&n_extra, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         const int64_t n_items = n_cell + n_extra;
-        k_bmax<<<(unsigned)((n_items * 32 + 255) / 256), 256, 0, s>>>(n_items, n_cell, cnt, t->src, pk, cf, c, mo);
+        k_bmax<<<(unsigned)((n_items * 32 + 255) / 256), 256, 0, s>>>(n_items, n_cell, cnt, t->src, pk, cf, c, mo,
+                                                                      sph ? 1 : 0);
         CUDA_TRY(cudaGetLastError());
     }
     RecArgs ra;
