@@ -361,73 +361,81 @@ __global__ void k_expand_write(int32_t lo, int32_t hi, int L, int32_t next_base,
 struct Moments {
     double* m;      // [cap]
     double* com;    // [cap][3]
-    double* q;      // [cap][6] Qxx Qyy Qzz Qxy Qxz Qyz
+    double* q;      // [cap][6] central second moment Cxx Cyy Czz Cxy Cxz Cyz
     double* b2;     // [cap]
     unsigned long long* dmax2;  // [cap] bits of the largest squared distance (FP64), or of
                                 //   the SPH radius (FP32, zero-extended)
 };
 
-// Cells [lo, hi): a leaf sums its particles (mass and mass-weighted
-// position, then the second moments about the centre of mass); a parent
-// combines its children, shifting each child's moments to the parent's
-// centre of mass: Q += m_c (3 d d^T - |d|^2 I), B_2 += m_c |d|^2, d = com_c -
-// com.  mode 1: leaves only; 2: parents only (their children done); else all.
+// Cells [lo, hi), one thread each, in one pass over the cell's members
+// (its particles for a leaf, its children for a parent): with x0 a member's
+// position (a leaf's first particle, a parent's heaviest child's centre of
+// mass) and d = x - x0, M = sum m, S1 = sum m d, S2 = sum m d d^T (+ the
+// child's own central second moment C_c), then com = x0 + S1 / M and the
+// central second moment C = S2 - S1 S1^T / M (the parallel-axis shift to the
+// centre of mass).  S1 S1^T / M = M g g^T with g = com - x0, while C holds
+// at least m_0 M / (M - m_0) g g^T (the reference member, mass m_0, against
+// the rest), so the subtraction loses about log2((M - m_0) / m_0) bits: under
+// 3 for a parent (the heaviest of up to 8 children), about log2 of the leaf
+// size for equal masses in a leaf.  Stored: m, com, C (Cxx Cyy Czz Cxy Cxz
+// Cyz) and B_2 = tr C; the records take the quadrupole Q = 3 C - tr(C) I.
+// mode 1: leaves only; 2: parents only (their children done); else all.
 __global__ void k_moments(int32_t lo, int32_t hi, const otoo_src* __restrict__ src, Cells c, Moments mo, int mode)
 {
     const int32_t cell = lo + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (cell >= hi) return;
-    double m = 0, s[3] = {0, 0, 0}, q[6] = {0, 0, 0, 0, 0, 0}, b2 = 0, com[3];
     const int32_t nch = c.nchild[cell];
     if ((mode == 1 && nch != 0) || (mode == 2 && nch == 0)) return;
+    double m = 0, s1[3] = {0, 0, 0}, s2[6] = {0, 0, 0, 0, 0, 0}, x0[3];
     if (nch == 0) {
         const int32_t b = c.begin[cell], e = c.end[cell];
-        for (int32_t i = b; i < e; ++i) {
-            const otoo_src p = src[i];
-            const double mi = p.m;
-            m += mi;
-            s[0] += mi * p.x;
-            s[1] += mi * p.y;
-            s[2] += mi * p.z;
+        {
+            const otoo_src p = src[b];
+            x0[0] = p.x, x0[1] = p.y, x0[2] = p.z;
         }
-        for (int a = 0; a < 3; ++a) com[a] = s[a] / m;
+#pragma unroll 1
         for (int32_t i = b; i < e; ++i) {
             const otoo_src p = src[i];
             const double mi = p.m;
-            const double dx = p.x - com[0], dy = p.y - com[1], dz = p.z - com[2];
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            b2 += mi * d2;
-            q[0] += mi * (3 * dx * dx - d2);
-            q[1] += mi * (3 * dy * dy - d2);
-            q[2] += mi * (3 * dz * dz - d2);
-            q[3] += mi * 3 * dx * dy;
-            q[4] += mi * 3 * dx * dz;
-            q[5] += mi * 3 * dy * dz;
+            const double dx = p.x - x0[0], dy = p.y - x0[1], dz = p.z - x0[2];
+            const double mx = mi * dx, my = mi * dy, mz = mi * dz;
+            m += mi;
+            s1[0] += mx, s1[1] += my, s1[2] += mz;
+            s2[0] = fma(mx, dx, s2[0]), s2[1] = fma(my, dy, s2[1]), s2[2] = fma(mz, dz, s2[2]);
+            s2[3] = fma(mx, dy, s2[3]), s2[4] = fma(mx, dz, s2[4]), s2[5] = fma(my, dz, s2[5]);
         }
     } else {
         const int32_t c0 = c.child0[cell];
+        int32_t kh = c0;  // the heaviest child (positive doubles order like their bits)
+        unsigned long long mh = 0;
         for (int32_t k = c0; k < c0 + nch; ++k) {
-            const double mk = mo.m[k];
-            m += mk;
-            for (int a = 0; a < 3; ++a) s[a] += mk * mo.com[3 * k + a];
+            const unsigned long long mb = (unsigned long long)__double_as_longlong(mo.m[k]);
+            if (mb > mh) mh = mb, kh = k;
         }
-        for (int a = 0; a < 3; ++a) com[a] = s[a] / m;
+        for (int a = 0; a < 3; ++a) x0[a] = mo.com[3 * kh + a];
+#pragma unroll 1
         for (int32_t k = c0; k < c0 + nch; ++k) {
             const double mk = mo.m[k];
-            const double dx = mo.com[3 * k] - com[0], dy = mo.com[3 * k + 1] - com[1], dz = mo.com[3 * k + 2] - com[2];
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            b2 += mo.b2[k] + mk * d2;
-            q[0] += mo.q[6 * k] + mk * (3 * dx * dx - d2);
-            q[1] += mo.q[6 * k + 1] + mk * (3 * dy * dy - d2);
-            q[2] += mo.q[6 * k + 2] + mk * (3 * dz * dz - d2);
-            q[3] += mo.q[6 * k + 3] + mk * 3 * dx * dy;
-            q[4] += mo.q[6 * k + 4] + mk * 3 * dx * dz;
-            q[5] += mo.q[6 * k + 5] + mk * 3 * dy * dz;
+            const double dx = mo.com[3 * k] - x0[0], dy = mo.com[3 * k + 1] - x0[1], dz = mo.com[3 * k + 2] - x0[2];
+            const double mx = mk * dx, my = mk * dy, mz = mk * dz;
+            m += mk;
+            s1[0] += mx, s1[1] += my, s1[2] += mz;
+            s2[0] = fma(mx, dx, s2[0] + mo.q[6 * k]), s2[1] = fma(my, dy, s2[1] + mo.q[6 * k + 1]);
+            s2[2] = fma(mz, dz, s2[2] + mo.q[6 * k + 2]), s2[3] = fma(mx, dy, s2[3] + mo.q[6 * k + 3]);
+            s2[4] = fma(mx, dz, s2[4] + mo.q[6 * k + 4]), s2[5] = fma(my, dz, s2[5] + mo.q[6 * k + 5]);
         }
     }
+    const double inv = 1.0 / m;
+    const double gx = s1[0] * inv, gy = s1[1] * inv, gz = s1[2] * inv;  // com - x0
     mo.m[cell] = m;
-    for (int a = 0; a < 3; ++a) mo.com[3 * cell + a] = com[a];
-    for (int k = 0; k < 6; ++k) mo.q[6 * cell + k] = q[k];
-    mo.b2[cell] = b2;
+    mo.com[3 * cell] = x0[0] + gx;
+    mo.com[3 * cell + 1] = x0[1] + gy;
+    mo.com[3 * cell + 2] = x0[2] + gz;
+    const double cxx = fma(-s1[0], gx, s2[0]), cyy = fma(-s1[1], gy, s2[1]), czz = fma(-s1[2], gz, s2[2]);
+    double* q = mo.q + 6 * (int64_t)cell;
+    q[0] = cxx, q[1] = cyy, q[2] = czz;
+    q[3] = fma(-s1[0], gy, s2[3]), q[4] = fma(-s1[0], gz, s2[4]), q[5] = fma(-s1[1], gz, s2[5]);
+    mo.b2[cell] = cxx + cyy + czz;
     mo.dmax2[cell] = 0ull;
 }
 
@@ -595,12 +603,15 @@ __global__ void k_records(RecArgs ra, const Geom* __restrict__ g, Cells c, Momen
     src[ra.n_part + cell] = s;
     otoo_quad qd;
     const bool u = ra.use_quad != 0;
-    qd.xx = u ? (float)mo.q[6 * cell] : 0.f;
-    qd.yy = u ? (float)mo.q[6 * cell + 1] : 0.f;
-    qd.zz = u ? (float)mo.q[6 * cell + 2] : 0.f;
-    qd.xy = u ? (float)mo.q[6 * cell + 3] : 0.f;
-    qd.xz = u ? (float)mo.q[6 * cell + 4] : 0.f;
-    qd.yz = u ? (float)mo.q[6 * cell + 5] : 0.f;
+    // Q = 3 C - tr(C) I from the central second moment C
+    const double* cm = mo.q + 6 * (int64_t)cell;
+    const double tr = mo.b2[cell];
+    qd.xx = u ? (float)(3.0 * cm[0] - tr) : 0.f;
+    qd.yy = u ? (float)(3.0 * cm[1] - tr) : 0.f;
+    qd.zz = u ? (float)(3.0 * cm[2] - tr) : 0.f;
+    qd.xy = u ? (float)(3.0 * cm[3]) : 0.f;
+    qd.xz = u ? (float)(3.0 * cm[4]) : 0.f;
+    qd.yz = u ? (float)(3.0 * cm[5]) : 0.f;
     qd.pad0 = qd.pad1 = 0.f;
     quad[cell] = qd;
     const double dm = __longlong_as_double((long long)mo.dmax2[cell]);
