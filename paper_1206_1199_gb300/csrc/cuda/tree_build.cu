@@ -165,12 +165,14 @@ __global__ void k_keys(const double* __restrict__ pos, int64_t n, const Geom* __
 }
 
 // ---- stable LSD radix sort ----------------------------------------------------
-// Block b sorts nothing itself: it counts the digits of its tile (hist,
-// digit-major: hist[d * nblk + b]); an exclusive scan of hist gives each
-// (digit, block) its output start; the scatter places each key after all
-// keys of smaller digit and after the keys of equal digit that precede it in
-// the input (earlier blocks, earlier warps of the block, earlier rounds and
-// lower lanes of the warp), which keeps the sort stable.
+// Block b counts the digits of its tile (hist, digit-major: hist[d * nblk +
+// b]); an exclusive scan of hist gives each (digit, block) its output start.
+// The scatter ranks each key after the keys of smaller digit in its tile and
+// after the keys of equal digit that precede it (earlier warps of the block,
+// earlier rounds and lower lanes of the warp), which keeps the sort stable;
+// it stages the tile in that order in shared memory and then writes each
+// digit's run of the tile to consecutive addresses from the run's global
+// start (coalesced stores instead of one scattered store per key).
 
 __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
                                                          int32_t* __restrict__ hist, int nblk)
@@ -187,18 +189,24 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t* __restri
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
+static_assert(kRsThreads == 256, "the scatter gives each of the 256 digits one thread");
+
 __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __restrict__ kin,
                                                             const uint32_t* __restrict__ vin, int64_t n, int shift,
                                                             const int32_t* __restrict__ offs, int nblk,
                                                             uint64_t* __restrict__ kout, uint32_t* __restrict__ vout)
 {
     __shared__ int32_t wcount[kRsWarps][256];
+    __shared__ int32_t dstart[256], gstart[256], wsum[kRsWarps];
+    __shared__ uint64_t skey[kRsTile];
+    __shared__ uint32_t sval[kRsTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     for (int d = lane; d < 256; d += 32) wcount[w][d] = 0;
     __syncwarp();
     // warp w owns the contiguous run [base, base + 32 kRsItems) of the tile
-    const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)w * 32 * kRsItems;
+    const int64_t b0 = (int64_t)blockIdx.x * kRsTile;
+    const int64_t base = b0 + (int64_t)w * 32 * kRsItems;
     uint64_t key[kRsItems];
     uint32_t val[kRsItems];
     int dig[kRsItems];
@@ -214,30 +222,53 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __res
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over the warps of the block, per digit, plus the
-    // block's start in the global order of that digit
-    for (int d = threadIdx.x; d < 256; d += kRsThreads) {
-        int32_t run = offs[(int64_t)d * nblk + blockIdx.x];
+    // digit d = thread: exclusive prefix over the warps, the tile's count of
+    // d, and (a block-wide scan over digits) the start of d's run in the tile
+    {
+        const int d = threadIdx.x;
+        int32_t run = 0;
         for (int k = 0; k < kRsWarps; ++k) {
             const int32_t c = wcount[k][d];
             wcount[k][d] = run;
             run += c;
         }
+        int32_t incl = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        int32_t excl = incl - run;
+        for (int k = 0; k < w; ++k) excl += wsum[k];
+        dstart[d] = excl;
+        gstart[d] = offs[(int64_t)d * nblk + blockIdx.x];
+        for (int k = 0; k < kRsWarps; ++k) wcount[k][d] += excl;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRsItems; ++r) {
         const unsigned peers = __match_any_sync(kFull, dig[r]);
         const bool ok = dig[r] < 256;
-        int32_t pos = 0;
-        if (ok) pos = wcount[w][dig[r]] + __popc(peers & lt);
+        int32_t lp = 0;
+        if (ok) lp = wcount[w][dig[r]] + __popc(peers & lt);
         __syncwarp();
         if (ok && (peers & lt) == 0) wcount[w][dig[r]] += __popc(peers);
         __syncwarp();
         if (ok) {
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            skey[lp] = key[r];
+            sval[lp] = val[r];
         }
+    }
+    __syncthreads();
+    // the tile's valid keys fill [0, nvalid) of the staging in digit order
+    const int nvalid = (int)(n - b0 < kRsTile ? n - b0 : kRsTile);
+    for (int j = threadIdx.x; j < nvalid; j += kRsThreads) {
+        const uint64_t k = skey[j];
+        const int d = (int)((k >> shift) & 255u);
+        const int64_t gp = (int64_t)gstart[d] + (j - dstart[d]);
+        kout[gp] = k;
+        vout[gp] = sval[j];
     }
 }
 
