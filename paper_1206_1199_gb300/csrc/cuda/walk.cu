@@ -1067,38 +1067,72 @@ PlanScratch plan_layout(int32_t* base, int64_t G)
     return p;
 }
 
-__global__ void k_plan_count(const otoo_group* __restrict__ groups, int32_t G, const ChunkTable tab, int32_t split,
-                             PlanScratch p, int64_t* __restrict__ totals)
+// The plan kernels run 256 threads per block, one group each.  The chunk
+// table (a kernel parameter) is copied to shared memory first: threads index
+// it by their own group sizes, which the parameter bank would serialise.
+// Counts and totals are summed per block in shared memory, so each block
+// makes one global atomic per class and per total instead of one per group.
+constexpr int kPlanThreads = 256;
+
+__device__ void plan_table_to_shared(const ChunkTable& tab, ChunkTable& st)
 {
+    for (int k = threadIdx.x; k <= kMaxGroup; k += blockDim.x) st.last[k] = tab.last[k];
+    if (threadIdx.x == 0) st.ib = tab.ib;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan_count(const otoo_group* __restrict__ groups, int32_t G,
+                                                             const ChunkTable tab, int32_t split, PlanScratch p,
+                                                             int64_t* __restrict__ totals)
+{
+    __shared__ ChunkTable st;
+    __shared__ int32_t shist[kClasses];
+    __shared__ unsigned long long s_items, s_split_groups, s_split_chunks, s_max;
+    plan_table_to_shared(tab, st);
+    for (int c = threadIdx.x; c < kClasses; c += blockDim.x) shist[c] = 0;
+    if (threadIdx.x == 0) s_items = s_split_groups = s_split_chunks = s_max = 0;
+    __syncthreads();
     const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
-    const otoo_group gr = groups[g];
-    atomicMax(reinterpret_cast<unsigned long long*>(totals + 3), (unsigned long long)(gr.count > 1 ? gr.count : 1));
-    const int64_t len = (int64_t)gr.n_cell + gr.n_part;
-    int32_t nic = 0, nch = 0, cls = 0;
-    if (len > 0 && gr.count > 0 && gr.count <= kMaxGroup) {
-        // the host plan's particle chunks (plan_chunks.h)
-        int32_t big = 0;
-        nic = chunk_count(tab, gr.count, &big);
-        nch = (int32_t)((len + split - 1) / split);
-        // cost class: 4 * log2 of the largest item's ni * (j1 - j0), in quarter octaves
-        const int64_t c0 = (int64_t)big * ((len + nch - 1) / nch);
-        const int msb = 63 - __clzll((long long)c0);
-        const int frac = msb >= 2 ? (int)((c0 >> (msb - 2)) & 3) : (int)((c0 << (2 - msb)) & 3);
-        cls = 4 * msb + frac;
-        if (cls >= kClasses) cls = kClasses - 1;
-        atomicAdd(p.hist + cls, nic * nch);
-        atomicAdd(reinterpret_cast<unsigned long long*>(totals), (unsigned long long)(nic * nch));
-        if (nch > 1) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(totals + 1), 1ull);
-            atomicAdd(reinterpret_cast<unsigned long long*>(totals + 2), (unsigned long long)nch);
+    if (g < G) {
+        const otoo_group gr = groups[g];
+        atomicMax(&s_max, (unsigned long long)(gr.count > 1 ? gr.count : 1));
+        const int64_t len = (int64_t)gr.n_cell + gr.n_part;
+        int32_t nic = 0, nch = 0, cls = 0;
+        if (len > 0 && gr.count > 0 && gr.count <= kMaxGroup) {
+            // the host plan's particle chunks (plan_chunks.h)
+            int32_t big = 0;
+            nic = chunk_count(st, gr.count, &big);
+            nch = (int32_t)((len + split - 1) / split);
+            // cost class: 4 * log2 of the largest item's ni * (j1 - j0), in quarter octaves
+            const int64_t c0 = (int64_t)big * ((len + nch - 1) / nch);
+            const int msb = 63 - __clzll((long long)c0);
+            const int frac = msb >= 2 ? (int)((c0 >> (msb - 2)) & 3) : (int)((c0 << (2 - msb)) & 3);
+            cls = 4 * msb + frac;
+            if (cls >= kClasses) cls = kClasses - 1;
+            atomicAdd(shist + cls, nic * nch);
+            atomicAdd(&s_items, (unsigned long long)(nic * nch));
+            if (nch > 1) {
+                atomicAdd(&s_split_groups, 1ull);
+                atomicAdd(&s_split_chunks, (unsigned long long)nch);
+            }
         }
+        p.nic[g] = nic;
+        p.nch[g] = nch;
+        p.slot0[g] = nch > 1 ? nch : 0;
+        p.sidx[g] = nch > 1 ? 1 : 0;
+        p.cls[g] = cls;
     }
-    p.nic[g] = nic;
-    p.nch[g] = nch;
-    p.slot0[g] = nch > 1 ? nch : 0;
-    p.sidx[g] = nch > 1 ? 1 : 0;
-    p.cls[g] = cls;
+    __syncthreads();
+    for (int c = threadIdx.x; c < kClasses; c += blockDim.x)
+        if (shist[c]) atomicAdd(p.hist + c, shist[c]);
+    if (threadIdx.x == 0) {
+        unsigned long long* t = reinterpret_cast<unsigned long long*>(totals);
+        if (s_items) atomicAdd(t, s_items);
+        if (s_split_groups) {
+            atomicAdd(t + 1, s_split_groups);
+            atomicAdd(t + 2, s_split_chunks);
+        }
+        atomicMax(t + 3, s_max);
+    }
 }
 
 __global__ void k_plan_cursor(PlanScratch p)
@@ -1111,18 +1145,32 @@ __global__ void k_plan_cursor(PlanScratch p)
     }
 }
 
-__global__ void k_plan_fill(const otoo_group* __restrict__ groups, int32_t G, const ChunkTable tab, PlanScratch p,
-                            otoo_item* __restrict__ items, int64_t items_cap, otoo_split* __restrict__ splits,
-                            int64_t splits_cap, uint32_t* __restrict__ status)
+__global__ void __launch_bounds__(kPlanThreads) k_plan_fill(const otoo_group* __restrict__ groups, int32_t G,
+                                                            const ChunkTable tab, PlanScratch p,
+                                                            otoo_item* __restrict__ items, int64_t items_cap,
+                                                            otoo_split* __restrict__ splits, int64_t splits_cap,
+                                                            uint32_t* __restrict__ status)
 {
+    __shared__ ChunkTable st;
+    __shared__ int32_t scount[kClasses], sbase[kClasses];
+    plan_table_to_shared(tab, st);
+    for (int c = threadIdx.x; c < kClasses; c += blockDim.x) scount[c] = 0;
+    __syncthreads();
+    // the block's items of each class take one run of that class's items
     const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
-    const int32_t nic = p.nic[g], nch = p.nch[g];
-    if (nic == 0 || nch == 0) return;
+    const int32_t nic = g < G ? p.nic[g] : 0, nch = g < G ? p.nch[g] : 0;
+    const bool on = nic > 0 && nch > 0;
+    const int32_t cls = on ? p.cls[g] : 0;
+    const int32_t local = on ? atomicAdd(scount + cls, nic * nch) : 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < kClasses; c += blockDim.x)
+        if (scount[c]) sbase[c] = atomicAdd(p.cursor + c, scount[c]);
+    __syncthreads();
+    if (!on) return;
     const otoo_group gr = groups[g];
     const int64_t len = (int64_t)gr.n_cell + gr.n_part;
     const int32_t slot0 = p.slot0[g];
-    const int32_t pos = atomicAdd(p.cursor + p.cls[g], nic * nch);
+    const int32_t pos = sbase[cls] + local;
     if ((int64_t)pos + nic * nch > items_cap) {
         atomicOr(status, kWalkNoRoom);
         return;
@@ -1142,7 +1190,7 @@ __global__ void k_plan_fill(const otoo_group* __restrict__ groups, int32_t G, co
     }
     int32_t k = pos, i0 = 0;
     for (int32_t rest = gr.count; rest > 0;) {
-        const int32_t ni = tab.last[rest];
+        const int32_t ni = st.last[rest];
         for (int32_t q = 0; q < nch; ++q) {
             otoo_item it;
             it.g = g;
@@ -1370,8 +1418,8 @@ int otoo_plan_count(const otoo_group* groups, int32_t n_groups, const otoo_tune*
     PlanScratch p = plan_layout(plan_scratch, n_groups);
     CUDA_TRY(cudaMemsetAsync(plan_totals, 0, 4 * sizeof(int64_t), s));
     CUDA_TRY(cudaMemsetAsync(p.hist, 0, kClasses * sizeof(int32_t), s));
-    k_plan_count<<<(n_groups + 255) / 256, 256, 0, s>>>(groups, n_groups, chunk_table(ib), tune->split, p,
-                                                         plan_totals);
+    k_plan_count<<<(n_groups + kPlanThreads - 1) / kPlanThreads, kPlanThreads, 0, s>>>(
+        groups, n_groups, chunk_table(ib), tune->split, p, plan_totals);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(excl_scan(I32In{p.slot0}, I32Out{p.slot0}, n_groups, p.bsum, nullptr, s));
     CUDA_TRY(excl_scan(I32In{p.sidx}, I32Out{p.sidx}, n_groups, p.bsum, nullptr, s));
@@ -1393,8 +1441,8 @@ int otoo_plan_fill(const otoo_group* groups, int32_t n_groups, const otoo_tune* 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int32_t ib = tune->iblock > 1 ? tune->iblock : 1;
     PlanScratch p = plan_layout(plan_scratch, n_groups);
-    k_plan_fill<<<(n_groups + 255) / 256, 256, 0, s>>>(groups, n_groups, chunk_table(ib), p, items, items_capacity,
-                                                        splits, splits_capacity, counter + 1);
+    k_plan_fill<<<(n_groups + kPlanThreads - 1) / kPlanThreads, kPlanThreads, 0, s>>>(
+        groups, n_groups, chunk_table(ib), p, items, items_capacity, splits, splits_capacity, counter + 1);
     CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }
