@@ -5,6 +5,7 @@ independently written oracle."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -44,6 +45,33 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(L.Src) == 32 and ctypes.sizeof(L.Quad) == 32 and ctypes.sizeof(L.Group) == 64
     assert ctypes.sizeof(L.Item) == 32 and ctypes.sizeof(L.Split) == 16
     assert ctypes.sizeof(L.WCell) == 64 and ctypes.sizeof(L.WCell64) == 96
+
+
+C_STRUCTS = {"Params": "otoo_params", "Tune": "otoo_tune", "Src": "otoo_src", "Quad": "otoo_quad",
+             "Group": "otoo_group", "Item": "otoo_item", "Split": "otoo_split", "DevSystem": "otoo_dev_system",
+             "ListsView": "otoo_lists_view", "PlanInfo": "otoo_plan_info", "TreeView": "otoo_tree_view",
+             "WCell": "otoo_wcell", "WCell64": "otoo_wcell64", "DevWalk": "otoo_dev_walk", "DevTree": "otoo_devtree"}
+
+
+def test_ctypes_layouts_match_the_c_header(tmp_path):
+    # every struct the binding mirrors: size and every field's offset as a C
+    # compiler lays out include/otoo.h (a field the header lacks fails to build)
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "otoo.h"', "int main(void) {"]
+    expect = []
+    for py, c in C_STRUCTS.items():
+        cls = getattr(L, py)
+        lines.append('printf("%%zu\\n", sizeof(%s));' % c)
+        expect.append(ctypes.sizeof(cls))
+        for f in cls._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (c, f[0]))
+            expect.append(getattr(cls, f[0]).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == expect
 
 
 def tree_and_lists(pos, mass, theta=0.5, n_crit=64, eps=0.01, quad=True, leaf=8):
