@@ -358,28 +358,41 @@ void find_groups(const otoo_tree* t, int n_crit, std::vector<GroupRange>& out)
     }
 }
 
-// Group MAC: accept cell c for the box [blo, bhi] when the cube misses the
-// box and d_min > l / theta + s (notation of Section II-B).
-inline bool mac_accept(const otoo_tree* t, int64_t c, const double blo[3], const double bhi[3], double theta)
+// s = |com - cube centre| of every cell (Section II-B), once per walk.
+void cell_offsets(const otoo_tree* t, std::vector<double>& s)
 {
-    if (!(theta > 0.0)) return false;
+    const int64_t nc = (int64_t)t->cells.size();
+    s.resize(nc);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < nc; ++c) {
+        double s2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            const double e = t->c_com[3 * c + a] - t->c_gc[3 * c + a];
+            s2 += e * e;
+        }
+        s[c] = std::sqrt(s2);
+    }
+}
+
+// Group MAC: accept cell c for the box [blo, bhi] when the cube misses the
+// box and d_min > l / theta + s (notation of Section II-B); thr = l / theta +
+// s comes from the caller (side / theta, then + s, in FP64).
+inline bool mac_accept(const otoo_tree* t, int64_t c, const double blo[3], const double bhi[3], double thr)
+{
     const double side = t->c_side[c];
     const double* clo = &t->c_lo[3 * c];
     if (clo[0] <= bhi[0] && blo[0] <= clo[0] + side && clo[1] <= bhi[1] && blo[1] <= clo[1] + side &&
         clo[2] <= bhi[2] && blo[2] <= clo[2] + side)
         return false;
     const double* com = &t->c_com[3 * c];
-    const double* gc = &t->c_gc[3 * c];
-    double d2 = 0, s2 = 0;
+    double d2 = 0;
     for (int a = 0; a < 3; ++a) {
         double d = 0;
         if (blo[a] - com[a] > d) d = blo[a] - com[a];
         if (com[a] - bhi[a] > d) d = com[a] - bhi[a];
         d2 += d * d;
-        const double e = com[a] - gc[a];
-        s2 += e * e;
     }
-    return std::sqrt(d2) > side / theta + std::sqrt(s2);
+    return std::sqrt(d2) > thr;
 }
 
 // Absolute MAC for the box [blo, bhi]: d_min (centre of mass to the box) > r_b.
@@ -512,6 +525,17 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
         } else if (sph) {
             sph_radii(t, p->h_sph, rb);
         }
+        // opening angle: s of every cell once, and with one angle for all
+        // groups the threshold l / theta + s too
+        std::vector<double> cs, thr;
+        if (!sw && !sph) {
+            cell_offsets(t, cs);
+            if (!p->theta_per_group && p->theta > 0.0) {
+                thr.resize(nc);
+#pragma omp parallel for schedule(static)
+                for (int64_t c = 0; c < nc; ++c) thr[c] = t->c_side[c] / p->theta + cs[c];
+            }
+        }
         // the walk: one shared list per group (Barnes 1990, Section III-D),
         // entries buffered per thread, then placed in group order
         const int nthr = omp_get_max_threads();
@@ -551,7 +575,10 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
                             const int64_t c0 = t->c_child0[c];
                             for (int k = t->c_nchild[c] - 1; k >= 0; --k) stack.push_back(c0 + k);
                         }
-                    } else if (sw ? sw_accept(t, c, blo, bhi, rb[c]) : mac_accept(t, c, blo, bhi, theta)) {
+                    } else if (sw ? sw_accept(t, c, blo, bhi, rb[c])
+                                  : theta > 0.0 &&
+                                        mac_accept(t, c, blo, bhi,
+                                                   thr.empty() ? t->c_side[c] / theta + cs[c] : thr[c])) {
                         buf.push_back((int32_t)(n + c));
                         ++ncell;
                     } else if (t->c_nchild[c] == 0) {
@@ -561,8 +588,9 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
                         for (int k = t->c_nchild[c] - 1; k >= 0; --k) stack.push_back(c0 + k);
                     }
                 }
-                // particle entries in increasing tree order after the cells
-                std::sort(parts.begin(), parts.end());
+                // particle entries in increasing tree order after the cells (the
+                // pre-order walk meets the leaves in tree order already)
+                if (!std::is_sorted(parts.begin(), parts.end())) std::sort(parts.begin(), parts.end());
                 buf.insert(buf.end(), parts.begin(), parts.end());
                 otoo_group& og = L->groups[g];
                 og.first = (int32_t)b;
