@@ -38,6 +38,41 @@ int set_error(int code, const char* fmt, ...)
 
 namespace {
 
+// Allocator whose construct() default-initialises: resize() then leaves
+// arithmetic elements unwritten instead of zero-filling them on one thread.
+// Every array that uses it is written whole by a parallel loop right after
+// its resize, which also touches its pages from the threads that use them.
+template <class T>
+struct NoInit : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInit<U>;
+    };
+    NoInit() = default;
+    template <class U>
+    NoInit(const NoInit<U>&) noexcept
+    {
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a)
+    {
+        if constexpr (sizeof...(A) == 0)
+            ::new ((void*)p) U;
+        else
+            ::new ((void*)p) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using filled_later = std::vector<T, NoInit<T>>;
+
+// (Hilbert key, caller index), ordered by key then index: the sort of
+// Section III-B.
+struct KeyIndex {
+    uint64_t key;
+    int64_t index;
+    bool operator<(const KeyIndex& o) const { return key < o.key || (key == o.key && index < o.index); }
+};
+
 struct Cell {
     int64_t begin, end;     // tree-order particle range
     int64_t child0;         // first child cell (children are consecutive)
@@ -54,27 +89,27 @@ struct otoo_tree {
     int leaf_size = 8;
     int depth = 0;
     double lo[3] = {0, 0, 0}, S = 1, h = 1;
-    std::vector<double> pos;        // [n][3] tree order
-    std::vector<float> mass;        // [n]
-    std::vector<int64_t> perm;      // tree -> caller index
-    std::vector<uint64_t> key;      // [n]
-    std::vector<int32_t> gq;        // [n][3] quantised coordinates
+    otoo::filled_later<double> pos;        // [n][3] tree order
+    otoo::filled_later<float> mass;        // [n]
+    otoo::filled_later<int64_t> perm;      // tree -> caller index
+    otoo::filled_later<uint64_t> key;      // [n]
+    otoo::filled_later<int32_t> gq;        // [n][3] quantised coordinates
     std::vector<otoo::Cell> cells;
     // flat per-cell arrays (exported, and used by the walk)
-    std::vector<int64_t> c_begin, c_end, c_child0, c_org;
-    std::vector<int32_t> c_level, c_nchild;
-    std::vector<double> c_com, c_mass, c_quad;     // [3], [1], [6]
-    std::vector<double> c_b2, c_bmax;               // spread about the centre of mass (Eq. B2)
-    std::vector<double> c_lo, c_side, c_gc;         // cube lower corner [3], side, centre [3]
+    otoo::filled_later<int64_t> c_begin, c_end, c_child0, c_org;
+    otoo::filled_later<int32_t> c_level, c_nchild;
+    otoo::filled_later<double> c_com, c_mass, c_quad;     // [3], [1], [6]
+    otoo::filled_later<double> c_b2, c_bmax;               // spread about the centre of mass (Eq. B2)
+    otoo::filled_later<double> c_lo, c_side, c_gc;         // cube lower corner [3], side, centre [3]
 };
 
 struct otoo_lists {
     int64_t n_part = 0, n_src = 0;
     int32_t n_sys = 1, use_quad = 0;
-    std::vector<otoo_src> src;
-    std::vector<otoo_quad> quad;
+    otoo::filled_later<otoo_src> src;      // written whole by fill_sources / the batch copy
+    otoo::filled_later<otoo_quad> quad;
     std::vector<otoo_group> groups;
-    std::vector<int32_t> list;
+    otoo::filled_later<int32_t> list;      // written whole by the per-group copies
     std::vector<int64_t> perm;
     std::vector<int64_t> sys_part_off;
     int64_t interactions = 0, cell_interactions = 0;
@@ -266,8 +301,8 @@ int otoo_build_tree(const double* pos, const float* mass, int64_t n, const otoo_
         root_cube(mn, mx, t->lo, &t->S, &t->h);
         const double scale = kGrid / t->S;
         // step 2: quantise and key
-        std::vector<std::pair<uint64_t, int64_t>> kv(n);
-        std::vector<int32_t> gq0(3 * n);
+        filled_later<KeyIndex> kv(n);
+        filled_later<int32_t> gq0(3 * n);
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             uint32_t g[3];
@@ -275,7 +310,7 @@ int otoo_build_tree(const double* pos, const float* mass, int64_t n, const otoo_
                 g[a] = quantize(pos[3 * i + a], t->lo[a], scale);
                 gq0[3 * i + a] = (int32_t)g[a];
             }
-            kv[i] = {hilbert_key(g[0], g[1], g[2]), i};
+            kv[i] = KeyIndex{hilbert_key(g[0], g[1], g[2]), i};
         }
         // step 3: sort (key, index) -- libstdc++ parallel mode, as in the paper
         __gnu_parallel::sort(kv.begin(), kv.end());
@@ -286,9 +321,9 @@ int otoo_build_tree(const double* pos, const float* mass, int64_t n, const otoo_
         t->gq.resize(3 * n);
 #pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < n; ++k) {
-            const int64_t i = kv[k].second;
+            const int64_t i = kv[k].index;
             t->perm[k] = i;
-            t->key[k] = kv[k].first;
+            t->key[k] = kv[k].key;
             t->mass[k] = mass[i];
             for (int a = 0; a < 3; ++a) {
                 t->pos[3 * k + a] = pos[3 * i + a];
@@ -630,7 +665,7 @@ int otoo_make_groups_and_lists(const otoo_tree* t, const otoo_params* p, otoo_li
         L->src.resize(n + nc);
         L->quad.resize(nc);
         fill_sources(t, L->use_quad, L->src.data(), L->quad.data());
-        L->perm = t->perm;
+        L->perm.assign(t->perm.begin(), t->perm.end());
         L->sys_part_off = {0, n};
         *out = L;
         return OTOO_OK;
