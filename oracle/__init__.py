@@ -18,6 +18,7 @@ with the GPU path (the two sides read the same seeded inputs and nothing else).
                   the bounding radius of Eq. SPH_RAD.
 * ``cell_moments`` / ``cell_field``  the multipole of one particle set and
                   its field at a point.
+* ``group_mac``   the opening-angle acceptance test of the group walk.
 * ``errors``      relative force error statistics against a reference.
 
 The C part is compiled by ``__graft_entry__.build()`` (gcc, -O2 -fopenmp
@@ -58,10 +59,13 @@ def _load():
         lib = ctypes.CDLL(_SO)
         lib.oracle_direct.argtypes = [_i64, _dp, _dp, _i64, _lp, ctypes.c_double, _dp, _dp]
         lib.oracle_direct.restype = ctypes.c_int
-        lib.oracle_cell_moments.argtypes = [_dp, _dp, _i64, _dp, _dp, _dp]
+        lib.oracle_cell_moments.argtypes = [_dp, _dp, _i64, _dp, _dp, _dp, _dp]
         lib.oracle_cell_moments.restype = ctypes.c_int
-        lib.oracle_cell_field.argtypes = [_dp, ctypes.c_double, _dp, _dp, ctypes.c_int,
+        lib.oracle_cell_field.argtypes = [_dp, ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_double, _dp, _dp]
+        lib.oracle_group_mac.argtypes = [_dp, ctypes.c_double, _dp, _dp, _dp, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_group_mac.restype = ctypes.c_int
         lib.oracle_cell_field.restype = ctypes.c_int
         lib.oracle_tree_new.argtypes = [_i64, _dp, _dp, ctypes.c_int, ctypes.c_int]
         lib.oracle_tree_new.restype = ctypes.c_void_p
@@ -113,16 +117,18 @@ def direct(pos, mass, eps, targets=None):
 
 
 def cell_moments(pos, mass):
-    """(mass, com[3], q[6]) with q = (Qxx, Qyy, Qzz, Qxy, Qxz, Qyz) about the com."""
+    """(mass, com[3], q[6], b2) with q = (Qxx, Qyy, Qzz, Qxy, Qxz, Qyz) the
+    traceless quadrupole about the com and b2 = sum m |x - com|^2."""
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     mass = np.ascontiguousarray(mass, dtype=np.float64)
     m = np.zeros(1)
     com = np.zeros(3)
     q = np.zeros(6)
-    if lib.oracle_cell_moments(_d(pos), _d(mass), pos.shape[0], _d(m), _d(com), _d(q)) != 0:
+    b2 = np.zeros(1)
+    if lib.oracle_cell_moments(_d(pos), _d(mass), pos.shape[0], _d(m), _d(com), _d(q), _d(b2)) != 0:
         raise ValueError("empty cell")
-    return float(m[0]), com, q
+    return float(m[0]), com, q, float(b2[0])
 
 
 def sw_radius(pos, mass, delta, m_limit=0.0, s_root=1.0):
@@ -160,16 +166,31 @@ def sph_density(pos, mass, h, targets=None):
     return rho
 
 
-def cell_field(x, m, com, q, use_quad, eps):
-    """Field (acc[3], pot) at point x of a cell with the given moments."""
+def cell_field(x, m, com, q, b2, use_quad, eps):
+    """Field (acc[3], pot) at point x of a cell with the given moments
+    (b2 = sum m |x - com|^2 enters the softened quadrupole term)."""
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.float64)
     com = np.ascontiguousarray(com, dtype=np.float64)
     q = np.ascontiguousarray(q, dtype=np.float64)
     acc = np.zeros(3)
     pot = np.zeros(1)
-    lib.oracle_cell_field(_d(x), float(m), _d(com), _d(q), int(use_quad), float(eps), _d(acc), _d(pot))
+    lib.oracle_cell_field(_d(x), float(m), _d(com), _d(q), float(b2), int(use_quad), float(eps), _d(acc),
+                          _d(pot))
     return acc, float(pot[0])
+
+
+def group_mac(cube_lo, side, com, blo, bhi, theta):
+    """The tree walk's opening-angle decision for one cell (cube corner
+    cube_lo, side, centre of mass com) and one group box [blo, bhi]:
+    True = accept the cell, False = open it."""
+    lib = _load()
+    v = [np.ascontiguousarray(a, dtype=np.float64) for a in (cube_lo, com, blo, bhi)]
+    out = ctypes.c_int(-1)
+    if lib.oracle_group_mac(_d(v[0]), float(side), _d(v[1]), _d(v[2]), _d(v[3]), float(theta),
+                            ctypes.byref(out)) != 0:
+        raise ValueError("bad cell or angle")
+    return bool(out.value)
 
 
 class Tree:

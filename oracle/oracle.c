@@ -184,14 +184,23 @@ static void moments(const double* pos, const double* mass, const int64_t* idx, i
 }
 
 /*
- * Field at x of a cell (mass m, centre of mass com, quadrupole q).  With
- * r = com - x and r_s^2 = |r|^2 + eps^2 the potential is
- *     phi = -m / r_s - (1/2) r.Q.r / r_s^5
+ * Field at x of a cell (mass m, centre of mass com, quadrupole q, B_2 =
+ * sum m |x_j - com|^2).  The cell stands for its particles (Section II: a
+ * cell acts as a virtual particle at its centre of mass); the quadrupole
+ * term is this library's extension: the second-order Taylor term of the
+ * softened pair law about the centre of mass.  With r = com - x,
+ * q = (|r|^2 + eps^2)^(-1/2) and the second moment D = sum m d d^T
+ * (d = x_j - com, so Q = 3 D - tr(D) I and tr(D) = B_2), the Hessian of q
+ * is 3 r r^T q^5 - I q^3, and one half of its contraction with D is
+ *     (1/2) (r.Q.r - B_2 eps^2) q^5.
+ * The potential is therefore
+ *     phi = -m q - (1/2) (r.Q.r - B_2 eps^2) q^5
  * and the acceleration a = -grad_x phi is
- *     a = m r / r_s^3 - Q r / r_s^5 + (5/2) (r.Q.r) r / r_s^7.
+ *     a = m q^3 r - q^5 Q r + (5/2) (r.Q.r - B_2 eps^2) q^7 r.
+ * Without softening the B_2 term vanishes (the Laplace multipole).
  * use_quad = 0 keeps the monopole only.
  */
-static void cell_field(const double x[3], double m, const double com[3], const double q[6],
+static void cell_field(const double x[3], double m, const double com[3], const double q[6], double b2,
                        int use_quad, double eps2, double acc[3], double* pot)
 {
     double rx = com[0] - x[0], ry = com[1] - x[1], rz = com[2] - x[2];
@@ -208,12 +217,13 @@ static void cell_field(const double x[3], double m, const double com[3], const d
     double Qr1 = q[3] * rx + q[1] * ry + q[5] * rz;
     double Qr2 = q[4] * rx + q[5] * ry + q[2] * rz;
     double rQr = rx * Qr0 + ry * Qr1 + rz * Qr2;
+    double w = rQr - b2 * eps2;
     double rinv5 = rinv3 * rinv2;
     double rinv7 = rinv5 * rinv2;
-    acc[0] += -Qr0 * rinv5 + 2.5 * rQr * rx * rinv7;
-    acc[1] += -Qr1 * rinv5 + 2.5 * rQr * ry * rinv7;
-    acc[2] += -Qr2 * rinv5 + 2.5 * rQr * rz * rinv7;
-    *pot -= 0.5 * rQr * rinv5;
+    acc[0] += -Qr0 * rinv5 + 2.5 * w * rx * rinv7;
+    acc[1] += -Qr1 * rinv5 + 2.5 * w * ry * rinv7;
+    acc[2] += -Qr2 * rinv5 + 2.5 * w * rz * rinv7;
+    *pot -= 0.5 * w * rinv5;
 }
 
 /*
@@ -268,25 +278,28 @@ int oracle_sw_radius(const double* pos, const double* mass, int64_t n, double de
     return 0;
 }
 
-/* Exposed for the tests: moments of a particle set and the field they make. */
+/* Exposed for the tests: moments of a particle set (mass, centre of mass,
+   traceless quadrupole, B_2) and the field they make. */
 int oracle_cell_moments(const double* pos, const double* mass, int64_t n,
-                        double* m_out, double* com, double* q)
+                        double* m_out, double* com, double* q, double* b2_out)
 {
     if (n <= 0) return -1;
     int64_t* idx = (int64_t*)malloc((size_t)n * sizeof(int64_t));
     if (!idx) return -2;
     for (int64_t k = 0; k < n; ++k) idx[k] = k;
     moments(pos, mass, idx, n, m_out, com, q);
+    double bmax;
+    spread(pos, mass, idx, n, com, b2_out, &bmax);
     free(idx);
     return 0;
 }
 
-int oracle_cell_field(const double* x, double m, const double* com, const double* q,
+int oracle_cell_field(const double* x, double m, const double* com, const double* q, double b2,
                       int use_quad, double eps, double* acc, double* pot)
 {
     double a[3] = {0.0, 0.0, 0.0};
     double p = 0.0;
-    cell_field(x, m, com, q, use_quad, eps * eps, a, &p);
+    cell_field(x, m, com, q, b2, use_quad, eps * eps, a, &p);
     acc[0] = a[0];
     acc[1] = a[1];
     acc[2] = a[2];
@@ -569,6 +582,30 @@ static int accept(const Node* c, const double blo[3], const double bhi[3], const
     return sqrt(d2) > c->side / theta + sqrt(s2);
 }
 
+/* Exposed for the tests: the opening-angle decision (kind 0 above) for one
+   cell given by its cube (lower corner cube_lo, side) and centre of mass
+   com, against the group box [blo, bhi].  The cube centre is cube_lo +
+   side / 2.  *out = 1 accept, 0 open. */
+int oracle_group_mac(const double* cube_lo, double side, const double* com, const double* blo, const double* bhi,
+                     double theta, int* out)
+{
+    if (!(side > 0.0) || !(theta >= 0.0) || !out) return -1;
+    Node c;
+    memset(&c, 0, sizeof(c));
+    for (int a = 0; a < 3; ++a) {
+        c.cube_lo[a] = cube_lo[a];
+        c.com[a] = com[a];
+        c.gc[a] = cube_lo[a] + side / 2.0;
+    }
+    c.side = side;
+    Mac mac;
+    memset(&mac, 0, sizeof(mac));
+    mac.kind = 0;
+    mac.theta = theta;
+    *out = accept(&c, blo, bhi, &mac);
+    return 0;
+}
+
 typedef struct Entries {
     int64_t n_cell, n_part, cap_cell, cap_part;
     const Node** cell;
@@ -692,7 +729,7 @@ int oracle_tree_eval(const void* handle, double theta, const double* theta_by_ke
                 double p = 0.0;
                 for (int64_t c = 0; c < ent.n_cell; ++c) {
                     const Node* cn = ent.cell[c];
-                    cell_field(xi, cn->m, cn->com, cn->q, use_quad, eps2, a, &p);
+                    cell_field(xi, cn->m, cn->com, cn->q, cn->b2, use_quad, eps2, a, &p);
                 }
                 for (int64_t c = 0; c < ent.n_part; ++c) {
                     int64_t j = ent.part[c];

@@ -82,16 +82,34 @@ def test_cell_field_quadrupole_on_axis():
     rows = [l for l in open(GOLDEN + "/quad_axis.txt") if l.strip() and not l.startswith("#")]
     v = np.array([float(x) for x in rows[0].split()])
     x, m, q = v[0:3], v[3], v[4:10]
-    m2, com, q2 = oracle.cell_moments(np.array([[0, 0, 1.0], [0, 0, -1.0]]), np.array([1.0, 1.0]))
-    assert m2 == m
+    m2, com, q2, b2 = oracle.cell_moments(np.array([[0, 0, 1.0], [0, 0, -1.0]]), np.array([1.0, 1.0]))
+    assert m2 == m and b2 == 2.0
     np.testing.assert_allclose(com, 0, atol=1e-15)
     np.testing.assert_allclose(q2, q, atol=1e-14)
-    acc, pot = oracle.cell_field(x, m, com, q, True, 1e-9)
+    acc, pot = oracle.cell_field(x, m, com, q, b2, True, 1e-9)
     np.testing.assert_allclose(acc, v[10:13], atol=1e-12)
     assert abs(pot - v[13]) < 1e-12
-    acc, pot = oracle.cell_field(x, m, com, q, False, 1e-9)
+    acc, pot = oracle.cell_field(x, m, com, q, b2, False, 1e-9)
     np.testing.assert_allclose(acc, v[14:17], atol=1e-12)
     assert abs(pot - v[17]) < 1e-12
+
+
+def test_cell_field_softened_quadrupole_on_axis():
+    # the quadrupole term is the second-order Taylor term of the softened
+    # pair law: with eps comparable to the distance its B_2 eps^2 part
+    # matters (hand-worked values in the fixture)
+    rows = [l for l in open(GOLDEN + "/quad_axis_soft.txt") if l.strip() and not l.startswith("#")]
+    v = np.array([float(x) for x in rows[0].split()])
+    x, eps, m, q, b2 = v[0:3], v[3], v[4], v[5:11], v[11]
+    m2, com, q2, b22 = oracle.cell_moments(np.array([[0, 0, 1.0], [0, 0, -1.0]]), np.array([1.0, 1.0]))
+    assert (m2, b22) == (m, b2)
+    np.testing.assert_allclose(q2, q, atol=1e-14)
+    acc, pot = oracle.cell_field(x, m, com, q, b2, True, eps)
+    np.testing.assert_allclose(acc, v[12:15], rtol=0, atol=1e-15)
+    assert abs(pot - v[15]) < 1e-15
+    acc, pot = oracle.cell_field(x, m, com, q, b2, False, eps)
+    np.testing.assert_allclose(acc, v[16:19], rtol=0, atol=1e-15)
+    assert abs(pot - v[19]) < 1e-15
 
 
 def test_multipole_far_field_slopes():
@@ -101,7 +119,7 @@ def test_multipole_far_field_slopes():
     rng = np.random.default_rng(15)
     pts = rng.uniform(-0.5, 0.5, (25, 3))
     ms = rng.uniform(0.5, 1.5, 25)
-    m, com, q = oracle.cell_moments(pts, ms)
+    m, com, q, b2 = oracle.cell_moments(pts, ms)
     u = np.array([0.48, -0.6, 0.64])
     u /= np.linalg.norm(u)
     ds = np.array([8.0, 16.0, 32.0, 64.0, 128.0])
@@ -112,13 +130,68 @@ def test_multipole_far_field_slopes():
         allm = np.concatenate([ms, [0.0]])
         ex_a, ex_p = oracle.direct(allp, allm, 1e-9, targets=[25])
         for quad in (0, 1):
-            a, p = oracle.cell_field(x, m, com, q, quad, 1e-9)
+            a, p = oracle.cell_field(x, m, com, q, b2, quad, 1e-9)
             err[quad].append(np.linalg.norm(a - ex_a[0]) / np.linalg.norm(ex_a[0]))
     s0 = np.polyfit(np.log(ds), np.log(err[0]), 1)[0]
     s1 = np.polyfit(np.log(ds), np.log(err[1]), 1)[0]
     assert abs(s0 + 2) < 0.15, s0
     assert abs(s1 + 3) < 0.15, s1
     assert all(e1 < e0 for e0, e1 in zip(err[0], err[1]))
+
+
+@pytest.mark.parametrize("eps_over_d", [0.5, 2.0])
+def test_softened_multipole_far_field_slopes(eps_over_d):
+    # The same with Plummer softening that grows with the distance (eps =
+    # c d): the expansion parameter is the cell size over sqrt(d^2 + eps^2),
+    # so the second-order term must leave a third-order error (slope -3) on
+    # the acceleration and the potential; a quadrupole without its B_2 eps^2
+    # part leaves a second-order one.
+    rng = np.random.default_rng(25)
+    pts = rng.uniform(-0.5, 0.5, (25, 3))
+    ms = rng.uniform(0.5, 1.5, 25)
+    m, com, q, b2 = oracle.cell_moments(pts, ms)
+    u = np.array([0.48, -0.6, 0.64])
+    u /= np.linalg.norm(u)
+    ds = np.array([8.0, 16.0, 32.0, 64.0, 128.0])
+    ea, ep = [], []
+    for d in ds:
+        x = com + d * u
+        eps = eps_over_d * d
+        allp = np.vstack([pts, x])
+        allm = np.concatenate([ms, [0.0]])
+        ex_a, ex_p = oracle.direct(allp, allm, eps, targets=[25])
+        a, p = oracle.cell_field(x, m, com, q, b2, True, eps)
+        ea.append(np.linalg.norm(a - ex_a[0]) / np.linalg.norm(ex_a[0]))
+        ep.append(abs(p - ex_p[0]) / abs(ex_p[0]))
+    sa = np.polyfit(np.log(ds), np.log(ea), 1)[0]
+    sp = np.polyfit(np.log(ds), np.log(ep), 1)[0]
+    assert abs(sa + 3) < 0.15, sa
+    assert abs(sp + 3) < 0.15, sp
+
+
+def test_group_mac_hand_worked_cases():
+    # threshold with s (just above, just below, exact tie), the cube-overlap
+    # clause (overlapping, touching, clear) and theta = 0; the geometry of
+    # each case is worked out in the fixture's comments
+    rows = np.loadtxt(GOLDEN + "/group_mac.txt", ndmin=2)
+    assert rows.shape == (7, 15)
+    for r in rows:
+        got = oracle.group_mac(r[0:3], r[3], r[4:7], r[7:10], r[10:13], r[13])
+        assert got == bool(r[14]), r
+
+
+def test_tree_quadrupole_with_large_softening():
+    # the batch configuration's regime (eps a sizeable fraction of the scale
+    # radius): the softened quadrupole must still beat the monopole clearly
+    pos, mass = ic.plummer(3000, 26)
+    eps = 4.0 * 3000 ** (-1.0 / 3.0)
+    t = oracle.Tree(pos, mass, 8, 64)
+    ad, pd = oracle.direct(pos, mass, eps)
+    e = {}
+    for quad in (False, True):
+        r = t.eval(0.5, eps, use_quad=quad)
+        e[quad] = oracle.errors(r["acc"], r["pot"], ad, pd)["acc_rms"]
+    assert e[True] < 0.3 * e[False], e
 
 
 @pytest.mark.parametrize("n,leaf,ncrit", [(1, 8, 64), (7, 8, 64), (200, 1, 4), (4096, 8, 64)])
@@ -237,7 +310,7 @@ def test_sw_monopole_error_within_delta(seed):
     n = 30 if seed < 3 else 2
     pos = rng.uniform(-0.5, 0.5, size=(n, 3)) * (1.0 if seed < 3 else np.array([1.0, 0.0, 0.0]))
     mass = rng.uniform(0.1, 1.0, n)
-    m, com, q = oracle.cell_moments(pos, mass)
+    m, com, q, _ = oracle.cell_moments(pos, mass)
     worst = 0.0
     for delta in (1e-1, 1e-3, 1e-5):
         b2, bmax, rb = oracle.sw_radius(pos, mass, delta)
@@ -251,7 +324,7 @@ def test_sw_monopole_error_within_delta(seed):
         allm = np.concatenate([mass, np.zeros(len(tgt))])
         ad, _ = oracle.direct(allp, allm, 1e-12, targets=np.arange(n, n + len(tgt)))
         for k in range(len(tgt)):
-            am, _ = oracle.cell_field(tgt[k], m, com, q, False, 1e-12)
+            am, _ = oracle.cell_field(tgt[k], m, com, q, 0.0, False, 1e-12)
             err = np.linalg.norm(am - ad[k])
             assert err <= delta * (1 + 1e-9), (delta, k, err)
             worst = max(worst, err / delta)
