@@ -76,17 +76,28 @@ def bf16_round(w):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def select_theta(w, feats, grid, log10_target, fallback):
-    """Largest grid angle whose prediction meets the target (grid[0] if
-    none does, fallback if a prediction is not finite); feats [g][k][6]."""
-    g, k, _ = feats.shape
-    y = forward(w, feats.reshape(g * k, NI)).reshape(g, k)
-    out = np.full(g, grid[0], np.float64)
+def choose_theta(y, grid, log10_target, fallback):
+    """Per group g (row of the prediction table y [g][k], one column per grid
+    angle, grid increasing): the largest grid[k] whose prediction y[g, k] is
+    at most the group's target (a prediction equal to the target passes);
+    grid[0] when no angle passes; fallback when any of the group's
+    predictions is not finite.  log10_target: one value or one per group."""
+    y = np.asarray(y, np.float64)
+    g, k = y.shape
+    tg = np.broadcast_to(np.asarray(log10_target, np.float64), (g,))
+    out = np.empty(g, np.float64)
     for a in range(g):
         if not np.all(np.isfinite(y[a])):
             out[a] = fallback
             continue
-        ok = [grid[j] for j in range(k) if y[a, j] <= log10_target]
-        if ok:
-            out[a] = max(max(ok), grid[0])
-    return out, y
+        passing = [grid[j] for j in range(k) if y[a, j] <= tg[a]]
+        out[a] = max(passing) if passing else grid[0]
+    return out
+
+
+def select_theta(w, feats, grid, log10_target, fallback):
+    """choose_theta on the network's predictions for rows feats [g][k][6]
+    (group g's features with angle grid[k]); returns (angles, predictions)."""
+    g, k, _ = feats.shape
+    y = forward(w, feats.reshape(g * k, NI)).reshape(g, k)
+    return choose_theta(y, grid, log10_target, fallback), y

@@ -451,3 +451,32 @@ def test_adam_first_step_and_bf16_rounding():
     # bf16: 8 significand bits, ties to even
     np.testing.assert_array_equal(omlp.bf16_round([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -3.0]),
                                   [1.0, 1.0, 1.0 + 2 ** -6, -3.0])
+
+
+def test_choose_theta_hand_built_tables():
+    # the angle choice on hand-built prediction tables (cases described in
+    # the fixture): largest passing angle, ties pass, none -> grid[0],
+    # non-finite -> fallback, per-group targets
+    from oracle import mlp as om
+    rows = np.genfromtxt(GOLDEN + "/select_theta.txt", comments="#")
+    grid = [0.3, 0.4, 0.5, 0.6]
+    got = om.choose_theta(rows[:, 0:4], grid, rows[:, 4], 0.45)
+    np.testing.assert_array_equal(got, rows[:, 5])
+    # one target for every group gives the same answer where it is the same
+    same = rows[:, 4] == -3.0
+    np.testing.assert_array_equal(om.choose_theta(rows[same, 0:4], grid, -3.0, 0.45), rows[same, 5])
+
+
+def test_select_theta_wires_the_network_to_the_choice():
+    # a bias-only network predicts the same value for every row: all angles
+    # pass below the target, none above it
+    from oracle import mlp as om
+    w = np.zeros(om.NP)
+    feats = np.random.default_rng(40).normal(size=(5, 4, om.NI))
+    grid = [0.3, 0.4, 0.5, 0.6]
+    w[-1] = -3.2
+    th, y = om.select_theta(w, feats, grid, -3.0, 0.45)
+    assert np.all(y == -3.2) and np.all(th == 0.6)
+    w[-1] = -2.8
+    th, _ = om.select_theta(w, feats, grid, -3.0, 0.45)
+    assert np.all(th == 0.3)
