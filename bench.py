@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--err-targets", type=int, default=512)
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-fraction", type=float, default=1.0 / 16,
+                    help="share of the workload's groups in the CPU oracle's seeded sample (both arms)")
+    ap.add_argument("--cpu-repeats", type=int, default=3, help="timed repeats of the CPU sample (this arm)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the batched 64-system step and the learned-angle comparison")
     ap.add_argument("--skip-walk", action="store_true", help="skip the device-walk step")
@@ -278,10 +280,17 @@ def run_ours(args):
         e2e = dict(e2e_lists, path="host-built groups, lists and work items copied in; force; results out")
 
     flops = 20.0 * mono_inter + (60.0 if lists.use_quad else 20.0) * cell_inter
+    # the FP32 operations the pair kernels issue (fma = 2 flop; the MUFU
+    # reciprocal square root not counted): 19 per particle or monopole pair,
+    # 54 per quadrupole pair
+    flops_code = 19.0 * mono_inter + (54.0 if lists.use_quad else 19.0) * cell_inter
     props = torch.cuda.get_device_properties(local)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (ms * 1e-3) / 1e12
+    achieved_code = flops_code / (ms * 1e-3) / 1e12
+    probe = guarded_extra(fma_probe, dev_name, local, stream) if rank == 0 else None
+    measured = probe.get("tflops") if probe and "error" not in probe else None
     line = {
         "metric": "force interactions/s (FP32 centre-relative + Kahan) at N=2^23",
         "value": value,
@@ -311,8 +320,16 @@ def run_ours(args):
                      "traffic_note": "DRAM bytes per force-kernel launch from one ncu capture of this configuration",
                      "timing": "achieved uses the CUDA-event time of the whole step (float-pair split 0.26 ms included)",
                      "flops_per_step": flops,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived; no measured FP32 peak)",
-                     "flop_convention": "20 per monopole/particle interaction, 60 per quadrupole cell interaction"},
+                     "peak_basis": "%d SMs x %d FP32 lanes x 2 flop x %.0f MHz max SM clock (derived from unit "
+                                   "counts and the clock)" % (props.multi_processor_count, FP32_LANES_PER_SM, sm_max),
+                     "flop_convention": "20 per monopole/particle interaction, 60 per quadrupole cell interaction",
+                     "peak_measured": measured,
+                     "frac_of_measured": achieved / measured if measured else None,
+                     "fma_probe": probe,
+                     "flops_code_per_step": flops_code,
+                     "frac_code_flops": achieved_code / peak,
+                     "code_flop_convention": "FP32 operations the pair kernels issue: 19 per particle/monopole pair, "
+                                             "54 per quadrupole pair (fma = 2), reciprocal square root not counted"},
         "fp64_form": fp64,
         "errors": errors,
         "e2e": e2e,
@@ -331,7 +348,7 @@ def run_ours(args):
     if rank == 0 and not args.skip_sw and errors is not None:
         line["sw_sweep"] = guarded_extra(run_sw_sweep, args, dev_name, tree, w, tune, stream, sub, ad)
     if rank == 0 and not args.skip_cpu:
-        line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_fraction, args.cpu_repeats)
     if rank == 0 and not args.skip_extras and args.workload == "hernquist8m":
         line["fused_walk_force"] = guarded_extra(run_fused, args, dev_name, pos, mass, w, tune, stream)
         line["paper_workloads"] = guarded_extra(run_paper_workloads, args, dev_name, tune, stream)
@@ -341,6 +358,41 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         tdist.destroy_process_group()
+
+
+def fma_probe(dev_name, local, stream):
+    """FP32 FMA throughput of this GPU (otoo_fma_probe: dependent chains of
+    scalar fma.rn.f32 and packed fma.rn.f32x2 on every resident thread),
+    CUDA events around 5 launches after one warm-up, clocks sampled."""
+    import ctypes
+
+    import torch
+
+    from paper_1206_1199_gb300 import _lib as L
+    n = int(L.load().otoo_fma_probe_threads())
+    sink = torch.empty(max(n, 1), dtype=torch.float32, device=dev_name)
+    out = {}
+    st = ctypes.c_void_p(stream.cuda_stream)
+    with Clocks(local) as clk:
+        for packed, iters, key in ((0, 1 << 17, "fma_f32"), (1, 1 << 16, "fma_f32x2")):
+            fl = ctypes.c_double(0.0)
+            L.call("otoo_fma_probe", iters, packed, sink.data_ptr(), ctypes.byref(fl), st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                L.call("otoo_fma_probe", iters, packed, sink.data_ptr(), ctypes.byref(fl), st)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[key] = 5 * fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    c = clk.summary()
+    mhz = c.get("sm_mhz") or c.get("sm_max_mhz")
+    out["tflops"] = max(out["fma_f32"], out["fma_f32x2"])
+    out["clocks"] = c
+    if mhz:
+        props = torch.cuda.get_device_properties(local)
+        # FP32 flop per SM per clock at the sampled clock (128 lanes x 2 = 256 nominal)
+        out["flop_per_sm_per_clock"] = out["tflops"] * 1e12 / (props.multi_processor_count * mhz * 1e6)
+    return out
 
 
 def guarded_extra(fn, *a):
@@ -835,28 +887,42 @@ def oracle_tree(w, pos, mass):
     return oracle.Tree(pos, mass, w["leaf_size"], w["n_crit"])
 
 
-def cpu_baseline(w, pos, mass, seconds, tree=None):
-    """The FP64 oracle tree code (as it stands) on a bounded sample of the
-    same workload: every k-th group, k chosen so the sample takes about
-    `seconds`; the oracle's own tree build is not timed."""
+CPU_SAMPLE_SEED = 12061199 + 777  # the groups both arms time on the CPU
+
+
+def cpu_sample(t, fraction):
+    """A seeded random sample of the oracle tree's groups (the same groups in
+    both arms and on every run of a workload)."""
+    from paper_1206_1199_gb300 import ic
+    k = max(1, min(t.n_groups, int(round(t.n_groups * fraction))))
+    return ic.subsample(t.n_groups, k, CPU_SAMPLE_SEED)
+
+
+def cpu_time_sample(w, t, sel):
+    """(interactions, seconds) of the FP64 oracle tree force -- walk and
+    evaluation of the sampled groups only -- on all host cores."""
+    t0 = time.perf_counter()
+    r = t.eval(w["theta"], w["eps"], w["use_quad"], groups=sel)
+    return r["interactions"], time.perf_counter() - t0
+
+
+def cpu_sample_text(t, sel, fraction, inter, secs):
+    return ("FP64 oracle tree force (walk + evaluation) of a seeded random sample of %d of %d groups (fraction "
+            "%.4g, seed %d): %d interactions, %.2f s per run; oracle tree build not timed"
+            % (len(sel), t.n_groups, fraction, CPU_SAMPLE_SEED, inter, secs))
+
+
+def cpu_baseline(w, pos, mass, fraction, repeats, tree=None):
+    """The FP64 oracle tree code (as it stands) on a seeded sample of the
+    workload's groups, timed `repeats` times: median rate and its spread."""
     t = tree if tree is not None else oracle_tree(w, pos, mass)
-    stride = max(1, t.n_groups // 2048)
-    # a small probe, then samples sized from the last measured rate until one
-    # takes at least 60% of the time asked for (a cold first probe
-    # underestimates the rate)
-    for attempt in range(3):
-        t0 = time.perf_counter()
-        r = t.eval(w["theta"], w["eps"], w["use_quad"], group_stride=stride)
-        dt = time.perf_counter() - t0
-        if attempt > 0 and (dt >= 0.6 * seconds or stride == 1):
-            break
-        rate = r["interactions"] / max(dt, 1e-9)
-        full_estimate = r["interactions"] * stride
-        stride = max(1, int(math.ceil(full_estimate / max(rate * seconds, 1.0))))
-    return {"value": r["interactions"] / dt, "unit": "interactions/s", "cores": cores(), "kind": "oracle",
-            "sample": "FP64 oracle tree force (walk + evaluation) for every %d-th of %d groups "
-                      "(%d interactions, %.1f s); oracle tree build not timed" % (stride, t.n_groups,
-                                                                                  r["interactions"], dt)}
+    sel = cpu_sample(t, fraction)
+    runs = [cpu_time_sample(w, t, sel) for _ in range(max(1, repeats))]
+    rates = [i / max(s, 1e-9) for i, s in runs]
+    med = float(np.median(rates))
+    return {"value": med, "unit": "interactions/s", "cores": cores(), "kind": "oracle", "repeats": len(runs),
+            "spread": [float(min(rates)), float(max(rates))],
+            "sample": cpu_sample_text(t, sel, fraction, runs[0][0], float(np.median([s for _, s in runs])))}
 
 
 def run_reference(args):
@@ -865,16 +931,15 @@ def run_reference(args):
         return
     w, pos, mass = workload(args, 0)
     pick_tune(w, args)  # the same n_crit as the GPU arm
-    steps = []
-    # about two minutes for the whole run, at most --cpu-seconds per step
-    per = min(args.cpu_seconds, max(2.0, 120.0 / max(1, args.steps + args.warmup)))
     tree = oracle_tree(w, pos, mass)
+    sel = cpu_sample(tree, args.cpu_fraction)
+    runs = []
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(w, pos, mass, per, tree)
+        r = cpu_time_sample(w, tree, sel)
         if k >= args.warmup:
-            steps.append(cb)
-    vals = [s["value"] for s in steps]
-    value = float(np.median(vals))
+            runs.append(r)
+    rates = [i / max(s, 1e-9) for i, s in runs]
+    value = float(np.median(rates))
     line = {"impl": "reference", "metric": "force interactions/s (FP32 centre-relative + Kahan) at N=2^23",
             "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -882,7 +947,9 @@ def run_reference(args):
             "config": {"workload": args.workload, "model": w["model"], "n": w["n"], "eps": w["eps"],
                        "theta": w["theta"], "n_crit": w["n_crit"], "quadrupole": w["use_quad"]},
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores(), "kind": "oracle",
-                             "sample": steps[-1]["sample"]},
+                             "repeats": len(runs), "spread": [float(min(rates)), float(max(rates))],
+                             "sample": cpu_sample_text(tree, sel, args.cpu_fraction, runs[-1][0],
+                                                       float(np.median([s for _, s in runs])))},
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

@@ -102,10 +102,15 @@ typedef struct otoo_src {
     int32_t pad;
 } otoo_src;
 
-/* Traceless quadrupole of cell (n_part + k), k in [0, n_cell):
-   Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab), d = x - com.  32 bytes. */
+/* Quadrupole of cell (n_part + k), k in [0, n_cell): the traceless
+   Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab), d = x - com, and b2 = B_2 =
+   sum m |d|^2 (Eq. B2; the trace of the second moment), which the softened
+   quadrupole term needs: with q = (r^2 + eps^2)^(-1/2) and w = r.Q.r -
+   b2 eps^2, a cell adds -(1/2) w q^5 to the potential and
+   (5/2) w q^7 r - q^5 Q r to the acceleration (r = com - x), the
+   second-order Taylor term of the softened pair law.  32 bytes. */
 typedef struct otoo_quad {
-    float xx, yy, zz, xy, xz, yz, pad0, pad1;
+    float xx, yy, zz, xy, xz, yz, b2, pad;
 } otoo_quad;
 
 /* One group: particles [first, first + count) in tree order share the list
@@ -141,6 +146,8 @@ typedef struct otoo_dev_system {
     int64_t n_part;                /* target particles (tree order) */
     int64_t n_src;                 /* n_part + number of cells */
     int64_t n_list;                /* entries in list */
+    int64_t partial_doubles;       /* length of partial in doubles; a work item or split whose
+                                      slots reach past it is skipped and flagged (OTOO_EDEVICE) */
     int32_t n_groups, n_items, n_splits, n_crit_max;
     const otoo_src* src;           /* [n_src] */
     const otoo_quad* quad;         /* [n_src - n_part], NULL = monopole cells; 32-byte aligned */
@@ -149,7 +156,8 @@ typedef struct otoo_dev_system {
     const otoo_item* items;        /* [n_items], in launch order */
     const otoo_split* splits;      /* [n_splits] */
     const int64_t* perm;           /* [n_part] output index of each tree particle, NULL = tree order */
-    double* partial;               /* scratch, >= otoo_plan_info.partial_doubles doubles */
+    double* partial;               /* scratch, partial_doubles doubles (>= the plan's
+                                      otoo_plan_info.partial_doubles) */
     uint32_t* counter;             /* scratch, >= 4 uint32 (work ticket and status) */
     void* split;                   /* scratch for OTOO_FP32K, >= 32 * n_src bytes, 32-byte aligned: each source's
                                       position as a float pair (hi = x rounded to FP32,
@@ -290,7 +298,12 @@ int otoo_default_tune(int32_t n_crit, otoo_tune* tune);
    precision: OTOO_FP32K or OTOO_FP64.  tune: the tuning the plan was made with.
    The step (ticket reset, persistent force kernel, chunk merge) is recorded
    once per distinct argument set into a CUDA graph and replayed on stream.
-   Errors: OTOO_EINVAL (sizes, NULL pointers, tune), OTOO_ECUDA. */
+   Every work item, list index and split record is bounds-checked on the
+   device before it is used (groups, list, sources, and the partial slots
+   against sys->partial_doubles); a bad one is skipped, its targets are not
+   written, and the status word records it for otoo_check_status.
+   Errors: OTOO_EINVAL (sizes, NULL pointers, tune, split lists without
+   partial scratch of at least 4 * n_crit_max doubles), OTOO_ECUDA. */
 int otoo_force(const otoo_dev_system* sys, double* accel, double* pot, int32_t precision,
                const otoo_tune* tune, void* stream);
 
@@ -300,6 +313,17 @@ int otoo_force(const otoo_dev_system* sys, double* accel, double* pot, int32_t p
    Device buffers are kept for the next call of the same size. */
 int otoo_force_host(const otoo_lists_view* lists, const otoo_plan_info* plan, double* accel,
                     double* pot, int32_t precision, const otoo_tune* tune, void* stream);
+
+/* The centre-relative coordinates the FP32 form computes (the group-centre
+   subtraction of its FP32 pairs; the paper's single-precision kernel works
+   on absolute coordinates), exposed for checks:
+   out[s][a] = ((hi - c_a) + lo) in FP32, where (hi, lo) is the float pair
+   of src[s]'s coordinate a (hi = x rounded to FP32, lo = (x - hi) rounded)
+   and c_a = c[a] rounded to FP32 -- the same k_split and the same device
+   function as the force kernels' staging.  src: device [n]; c: host, 3
+   doubles; out: device [n][3] FP32; scratch: device, 32 * n bytes, 32-byte
+   aligned.  Asynchronous on stream.  Errors: OTOO_EINVAL, OTOO_ECUDA. */
+int otoo_centre_relative(const otoo_src* src, int64_t n, const double* c, float* out, void* scratch, void* stream);
 
 /* Reads the status word a previous otoo_force wrote (device counter[1]);
    returns OTOO_EDEVICE if a kernel flagged bad data.  Synchronises stream. */
@@ -315,9 +339,11 @@ int otoo_check_status(const otoo_dev_system* sys, void* stream);
    GPU's memory, an embedding runtime whose allocator must not be bypassed),
    and latency-critical loops that must not enter the CUDA runtime's allocator.
    There is no counterpart in the paper; this is a deployment option.
-     sys:       as for otoo_force; its partial, counter and split fields are
-                ignored (the array is used instead).
-     partial_doubles: the plan's otoo_plan_info.partial_doubles.
+     sys:       as for otoo_force; its partial, partial_doubles, counter and
+                split fields are ignored (the array is used instead).
+     partial_doubles: the plan's otoo_plan_info.partial_doubles (the part of
+                the array given to the chunk partials; work items whose slots
+                reach past it are skipped and flagged, as in otoo_force).
      Scratch limit: otoo_force_static_capacity() bytes (16 MiB), shared as
                 256 bytes + 32 * n_src bytes (OTOO_FP32K only) + 8 *
                 partial_doubles bytes, each part rounded up to 256 bytes;
@@ -330,10 +356,18 @@ int otoo_check_status(const otoo_dev_system* sys, void* stream);
    are cleared by each call, everything else is overwritten before it is
    read.  Calls whose work overlaps on the GPU (other streams, other host
    threads) race on the array: serialise them.  The kernels are launched
-   directly on stream, asynchronously; otoo_check_status cannot read this
-   call's status word (it lives in the array). */
+   directly on stream, asynchronously; the call's status word lives in the
+   array and is read by otoo_force_static_status.  The array's address is
+   cached per device for the life of the process: do not use this call on a
+   device after cudaDeviceReset (the module is reloaded at a new address). */
 int otoo_force_static(const otoo_dev_system* sys, int64_t partial_doubles, double* accel, double* pot,
                       int32_t precision, const otoo_tune* tune, void* stream);
+
+/* Status of the last otoo_force_static on the current device: copies the
+   status word out of the library's array on stream and synchronises it;
+   OTOO_EDEVICE when a kernel skipped a bad work item or list index, OTOO_OK
+   otherwise (also before any call).  Allocates nothing. */
+int otoo_force_static_status(void* stream);
 
 /* Size in bytes of the array otoo_force_static uses. */
 int64_t otoo_force_static_capacity(void);
@@ -351,6 +385,17 @@ int64_t otoo_force_static_capacity(void);
 int64_t otoo_direct_chunks(int64_t n_src, int64_t n_tgt);
 int otoo_direct(const otoo_src* src, int64_t n_src, const int64_t* targets, int64_t n_tgt, double eps2,
                 double* accel, double* pot, double* scratch, uint32_t* status, void* stream);
+
+/* FP32 FMA throughput probe, the measured counterpart of the peak the FP32
+   form's roofline divides by (not part of the force step): a grid of all
+   resident 256-thread blocks, each thread running 8 independent chains of
+   iters dependent fused multiply-adds, scalar fma.rn.f32 (packed = 0, 2 flop
+   each) or packed fma.rn.f32x2 (packed = 1, 4 flop each).  *flops (host)
+   receives the flop count of the launch; time the call with CUDA events on
+   stream.  sink: device, otoo_fma_probe_threads() floats (never written in
+   practice; it keeps the chains live).  Errors: OTOO_EINVAL, OTOO_ECUDA. */
+int64_t otoo_fma_probe_threads(void);
+int otoo_fma_probe(int32_t iters, int32_t packed, float* sink, double* flops, void* stream);
 
 /* ---- the walk on the device ------------------------------------------------------
    Section III-D: the paper walks the tree on the GPU, one group of particles
@@ -630,6 +675,13 @@ int otoo_mlp_train_step(float* w, uint16_t* wbf16, float* m, float* v, float* sc
 /* Round FP32 weights to the bf16 copy (round to nearest even). */
 int otoo_mlp_to_bf16(const float* w, uint16_t* wbf16, int32_t n, void* stream);
 
+/* Rows standardised for the network with the training set's statistics:
+   out[r][k] = (x[r][k] - mean[k]) / std[k] in FP32 (the same arithmetic as
+   otoo_learned_theta).  Device arrays x, out [n_rows][6], mean, std [6].
+   x and out may be the same array.  Asynchronous on stream. */
+int otoo_mlp_standardise(const float* x, int64_t n_rows, const float* mean, const float* std, float* out,
+                         void* stream);
+
 /* Per-group opening angle: x holds n_groups * n_theta rows, row (g, k) being
    group g's features with the angle theta_grid[k] (grid increasing).
    theta_out[g] = the largest theta_grid[k] whose prediction y(g, k) <= the
@@ -640,6 +692,63 @@ int otoo_select_theta(const uint16_t* wbf16, const float* x, const float* theta_
                       int32_t n_theta, int64_t n_groups, float log10_target,
                       const float* log10_target_per_group, float fallback, float* theta_out,
                       void* stream);
+
+/* The learned opening angle from raw list statistics, every step on the
+   device (the library's replacement of the paper's accuracy control, the
+   Delta of the absolute MAC, Section II-B): per group g of a base walk at
+   theta0 with statistics feat[g] (otoo_group_features, 5 floats) and count[g]
+   particles,
+     1. range: a group whose statistics are not finite or lie outside the
+        training range [lo, hi] takes the fallback angle;
+     2. budget: y0 = network(standardised (feat[g], theta0)) is its predicted
+        log10 error at theta0, L = 2^feat[g][0] its list length; its weight is
+        w = 10^(alpha y0 + beta log10 L), and its target
+          e_g = lambda w,  lambda = calib target_rms / sqrt(sum n w^2 / sum n)
+        over the groups in range (n = count), so that the particle-weighted
+        RMS of the targets is calib * target_rms.  With a group error
+        ~ c theta^k and a list length ~ theta^-3, the targets that minimise
+        the interactions at a fixed particle-weighted RMS have alpha =
+        3 / (2k + 3), beta = k / (2k + 3); alpha = beta = 0 gives every
+        group the same target;
+     3. choice: theta_out[g] = the largest grid[k] whose prediction
+        network(standardised (feat[g], grid[k])) <= log10 e_g, grid[0] when
+        none; the fallback when a prediction is not finite.
+   Standardised = (x - mean) / std per input.  Device arrays: feat
+   [n_groups][5], count [n_groups], grid [n_theta] (increasing), scratch
+   otoo_learned_theta_scratch_floats(n_groups) floats (8-byte aligned),
+   log10_target [n_groups] (may be NULL; NaN for groups out of range),
+   theta_out [n_groups].  FP32 network and targets, FP64 sums in a fixed
+   order (deterministic).  Asynchronous on stream. */
+typedef struct otoo_theta_net {
+    const uint16_t* wbf16;         /* device [OTOO_MLP_NPARAM] bf16 weights */
+    const float* mean;             /* device [OTOO_MLP_IN] input means of the training rows */
+    const float* std;              /* device [OTOO_MLP_IN] their standard deviations (> 0) */
+    const float* lo;               /* device [OTOO_MLP_IN - 1] training range of the statistics, or */
+    const float* hi;               /* NULL (both) for no range check */
+} otoo_theta_net;
+
+typedef struct otoo_theta_rule {
+    float theta0;                  /* angle of the base walk the statistics come from (> 0) */
+    float target_rms;              /* particle-weighted RMS relative acceleration error aimed at */
+    float calib;                   /* calibration of the network: the groups aim at calib * target_rms */
+    float alpha, beta;             /* budget exponents (0, 0: equal targets) */
+    float fallback;                /* angle for groups out of range or with a non-finite prediction */
+} otoo_theta_rule;
+
+int64_t otoo_learned_theta_scratch_floats(int64_t n_groups);
+int otoo_learned_theta(const otoo_theta_net* net, const otoo_theta_rule* rule, const float* feat,
+                       const int32_t* count, int64_t n_groups, const float* grid, int32_t n_theta, float* scratch,
+                       float* log10_target, float* theta_out, void* stream);
+
+/* Training labels of the learned angle: per group g, the RMS over its
+   targets [group_off[g], group_off[g + 1]) of the relative acceleration
+   error |acc - ref| / |ref| (acc, ref: device [n][3] FP64, ref the FP64
+   direct sum), as log10_rms[g] = log10(max(rms, floor_value)) (device
+   [n_groups] FP32).  group_off: device [n_groups + 1], non-decreasing; an
+   empty or negative range sets status (device, one uint32) and gives NaN.
+   One warp per group, sums in a fixed order.  Asynchronous on stream. */
+int otoo_group_rms_error(const double* acc, const double* ref, const int64_t* group_off, int64_t n_groups,
+                         float floor_value, float* log10_rms, uint32_t* status, void* stream);
 
 const char* otoo_last_error(void);
 

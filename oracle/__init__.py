@@ -76,8 +76,8 @@ def _load():
         lib.oracle_tree_n_cells.argtypes = [ctypes.c_void_p]
         lib.oracle_tree_n_cells.restype = _i64
         lib.oracle_tree_eval.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, ctypes.c_int, ctypes.c_double,
-                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _i64, _dp, _dp, _lp,
-                                         _lp, _lp, _lp, _dp, _lp]
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _i64, _lp, _i64, _dp,
+                                         _dp, _lp, _lp, _lp, _lp, _dp, _lp]
         lib.oracle_tree_eval.restype = ctypes.c_int
         lib.oracle_sw_radius.argtypes = [_dp, _dp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
         lib.oracle_sw_radius.restype = ctypes.c_int
@@ -214,11 +214,14 @@ class Tree:
             self._h = None
 
     def eval(self, theta, eps, use_quad=False, theta_by_key=None, group_stride=1, mac="theta", delta=0.0,
-             m_limit=0.0):
+             m_limit=0.0, groups=None):
         """Tree force.  mac = "theta" (opening angle theta, or theta_by_key)
         or "sw" (absolute MAC with accuracy delta; cells heavier than m_limit
-        > 0 are never accepted).  Returns dict with acc, pot (caller order;
-        NaN for particles of skipped groups) and per-group statistics."""
+        > 0 are never accepted).  Every group is walked and every
+        group_stride-th one evaluated; or, with groups (group indices), only
+        those are walked and evaluated.  Returns dict with acc, pot (caller
+        order; NaN for particles of skipped groups) and per-group statistics
+        (zero for groups that were not walked)."""
         ng = self.n_groups
         acc = np.full((self.n, 3), np.nan)
         pot = np.full(self.n, np.nan)
@@ -233,10 +236,12 @@ class Tree:
             tbk = np.ascontiguousarray(theta_by_key, dtype=np.float64)
             assert tbk.shape[0] == self.n
         kind = {"theta": 0, "sw": 1}[mac]
+        sel = None if groups is None else np.ascontiguousarray(groups, dtype=np.int64)
         rc = self._lib.oracle_tree_eval(self._h, float(theta), _d(tbk) if tbk is not None else None,
-                                        kind, float(delta), float(m_limit), float(eps), int(bool(use_quad)), int(group_stride),
-                                        _d(acc), _d(pot), _l(key), _l(cnt), _l(ncell), _l(npart),
-                                        _d(gmass), _l(inter))
+                                        kind, float(delta), float(m_limit), float(eps), int(bool(use_quad)),
+                                        int(group_stride), _l(sel) if sel is not None else None,
+                                        0 if sel is None else sel.shape[0], _d(acc), _d(pot), _l(key), _l(cnt),
+                                        _l(ncell), _l(npart), _d(gmass), _l(inter))
         if rc != 0:
             raise ValueError("oracle_tree_eval failed (%d)" % rc)
         return dict(acc=acc, pot=pot, key=key, count=cnt, n_cell=ncell, n_part=npart,

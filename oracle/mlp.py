@@ -101,3 +101,47 @@ def select_theta(w, feats, grid, log10_target, fallback):
     g, k, _ = feats.shape
     y = forward(w, feats.reshape(g * k, NI)).reshape(g, k)
     return choose_theta(y, grid, log10_target, fallback), y
+
+
+def budget_targets(y0, log2_len, count, target_rms, alpha, beta):
+    """Per-group error targets e_g = lambda w_g with w_g = 10^(alpha y0_g +
+    beta log10 L_g) (y0: predicted log10 error at theta0, L = 2^log2_len the
+    list length at theta0) and lambda fixing the particle-weighted RMS of
+    the targets: sum_g n_g e_g^2 / sum_g n_g = target_rms^2.  Returns
+    log10 e_g.  (With a group error c theta^k and a list length a theta^-3,
+    minimising sum n a theta^-3 at fixed sum n c^2 theta^(2k) gives
+    e ~ c^(3/(2k+3)) a^(k/(2k+3)): alpha = 3/(2k+3), beta = k/(2k+3).)"""
+    y0 = np.asarray(y0, np.float64)
+    n = np.asarray(count, np.float64)
+    w = 10.0 ** (alpha * y0 + beta * np.asarray(log2_len, np.float64) * np.log10(2.0))
+    lam = target_rms / np.sqrt(np.sum(n * w * w) / np.sum(n))
+    return np.log10(lam * w)
+
+
+def learned_theta(w, mean, std, lo, hi, feats, count, grid, theta0, target_rms, calib, alpha, beta, fallback):
+    """The learned per-group angle from raw list statistics feats [g][5]:
+    groups with a non-finite statistic or one outside [lo, hi] take the
+    fallback; the others get budget_targets (aimed at calib * target_rms,
+    from the prediction at theta0 on the standardised row (x - mean) / std)
+    and choose_theta over the grid (a non-finite prediction: fallback).
+    Returns (angles, log10 targets with NaN where out of range)."""
+    f = np.asarray(feats, np.float64)
+    g = f.shape[0]
+    ok = np.all(np.isfinite(f), axis=1)
+    if lo is not None:
+        ok &= np.all((f >= np.asarray(lo, np.float64)) & (f <= np.asarray(hi, np.float64)), axis=1)
+    mean = np.asarray(mean, np.float64)
+    std = np.asarray(std, np.float64)
+
+    def rows(th):
+        return (np.concatenate([f, np.full((g, 1), th)], 1) - mean) / std
+
+    y0 = forward(w, rows(theta0))
+    ok &= np.isfinite(y0)
+    out = np.full(g, fallback, np.float64)
+    tg = np.full(g, np.nan)
+    if ok.any():
+        tg[ok] = budget_targets(y0[ok], f[ok, 0], np.asarray(count)[ok], calib * target_rms, alpha, beta)
+        y = np.stack([forward(w, rows(th))[ok] for th in grid], 1)
+        out[ok] = choose_theta(y, grid, tg[ok], fallback)
+    return out, tg

@@ -670,20 +670,32 @@ static int walk(const OracleTree* t, const Node* c, const double blo[3], const d
  *   g_ncell  cell entries,  g_npart  particle entries,
  *   g_mass   mass of all entries (equals the total mass when the walk is complete).
  * *interactions receives sum over evaluated groups of count * (ncell + npart).
+ * group_sel (n_sel entries, group indices), if not NULL, replaces the
+ * stride: only those groups are walked and evaluated (the statistics of the
+ * other groups are left untouched), so that a sample of groups costs what
+ * its own walks and sums cost.
  */
 int oracle_tree_eval(const void* handle, double theta, const double* theta_by_key, int mac_kind, double delta,
-                     double m_limit, double eps, int use_quad, int64_t group_stride, double* acc, double* pot,
-                     int64_t* g_key, int64_t* g_count, int64_t* g_ncell, int64_t* g_npart,
-                     double* g_mass, int64_t* interactions)
+                     double m_limit, double eps, int use_quad, int64_t group_stride, const int64_t* group_sel,
+                     int64_t n_sel, double* acc, double* pot, int64_t* g_key, int64_t* g_count, int64_t* g_ncell,
+                     int64_t* g_npart, double* g_mass, int64_t* interactions)
 {
     const OracleTree* t = (const OracleTree*)handle;
     if (!t || !(eps > 0.0) || group_stride < 1 || mac_kind < 0 || mac_kind > 1) return -1;
+    if (group_sel) {
+        if (n_sel < 0) return -1;
+        for (int64_t q = 0; q < n_sel; ++q)
+            if (group_sel[q] < 0 || group_sel[q] >= t->n_groups) return -1;
+    }
+    const int64_t n_loop = group_sel ? n_sel : t->n_groups;
     double eps2 = eps * eps;
     int64_t total = 0;
     int err = 0;
-    int64_t g;
+    int64_t q;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : total) reduction(| : err)
-    for (g = 0; g < t->n_groups; ++g) {
+    for (q = 0; q < n_loop; ++q) {
+        const int64_t g = group_sel ? group_sel[q] : q;
+        const int evaluate = group_sel ? 1 : (g % group_stride == 0);
         int64_t b = t->grp_begin[g], e_ = t->grp_end[g];
         double blo[3], bhi[3];
         int64_t key = t->idx[b];
@@ -720,7 +732,7 @@ int oracle_tree_eval(const void* handle, double theta, const double* theta_by_ke
             for (int64_t k = 0; k < ent.n_part; ++k) ms += t->mass[ent.part[k]];
             g_mass[g] = ms;
         }
-        if (g % group_stride == 0) {
+        if (evaluate) {
             total += (e_ - b) * (ent.n_cell + ent.n_part);
             for (int64_t k = b; k < e_; ++k) {
                 int64_t i = t->idx[k];

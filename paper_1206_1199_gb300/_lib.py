@@ -56,7 +56,7 @@ class Src(ctypes.Structure):
 
 
 class Quad(ctypes.Structure):
-    _fields_ = [(k, f32) for k in ("xx", "yy", "zz", "xy", "xz", "yz", "pad0", "pad1")]
+    _fields_ = [(k, f32) for k in ("xx", "yy", "zz", "xy", "xz", "yz", "b2", "pad")]
 
 
 class Group(ctypes.Structure):
@@ -74,8 +74,8 @@ class Split(ctypes.Structure):
 
 
 class DevSystem(ctypes.Structure):
-    _fields_ = [("n_part", i64), ("n_src", i64), ("n_list", i64), ("n_groups", i32), ("n_items", i32),
-                ("n_splits", i32), ("n_crit_max", i32), ("src", vp), ("quad", vp), ("groups", vp),
+    _fields_ = [("n_part", i64), ("n_src", i64), ("n_list", i64), ("partial_doubles", i64), ("n_groups", i32),
+                ("n_items", i32), ("n_splits", i32), ("n_crit_max", i32), ("src", vp), ("quad", vp), ("groups", vp),
                 ("list", vp), ("items", vp), ("splits", vp), ("perm", vp), ("partial", vp), ("counter", vp),
                 ("split", vp)]
 
@@ -115,6 +115,15 @@ class DevWalk(ctypes.Structure):
                 ("group_count", vp), ("theta_per_group", vp), ("counter", vp), ("totals", vp)]
 
 
+class ThetaNet(ctypes.Structure):
+    _fields_ = [("wbf16", vp), ("mean", vp), ("std", vp), ("lo", vp), ("hi", vp)]
+
+
+class ThetaRule(ctypes.Structure):
+    _fields_ = [("theta0", f32), ("target_rms", f32), ("calib", f32), ("alpha", f32), ("beta", f32),
+                ("fallback", f32)]
+
+
 class DevTree(ctypes.Structure):
     _fields_ = [("n_part", i64), ("cap_cell", i64), ("leaf_size", i32), ("n_crit", i32), ("use_quad", i32),
                 ("mac", i32), ("delta", f64), ("m_limit", f64), ("h_sph", vp), ("n_cell", i64), ("n_groups", i64), ("depth", i32),
@@ -143,8 +152,12 @@ _SIGS = {
     "otoo_force": [ctypes.POINTER(DevSystem), vp, vp, i32, ctypes.POINTER(Tune), vp],
     "otoo_force_host": [ctypes.POINTER(ListsView), ctypes.POINTER(PlanInfo), vp, vp, i32, ctypes.POINTER(Tune), vp],
     "otoo_check_status": [ctypes.POINTER(DevSystem), vp],
+    "otoo_centre_relative": [vp, i64, ctypes.POINTER(f64), vp, vp, vp],
     "otoo_force_static": [ctypes.POINTER(DevSystem), i64, vp, vp, i32, ctypes.POINTER(Tune), vp],
     "otoo_force_static_capacity": [],
+    "otoo_force_static_status": [vp],
+    "otoo_fma_probe_threads": [],
+    "otoo_fma_probe": [i32, i32, vp, ctypes.POINTER(f64), vp],
     "otoo_direct_chunks": [i64, i64],
     "otoo_direct": [vp, i64, vp, i64, f64, vp, vp, vp, vp, vp],
     "otoo_mlp_predict": [vp, vp, vp, i64, vp],
@@ -153,6 +166,10 @@ _SIGS = {
     "otoo_mlp_train_step": [vp, vp, vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp],
     "otoo_mlp_to_bf16": [vp, vp, i32, vp],
     "otoo_select_theta": [vp, vp, vp, i32, i64, f32, vp, f32, vp, vp],
+    "otoo_learned_theta_scratch_floats": [i64],
+    "otoo_mlp_standardise": [vp, i64, vp, vp, vp, vp],
+    "otoo_learned_theta": [ctypes.POINTER(ThetaNet), ctypes.POINTER(ThetaRule), vp, vp, i64, vp, i32, vp, vp, vp, vp],
+    "otoo_group_rms_error": [vp, vp, vp, i64, f32, vp, vp, vp],
     "otoo_find_groups": [vp, i32, vp, vp, i64, ctypes.POINTER(i64)],
     "otoo_tree_device_arrays": [vp, i32, ctypes.POINTER(Params), vp, vp, vp, vp],
     "otoo_walk_totals_len": [i64],
@@ -171,7 +188,7 @@ _SIGS = {
     "otoo_devtree_build": [vp, vp, ctypes.POINTER(DevTree), vp, i64, vp],
     "otoo_last_error": [],
 }
-_RET_I64 = {"otoo_mlp_scratch_floats", "otoo_force_static_capacity", "otoo_direct_chunks", "otoo_walk_totals_len",
+_RET_I64 = {"otoo_mlp_scratch_floats", "otoo_learned_theta_scratch_floats", "otoo_force_static_capacity", "otoo_fma_probe_threads", "otoo_direct_chunks", "otoo_walk_totals_len",
             "otoo_plan_scratch_ints", "otoo_devtree_scratch_bytes"}
 _VOID = {"otoo_tree_free", "otoo_lists_free", "otoo_plan_free"}
 _OPTIONAL = set()

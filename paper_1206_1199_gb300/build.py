@@ -17,7 +17,8 @@ LIB = os.path.join(PKG, "libotoo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["host/tree.cpp"]
 CUDA_HDR = ["cuda/force_warp.cuh", "cuda/force_warp2.cuh", "cuda/pair.cuh"]
-CUDA_SRC = ["cuda/force.cu", "cuda/mlp.cu", "cuda/direct.cu", "cuda/walk.cu", "cuda/tree_build.cu", "cuda/sph.cu"]
+CUDA_SRC = ["cuda/force.cu", "cuda/mlp.cu", "cuda/direct.cu", "cuda/walk.cu", "cuda/tree_build.cu", "cuda/sph.cu",
+            "cuda/peak.cu"]
 
 
 def _nvcc():

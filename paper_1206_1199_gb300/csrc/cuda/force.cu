@@ -52,6 +52,13 @@ __device__ __forceinline__ void load_src(const otoo_src* src, int64_t idx, doubl
     m = __int_as_float((int)(__double_as_longlong(b.y) & 0xffffffffll));
 }
 
+// Partial slots [slot0, slot0 + n) lie inside sys.partial (each slot holds
+// n_crit_max targets of 4 doubles).
+__device__ __forceinline__ bool slots_fit(const otoo_dev_system& sys, int64_t slot0, int64_t n)
+{
+    return slot0 >= 0 && n >= 0 && (slot0 + n) * sys.n_crit_max * 4 <= sys.partial_doubles;
+}
+
 // Checks an item against the system's sizes; fills grp.
 __device__ __forceinline__ bool item_ok(const otoo_dev_system& sys, const otoo_item& item, otoo_group& grp, int max_ni)
 {
@@ -61,7 +68,8 @@ __device__ __forceinline__ bool item_ok(const otoo_dev_system& sys, const otoo_i
     return grp.count >= 1 && grp.first >= 0 && (int64_t)grp.first + grp.count <= sys.n_part && grp.n_cell >= 0 &&
            grp.n_part >= 0 && item.ni >= 1 && item.ni <= max_ni && item.i0 >= 0 &&
            (int64_t)item.i0 + item.ni <= grp.count && item.j0 >= 0 && item.j0 <= item.j1 && item.j1 <= L &&
-           grp.list_off >= 0 && grp.list_off + L <= sys.n_list && (item.slot < 0 || grp.count <= sys.n_crit_max);
+           grp.list_off >= 0 && grp.list_off + L <= sys.n_list &&
+           (item.slot < 0 || (grp.count <= sys.n_crit_max && slots_fit(sys, item.slot, 1)));
 }
 
 // Final write of one target: the output, or the FP64 partial of the item's
@@ -107,6 +115,19 @@ __global__ void k_split(const otoo_src* __restrict__ src, float4* __restrict__ o
                                  __double2float_rn(z - (double)hz), 0.f);
 }
 
+// Centre-relative coordinates of n sources as the FP32 force kernels stage
+// them (otoo_centre_relative): rel32 of each float pair written by k_split.
+__global__ void k_centre_relative(const float4* __restrict__ pairs, int64_t n, float cx, float cy, float cz,
+                                  float* __restrict__ out)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const float4 h = pairs[2 * s], l = pairs[2 * s + 1];
+    out[3 * s] = rel32(h.x, l.x, cx);
+    out[3 * s + 1] = rel32(h.y, l.y, cy);
+    out[3 * s + 2] = rel32(h.z, l.z, cz);
+}
+
 #include "force_warp.cuh"
 #include "force_warp2.cuh"
 
@@ -118,7 +139,7 @@ __global__ void __launch_bounds__(B) k_force_f64(const otoo_dev_system sys, doub
 {
     __shared__ V4<double> s_src[B];
     __shared__ V4<double> s_qa[B];
-    __shared__ V2<double> s_qb[B];
+    __shared__ V4<double> s_qb[B];
     __shared__ double s_red[B * IB * 4];
     __shared__ int s_ticket;
 
@@ -193,7 +214,8 @@ __global__ void __launch_bounds__(B) k_force_f64(const otoo_dev_system sys, doub
                             b = __ldg(qp + 1);
                         }
                         s_qa[tid] = V4<double>{a.x, a.y, a.z, a.w};
-                        s_qb[tid] = V2<double>{b.x, b.y};
+                        // (xz, yz, B_2 eps^2, -) for the softened quadrupole term
+                        s_qb[tid] = V4<double>{b.x, b.y, (double)b.z * eps2, 0.0};
                     }
                 }
                 __syncthreads();
@@ -205,7 +227,7 @@ __global__ void __launch_bounds__(B) k_force_f64(const otoo_dev_system sys, doub
                         for (int j = js; j < cnt; j += nsplit) {
                             const V4<double> s = s_src[j];
                             const V4<double> qa = s_qa[j];
-                            const V2<double> qb = s_qb[j];
+                            const V4<double> qb = s_qb[j];
 #pragma unroll
                             for (int k = 0; k < IB; ++k) pair_quad(s, qa, qb, xi[k], yi[k], zi[k], eps2, p[k]);
                         }
@@ -256,7 +278,7 @@ __global__ void k_merge(const otoo_dev_system sys, double* __restrict__ accel, d
     const int lane = threadIdx.x & 31;
     if (w >= sys.n_splits) return;
     const otoo_split sp = sys.splits[w];
-    bool ok = sp.g >= 0 && sp.g < sys.n_groups && sp.slot0 >= 0 && sp.n_chunks >= 1;
+    bool ok = sp.g >= 0 && sp.g < sys.n_groups && sp.n_chunks >= 1 && slots_fit(sys, sp.slot0, sp.n_chunks);
     otoo_group grp;
     if (ok) {
         grp = sys.groups[sp.g];
@@ -330,6 +352,19 @@ int check_tune(const otoo_tune* t)
         cudaError_t e_ = (expr);                                                                       \
         if (e_ != cudaSuccess) return set_error(OTOO_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));  \
     } while (0)
+
+// Copies the work ticket and status word (counter[0..1], device) out on
+// stream, synchronises it and turns the status bits into an error code.
+int read_status(const uint32_t* counter, void* stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t h[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(h, counter, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (h[1] & kBadItem) return set_error(OTOO_EDEVICE, "a work item, split or group failed its bounds check");
+    if (h[1] & kBadIndex) return set_error(OTOO_EDEVICE, "a list entry indexed outside its source range");
+    return OTOO_OK;
+}
 
 // Records the launches of one force step on stream s.
 }  // namespace
@@ -406,7 +441,10 @@ int validate_sys(const otoo_dev_system* sys)
     OTOO_REQUIRE(sys->n_crit_max >= 1 && sys->n_crit_max <= kMaxGroup, OTOO_EINVAL, "n_crit_max out of range");
     OTOO_REQUIRE(sys->src && sys->groups && sys->counter && (sys->n_items == 0 || (sys->items && sys->list)),
                  OTOO_EINVAL, "NULL device array");
-    OTOO_REQUIRE(sys->n_splits == 0 || (sys->splits && sys->partial), OTOO_EINVAL, "split lists need partial scratch");
+    OTOO_REQUIRE(sys->partial_doubles >= 0, OTOO_EINVAL, "partial_doubles < 0");
+    OTOO_REQUIRE(sys->n_splits == 0 ||
+                     (sys->splits && sys->partial && sys->partial_doubles >= 4 * (int64_t)sys->n_crit_max),
+                 OTOO_EINVAL, "split lists need partial scratch (at least 4 * n_crit_max doubles)");
     OTOO_REQUIRE((reinterpret_cast<uintptr_t>(sys->quad) & 31) == 0 && (reinterpret_cast<uintptr_t>(sys->split) & 31) == 0,
                  OTOO_EINVAL, "quad and split must be 32-byte aligned (one 32-byte load per record)");
     return OTOO_OK;
@@ -481,13 +519,7 @@ int otoo_force(const otoo_dev_system* sys, double* accel, double* pot, int32_t p
 int otoo_check_status(const otoo_dev_system* sys, void* stream)
 {
     OTOO_REQUIRE(sys && sys->counter, OTOO_EINVAL, "sys/counter is NULL");
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    uint32_t h[2] = {0, 0};
-    CUDA_TRY(cudaMemcpyAsync(h, sys->counter, sizeof(h), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if (h[1] & kBadItem) return set_error(OTOO_EDEVICE, "a work item or group failed its bounds check");
-    if (h[1] & kBadIndex) return set_error(OTOO_EDEVICE, "a list entry indexed outside its source range");
-    return OTOO_OK;
+    return read_status(sys->counter, stream);
 }
 
 }  // extern "C"
@@ -519,6 +551,23 @@ int ensure(int k, size_t bytes)
 }
 
 }  // namespace
+
+extern "C" int otoo_centre_relative(const otoo_src* src, int64_t n, const double* c, float* out, void* scratch,
+                                    void* stream)
+{
+    OTOO_REQUIRE(src && c && out && scratch, OTOO_EINVAL, "otoo_centre_relative: NULL pointer");
+    OTOO_REQUIRE(n >= 1 && n <= INT32_MAX, OTOO_EINVAL, "otoo_centre_relative: bad n");
+    OTOO_REQUIRE((reinterpret_cast<uintptr_t>(scratch) & 31) == 0, OTOO_EINVAL,
+                 "otoo_centre_relative: scratch must be 32-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float4* pairs = static_cast<float4*>(scratch);
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    k_split<<<nb, 256, 0, s>>>(src, pairs, n);
+    CUDA_TRY(cudaGetLastError());
+    k_centre_relative<<<nb, 256, 0, s>>>(pairs, n, (float)c[0], (float)c[1], (float)c[2], out);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
 
 extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* pl, double* accel, double* pot,
                                int32_t precision, const otoo_tune* tune, void* stream)
@@ -575,6 +624,7 @@ extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* 
     sys.perm = (const int64_t*)g_host.p[6];
     double* out = (double*)g_host.p[7];
     sys.partial = out + 4 * lv->n_part;
+    sys.partial_doubles = std::max<int64_t>(pl->partial_doubles, 1);
     sys.counter = (uint32_t*)g_host.p[8];
     sys.split = g_host.p[9];
     int rc = otoo_force(&sys, out, out + 3 * lv->n_part, precision, tune, stream);
@@ -649,9 +699,18 @@ extern "C" int otoo_force_static(const otoo_dev_system* sys, int64_t partial_dou
     s.counter = reinterpret_cast<uint32_t*>(b);
     s.split = need_split ? b + need_counter : nullptr;
     s.partial = need_partial ? reinterpret_cast<double*>(b + need_counter + need_split) : nullptr;
+    s.partial_doubles = partial_doubles;
     rc = validate_sys(&s);
     if (rc) return rc;
     rc = check_tune(tune);
     if (rc) return rc;
     return enqueue_force(&s, accel, pot, precision, tune, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int otoo_force_static_status(void* stream)
+{
+    void* base = nullptr;
+    int rc = static_scratch_ptr(&base);
+    if (rc) return rc;
+    return read_status(static_cast<const uint32_t*>(base), stream);
 }

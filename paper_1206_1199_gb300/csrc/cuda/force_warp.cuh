@@ -77,9 +77,9 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
                 const int64_t t = (int64_t)grp.first + item.i0 + i;
                 const float4 h = __ldg(ff + 2 * t);
                 const float4 l = __ldg(ff + 2 * t + 1);
-                xi[k] = (h.x - cx) + l.x;
-                yi[k] = (h.y - cy) + l.y;
-                zi[k] = (h.z - cz) + l.z;
+                xi[k] = rel32(h.x, l.x, cx);
+                yi[k] = rel32(h.y, l.y, cy);
+                zi[k] = rel32(h.z, l.z, cz);
             }
             acc[k].zero();
         }
@@ -150,12 +150,13 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
                     const int k = lane + 32 * (e0 + u);
                     // padding and rejected entries loaded as zeros: mass (and
                     // quadrupole) 0, so they add exactly nothing
-                    const float4 a = make_float4((h[u].x - cx) + l[u].x, (h[u].y - cy) + l[u].y,
-                                                 (h[u].z - cz) + l[u].z, h[u].w);
+                    const float4 a = make_float4(rel32(h[u].x, l[u].x, cx), rel32(h[u].y, l[u].y, cy),
+                                                 rel32(h[u].z, l[u].z, cz), h[u].w);
                     if (cq) {
                         rec[3 * k] = a;
                         rec[3 * k + 1] = qa[u];
-                        rec[3 * k + 2] = qb[u];
+                        // (xz, yz, B_2 eps^2, -) for the softened quadrupole term
+                        rec[3 * k + 2] = make_float4(qb[u].x, qb[u].y, qb[u].z * eps2, 0.f);
                     } else {
                         rec[k] = a;
                     }
@@ -180,9 +181,9 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
 #pragma unroll
                         for (int k = 0; k < IB; ++k) {
                             pair_quad(V4<float>{sa.x, sa.y, sa.z, sa.w}, V4<float>{qa.x, qa.y, qa.z, qa.w},
-                                      V2<float>{qb.x, qb.y}, xi[k], yi[k], zi[k], eps2, p[k]);
+                                      V4<float>{qb.x, qb.y, qb.z, qb.w}, xi[k], yi[k], zi[k], eps2, p[k]);
                             pair_quad(V4<float>{sb.x, sb.y, sb.z, sb.w}, V4<float>{qc.x, qc.y, qc.z, qc.w},
-                                      V2<float>{qd.x, qd.y}, xi[k], yi[k], zi[k], eps2, p[k]);
+                                      V4<float>{qd.x, qd.y, qd.z, qd.w}, xi[k], yi[k], zi[k], eps2, p[k]);
                         }
                     }
                     if (niter & 1) {
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(NW * 32, warp_min_blocks(NW, IB)) k_force_warp
 #pragma unroll
                         for (int k = 0; k < IB; ++k)
                             pair_quad(V4<float>{sa.x, sa.y, sa.z, sa.w}, V4<float>{qa.x, qa.y, qa.z, qa.w},
-                                      V2<float>{qb.x, qb.y}, xi[k], yi[k], zi[k], eps2, p[k]);
+                                      V4<float>{qb.x, qb.y, qb.z, qb.w}, xi[k], yi[k], zi[k], eps2, p[k]);
                     }
                 } else {
                     const float4* __restrict__ r0 = rec + js;

@@ -10,13 +10,15 @@
 // FP32 operations, so the FP32 pipe rather than instruction issue bounds the
 // kernel.  The reciprocal square root stays two scalar MUFU operations.
 //
-// Pair records: a cell tile stores 80 bytes per pair (x | y | z | m | -Qxx |
-// -Qyy | -Qzz | -Qxy | -Qxz | -Qyz, each two floats); a particle tile 32
-// bytes (x | y | z | m).  The quadrupole is stored negated so that the law
-// needs no negation: with n = -Q r and u = r.n = -(r.Q.r),
+// Pair records: a cell tile stores 96 bytes per pair (x | y | z | m | -Qxx |
+// -Qyy | -Qzz | -Qxy | -Qxz | -Qyz | B_2 eps^2, each two floats, and one
+// unused pair); a particle tile 32 bytes (x | y | z | m).  Each field loads
+// straight into a packed operand.  The quadrupole is stored negated so that
+// the law needs no negation: with n = -Q r and u = r.n + B_2 eps^2,
 //   phi -= m q - (1/2) u q^5,  a += (m q^3 - (5/2) u q^7) r + q^5 n.
 // The potential is accumulated as a positive sum and negated at the end.
-// The packed arithmetic (f2 operations, pair_mono2, pair_quad2) is in pair.cuh.
+// The packed arithmetic (f2 operations, pair_mono2, pair_quad2, the record
+// layout and the evaluation loops) is in pair.cuh.
 
 // Packed operands take register pairs: fewer resident warps than the scalar
 // kernel, each with twice the independent FP32 work per instruction.
@@ -29,8 +31,6 @@
 #ifndef OTOO_W2_MUNROLL
 #define OTOO_W2_MUNROLL 3  // pair records per step of the particle loop (3: 45.1 ms, 2: 45.3, 4: 45.6)
 #endif
-#define OTOO_PRAGMA_(x) _Pragma(#x)
-#define OTOO_UNROLL_(n) OTOO_PRAGMA_(unroll n)
 constexpr int warp2_min_blocks(int nw, int ib) { return (ib == 1 ? 20 : OTOO_W2_WARPS) / nw; }
 
 template <int NW, int IB, int SPL>
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
     constexpr int T = 32 * SPL;          // entries per tile at most
     constexpr int TP = T / 2;            // pair records per tile at most
     constexpr int PPL = (TP + 31) / 32;  // pair records staged per lane
-    __shared__ float4 s_rec[NW][5 * TP];
+    __shared__ float4 s_rec[NW][kCellRecF4 * TP];
 
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
     const float4* __restrict__ ff = reinterpret_cast<const float4*>(sys.split);
     const bool has_quad = sys.quad != nullptr;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const f2 mhalf = f2pack(-0.5f, -0.5f), m5half = f2pack(-2.5f, -2.5f), zero2 = f2pack(0.f, 0.f);
+    const f2 zero2 = f2pack(0.f, 0.f);
 
     for (;;) {
         int it = 0;
@@ -87,9 +87,9 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
                 const int64_t t = (int64_t)grp.first + item.i0 + i;
                 const float4 h = __ldg(ff + 2 * t);
                 const float4 l = __ldg(ff + 2 * t + 1);
-                x = (h.x - cx) + l.x;
-                y = (h.y - cy) + l.y;
-                z = (h.z - cz) + l.z;
+                x = rel32(h.x, l.x, cx);
+                y = rel32(h.y, l.y, cy);
+                z = rel32(h.z, l.z, cz);
             }
             nx[k] = f2pack(-x, -x);
             ny[k] = f2pack(-y, -y);
@@ -160,24 +160,12 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
                 for (int h = 0; h < 2; ++h) {
                     // padding and rejected entries loaded as zeros: mass (and
                     // quadrupole) 0, so they add exactly nothing
-                    x[h] = (hh[h].x - cx) + ll[h].x;
-                    y[h] = (hh[h].y - cy) + ll[h].y;
-                    z[h] = (hh[h].z - cz) + ll[h].z;
+                    x[h] = rel32(hh[h].x, ll[h].x, cx);
+                    y[h] = rel32(hh[h].y, ll[h].y, cy);
+                    z[h] = rel32(hh[h].z, ll[h].z, cz);
                     w[h] = hh[h].w;
                 }
-                if (cq) {
-                    float4* r = rec + 5 * m;
-                    r[0] = make_float4(x[0], x[1], y[0], y[1]);
-                    r[1] = make_float4(z[0], z[1], w[0], w[1]);
-                    // qa = (xx, yy, zz, xy), qb = (xz, yz, -, -), stored negated
-                    r[2] = make_float4(-qa[0].x, -qa[1].x, -qa[0].y, -qa[1].y);
-                    r[3] = make_float4(-qa[0].z, -qa[1].z, -qa[0].w, -qa[1].w);
-                    r[4] = make_float4(-qb[0].x, -qb[1].x, -qb[0].y, -qb[1].y);
-                } else {
-                    float4* r = rec + 2 * m;
-                    r[0] = make_float4(x[0], x[1], y[0], y[1]);
-                    r[1] = make_float4(z[0], z[1], w[0], w[1]);
-                }
+                put_rec2(rec, m, cq, x, y, z, w, qa, qb, eps2);
             }
             if (t + 1 < nt) load_idx(t + 1);
             __syncwarp();
@@ -187,33 +175,10 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
 #pragma unroll
                 for (int k = 0; k < IB; ++k) P2[k].v[0] = P2[k].v[1] = P2[k].v[2] = P2[k].v[3] = zero2;
                 const int niter = npair_pad / nsub;
-                if (cq) {
-                    const float4* __restrict__ r = rec + 5 * js;
-                    const int S = 5 * nsub;
-                    OTOO_UNROLL_(OTOO_W2_QUNROLL)
-                    for (int n = 0; n < niter; ++n, r += S) {
-                        const float4 a = r[0], b = r[1], c = r[2], d = r[3], e = r[4];
-                        const f2 sx = f2pack(a.x, a.y), sy = f2pack(a.z, a.w), sz = f2pack(b.x, b.y);
-                        const f2 sm = f2pack(b.z, b.w);
-                        const f2 qxx = f2pack(c.x, c.y), qyy = f2pack(c.z, c.w), qzz = f2pack(d.x, d.y);
-                        const f2 qxy = f2pack(d.z, d.w), qxz = f2pack(e.x, e.y), qyz = f2pack(e.z, e.w);
-#pragma unroll
-                        for (int k = 0; k < IB; ++k)
-                            pair_quad2(sx, sy, sz, sm, qxx, qyy, qzz, qxy, qxz, qyz, nx[k], ny[k], nz[k], e2, mhalf,
-                                       m5half, P2[k]);
-                    }
-                } else {
-                    const float4* __restrict__ r = rec + 2 * js;
-                    const int S = 2 * nsub;
-                    OTOO_UNROLL_(OTOO_W2_MUNROLL)
-                    for (int n = 0; n < niter; ++n, r += S) {
-                        const float4 a = r[0], b = r[1];
-                        const f2 sx = f2pack(a.x, a.y), sy = f2pack(a.z, a.w), sz = f2pack(b.x, b.y);
-                        const f2 sm = f2pack(b.z, b.w);
-#pragma unroll
-                        for (int k = 0; k < IB; ++k) pair_mono2(sx, sy, sz, sm, nx[k], ny[k], nz[k], e2, P2[k]);
-                    }
-                }
+                if (cq)
+                    eval_cells2<IB, OTOO_W2_QUNROLL>(rec, js, nsub, niter, nx, ny, nz, e2, P2);
+                else
+                    eval_parts2<IB, OTOO_W2_MUNROLL>(rec, js, nsub, niter, nx, ny, nz, e2, P2);
 #pragma unroll
                 for (int k = 0; k < IB; ++k) {
                     float s[4];

@@ -16,6 +16,12 @@
 //                   the bf16 copy (round to nearest even).
 //   k_select_theta  one thread per group: the largest grid angle whose
 //                   predicted error meets the target.
+//   k_theta_weights, k_theta_lambda, k_theta_choose
+//                   the whole per-group selection from raw list statistics
+//                   (otoo_learned_theta): range check, standardisation,
+//                   budgeted per-group targets normalised to the global RMS
+//                   target, the choice over the angle grid.
+//   k_group_rms     per-group RMS relative acceleration error (labels).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -233,6 +239,175 @@ __global__ void k_select_theta(const uint16_t* __restrict__ wbf16, const float* 
     out[g] = bad ? fallback : best;
 }
 
+// ---- learned angle from raw list statistics ---------------------------------
+
+constexpr int kThetaBlock = 128;
+
+struct ThetaArgs {
+    const uint16_t* wbf16;
+    const float* mean;
+    const float* std;
+    const float* lo;
+    const float* hi;
+    const float* feat;     // [n][NI - 1]
+    const int32_t* count;  // [n]
+    int64_t n;
+    float theta0, alpha, beta;
+};
+
+// Standardised row of group g's statistics with angle th.
+__device__ __forceinline__ void theta_row(const ThetaArgs& a, int64_t g, float th, float x[NI])
+{
+#pragma unroll
+    for (int k = 0; k < NI - 1; ++k) x[k] = __fdiv_rn(__fsub_rn(a.feat[g * (NI - 1) + k], a.mean[k]), a.std[k]);
+    x[NI - 1] = __fdiv_rn(__fsub_rn(th, a.mean[NI - 1]), a.std[NI - 1]);
+}
+
+// Budget weight of every group (0 outside the training range or for a
+// non-finite prediction): w = 10^(alpha y0 + beta log10 L), y0 the predicted
+// log10 error at theta0, L = 2^feat[0] the list length at theta0; and the
+// block's sums of count * w^2 and count over the groups that have a weight,
+// in a fixed order (FP64).
+__global__ void __launch_bounds__(kThetaBlock) k_theta_weights(const ThetaArgs a, float* __restrict__ wg,
+                                                               double* __restrict__ part)
+{
+    __shared__ float s_w[NP];
+    __shared__ double s_a[kThetaBlock], s_b[kThetaBlock];
+    load_weights(a.wbf16, s_w);
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double nw2 = 0.0, nn = 0.0;
+    if (g < a.n) {
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < NI - 1; ++k) {
+            const float f = a.feat[g * (NI - 1) + k];
+            ok = ok && isfinite(f);
+            if (a.lo) ok = ok && f >= a.lo[k] && f <= a.hi[k];
+        }
+        float w = 0.f;
+        if (ok) {
+            float x[NI], h1[NH], h2[NH];
+            theta_row(a, g, a.theta0, x);
+            const float y0 = forward_row(s_w, x, h1, h2);
+            // log10 L = feat[0] log10(2)
+            const float e = fmaf(a.alpha, y0, a.beta * a.feat[g * (NI - 1)] * 0.30102999566398120f);
+            w = isfinite(e) ? exp10f(e) : 0.f;
+            if (!(w > 0.f) || !isfinite(w)) w = 0.f;
+        }
+        wg[g] = w;
+        if (w > 0.f) {
+            const double c = (double)a.count[g];
+            nw2 = c * (double)w * (double)w;
+            nn = c;
+        }
+    }
+    s_a[threadIdx.x] = nw2;
+    s_b[threadIdx.x] = nn;
+    __syncthreads();
+    for (int h = kThetaBlock / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s_a[threadIdx.x] += s_a[threadIdx.x + h];
+            s_b[threadIdx.x] += s_b[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s_a[0];
+        part[2 * blockIdx.x + 1] = s_b[0];
+    }
+}
+
+// lambda = target / sqrt(sum count w^2 / sum count): the common factor that
+// makes the particle-weighted RMS of the group targets equal to target.
+// One thread sums the block partials in block order.
+__global__ void k_theta_lambda(const double* __restrict__ part, int nblk, double target, double* __restrict__ lambda)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nblk; ++k) {
+        a += part[2 * k];
+        b += part[2 * k + 1];
+    }
+    lambda[0] = (a > 0.0 && b > 0.0) ? target / sqrt(a / b) : target;
+}
+
+// The choice: groups with a weight aim at log10(lambda w), the largest grid
+// angle whose prediction is at most that (grid[0] when none); the others,
+// and groups with a non-finite prediction, take the fallback angle.
+__global__ void __launch_bounds__(kThetaBlock) k_theta_choose(const ThetaArgs a, const float* __restrict__ wg,
+                                                              const double* __restrict__ lambda,
+                                                              const float* __restrict__ grid, int nth,
+                                                              float fallback, float* __restrict__ tgt_out,
+                                                              float* __restrict__ out)
+{
+    __shared__ float s_w[NP];
+    load_weights(a.wbf16, s_w);
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    const float w = wg[g];
+    if (!(w > 0.f)) {
+        if (tgt_out) tgt_out[g] = __int_as_float(0x7fc00000);  // no target: NaN
+        out[g] = fallback;
+        return;
+    }
+    const float target = (float)log10(lambda[0] * (double)w);
+    if (tgt_out) tgt_out[g] = target;
+    float best = grid[0];
+    bool bad = false;
+    for (int k = 0; k < nth; ++k) {
+        float x[NI], h1[NH], h2[NH];
+        theta_row(a, g, grid[k], x);
+        const float y = forward_row(s_w, x, h1, h2);
+        if (!isfinite(y)) bad = true;
+        if (y <= target) best = fmaxf(best, grid[k]);
+    }
+    out[g] = bad ? fallback : best;
+}
+
+// Rows standardised with the training set's statistics: (x - mean) / std.
+__global__ void k_standardise(const float* __restrict__ x, int64_t n, const float* __restrict__ mean,
+                              const float* __restrict__ std, float* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * NI) return;
+    const int k = (int)(i % NI);
+    out[i] = __fdiv_rn(__fsub_rn(x[i], mean[k]), std[k]);
+}
+
+// Per-group RMS of the relative acceleration error |a - ref| / |ref| over the
+// targets [off[g], off[g + 1]) (one warp per group, lanes in a fixed order):
+// out[g] = log10(max(rms, floor)).
+__global__ void k_group_rms(const double* __restrict__ acc, const double* __restrict__ ref,
+                            const int64_t* __restrict__ off, int64_t ng, float floor_v, float* __restrict__ out,
+                            uint32_t* __restrict__ status)
+{
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    const int64_t b = off[g], e = off[g + 1];
+    if (b < 0 || e <= b) {
+        if (lane == 0) {
+            atomicOr(status, 1u);
+            out[g] = __int_as_float(0x7fc00000);
+        }
+        return;
+    }
+    double s = 0.0;
+    for (int64_t t = b + lane; t < e; t += 32) {
+        double d2 = 0.0, r2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double d = acc[3 * t + c] - ref[3 * t + c];
+            d2 = fma(d, d, d2);
+            r2 = fma(ref[3 * t + c], ref[3 * t + c], r2);
+        }
+        s += d2 / r2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[g] = (float)log10(fmax(sqrt(s / (double)(e - b)), (double)floor_v));
+}
+
 #define CUDA_TRY(expr)                                                                                 \
     do {                                                                                               \
         cudaError_t e_ = (expr);                                                                       \
@@ -329,6 +504,86 @@ int otoo_select_theta(const uint16_t* wbf16, const float* x, const float* theta_
     k_select_theta<<<(unsigned)((n_groups + 127) / 128), 128, 0, s>>>(wbf16, x, theta_grid, n_theta, n_groups,
                                                                       log10_target, log10_target_per_group, fallback,
                                                                       theta_out);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+int otoo_mlp_standardise(const float* x, int64_t n_rows, const float* mean, const float* std, float* out,
+                         void* stream)
+{
+    OTOO_REQUIRE(x && mean && std && out && n_rows >= 0, OTOO_EINVAL, "otoo_mlp_standardise: bad argument");
+    if (n_rows == 0) return OTOO_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = n_rows * NI;
+    k_standardise<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n_rows, mean, std, out);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+int64_t otoo_learned_theta_scratch_floats(int64_t n_groups)
+{
+    if (n_groups < 1) return 0;
+    const int64_t nblk = (n_groups + kThetaBlock - 1) / kThetaBlock;
+    // weights, then (aligned to 8 bytes) 2 doubles per block and lambda
+    return ((n_groups + 1) & ~(int64_t)1) + 4 * nblk + 2;
+}
+
+int otoo_learned_theta(const otoo_theta_net* net, const otoo_theta_rule* rule, const float* feat,
+                       const int32_t* count, int64_t n_groups, const float* grid, int32_t n_theta, float* scratch,
+                       float* log10_target, float* theta_out, void* stream)
+{
+    otoo::Range range_("otoo_learned_theta");
+    OTOO_REQUIRE(net && rule && feat && count && grid && scratch && theta_out, OTOO_EINVAL,
+                 "otoo_learned_theta: NULL pointer");
+    OTOO_REQUIRE(net->wbf16 && net->mean && net->std && ((net->lo == nullptr) == (net->hi == nullptr)), OTOO_EINVAL,
+                 "otoo_learned_theta: network arrays missing (lo and hi are both set or both NULL)");
+    OTOO_REQUIRE(n_theta >= 1 && n_groups >= 0 && n_groups < ((int64_t)1 << 31), OTOO_EINVAL,
+                 "otoo_learned_theta: bad sizes");
+    OTOO_REQUIRE(rule->target_rms > 0.f && rule->calib > 0.f && rule->theta0 > 0.f && std::isfinite(rule->alpha) &&
+                     std::isfinite(rule->beta) && std::isfinite(rule->target_rms * rule->calib),
+                 OTOO_EINVAL, "otoo_learned_theta: bad rule");
+    OTOO_REQUIRE((reinterpret_cast<uintptr_t>(scratch) & 7) == 0, OTOO_EINVAL,
+                 "otoo_learned_theta: scratch must be 8-byte aligned");
+    if (n_groups == 0) return OTOO_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ThetaArgs a;
+    a.wbf16 = net->wbf16;
+    a.mean = net->mean;
+    a.std = net->std;
+    a.lo = net->lo;
+    a.hi = net->hi;
+    a.feat = feat;
+    a.count = count;
+    a.n = n_groups;
+    a.theta0 = rule->theta0;
+    a.alpha = rule->alpha;
+    a.beta = rule->beta;
+    const int nblk = (int)((n_groups + kThetaBlock - 1) / kThetaBlock);
+    float* wg = scratch;
+    double* part = reinterpret_cast<double*>(scratch + ((n_groups + 1) & ~(int64_t)1));
+    double* lambda = part + 2 * nblk;
+    k_theta_weights<<<nblk, kThetaBlock, 0, s>>>(a, wg, part);
+    CUDA_TRY(cudaGetLastError());
+    k_theta_lambda<<<1, 32, 0, s>>>(part, nblk, (double)rule->target_rms * (double)rule->calib, lambda);
+    CUDA_TRY(cudaGetLastError());
+    k_theta_choose<<<nblk, kThetaBlock, 0, s>>>(a, wg, lambda, grid, n_theta, rule->fallback, log10_target,
+                                                 theta_out);
+    CUDA_TRY(cudaGetLastError());
+    return OTOO_OK;
+}
+
+int otoo_group_rms_error(const double* acc, const double* ref, const int64_t* group_off, int64_t n_groups,
+                         float floor_value, float* log10_rms, uint32_t* status, void* stream)
+{
+    otoo::Range range_("otoo_group_rms_error");
+    OTOO_REQUIRE(acc && ref && group_off && log10_rms && status, OTOO_EINVAL, "otoo_group_rms_error: NULL pointer");
+    OTOO_REQUIRE(n_groups >= 0 && floor_value > 0.f, OTOO_EINVAL, "otoo_group_rms_error: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+    if (n_groups == 0) return OTOO_OK;
+    const int64_t threads = 32 * n_groups;
+    k_group_rms<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(acc, ref, group_off, n_groups, floor_value,
+                                                                  log10_rms, status);
     CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }

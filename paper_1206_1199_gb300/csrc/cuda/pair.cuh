@@ -25,6 +25,14 @@ __device__ __forceinline__ float rsqrt_r(float x)
 }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
+// Centre-relative FP32 coordinate of the FP32 form: (hi - c) + lo, with
+// (hi, lo) the float pair of an FP64 coordinate (hi = x rounded to FP32, lo
+// = (x - hi) rounded) and c the group centre rounded to FP32.  hi - c is
+// exact whenever hi is within a factor of two of c (Sterbenz), so near
+// entries get the FP64 difference rounded once (up to the rounding of lo,
+// 2^-25 of an FP32 ulp of x); far entries are within about one FP32 ulp.
+__device__ __forceinline__ float rel32(float hi, float lo, float c) { return __fadd_rn(__fsub_rn(hi, c), lo); }
+
 constexpr unsigned kFull = 0xffffffffu;
 
 // Running sum of one target particle: FP32 with Kahan compensation c (the sum
@@ -73,10 +81,14 @@ __device__ __forceinline__ void pair_mono(const V4<R>& s, R xi, R yi, R zi, R ep
     p[2] = fma(mq3, rz, p[2]);
 }
 
-// Quadrupole cell: with q = (r^2 + eps^2)^(-1/2),
-// phi -= m q + (1/2) (r.Q.r) q^5,  a += (m q^3 + (5/2) (r.Q.r) q^7) r - q^5 Q r.
+// Quadrupole cell: the second-order Taylor term of the softened pair law
+// about the cell's centre of mass.  With q = (r^2 + eps^2)^(-1/2), the
+// traceless Q and w = r.Q.r - B_2 eps^2 (B_2 = sum m |x - com|^2; the B_2
+// part vanishes without softening):
+//   phi -= m q + (1/2) w q^5,  a += (m q^3 + (5/2) w q^7) r - q^5 Q r.
+// qa = (Qxx, Qyy, Qzz, Qxy), qb = (Qxz, Qyz, B_2 eps^2, -).
 template <typename R>
-__device__ __forceinline__ void pair_quad(const V4<R>& s, const V4<R>& qa, const V2<R>& qb, R xi, R yi, R zi,
+__device__ __forceinline__ void pair_quad(const V4<R>& s, const V4<R>& qa, const V4<R>& qb, R xi, R yi, R zi,
                                           R eps2, R p[4])
 {
     const R rx = s.x - xi, ry = s.y - yi, rz = s.z - zi;
@@ -85,13 +97,12 @@ __device__ __forceinline__ void pair_quad(const V4<R>& s, const V4<R>& qa, const
     const R q2 = q * q;
     const R mq = s.w * q;
     const R mq3 = mq * q2;
-    // qa = (xx, yy, zz, xy), qb = (xz, yz)
     const R qr0 = fma(qa.x, rx, fma(qa.w, ry, qb.x * rz));
     const R qr1 = fma(qa.w, rx, fma(qa.y, ry, qb.y * rz));
     const R qr2 = fma(qb.x, rx, fma(qb.y, ry, qa.z * rz));
-    const R rqr = fma(rx, qr0, fma(ry, qr1, rz * qr2));
+    const R w = fma(rx, qr0, fma(ry, qr1, fma(rz, qr2, -qb.z)));
     const R q5 = q * (q2 * q2);
-    const R t = rqr * q5;
+    const R t = w * q5;
     p[3] -= fma(R(0.5), t, mq);
     const R cr = fma(R(2.5) * t, q2, mq3);
     p[0] = fma(cr, rx, fma(-q5, qr0, p[0]));
@@ -157,10 +168,12 @@ __device__ __forceinline__ void pair_mono2(f2 sx, f2 sy, f2 sz, f2 m, f2 nx, f2 
     A.v[2] = f2fma(mq3, rz, A.v[2]);
 }
 
-// Two quadrupole cells against one target (the fields of -Q as above);
+// Two quadrupole cells against one target: the law of pair_quad with the
+// fields of -Q, n = -Q r and u = r.n + B_2 eps^2 = -w (te = B_2 eps^2):
+//   phi -= m q - (1/2) u q^5,  a += (m q^3 - (5/2) u q^7) r + q^5 n;
 // mhalf = (-1/2, -1/2), m5half = (-5/2, -5/2).
 __device__ __forceinline__ void pair_quad2(f2 sx, f2 sy, f2 sz, f2 m, f2 nqxx, f2 nqyy, f2 nqzz, f2 nqxy, f2 nqxz,
-                                           f2 nqyz, f2 nx, f2 ny, f2 nz, f2 e2, f2 mhalf, f2 m5half, Acc2& A)
+                                           f2 nqyz, f2 te, f2 nx, f2 ny, f2 nz, f2 e2, f2 mhalf, f2 m5half, Acc2& A)
 {
     const f2 rx = f2add(sx, nx), ry = f2add(sy, ny), rz = f2add(sz, nz);
     const f2 r2 = f2fma(rx, rx, f2fma(ry, ry, f2fma(rz, rz, e2)));
@@ -171,7 +184,7 @@ __device__ __forceinline__ void pair_quad2(f2 sx, f2 sy, f2 sz, f2 m, f2 nqxx, f
     const f2 n0 = f2fma(nqxx, rx, f2fma(nqxy, ry, f2mul(nqxz, rz)));
     const f2 n1 = f2fma(nqxy, rx, f2fma(nqyy, ry, f2mul(nqyz, rz)));
     const f2 n2 = f2fma(nqxz, rx, f2fma(nqyz, ry, f2mul(nqzz, rz)));
-    const f2 u = f2fma(rx, n0, f2fma(ry, n1, f2mul(rz, n2)));
+    const f2 u = f2fma(rx, n0, f2fma(ry, n1, f2fma(rz, n2, te)));
     const f2 q5 = f2mul(q, f2mul(q2, q2));
     const f2 tu = f2mul(u, q5);
     A.v[3] = f2add(A.v[3], f2fma(mhalf, tu, mq));
@@ -179,6 +192,73 @@ __device__ __forceinline__ void pair_quad2(f2 sx, f2 sy, f2 sz, f2 m, f2 nqxx, f
     A.v[0] = f2fma(cr, rx, f2fma(q5, n0, A.v[0]));
     A.v[1] = f2fma(cr, ry, f2fma(q5, n1, A.v[1]));
     A.v[2] = f2fma(cr, rz, f2fma(q5, n2, A.v[2]));
+}
+
+// Pair records of the packed kernels (k_force_warp2 and the walk fused with
+// the force): two consecutive entries of a tile, each field a float pair
+// (entry 2m, entry 2m + 1) so that it loads straight into the 64-bit
+// operand of a packed instruction.  A particle record holds x | y | z | m
+// (32 bytes); a cell record also the negated quadrupole and B_2 eps^2
+// (96 bytes, the last float pair unused).  Coordinates are relative to the
+// group centre.
+constexpr int kPartRecF4 = 2;  // 16-byte slots per particle record
+constexpr int kCellRecF4 = 6;  // 16-byte slots per cell record
+
+// Writes pair record m of a tile from the two entries' centre-relative
+// positions x, y, z, masses w and (cells) quadrupoles qa = (xx, yy, zz, xy),
+// qb = (xz, yz, B_2, -), with e2 the group's softening^2.
+__device__ __forceinline__ void put_rec2(float4* rec, int m, bool cellq, const float x[2], const float y[2],
+                                         const float z[2], const float w[2], const float4 qa[2], const float4 qb[2],
+                                         float e2)
+{
+    if (cellq) {
+        float4* r = rec + kCellRecF4 * m;
+        r[0] = make_float4(x[0], x[1], y[0], y[1]);
+        r[1] = make_float4(z[0], z[1], w[0], w[1]);
+        r[2] = make_float4(-qa[0].x, -qa[1].x, -qa[0].y, -qa[1].y);
+        r[3] = make_float4(-qa[0].z, -qa[1].z, -qa[0].w, -qa[1].w);
+        r[4] = make_float4(-qb[0].x, -qb[1].x, -qb[0].y, -qb[1].y);
+        r[5] = make_float4(qb[0].z * e2, qb[1].z * e2, 0.f, 0.f);
+    } else {
+        float4* r = rec + kPartRecF4 * m;
+        r[0] = make_float4(x[0], x[1], y[0], y[1]);
+        r[1] = make_float4(z[0], z[1], w[0], w[1]);
+    }
+}
+
+// Evaluates niter pair records per lane subset (records js, js + nsub, ...)
+// against the lane's IB targets (nx, ny, nz = minus the target's
+// centre-relative coordinates, as float pairs), accumulating into P2.
+template <int IB, int UNROLL>
+__device__ __forceinline__ void eval_cells2(const float4* rec, int js, int nsub, int niter, const f2 nx[IB],
+                                            const f2 ny[IB], const f2 nz[IB], f2 e2, Acc2 P2[IB])
+{
+    const f2 mhalf = f2pack(-0.5f, -0.5f), m5half = f2pack(-2.5f, -2.5f);
+    const ulonglong2* __restrict__ r = reinterpret_cast<const ulonglong2*>(rec) + kCellRecF4 * js;
+    const int S = kCellRecF4 * nsub;
+#pragma unroll UNROLL
+    for (int n = 0; n < niter; ++n, r += S) {
+        const ulonglong2 a = r[0], b = r[1], c = r[2], d = r[3], e = r[4];
+        const f2 te = r[5].x;
+#pragma unroll
+        for (int k = 0; k < IB; ++k)
+            pair_quad2(a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, e.x, e.y, te, nx[k], ny[k], nz[k], e2, mhalf, m5half,
+                       P2[k]);
+    }
+}
+
+template <int IB, int UNROLL>
+__device__ __forceinline__ void eval_parts2(const float4* rec, int js, int nsub, int niter, const f2 nx[IB],
+                                            const f2 ny[IB], const f2 nz[IB], f2 e2, Acc2 P2[IB])
+{
+    const ulonglong2* __restrict__ r = reinterpret_cast<const ulonglong2*>(rec) + kPartRecF4 * js;
+    const int S = kPartRecF4 * nsub;
+#pragma unroll UNROLL
+    for (int n = 0; n < niter; ++n, r += S) {
+        const ulonglong2 a = r[0], b = r[1];
+#pragma unroll
+        for (int k = 0; k < IB; ++k) pair_mono2(a.x, a.y, b.x, b.y, nx[k], ny[k], nz[k], e2, P2[k]);
+    }
 }
 
 // Merges the compensated sums (S, C) of a warp's nsub lane subsets into the

@@ -78,6 +78,12 @@ __device__ __forceinline__ float w_m4(float q)
     return q <= 0.5f ? inner : (q < 1.0f ? 2.0f * a * a * a : 0.0f);
 }
 
+// Partial slots [slot0, slot0 + n) lie inside sys.partial.
+__device__ __forceinline__ bool sph_slots_fit(const otoo_dev_system& sys, int64_t slot0, int64_t n)
+{
+    return slot0 >= 0 && n >= 0 && (slot0 + n) * sys.n_crit_max * 4 <= sys.partial_doubles;
+}
+
 template <int IB>
 __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const float4* __restrict__ rec,
                                                       double* __restrict__ rho)
@@ -100,7 +106,7 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
             ok = it.i0 >= 0 && it.ni >= 1 && it.ni <= 32 * IB && it.i0 + it.ni <= g.count && it.j0 >= 0 &&
                  it.j0 <= it.j1 && it.j1 <= len && g.list_off >= 0 && g.list_off + len <= sys.n_list &&
                  g.first >= 0 && (int64_t)g.first + g.count <= sys.n_part &&
-                 (it.slot < 0 || g.count <= sys.n_crit_max);
+                 (it.slot < 0 || (g.count <= sys.n_crit_max && sph_slots_fit(sys, it.slot, 1)));
         }
         if (!ok) {
             if (lane == 0) atomicOr(counter + 1, kBadItem);
@@ -124,9 +130,9 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
             if (active && k < it.ni) {
                 float4 a, b;
                 ld256x2(rec + 2 * ((int64_t)g.first + it.i0 + k), a, b);
-                xi[r] = (a.x - cx) + b.x;
-                yi[r] = (a.y - cy) + b.y;
-                zi[r] = (a.z - cz) + b.z;
+                xi[r] = rel32(a.x, b.x, cx);
+                yi[r] = rel32(a.y, b.y, cy);
+                zi[r] = rel32(a.z, b.z, cz);
                 blo[0] = fminf(blo[0], xi[r]), bhi[0] = fmaxf(bhi[0], xi[r]);
                 blo[1] = fminf(blo[1], yi[r]), bhi[1] = fmaxf(bhi[1], yi[r]);
                 blo[2] = fminf(blo[2], zi[r]), bhi[2] = fmaxf(bhi[2], zi[r]);
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
                     float4 a, b;
                     ld256x2(rec + 2 * (int64_t)e, a, b);
                     ih = b.w;
-                    p = make_float4((a.x - cx) + b.x, (a.y - cy) + b.y, (a.z - cz) + b.z, a.w);
+                    p = make_float4(rel32(a.x, b.x, cx), rel32(a.y, b.y, cy), rel32(a.z, b.z, cz), a.w);
                     // distance from the entry to the target box against its
                     // support: kept unless d >= (1 + 2^-10) h, where every
                     // target's q = r / h exceeds 1 even after rounding
@@ -237,7 +243,7 @@ __global__ void k_density_merge(otoo_dev_system sys, double* __restrict__ rho)
     const int lane = threadIdx.x & 31;
     if (wid >= sys.n_splits) return;
     const otoo_split sp = sys.splits[wid];
-    if (sp.g < 0 || sp.g >= sys.n_groups || sp.slot0 < 0 || sp.n_chunks < 1) {
+    if (sp.g < 0 || sp.g >= sys.n_groups || sp.n_chunks < 1 || !sph_slots_fit(sys, sp.slot0, sp.n_chunks)) {
         if (lane == 0) atomicOr(sys.counter + 1, kBadItem);
         return;
     }
@@ -337,8 +343,8 @@ int otoo_sph_density(const otoo_dev_system* sys, const float* h, double* rho, co
                  "otoo_sph_density: NULL device array");
     OTOO_REQUIRE(sys->n_part >= 1 && sys->n_groups >= 1 && sys->n_items >= 0 && sys->n_crit_max >= 1, OTOO_EINVAL,
                  "otoo_sph_density: bad sizes");
-    OTOO_REQUIRE(sys->n_splits == 0 || (sys->splits && sys->partial), OTOO_EINVAL,
-                 "otoo_sph_density: split lists need splits and partial");
+    OTOO_REQUIRE(sys->n_splits == 0 || (sys->splits && sys->partial && sys->partial_doubles >= 4 * (int64_t)sys->n_crit_max),
+                 OTOO_EINVAL, "otoo_sph_density: split lists need splits and partial scratch");
     const int ib = tune->iblock;
     OTOO_REQUIRE(ib == 1 || ib == 2 || ib == 4, OTOO_EINVAL, "otoo_sph_density: iblock must be 1, 2 or 4");
     OTOO_REQUIRE((reinterpret_cast<uintptr_t>(sys->split) & 31) == 0, OTOO_EINVAL,

@@ -643,7 +643,8 @@ __global__ void k_records(RecArgs ra, const Geom* __restrict__ g, Cells c, Momen
     qd.xy = u ? (float)(3.0 * cm[3]) : 0.f;
     qd.xz = u ? (float)(3.0 * cm[4]) : 0.f;
     qd.yz = u ? (float)(3.0 * cm[5]) : 0.f;
-    qd.pad0 = qd.pad1 = 0.f;
+    qd.b2 = u ? (float)tr : 0.f;
+    qd.pad = 0.f;
     quad[cell] = qd;
     const double dm = __longlong_as_double((long long)mo.dmax2[cell]);
     const double rb = ra.mac == OTOO_MAC_SW    ? sw_radius(mo.b2[cell], __dsqrt_rn(dm), m, ra.delta, ra.m_limit, g->S)

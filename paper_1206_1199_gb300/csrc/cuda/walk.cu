@@ -616,7 +616,7 @@ template <int IB>
 __device__ __forceinline__ void fuse_tile(const WalkArgs& a, const FuseArgs& f, const int32_t* buf, int cnt, bool cell,
                                           float4* rec, int lane, int nsub, int js, bool active, float cx, float cy,
                                           float cz, const f2 nx[IB], const f2 ny[IB], const f2 nz[IB], f2 e2,
-                                          Acc<float> acc[IB], uint32_t* status)
+                                          float eps2, Acc<float> acc[IB], uint32_t* status)
 {
     const bool cq = cell && f.quad != nullptr;
     const int npair = (cnt + 1) / 2;
@@ -653,60 +653,26 @@ __device__ __forceinline__ void fuse_tile(const WalkArgs& a, const FuseArgs& f, 
         float x[2], y[2], z[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            x[h] = (hh[h].x - cx) + ll[h].x;
-            y[h] = (hh[h].y - cy) + ll[h].y;
-            z[h] = (hh[h].z - cz) + ll[h].z;
+            x[h] = rel32(hh[h].x, ll[h].x, cx);
+            y[h] = rel32(hh[h].y, ll[h].y, cy);
+            z[h] = rel32(hh[h].z, ll[h].z, cz);
         }
-        if (cq) {
-            float4* r = rec + 5 * m;
-            r[0] = make_float4(x[0], x[1], y[0], y[1]);
-            r[1] = make_float4(z[0], z[1], hh[0].w, hh[1].w);
-            // qa = (xx, yy, zz, xy), qb = (xz, yz, -, -), stored negated
-            r[2] = make_float4(-qa[0].x, -qa[1].x, -qa[0].y, -qa[1].y);
-            r[3] = make_float4(-qa[0].z, -qa[1].z, -qa[0].w, -qa[1].w);
-            r[4] = make_float4(-qb[0].x, -qb[1].x, -qb[0].y, -qb[1].y);
-        } else {
-            float4* r = rec + 2 * m;
-            r[0] = make_float4(x[0], x[1], y[0], y[1]);
-            r[1] = make_float4(z[0], z[1], hh[0].w, hh[1].w);
-        }
+        const float w[2] = {hh[0].w, hh[1].w};
+        put_rec2(rec, m, cq, x, y, z, w, qa, qb, eps2);
     }
     __syncwarp();
     if (active) {
-        const f2 mhalf = f2pack(-0.5f, -0.5f), m5half = f2pack(-2.5f, -2.5f), zero2 = f2pack(0.f, 0.f);
+        const f2 zero2 = f2pack(0.f, 0.f);
         Acc2 P2[IB];
 #pragma unroll
         for (int k = 0; k < IB; ++k) P2[k].v[0] = P2[k].v[1] = P2[k].v[2] = P2[k].v[3] = zero2;
         const int niter = npair_pad / nsub;
         // loops not unrolled: the walk and the evaluation alternate in one
         // warp and must fit the instruction cache together
-        if (cq) {
-            const float4* __restrict__ r = rec + 5 * js;
-            const int S = 5 * nsub;
-#pragma unroll 1
-            for (int n = 0; n < niter; ++n, r += S) {
-                const float4 v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4];
-                const f2 sx = f2pack(v0.x, v0.y), sy = f2pack(v0.z, v0.w), sz = f2pack(v1.x, v1.y);
-                const f2 sm = f2pack(v1.z, v1.w);
-                const f2 qxx = f2pack(v2.x, v2.y), qyy = f2pack(v2.z, v2.w), qzz = f2pack(v3.x, v3.y);
-                const f2 qxy = f2pack(v3.z, v3.w), qxz = f2pack(v4.x, v4.y), qyz = f2pack(v4.z, v4.w);
-#pragma unroll
-                for (int k = 0; k < IB; ++k)
-                    pair_quad2(sx, sy, sz, sm, qxx, qyy, qzz, qxy, qxz, qyz, nx[k], ny[k], nz[k], e2, mhalf, m5half,
-                               P2[k]);
-            }
-        } else {
-            const float4* __restrict__ r = rec + 2 * js;
-            const int S = 2 * nsub;
-#pragma unroll 1
-            for (int n = 0; n < niter; ++n, r += S) {
-                const float4 v0 = r[0], v1 = r[1];
-                const f2 sx = f2pack(v0.x, v0.y), sy = f2pack(v0.z, v0.w), sz = f2pack(v1.x, v1.y);
-                const f2 sm = f2pack(v1.z, v1.w);
-#pragma unroll
-                for (int k = 0; k < IB; ++k) pair_mono2(sx, sy, sz, sm, nx[k], ny[k], nz[k], e2, P2[k]);
-            }
-        }
+        if (cq)
+            eval_cells2<IB, 1>(rec, js, nsub, niter, nx, ny, nz, e2, P2);
+        else
+            eval_parts2<IB, 1>(rec, js, nsub, niter, nx, ny, nz, e2, P2);
 #pragma unroll
         for (int k = 0; k < IB; ++k) {
             float t4[4];
@@ -738,7 +704,7 @@ __global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_
     __shared__ uint32_t stack_s[kFuseWarps][kStack];
     __shared__ int32_t cbuf_s[kFuseWarps][kFuseBuf];
     __shared__ int32_t pbuf_s[kFuseWarps][kFuseBuf];
-    __shared__ float4 rec_s[kFuseWarps][5 * kFuseTP];
+    __shared__ float4 rec_s[kFuseWarps][kCellRecF4 * kFuseTP];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     uint32_t* stk = stack_s[wid];
@@ -781,9 +747,9 @@ __global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_
                 const int64_t t = (int64_t)first + i;
                 const float4 h = __ldg(f.split + 2 * t);
                 const float4 l = __ldg(f.split + 2 * t + 1);
-                x = (h.x - cx) + l.x;
-                y = (h.y - cy) + l.y;
-                z = (h.z - cz) + l.z;
+                x = rel32(h.x, l.x, cx);
+                y = rel32(h.y, l.y, cy);
+                z = rel32(h.z, l.z, cz);
             }
             nx[k] = f2pack(-x, -x);
             ny[k] = f2pack(-y, -y);
@@ -831,7 +797,7 @@ __global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_
                     done += take;
                     while (npb >= TE) {
                         fuse_tile<IB>(a, f, pbuf, TE, false, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2,
-                                      acc, status);
+                                      eps2, acc, status);
                         fuse_shift(pbuf, npb, TE, lane);
                         npb -= TE;
                     }
@@ -839,7 +805,7 @@ __global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_
             }
             walk_push(stk, sp, sc, lt);
             while (nc >= TE) {
-                fuse_tile<IB>(a, f, cbuf, TE, true, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, acc,
+                fuse_tile<IB>(a, f, cbuf, TE, true, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, eps2, acc,
                               status);
                 fuse_shift(cbuf, nc, TE, lane);
                 nc -= TE;
@@ -850,9 +816,9 @@ __global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_
             continue;
         }
         if (nc > 0)
-            fuse_tile<IB>(a, f, cbuf, nc, true, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, acc, status);
+            fuse_tile<IB>(a, f, cbuf, nc, true, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, eps2, acc, status);
         if (npb > 0)
-            fuse_tile<IB>(a, f, pbuf, npb, false, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, acc,
+            fuse_tile<IB>(a, f, pbuf, npb, false, rec, lane, nsub, js, active, cx, cy, cz, nx, ny, nz, e2, eps2, acc,
                           status);
 
         // merge the lane subsets, FP64 outputs in caller order; the self pair

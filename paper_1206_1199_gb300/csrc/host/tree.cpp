@@ -508,7 +508,8 @@ void fill_sources(const otoo_tree* t, int use_quad, otoo_src* src, otoo_quad* qu
             q.xy = u ? (float)qq[3] : 0.f;
             q.xz = u ? (float)qq[4] : 0.f;
             q.yz = u ? (float)qq[5] : 0.f;
-            q.pad0 = q.pad1 = 0.f;
+            q.b2 = u ? (float)t->c_b2[c] : 0.f;
+            q.pad = 0.f;
         }
     }
 }

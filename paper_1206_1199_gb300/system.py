@@ -210,6 +210,7 @@ class DeviceSystem:
         b["split"] = torch.empty(lists.n_src * 8, dtype=torch.float32, device=device)
         s = L.DevSystem()
         s.n_part, s.n_src, s.n_list = lists.n_part, lists.n_src, lists.n_list
+        s.partial_doubles = b["partial"].numel()
         s.n_groups, s.n_items, s.n_splits, s.n_crit_max = lists.n_groups, plan.n_items, plan.n_splits, plan.n_crit_max
         for k in ("src", "quad", "groups", "list", "items", "splits", "perm", "partial", "counter", "split"):
             setattr(s, k, b[k].data_ptr() if b[k] is not None else None)
@@ -667,6 +668,7 @@ class DeviceStep:
                          split=alloc("split", dl.n_src * 8, torch.float32))
         s = L.DevSystem()
         s.n_part, s.n_src, s.n_list = dl.n_part, dl.n_src, dl.n_list
+        s.partial_doubles = self.bufs["partial"].numel()
         s.n_groups, s.n_items, s.n_splits, s.n_crit_max = dl.n_groups, plan.n_items, plan.n_splits, plan.n_crit_max
         for k in ("src", "quad", "groups", "list", "items", "splits", "perm", "partial", "counter", "split"):
             setattr(s, k, self.bufs[k].data_ptr() if self.bufs[k] is not None else None)

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_contract_line():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "65536", "--steps", "2",
-           "--warmup", "1", "--cpu-seconds", "0.5"]
+           "--warmup", "1"]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
@@ -28,13 +28,14 @@ def test_reference_arm_prints_one_contract_line():
     assert d["steps"] == 2 and d["warmup"] == 1 and d["config"]["n"] == 65536
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "groups" in cb["sample"]
+    assert cb["spread"][0] <= cb["value"] <= cb["spread"][1] and cb["repeats"] == 2
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
 
 
 @pytest.mark.gpu
 def test_gpu_arm_prints_one_contract_line():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--n", "65536", "--steps", "3", "--warmup", "3",
-           "--err-targets", "64", "--cpu-seconds", "0.5", "--skip-extras", "--skip-walk", "--skip-sw", "--skip-step",
+           "--err-targets", "64", "--cpu-repeats", "1", "--skip-extras", "--skip-walk", "--skip-sw", "--skip-step",
            "--skip-sph"]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]

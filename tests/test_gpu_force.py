@@ -211,3 +211,52 @@ def test_batch_packed_equals_separate(torch):
     for k, (pos, mass, eps) in enumerate(systems):
         ad, _ = oracle.direct(pos, mass, eps)
         assert np.sqrt(np.mean(rel(a[off[k]:off[k + 1]], ad) ** 2)) < 2e-3
+
+
+def test_partial_slots_past_the_buffer_are_reported(torch):
+    # a work item or a split record whose partial slots reach past
+    # sys.partial_doubles (a stale plan, a wrong size) is skipped and reported
+    # as OTOO_EDEVICE; guard values after the buffer stay as they were
+    pos, mass = ic.plummer(6000, 9)
+    tune = L.default_tune(64)
+    tune.split = 300
+    tree, lists, plan = S.build_system(pos, mass, 0.5, 64, 1e-2, tune=tune)
+    assert plan.n_splits > 0
+    dev = S.DeviceSystem.upload(lists, plan, "cuda")
+    need = plan.partial_doubles
+    per_slot = 4 * plan.n_crit_max
+    n_slots = need // per_slot
+    assert n_slots * per_slot == need
+    sentinel = 12345.0
+    buf = torch.full((need + 8 * per_slot,), sentinel, dtype=torch.float64, device="cuda")
+    dev.struct.partial = buf.data_ptr()
+    dev.struct.partial_doubles = need
+    ref, _ = S.force(dev, precision=L.OTOO_FP32K)  # the healthy plan passes its status check
+    items = plan.items.copy()
+    k = int(np.nonzero(items["slot"] >= 0)[0][0])
+    items["slot"][k] = n_slots  # one slot past the end
+    bad_items = torch.from_numpy(items.view(np.uint8).copy()).cuda()
+    dev.struct.items = bad_items.data_ptr()
+    for prec in (L.OTOO_FP32K, L.OTOO_FP64):
+        with pytest.raises(L.OtooError) as ei:
+            S.force(dev, precision=prec)
+        assert ei.value.code == L.OTOO_EDEVICE
+        assert bool(torch.all(buf[need:] == sentinel))
+    dev.struct.items = dev.bufs["items"].data_ptr()
+    splits = plan.splits.copy()
+    splits["slot0"][0] = n_slots - splits["n_chunks"][0] + 1  # its last chunk lies past the end
+    bad_splits = torch.from_numpy(splits.view(np.uint8).copy()).cuda()
+    dev.struct.splits = bad_splits.data_ptr()
+    with pytest.raises(L.OtooError) as ei:
+        S.force(dev, precision=L.OTOO_FP32K)
+    assert ei.value.code == L.OTOO_EDEVICE
+    assert bool(torch.all(buf[need:] == sentinel))
+    dev.struct.splits = dev.bufs["splits"].data_ptr()
+    # too small a buffer for any split list is refused before launch
+    dev.struct.partial_doubles = per_slot - 1
+    with pytest.raises(L.OtooError) as ei:
+        S.force(dev, precision=L.OTOO_FP32K)
+    assert ei.value.code == L.OTOO_EINVAL
+    dev.struct.partial_doubles = need
+    a, _ = S.force(dev, precision=L.OTOO_FP32K)
+    assert torch.equal(a, ref)

@@ -81,3 +81,46 @@ def test_fullsize_plummer_theta_sweep(theta):
     if theta <= 0.5:
         assert rms <= 2e-3
     assert rms <= {0.3: 1e-4, 0.5: 5e-4, 0.75: 3e-3}[theta]
+
+
+def test_fullsize_batch_of_64_systems():
+    # 64 Plummer / King systems of 2^10..2^18 particles packed into one
+    # ragged buffer and one launch in the bench's tune: every system's FP32
+    # forces against its own FP64 direct sum (min(N, 1024) sampled targets,
+    # RMS <= 2e-3 at theta 0.5), the FP64 form of the same launch beside it;
+    # the packed launch bit-identical to separate launches (a spread of sizes)
+    import torch  # noqa: F401
+    L.load()
+    w = ic.WORKLOADS["batch64"]
+    systems = ic.batch_systems(w["n_sys"], w["seed"])
+    sizes = np.array([len(p) for p, _, _ in systems])
+    assert len(systems) == 64 and sizes.min() >= 2 ** 10 and sizes.max() <= 2 ** 18
+    per = [S.Tree(p, m, w["leaf_size"]).lists(w["theta"], w["n_crit"], e, w["use_quad"]) for p, m, e in systems]
+    packed = S.Lists.pack(per)
+    tune = L.Tune(block=128, iblock=2, tile=256, split=16384, ctas_per_sm=0, packed=1)
+    dev = S.DeviceSystem.upload(packed, packed.plan(tune), "cuda")
+    a32, p32 = S.force(dev, precision=L.OTOO_FP32K, tune=tune)
+    a64, _ = S.force(dev, precision=L.OTOO_FP64, tune=tune)
+    a32, p32, a64 = a32.cpu().numpy(), p32.cpu().numpy(), a64.cpu().numpy()
+    off = packed.sys_part_off
+    rms32, rms64 = [], []
+    for k, (pos, mass, eps) in enumerate(systems):
+        sub = ic.subsample(len(pos), 1024, 300 + k)
+        ad, _ = oracle.direct(pos, mass, eps, targets=sub)
+        d32 = rel(a32[off[k] + sub], ad)
+        d64 = rel(a64[off[k] + sub], ad)
+        rms32.append(np.sqrt(np.mean(d32 * d32)))
+        rms64.append(np.sqrt(np.mean(d64 * d64)))
+    rms32, rms64 = np.array(rms32), np.array(rms64)
+    worst = int(np.argmax(rms32))
+    print("batch64: worst system %d (N = %d) FP32 RMS %.3e, FP64 form %.3e" % (worst, sizes[worst], rms32[worst],
+                                                                              rms64[worst]))
+    assert rms32.max() <= 2e-3
+    # the FP32 form adds arithmetic error only to the tree error of theta
+    assert np.all(np.abs(rms32 - rms64) <= 1e-5 + 1e-2 * rms64)
+    order = np.argsort(sizes)
+    for k in (int(order[0]), int(order[21]), int(order[42]), int(order[-1])):
+        d = S.DeviceSystem.upload(per[k], per[k].plan(tune), "cuda")
+        ak, pk = S.force(d, precision=L.OTOO_FP32K, tune=tune)
+        np.testing.assert_array_equal(a32[off[k]:off[k + 1]], ak.cpu().numpy())
+        np.testing.assert_array_equal(p32[off[k]:off[k + 1]], pk.cpu().numpy())

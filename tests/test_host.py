@@ -50,7 +50,8 @@ def test_struct_sizes_match_header():
 C_STRUCTS = {"Params": "otoo_params", "Tune": "otoo_tune", "Src": "otoo_src", "Quad": "otoo_quad",
              "Group": "otoo_group", "Item": "otoo_item", "Split": "otoo_split", "DevSystem": "otoo_dev_system",
              "ListsView": "otoo_lists_view", "PlanInfo": "otoo_plan_info", "TreeView": "otoo_tree_view",
-             "WCell": "otoo_wcell", "WCell64": "otoo_wcell64", "DevWalk": "otoo_dev_walk", "DevTree": "otoo_devtree"}
+             "WCell": "otoo_wcell", "WCell64": "otoo_wcell64", "DevWalk": "otoo_dev_walk", "DevTree": "otoo_devtree",
+             "ThetaNet": "otoo_theta_net", "ThetaRule": "otoo_theta_rule"}
 
 
 def test_ctypes_layouts_match_the_c_header(tmp_path):

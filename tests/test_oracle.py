@@ -480,3 +480,43 @@ def test_select_theta_wires_the_network_to_the_choice():
     w[-1] = -2.8
     th, _ = om.select_theta(w, feats, grid, -3.0, 0.45)
     assert np.all(th == 0.3)
+
+
+def test_budget_targets_closed_forms():
+    from oracle import mlp as om
+    # equal predictions and lists: every group aims at the RMS target itself
+    t = om.budget_targets([-3.0, -3.0, -3.0], [10, 10, 10], [5, 7, 9], 1e-3, 1.0 / 3, 1.0 / 3)
+    np.testing.assert_allclose(t, -3.0, atol=1e-12)
+    # two groups of equal size, predictions 10^-2 and 10^-4 at theta0, equal
+    # lists, alpha = 1/2: weights 10^-1 and 10^-2; lambda = T / sqrt((10^-2
+    # + 10^-4) / 2), worked by hand for T = 1e-3
+    t = om.budget_targets([-2.0, -4.0], [8, 8], [10, 10], 1e-3, 0.5, 0.0)
+    lam = 1e-3 / np.sqrt((1e-2 + 1e-4) / 2)
+    np.testing.assert_allclose(t, np.log10([lam * 0.1, lam * 0.01]), rtol=0, atol=1e-12)
+    # the list-length exponent: equal predictions, lists of 2^10 and 2^13
+    # with beta = 1/3 give targets in the ratio 2
+    t = om.budget_targets([-3.0, -3.0], [10, 13], [1, 1], 1e-3, 1.0 / 3, 1.0 / 3)
+    np.testing.assert_allclose(t[1] - t[0], np.log10(2.0), atol=1e-12)
+    # always: the particle-weighted RMS of the targets is the RMS target
+    rng = np.random.default_rng(41)
+    y0, ll, n = rng.normal(-3, 1, 50), rng.uniform(5, 14, 50), rng.integers(1, 128, 50)
+    t = om.budget_targets(y0, ll, n, 2e-3, 1.0 / 3, 1.0 / 3)
+    np.testing.assert_allclose(np.sqrt(np.sum(n * 100.0 ** t) / n.sum()), 2e-3, rtol=1e-12)
+
+
+def test_learned_theta_range_and_fallback():
+    # a bias-only network (prediction -3.2 everywhere): groups in range all
+    # pass every angle; a statistic outside [lo, hi] or a NaN gives the
+    # fallback, and the out-of-range groups do not enter lambda
+    from oracle import mlp as om
+    w = np.zeros(om.NP)
+    w[-1] = -3.2
+    feats = np.array([[10.0, 0.5, 1.0, 0.4, -1.0], [11.0, 0.5, 1.0, 0.4, -1.0], [30.0, 0.5, 1.0, 0.4, -1.0],
+                      [10.0, np.nan, 1.0, 0.4, -1.0]])
+    lo, hi = np.full(5, -20.0), np.full(5, 20.0)
+    grid = [0.3, 0.5, 0.7]
+    th, tg = om.learned_theta(w, np.zeros(6), np.ones(6), lo, hi, feats, [4, 4, 4, 4], grid, 0.5, 1e-3, 1.0, 1.0 / 3,
+                              0.0, 0.45)
+    np.testing.assert_array_equal(th, [0.7, 0.7, 0.45, 0.45])
+    np.testing.assert_allclose(tg[:2], -3.0, atol=1e-12)
+    assert np.all(np.isnan(tg[2:]))

@@ -29,7 +29,8 @@ def static_force(dev, precision, tune):
     st = torch.cuda.current_stream()
     L.call("otoo_force_static", ctypes.byref(dev.struct), dev.plan.partial_doubles, acc.data_ptr(), pot.data_ptr(),
            int(precision), ctypes.byref(tune), ctypes.c_void_p(st.cuda_stream))
-    torch.cuda.synchronize()
+    # the status word of the call lives in the library's array too
+    L.call("otoo_force_static_status", ctypes.c_void_p(st.cuda_stream))
     return acc.cpu().numpy(), pot.cpu().numpy()
 
 
@@ -67,3 +68,28 @@ def test_static_scratch_rejects_oversized_step():
         L.call("otoo_force_static", ctypes.byref(dev.struct), cap // 8, dev.bufs["partial"].data_ptr(),
                dev.bufs["partial"].data_ptr(), L.OTOO_FP32K, ctypes.byref(plan.tune), None)
     assert e.value.code == L.OTOO_EINVAL and "scratch" in str(e.value)
+
+
+def test_static_status_reports_slots_past_the_partial_part():
+    # a partial part smaller than the plan needs: the items and splits whose
+    # slots reach past it are skipped, and otoo_force_static_status says so
+    import torch
+    L.load()
+    pos, mass = ic.plummer(10000, 31)
+    tune = L.default_tune(64)
+    tune.split = 1000
+    tree, lists, plan = S.build_system(pos, mass, 0.5, 64, 1e-2, tune=tune)
+    assert plan.partial_doubles > 4 * plan.n_crit_max
+    dev = S.DeviceSystem.upload(lists, plan, "cuda")
+    n = lists.n_part
+    acc = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    pot = torch.zeros((n,), dtype=torch.float64, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L.call("otoo_force_static", ctypes.byref(dev.struct), 4 * plan.n_crit_max, acc.data_ptr(), pot.data_ptr(),
+           L.OTOO_FP32K, ctypes.byref(tune), st)
+    with pytest.raises(L.OtooError) as e:
+        L.call("otoo_force_static_status", st)
+    assert e.value.code == L.OTOO_EDEVICE
+    # the next call clears the status word
+    a, p = static_force(dev, L.OTOO_FP32K, tune)
+    assert np.all(np.isfinite(a))
