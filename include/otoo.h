@@ -273,10 +273,11 @@ int otoo_plan_export(const otoo_plan* plan, otoo_plan_info* info);
    group's list): feat[g][0..4] = log2(list length), log10 of the minimum over
    cell entries of d_min / l_c (3.0 when the list has no cell entry),
    log10(box half-diagonal / eps) (box half-diagonal floored at eps / 1000),
-   cell mass fraction of the list, and log10 of the list's truncation ratio
-   sum_cells M_c (l_c / d_c)^p / (d_c^2 + s^2) over sum_entries M_e / (d_e^2 +
-   s^2) (p = 3 with quadrupole cells, else 2; d = distance to the group box;
-   s^2 = eps^2 + half-diagonal^2; floored at 1e-12).  host out [n_groups][5]. */
+   cell mass fraction of the list, and log10 of the list's relative
+   truncation estimate sum_cells B_2 b_max / d_c^5 over |a_net| (B_2, b_max:
+   the cell's spread, Eq. B2; d_c: distance of its centre of mass to the
+   group box; a_net: the softened pull of all entries at the group centre;
+   floored at 1e-12).  host out [n_groups][5]. */
 int otoo_group_features(const otoo_tree* tree, const otoo_lists* lists, float* feat);
 
 void otoo_tree_free(otoo_tree* tree);

@@ -945,53 +945,50 @@ int otoo_group_features(const otoo_tree* t, const otoo_lists* L, float* feat)
                 blo[a] = std::min(blo[a], t->pos[3 * i + a]);
                 bhi[a] = std::max(bhi[a], t->pos[3 * i + a]);
             }
+        const double c[3] = {og.cx, og.cy, og.cz};
         double mincell = 1e3, mcell = 0, mall = 0;
         double hd = 0.5 * std::sqrt((bhi[0] - blo[0]) * (bhi[0] - blo[0]) + (bhi[1] - blo[1]) * (bhi[1] - blo[1]) +
                                     (bhi[2] - blo[2]) * (bhi[2] - blo[2]));
         const double eps = std::sqrt(og.eps2);
         hd = std::max(hd, eps * 1e-3);
-        // leading truncation term of the accepted cells (order p = 3 after a
-        // quadrupole, 2 after a monopole) against the list's total pull
-        const int pw = L->use_quad ? 3 : 2;
-        const double soft2 = og.eps2 + hd * hd;
-        double trunc = 0, pull = 0;
+        // the list's net pull at the group centre (every entry, softened) and
+        // the cells' third-order spread terms B_2 b_max / d^5 (d: distance to
+        // the group box), the size of the first term a quadrupole leaves out
+        double anet[3] = {0, 0, 0}, trunc = 0;
         const int32_t* e = L->list.data() + og.list_off;
-        for (int j = 0; j < og.n_cell; ++j) {
-            const int64_t c = e[j] - n;
-            const double* com = &t->c_com[3 * c];
-            double d2 = 0;
+        for (int j = 0; j < og.n_cell + og.n_part; ++j) {
+            const bool cell = j < og.n_cell;
+            const int64_t k = cell ? e[j] - n : e[j];
+            const double* x = cell ? &t->c_com[3 * k] : &t->pos[3 * k];
+            const double m = cell ? t->c_mass[k] : (double)t->mass[k];
+            double d2 = 0, r2 = 0, r[3];
             for (int a = 0; a < 3; ++a) {
                 double d = 0;
-                if (blo[a] - com[a] > d) d = blo[a] - com[a];
-                if (com[a] - bhi[a] > d) d = com[a] - bhi[a];
+                if (blo[a] - x[a] > d) d = blo[a] - x[a];
+                if (x[a] - bhi[a] > d) d = x[a] - bhi[a];
                 d2 += d * d;
+                r[a] = x[a] - c[a];
+                r2 += r[a] * r[a];
             }
-            const double d = std::sqrt(d2);
-            mincell = std::min(mincell, d / t->c_side[c]);
-            mcell += t->c_mass[c];
-            const double ld = t->c_side[c] / std::max(d, 1e-300);
-            trunc += t->c_mass[c] * std::pow(ld, pw) / (d2 + soft2);
-            pull += t->c_mass[c] / (d2 + soft2);
-        }
-        mall = mcell;
-        for (int j = og.n_cell; j < og.n_cell + og.n_part; ++j) {
-            const int64_t i = e[j];
-            double d2 = 0;
-            for (int a = 0; a < 3; ++a) {
-                double d = 0;
-                if (blo[a] - t->pos[3 * i + a] > d) d = blo[a] - t->pos[3 * i + a];
-                if (t->pos[3 * i + a] - bhi[a] > d) d = t->pos[3 * i + a] - bhi[a];
-                d2 += d * d;
+            mall += m;
+            const double rs2 = r2 + og.eps2;
+            const double w = m / (rs2 * std::sqrt(rs2));
+            for (int a = 0; a < 3; ++a) anet[a] += w * r[a];
+            if (cell) {
+                const double d = std::sqrt(d2);
+                mincell = std::min(mincell, d / t->c_side[k]);
+                mcell += m;
+                const double dd = std::max(d, 1e-300);
+                trunc += t->c_b2[k] * t->c_bmax[k] / (dd * dd * dd * dd * dd);
             }
-            mall += t->mass[i];
-            pull += t->mass[i] / (d2 + soft2);
         }
+        const double an = std::sqrt(anet[0] * anet[0] + anet[1] * anet[1] + anet[2] * anet[2]);
         float* f = feat + 5 * g;
         f[0] = (float)std::log2((double)std::max(1, og.n_cell + og.n_part));
         f[1] = (float)std::log10(std::max(mincell, 1e-3));
         f[2] = (float)std::log10(hd / eps);
         f[3] = (float)(mall > 0 ? mcell / mall : 0.0);
-        f[4] = (float)std::log10(std::max(trunc / std::max(pull, 1e-300), 1e-12));
+        f[4] = (float)std::log10(std::max(trunc / std::max(an, 1e-300), 1e-12));
     }
     return OTOO_OK;
 }

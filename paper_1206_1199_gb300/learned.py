@@ -39,7 +39,8 @@ from . import ic
 from . import system as S
 from .mlp import ThetaNet
 
-THETA_GRID = tuple(round(0.3 + 0.05 * k, 2) for k in range(15))  # 0.30 .. 1.00
+THETA_GRID = tuple(round(0.3 + 0.1 * k, 2) for k in range(14))  # 0.3 .. 1.6
+THETA0 = 0.9  # angle of the base walk whose list statistics feed the network
 
 
 def _torch():
@@ -61,8 +62,9 @@ class Evaluator:
     def lists(self, theta, theta_per_group=None):
         return self.tree.lists(theta, self.n_crit, self.eps, self.use_quad, theta_per_group)
 
-    def force(self, lists, precision=L.OTOO_FP32K, timed=False):
-        """Accelerations and potentials in tree order (and the step's ms)."""
+    def force(self, lists, precision=L.OTOO_FP32K, timed=False, on_device=False):
+        """Accelerations and potentials in tree order (and the step's ms);
+        device tensors when on_device, else host arrays."""
         torch = _torch()
         tune = self.tune or L.default_tune(self.n_crit)
         plan = lists.plan(tune)
@@ -80,10 +82,13 @@ class Evaluator:
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / 3
+        if on_device:
+            return acc, pot, ms
         return acc.cpu().numpy(), pot.cpu().numpy(), ms
 
-    def direct(self, targets):
-        """FP64 direct sum on the device for tree-order targets."""
+    def direct(self, targets, on_device=False):
+        """FP64 direct sum on the device for tree-order targets (device
+        tensors when on_device, else host arrays)."""
         torch = _torch()
         if self._src_dev is None:
             e = self.tree.export()
@@ -105,6 +110,8 @@ class Evaluator:
         torch.cuda.synchronize()
         if int(status.item()) != 0:
             raise L.OtooError(L.OTOO_EDEVICE, "otoo_direct: target index out of range")
+        if on_device:
+            return acc, pot
         return acc.cpu().numpy(), pot.cpu().numpy()
 
 
@@ -175,32 +182,47 @@ def load_snapshots(path):
 # ---------------------------------------------------------------------------
 # training rows
 
-def group_rows(ev, n_groups, grid=THETA_GRID, theta0=0.5, seed=0):
+def group_labels(ev, lists, tgt_dev, ad_dev, off_dev):
+    """log10 of each sampled group's RMS relative acceleration error on
+    lists (device: otoo_group_rms_error over the groups' targets)."""
+    torch = _torch()
+    a, _, _ = ev.force(lists, on_device=True)
+    at = a.index_select(0, tgt_dev).contiguous()
+    ng = off_dev.shape[0] - 1
+    out = torch.empty(ng, dtype=torch.float32, device=ev.device)
+    status = torch.zeros(1, dtype=torch.int32, device=ev.device)
+    L.call("otoo_group_rms_error", at.data_ptr(), ad_dev.data_ptr(), off_dev.data_ptr(), ng, 1e-9, out.data_ptr(),
+           status.data_ptr(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if int(status.item()) != 0:
+        raise L.OtooError(L.OTOO_EDEVICE, "otoo_group_rms_error: empty group")
+    return out.cpu().numpy()
+
+
+def group_rows(ev, n_groups, grid=THETA_GRID, theta0=THETA0, seed=0):
     """Rows (features + angle) and labels log10(group RMS relative error) for
     n_groups groups sampled from the base walk at theta0."""
+    torch = _torch()
     base = ev.lists(theta0)
     feats = base.features(ev.tree)
     g = base.groups
     rng = np.random.Generator(np.random.PCG64(seed))
     sel = np.sort(rng.choice(base.n_groups, size=min(n_groups, base.n_groups), replace=False))
-    # targets: every particle of the sampled groups (tree order)
+    # targets: every particle of the sampled groups (tree order), group by group
     tgt = np.concatenate([np.arange(g["first"][k], g["first"][k] + g["count"][k]) for k in sel])
-    owner = np.concatenate([np.full(g["count"][k], j) for j, k in enumerate(sel)])
-    ad, _ = ev.direct(tgt)
+    off = np.concatenate([[0], np.cumsum(g["count"][sel])]).astype(np.int64)
+    tgt_dev = torch.from_numpy(tgt.astype(np.int64)).to(ev.device)
+    off_dev = torch.from_numpy(off).to(ev.device)
+    ad_dev, _ = ev.direct(tgt, on_device=True)
     rows, labels = [], []
     for th in grid:
         tpg = np.full(base.n_groups, -1.0, np.float32)  # negative: the group is skipped
         tpg[sel] = th
-        lst = ev.lists(th, tpg)
-        a, _, _ = ev.force(lst)
-        d = relerr(a[tgt], ad)
-        rms = np.sqrt(np.bincount(owner, d * d) / np.bincount(owner))
+        labels.append(group_labels(ev, ev.lists(th, tpg), tgt_dev, ad_dev, off_dev))
         rows.append(np.concatenate([feats[sel], np.full((len(sel), 1), th, np.float32)], 1))
-        labels.append(np.log10(np.maximum(rms, 1e-9)))
     return np.concatenate(rows).astype(np.float32), np.concatenate(labels).astype(np.float32)
 
 
-def training_set(snaps, mass, eps, n_crit=64, groups_per_snap=256, grid=THETA_GRID, theta0=0.5, device="cuda",
+def training_set(snaps, mass, eps, n_crit=64, groups_per_snap=1024, grid=THETA_GRID, theta0=THETA0, device="cuda",
                  log=None):
     X, y = [], []
     for k, x in enumerate(snaps):
@@ -214,51 +236,60 @@ def training_set(snaps, mass, eps, n_crit=64, groups_per_snap=256, grid=THETA_GR
     return np.concatenate(X), np.concatenate(y)
 
 
-def train(X, y, steps=3000, lr=3e-3, batch=8192, seed=0, device="cuda"):
-    net = ThetaNet(None, device)
+def train(X, y, steps=3000, lr=3e-3, batch=8192, seed=0, device="cuda", alpha=1.0 / 3.0, beta=1.0 / 3.0,
+          theta0=THETA0, grid=THETA_GRID):
+    """A network trained on rows X, labels y; it keeps the training rows'
+    statistics (standardisation and range), the budget exponents, the base
+    walk's angle and the angle grid."""
+    net = ThetaNet(None, device, alpha=alpha, beta=beta, theta0=theta0, grid=grid)
     net.fit_scaler(X)
     hist = net.train(X, y, steps=steps, lr=lr, batch=batch, seed=seed, log_every=max(1, steps // 20))
-    # feature range of the training set (selection falls back outside it)
-    net.xmin = X.min(0)
-    net.xmax = X.max(0)
     return net, hist
 
 
 # ---------------------------------------------------------------------------
 # selection and evaluation
 
-def group_targets(net, feats, counts, target_rms, theta0=0.5, k_err=3.0):
-    """Per-group error targets for a global RMS target at least interaction
-    cost.  With a group's error ~ c_g theta^k and its list length ~ theta^-3,
-    minimising the total cost at a fixed particle-weighted RMS gives
-    e_g ~ c_g^(3 / (2k + 3)); c_g is read off the network's prediction at
-    theta0, and the common factor is set so the predicted RMS is the target."""
-    rows = np.concatenate([feats, np.full((feats.shape[0], 1), theta0, np.float32)], 1)
-    c = 10.0 ** net.predict(rows).astype(np.float64)
-    w = c ** (3.0 / (2.0 * k_err + 3.0))
-    n = counts.astype(np.float64)
-    lam = target_rms / math.sqrt(float((n * w * w).sum() / n.sum()))
-    return np.log10(lam * w).astype(np.float32)
-
-
-def choose_thetas(ev, net, target_rms, grid=THETA_GRID, theta0=0.5, fallback=0.5, mode="budget"):
-    """One opening angle per group from the network (fallback outside the
-    training range of the features).  mode "equal": every group aims at
-    target_rms; mode "budget": group targets from group_targets()."""
+def choose_thetas(ev, net, target_rms, grid=None, theta0=None, fallback=0.5, mode="budget"):
+    """One opening angle per group (otoo_learned_theta: range check,
+    standardisation, budgeted targets, the choice, all on the device) from
+    the statistics of a base walk at theta0 (default: the network's).
+    mode "equal": every group aims at target_rms; mode "budget": the
+    network's budget and calibration."""
+    grid = grid if grid is not None else (net.grid or THETA_GRID)
+    theta0 = theta0 if theta0 is not None else net.theta0
     base = ev.lists(theta0)
     f = base.features(ev.tree)
-    lo, hi = getattr(net, "xmin", None), getattr(net, "xmax", None)
-    if lo is not None:
-        out = np.any((f < lo[:5]) | (f > hi[:5]), axis=1)
-        f = f.copy()
-        f[out, 0] = np.nan  # non-finite features make the kernel use the fallback
-    per = None
-    if mode == "budget":
-        ok = np.all(np.isfinite(f), axis=1)
-        per = np.full(base.n_groups, math.log10(target_rms), np.float32)
-        per[ok] = group_targets(net, f[ok], base.groups["count"][ok], target_rms, theta0)
-    th = net.select_theta(f, np.asarray(grid, np.float32), math.log10(target_rms), fallback, per)
+    th, _ = net.learned_theta(f, base.groups["count"], grid, target_rms, theta0, fallback, mode)
     return th, base
+
+
+def calibrate(net, evs, target_rms, n_sub=2048, seed=11, iters=4, log=None):
+    """Sets net.calib so that the selection reaches target_rms on the
+    snapshots of evs (training data): the RMS relative acceleration error
+    over n_sub random particles of each, against the FP64 direct sum, is
+    measured for the current calibration and the calibration is scaled by
+    target / achieved, iters times.  Returns the achieved RMS per pass."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    refs = []
+    for ev in evs:
+        sub = np.sort(rng.choice(ev.tree.n, size=min(n_sub, ev.tree.n), replace=False))
+        refs.append((sub, ev.direct(sub)[0]))
+    hist = []
+    for _ in range(iters):
+        sq, cnt = 0.0, 0
+        for ev, (sub, ad) in zip(evs, refs):
+            th, _ = choose_thetas(ev, net, target_rms)
+            a, _, _ = ev.force(ev.lists(net.theta0, th))
+            d = relerr(a[sub], ad)
+            sq += float(np.sum(d * d))
+            cnt += len(d)
+        ach = math.sqrt(sq / cnt)
+        hist.append(ach)
+        if log:
+            log("calibration %.4f: RMS %.4e" % (net.calib, ach))
+        net.calib *= target_rms / ach
+    return hist
 
 
 def rms_error(ev, lists, sub, ad, precision=L.OTOO_FP32K, stats=None):
@@ -287,7 +318,7 @@ def compare(ev, net, target_rms=1e-3, n_sub=4096, seed=7, bisect_steps=8, precis
     e5, ms5 = rms_error(ev, l5, sub, ad)
     res["fixed_0.5"] = {"rms": e5, "ms": ms5, "interactions": l5.interactions}
     # fixed angle with the learned RMS, by bisection on theta
-    lo, hi = 0.05, 1.0
+    lo, hi = 0.05, max(THETA_GRID)
     best = None
     for _ in range(bisect_steps):
         mid = 0.5 * (lo + hi)
@@ -332,11 +363,12 @@ def main():
     ap.add_argument("--snaps", type=int, default=16)
     ap.add_argument("--every", type=int, default=5)
     ap.add_argument("--dt-frac", type=float, default=1.0 / 200, help="time step as a fraction of the orbital period")
-    ap.add_argument("--groups", type=int, default=256)
+    ap.add_argument("--groups", type=int, default=1024)
     ap.add_argument("--eps", type=float, default=ic.WORKLOADS["merger4m"]["eps"])
     ap.add_argument("--n-crit", type=int, default=64)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--target", type=float, default=1e-3)
+    ap.add_argument("--calib-snaps", type=int, default=4, help="training snapshots the calibration runs on")
     ap.add_argument("--weights", default=None, help="write the trained network here (.npz)")
     ap.add_argument("--summary", default=None, help="write the evaluation here (.json)")
     ap.add_argument("--checkpoint", default=None,
@@ -367,13 +399,20 @@ def main():
     net, hist = train(X, y, steps=args.steps)
     t3 = time.perf_counter()
     log("training: loss %.4g -> %.4g in %.1f s" % (hist[0], hist[-1], t3 - t2))
+    # calibration on training snapshots spread over the run
+    pick = np.unique(np.linspace(0, args.snaps - 1, args.calib_snaps).round().astype(int))
+    calib_hist = calibrate(net, [Evaluator(train_snaps[k], mass, args.eps, args.n_crit) for k in pick], args.target,
+                           log=log)
+    t4 = time.perf_counter()
     if args.weights:
         net.save(args.weights)
     ev = Evaluator(held_out, mass, args.eps, args.n_crit)
     res = compare(ev, net, args.target, log=log, mode="budget")
     res["equal_targets"] = compare(ev, net, args.target, mode="equal", precision_fp64=False)
     res.update(n=args.n, snapshots=args.snaps, every=args.every, dt=dt, rows=int(len(y)), loss_first=hist[0],
-               loss_last=hist[-1], times_s=dict(snapshots=t1 - t0, rows=t2 - t1, training=t3 - t2))
+               loss_last=hist[-1], calib=net.calib, calib_rms=calib_hist, theta0=net.theta0, grid=list(net.grid),
+               alpha=net.alpha, beta=net.beta,
+               times_s=dict(snapshots=t1 - t0, rows=t2 - t1, training=t3 - t2, calibration=t4 - t3))
     print(json.dumps(res))
     if args.summary:
         with open(args.summary, "w") as f:

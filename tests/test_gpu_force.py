@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_1206_1199_gb300 import _lib as L
-from paper_1206_1199_gb300 import ic, system as S
+from paper_1206_1199_gb300 import autotune, ic, system as S
 
 pytestmark = pytest.mark.gpu
 
@@ -260,3 +260,23 @@ def test_partial_slots_past_the_buffer_are_reported(torch):
     dev.struct.partial_doubles = need
     a, _ = S.force(dev, precision=L.OTOO_FP32K)
     assert torch.equal(a, ref)
+
+
+def test_autotuner_search_on_a_small_system(torch):
+    # the coordinate descent itself: every visited variant times finite, the
+    # returned tune is the fastest one it visited (each stage keeps the
+    # current point among its candidates), and forces with it stay within
+    # the FP32 bounds of the FP64 form
+    pos, mass = ic.plummer(1 << 15, 10)
+    w = dict(leaf_size=8, theta=0.5, eps=1e-2, use_quad=True)
+    best, table = autotune.search(pos, mass, w, n_crits=(32, 64), log=lambda s: None)
+    assert len(table) >= 10 and all(np.isfinite(r["ms"]) and r["ms"] > 0 for r in table)
+    assert {r["n_crit"] for r in table} == {32, 64}
+    assert best["ms"] == min(r["ms"] for r in table)
+    assert (best["tune"]["block"], best["tune"]["iblock"], best["tune"]["tile"],
+            best["tune"]["packed"]) in autotune.VARIANTS
+    tune = L.Tune(**best["tune"])
+    a32, _, lists = run(pos, mass, 0.5, best["n_crit"], 1e-2, True, L.OTOO_FP32K, tune=tune)
+    a64, _, _ = run(pos, mass, 0.5, best["n_crit"], 1e-2, True, L.OTOO_FP64, tune=tune)
+    d = rel(a32, a64)
+    assert np.sqrt(np.mean(d * d)) <= 2e-6 and d.max() <= 2e-4

@@ -11,6 +11,10 @@ from paper_1206_1199_gb300 import system as S
 
 pytestmark = pytest.mark.gpu
 
+# interactions saved by the learned angles at equal RMS error on an
+# independent realisation (measured with the committed network: see DESIGN)
+GAIN_MIN = 1.02
+
 
 @pytest.fixture(scope="module")
 def LR():
@@ -38,7 +42,7 @@ def test_group_labels_match_oracle(LR):
     eps = 1e-4
     ev = LR.Evaluator(pos, mass, eps, n_crit=64)
     grid = (0.3, 0.6, 0.9)
-    X, y = LR.group_rows(ev, 40, grid=grid, seed=3)
+    X, y = LR.group_rows(ev, 40, grid=grid, theta0=0.5, seed=3)
     base = ev.lists(0.5)
     g = base.groups
     perm = base.perm
@@ -61,10 +65,11 @@ def test_group_labels_match_oracle(LR):
         np.testing.assert_array_equal(X[a_i * len(sel):(a_i + 1) * len(sel), 5], np.float32(th))
 
 
-def test_learned_angles_gain_over_fixed_angle(LR):
-    # a network trained on method-generated snapshots of the two-polytrope
-    # system meets the error target with fewer interactions than the fixed
-    # angle that reaches the same RMS error
+def test_training_pipeline_reaches_its_target(LR):
+    # the whole pipeline on a small system: method-generated snapshots, rows,
+    # training on the GPU, calibration on two training snapshots; on a later
+    # snapshot the selection lands near its RMS target (the small system's
+    # statistics are too noisy for a gain)
     pos, mass, vel = LR.merger_ic(1 << 16)
     eps = 4e-4
     dt = LR.orbital_period() / 200
@@ -72,11 +77,33 @@ def test_learned_angles_gain_over_fixed_angle(LR):
     X, y = LR.training_set(snaps[:4], mass, eps, groups_per_snap=128)
     net, hist = LR.train(X, y, steps=1500, batch=4096)
     assert hist[-1] < 0.5 * hist[0]
+    LR.calibrate(net, [LR.Evaluator(snaps[k], mass, eps) for k in (0, 3)], 1e-3, iters=3)
     ev = LR.Evaluator(snaps[4], mass, eps)
-    res = LR.compare(ev, net, target_rms=1e-3, n_sub=2048, precision_fp64=False)
-    assert 0.2e-3 < res["learned"]["rms"] < 3e-3
+    res = LR.compare(ev, net, target_rms=1e-3, n_sub=2048, precision_fp64=False, bisect_steps=6)
+    assert 0.6e-3 < res["learned"]["rms"] < 1.4e-3, res["learned"]
     assert abs(res["fixed_equal_rms"]["rms"] - res["learned"]["rms"]) < 0.25 * res["learned"]["rms"]
-    assert res["gain_interactions"] > 1.0, res
+
+
+def test_trained_network_on_an_independent_realisation(LR):
+    # the committed network (trained on 16 method-generated snapshots of the
+    # N = 2^22 two-polytrope system, calibrated on four of them) on another
+    # realisation of that system: it meets its target, and at equal RMS it
+    # needs fewer interactions than the fixed angle, with a p99 error no worse
+    import os
+
+    from paper_1206_1199_gb300 import ic
+    from paper_1206_1199_gb300.mlp import ThetaNet
+    path = os.path.join(os.path.dirname(LR.__file__), "thetanet_merger4m.npz")
+    net = ThetaNet.load(path)
+    w = ic.WORKLOADS["merger4m"]
+    pos, mass, _ = LR.merger_ic(w["n"], w["seed"] + 100)
+    ev = LR.Evaluator(pos, mass, w["eps"], w["n_crit"])
+    res = LR.compare(ev, net, 1e-3, n_sub=4096, precision_fp64=False, bisect_steps=8)
+    lr, fx = res["learned"], res["fixed_equal_rms"]
+    assert 0.6e-3 <= lr["rms"] <= 1.1e-3, lr
+    assert abs(fx["rms"] - lr["rms"]) < 0.1 * lr["rms"], (fx, lr)
+    assert res["gain_interactions"] >= GAIN_MIN, res
+    assert lr["p99"] <= 1.05 * fx["p99"], (lr, fx)
 
 
 def test_direct_sum_helper_matches_oracle(LR):
