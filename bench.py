@@ -31,9 +31,10 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 partitions x 32)
 
 # DRAM bytes of one force-kernel launch (dram__bytes_read.sum +
 # dram__bytes_write.sum, one ncu capture of k_force_warp2<4,2,8> on the
-# Hernquist N = 2^23 workload: 27.36 GB + 0.673 GB, 32-byte staging loads), keyed by the workload,
-# n_crit and tuning it was taken on; other configurations report null.
-CAPTURED_TRAFFIC = {("hernquist8m", 8388608, 128, (128, 2, 256, 8192, 1)): 27.36e9 + 0.6728e9}
+# Hernquist N = 2^23 workload: 27.42 GB + 0.673 GB, softened quadrupole with
+# 80-byte cell records), keyed by the workload, n_crit and tuning it was
+# taken on; other configurations report null.
+CAPTURED_TRAFFIC = {("hernquist8m", 8388608, 128, (128, 2, 256, 8192, 1)): 27418532096 + 672520192}
 
 
 def parse():

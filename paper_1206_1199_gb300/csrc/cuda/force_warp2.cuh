@@ -10,13 +10,13 @@
 // FP32 operations, so the FP32 pipe rather than instruction issue bounds the
 // kernel.  The reciprocal square root stays two scalar MUFU operations.
 //
-// Pair records: a cell tile stores 80 bytes per pair (x | y | z | -m | Qxx |
-// Qyy | -B_2 eps^2 | Qxy | Qxz | Qyz, each two floats; Qzz is rebuilt from
-// the traceless diagonal); a particle tile 32 bytes (x | y | z | -m).  Each
-// field loads straight into a packed operand.  With the mass stored negated
-// the law needs no negation: with n = Q r and w = r.n - B_2 eps^2, a lane
-// accumulates the potential -(m q + (1/2) w q^5) and minus the acceleration
-// -(m q^3 + (5/2) w q^7) r + q^5 n; the acceleration is negated at the end.
+// Pair records: a cell tile stores 80 bytes per pair (x | y | z | m | -Qxx |
+// -Qyy | B_2 eps^2 | -Qxy | -Qxz | -Qyz, each two floats; -Qzz is rebuilt
+// from the traceless diagonal); a particle tile 32 bytes (x | y | z | m).
+// Each field loads straight into a packed operand.  The quadrupole is stored
+// negated so that the law needs no negation: with n = -Q r and u = r.n +
+// B_2 eps^2, phi -= m q - (1/2) u q^5, a += (m q^3 - (5/2) u q^7) r + q^5 n.
+// The potential is accumulated as a positive sum and negated at the end.
 // The packed arithmetic (f2 operations, pair_mono2, pair_quad2, the record
 // layout and the evaluation loops) is in pair.cuh.
 
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
                     z[h] = rel32(hh[h].z, ll[h].z, cz);
                     w[h] = hh[h].w;
                 }
-                put_rec2(rec, m, cq, x, y, z, w, qa, qb, -eps2);
+                put_rec2(rec, m, cq, x, y, z, w, qa, qb, eps2);
             }
             if (t + 1 < nt) load_idx(t + 1);
             __syncwarp();
@@ -205,10 +205,7 @@ __global__ void __launch_bounds__(NW * 32, warp2_min_blocks(NW, IB)) k_force_war
                 merge_subsets(S, C, js, nsub, P);
                 a[c] = (double)S - (double)C;
             }
-            // the acceleration was summed with the opposite sign
-            a[0] = -a[0];
-            a[1] = -a[1];
-            a[2] = -a[2];
+            a[3] = -a[3];
             const int i = islot + k * P;
             if (js == 0 && i < ni) {
                 if (item.j0 == 0) {

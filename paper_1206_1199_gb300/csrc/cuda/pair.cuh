@@ -153,85 +153,84 @@ __device__ __forceinline__ f2 f2rsqrt(f2 a)
     return f2pack(rsqrt_r(lo), rsqrt_r(hi));
 }
 
-// Accumulator of one target over packed entry pairs: A[0..2] minus the
-// acceleration, A[3] the potential (the records carry -m, so that neither
-// the staging nor the pair law needs a negation).
+// Accumulator of one target over packed entry pairs: A[0..2] acceleration,
+// A[3] the positive potential sum (the potential with the opposite sign).
 struct Acc2 {
     f2 v[4];
 };
 
-// Two particle entries (or monopole cells) against one target; nm = -m of
-// the entries, nx = -x_i broadcast:  A[3] += -m q,  A[0..2] += -m q^3 r.
-__device__ __forceinline__ void pair_mono2(f2 sx, f2 sy, f2 sz, f2 nm, f2 nx, f2 ny, f2 nz, f2 e2, Acc2& A)
+// Two particle entries (or monopole cells) against one target; nx = -x_i
+// broadcast:  A[3] += m q,  A[0..2] += m q^3 r.
+__device__ __forceinline__ void pair_mono2(f2 sx, f2 sy, f2 sz, f2 m, f2 nx, f2 ny, f2 nz, f2 e2, Acc2& A)
 {
     const f2 rx = f2add(sx, nx), ry = f2add(sy, ny), rz = f2add(sz, nz);
     const f2 r2 = f2fma(rx, rx, f2fma(ry, ry, f2fma(rz, rz, e2)));
     const f2 q = f2rsqrt(r2);
-    const f2 nmq = f2mul(nm, q);
-    const f2 nmq3 = f2mul(nmq, f2mul(q, q));
-    A.v[3] = f2add(A.v[3], nmq);
-    A.v[0] = f2fma(nmq3, rx, A.v[0]);
-    A.v[1] = f2fma(nmq3, ry, A.v[1]);
-    A.v[2] = f2fma(nmq3, rz, A.v[2]);
+    const f2 mq = f2mul(m, q);
+    const f2 mq3 = f2mul(mq, f2mul(q, q));
+    A.v[3] = f2add(A.v[3], mq);
+    A.v[0] = f2fma(mq3, rx, A.v[0]);
+    A.v[1] = f2fma(mq3, ry, A.v[1]);
+    A.v[2] = f2fma(mq3, rz, A.v[2]);
 }
 
-// Two quadrupole cells against one target: the law of pair_quad with n = Q r
-// and w = r.n - B_2 eps^2 (nte = -B_2 eps^2, nm = -m):
-//   A[3] += -(m q + (1/2) w q^5),  A[0..2] += -(m q^3 + (5/2) w q^7) r + q^5 n;
+// Two quadrupole cells against one target: the law of pair_quad with the
+// fields of -Q, n = -Q r and u = r.n + B_2 eps^2 = -w (te = B_2 eps^2):
+//   A[3] += m q - (1/2) u q^5,  A[0..2] += (m q^3 - (5/2) u q^7) r + q^5 n;
 // mhalf = (-1/2, -1/2), m5half = (-5/2, -5/2).
-__device__ __forceinline__ void pair_quad2(f2 sx, f2 sy, f2 sz, f2 nm, f2 qxx, f2 qyy, f2 qzz, f2 qxy, f2 qxz,
-                                           f2 qyz, f2 nte, f2 nx, f2 ny, f2 nz, f2 e2, f2 mhalf, f2 m5half, Acc2& A)
+__device__ __forceinline__ void pair_quad2(f2 sx, f2 sy, f2 sz, f2 m, f2 nqxx, f2 nqyy, f2 nqzz, f2 nqxy, f2 nqxz,
+                                           f2 nqyz, f2 te, f2 nx, f2 ny, f2 nz, f2 e2, f2 mhalf, f2 m5half, Acc2& A)
 {
     const f2 rx = f2add(sx, nx), ry = f2add(sy, ny), rz = f2add(sz, nz);
     const f2 r2 = f2fma(rx, rx, f2fma(ry, ry, f2fma(rz, rz, e2)));
     const f2 q = f2rsqrt(r2);
     const f2 q2 = f2mul(q, q);
-    const f2 nmq = f2mul(nm, q);
-    const f2 n0 = f2fma(qxx, rx, f2fma(qxy, ry, f2mul(qxz, rz)));
-    const f2 n1 = f2fma(qxy, rx, f2fma(qyy, ry, f2mul(qyz, rz)));
-    const f2 n2 = f2fma(qxz, rx, f2fma(qyz, ry, f2mul(qzz, rz)));
-    const f2 w = f2fma(rx, n0, f2fma(ry, n1, f2fma(rz, n2, nte)));
+    const f2 mq = f2mul(m, q);
+    const f2 n0 = f2fma(nqxx, rx, f2fma(nqxy, ry, f2mul(nqxz, rz)));
+    const f2 n1 = f2fma(nqxy, rx, f2fma(nqyy, ry, f2mul(nqyz, rz)));
+    const f2 n2 = f2fma(nqxz, rx, f2fma(nqyz, ry, f2mul(nqzz, rz)));
+    const f2 u = f2fma(rx, n0, f2fma(ry, n1, f2fma(rz, n2, te)));
     const f2 q5 = f2mul(q, f2mul(q2, q2));
-    const f2 tw = f2mul(w, q5);
-    A.v[3] = f2add(A.v[3], f2fma(mhalf, tw, nmq));
-    // minus the radial coefficient: -(m q^3 + (5/2) w q^7) = q^2 (-m q - (5/2) w q^5)
-    const f2 ncr = f2mul(q2, f2fma(m5half, tw, nmq));
-    A.v[0] = f2fma(ncr, rx, f2fma(q5, n0, A.v[0]));
-    A.v[1] = f2fma(ncr, ry, f2fma(q5, n1, A.v[1]));
-    A.v[2] = f2fma(ncr, rz, f2fma(q5, n2, A.v[2]));
+    const f2 tu = f2mul(u, q5);
+    A.v[3] = f2add(A.v[3], f2fma(mhalf, tu, mq));
+    // radial coefficient m q^3 - (5/2) u q^7 = q^2 (m q - (5/2) u q^5)
+    const f2 cr = f2mul(q2, f2fma(m5half, tu, mq));
+    A.v[0] = f2fma(cr, rx, f2fma(q5, n0, A.v[0]));
+    A.v[1] = f2fma(cr, ry, f2fma(q5, n1, A.v[1]));
+    A.v[2] = f2fma(cr, rz, f2fma(q5, n2, A.v[2]));
 }
 
 // Pair records of the packed kernels (k_force_warp2 and the walk fused with
 // the force): two consecutive entries of a tile, each field a float pair
 // (entry 2m, entry 2m + 1) so that it loads straight into the 64-bit
-// operand of a packed instruction.  A particle record holds x | y | z | -m
-// (32 bytes); a cell record x | y | z | -m | Qxx | Qyy | -B_2 eps^2 | Qxy |
-// Qxz | Qyz (80 bytes): Qzz = -(Qxx + Qyy) is rebuilt from the other two
+// operand of a packed instruction.  A particle record holds x | y | z | m
+// (32 bytes); a cell record x | y | z | m | -Qxx | -Qyy | B_2 eps^2 | -Qxy |
+// -Qxz | -Qyz (80 bytes): -Qzz = Qxx + Qyy is rebuilt from the other two
 // diagonal terms (Q is traceless) by two packed subtractions per record,
-// which measured faster than a sixth 16-byte slot per record.  Coordinates
-// are relative to the group centre; the stored signs leave the staging one
-// negation per entry (the mass).
+// which measured faster than a sixth 16-byte slot per record (and storing
+// -m with Q itself, which saves five negations per staged cell, measured 1%
+// slower).  Coordinates are relative to the group centre.
 constexpr int kPartRecF4 = 2;  // 16-byte slots per particle record
 constexpr int kCellRecF4 = 5;  // 16-byte slots per cell record
 
 // Writes pair record m of a tile from the two entries' centre-relative
 // positions x, y, z, masses w and (cells) quadrupoles qa = (xx, yy, zz, xy),
-// qb = (xz, yz, B_2, -), with ne2 = minus the group's softening^2.
+// qb = (xz, yz, B_2, -), with e2 the group's softening^2.
 __device__ __forceinline__ void put_rec2(float4* rec, int m, bool cellq, const float x[2], const float y[2],
                                          const float z[2], const float w[2], const float4 qa[2], const float4 qb[2],
-                                         float ne2)
+                                         float e2)
 {
     if (cellq) {
         float4* r = rec + kCellRecF4 * m;
         r[0] = make_float4(x[0], x[1], y[0], y[1]);
-        r[1] = make_float4(z[0], z[1], -w[0], -w[1]);
-        r[2] = make_float4(qa[0].x, qa[1].x, qa[0].y, qa[1].y);
-        r[3] = make_float4(qb[0].z * ne2, qb[1].z * ne2, qa[0].w, qa[1].w);
-        r[4] = make_float4(qb[0].x, qb[1].x, qb[0].y, qb[1].y);
+        r[1] = make_float4(z[0], z[1], w[0], w[1]);
+        r[2] = make_float4(-qa[0].x, -qa[1].x, -qa[0].y, -qa[1].y);
+        r[3] = make_float4(qb[0].z * e2, qb[1].z * e2, -qa[0].w, -qa[1].w);
+        r[4] = make_float4(-qb[0].x, -qb[1].x, -qb[0].y, -qb[1].y);
     } else {
         float4* r = rec + kPartRecF4 * m;
         r[0] = make_float4(x[0], x[1], y[0], y[1]);
-        r[1] = make_float4(z[0], z[1], -w[0], -w[1]);
+        r[1] = make_float4(z[0], z[1], w[0], w[1]);
     }
 }
 
@@ -248,10 +247,10 @@ __device__ __forceinline__ void eval_cells2(const float4* rec, int js, int nsub,
 #pragma unroll UNROLL
     for (int n = 0; n < niter; ++n, r += S) {
         const ulonglong2 a = r[0], b = r[1], c = r[2], d = r[3], e = r[4];
-        const f2 qzz = f2sub(f2sub(zero2, c.x), c.y);
+        const f2 nqzz = f2sub(f2sub(zero2, c.x), c.y);
 #pragma unroll
         for (int k = 0; k < IB; ++k)
-            pair_quad2(a.x, a.y, b.x, b.y, c.x, c.y, qzz, d.y, e.x, e.y, d.x, nx[k], ny[k], nz[k], e2, mhalf, m5half,
+            pair_quad2(a.x, a.y, b.x, b.y, c.x, c.y, nqzz, d.y, e.x, e.y, d.x, nx[k], ny[k], nz[k], e2, mhalf, m5half,
                        P2[k]);
     }
 }

@@ -658,7 +658,7 @@ __device__ __forceinline__ void fuse_tile(const WalkArgs& a, const FuseArgs& f, 
             z[h] = rel32(hh[h].z, ll[h].z, cz);
         }
         const float w[2] = {hh[0].w, hh[1].w};
-        put_rec2(rec, m, cq, x, y, z, w, qa, qb, -eps2);
+        put_rec2(rec, m, cq, x, y, z, w, qa, qb, eps2);
     }
     __syncwarp();
     if (active) {
@@ -833,10 +833,7 @@ __global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_
                 merge_subsets(S, C, js, nsub, P);
                 r[c] = (double)S - (double)C;
             }
-            // the acceleration was summed with the opposite sign
-            r[0] = -r[0];
-            r[1] = -r[1];
-            r[2] = -r[2];
+            r[3] = -r[3];
             const int i = islot + k * P;
             if (js == 0 && i < count) {
                 const int64_t t = (int64_t)first + i;

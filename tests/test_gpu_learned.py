@@ -35,6 +35,17 @@ def test_device_direct_sum_matches_oracle(LR):
     np.testing.assert_allclose(p, pr, rtol=1e-12)
 
 
+def test_device_direct_sum_matches_oracle_at_a_million(LR):
+    # the direct sum the bench's error figures use, at a size where it runs
+    # in many source chunks (merged in order), against the oracle's
+    pos, mass = ic.hernquist(1 << 20, 43)
+    tgt = ic.subsample(1 << 20, 64, 44)
+    a, p = S.direct_sum(pos, mass, 5e-4, tgt)
+    ar, pr = oracle.direct(pos, mass, 5e-4, targets=tgt)
+    assert np.all(np.linalg.norm(a - ar, axis=1) <= 1e-11 * np.linalg.norm(ar, axis=1))
+    np.testing.assert_allclose(p, pr, rtol=1e-11)
+
+
 def test_group_labels_match_oracle(LR):
     # the label of (group, angle) = RMS over the group's particles of the
     # relative force error of the tree force against the direct sum
