@@ -317,9 +317,11 @@ def compare(ev, net, target_rms=1e-3, n_sub=4096, seed=7, bisect_steps=8, precis
     l5 = ev.lists(0.5)
     e5, ms5 = rms_error(ev, l5, sub, ad)
     res["fixed_0.5"] = {"rms": e5, "ms": ms5, "interactions": l5.interactions}
-    # fixed angle with the learned RMS, by bisection on theta
+    # fixed angle with the learned RMS: bisection on theta, then the
+    # interactions and time of the fixed angle interpolated (log-log in the
+    # RMS) between the two bisection points that bracket the learned RMS
     lo, hi = 0.05, max(THETA_GRID)
-    best = None
+    best = above = None
     for _ in range(bisect_steps):
         mid = 0.5 * (lo + hi)
         lm = ev.lists(mid)
@@ -327,11 +329,13 @@ def compare(ev, net, target_rms=1e-3, n_sub=4096, seed=7, bisect_steps=8, precis
         em, msm = rms_error(ev, lm, sub, ad, stats=sm)
         if log:
             log("bisect theta %.4f rms %.3e" % (mid, em))
+        point = (mid, em, msm, lm.interactions, sm)
         if em > e_l:
             hi = mid
+            above = point
         else:
             lo = mid
-            best = (mid, em, msm, lm.interactions, sm)
+            best = point
     if best is None:
         lm = ev.lists(lo)
         sm = {}
@@ -342,8 +346,16 @@ def compare(ev, net, target_rms=1e-3, n_sub=4096, seed=7, bisect_steps=8, precis
         lf = ev.lists(best[0])
         e64, ms64 = rms_error(ev, lf, sub, ad, L.OTOO_FP64)
         res["fp64_equal_rms"] = {"theta": best[0], "rms": e64, "ms": ms64, "interactions": lf.interactions}
-    res["gain_interactions"] = best[3] / learned.interactions
-    res["gain_time"] = best[2] / ms_l
+    inter_eq, ms_eq = float(best[3]), float(best[2])
+    if above is not None and above[1] > best[1] > 0:
+        f = math.log(e_l / best[1]) / math.log(above[1] / best[1])
+        inter_eq = math.exp(math.log(best[3]) + f * math.log(above[3] / best[3]))
+        ms_eq = math.exp(math.log(best[2]) + f * math.log(above[2] / best[2]))
+        res["fixed_bracket_above"] = dict(above[4], theta=above[0], rms=above[1], ms=above[2], interactions=above[3])
+    res["fixed_interpolated"] = {"rms": e_l, "interactions": inter_eq, "ms": ms_eq}
+    res["gain_interactions"] = inter_eq / learned.interactions
+    res["gain_time"] = ms_eq / ms_l
+    res["gain_interactions_bracket"] = best[3] / learned.interactions
     return res
 
 
