@@ -520,3 +520,15 @@ def test_learned_theta_range_and_fallback():
     np.testing.assert_array_equal(th, [0.7, 0.7, 0.45, 0.45])
     np.testing.assert_allclose(tg[:2], -3.0, atol=1e-12)
     assert np.all(np.isnan(tg[2:]))
+
+
+def test_error_statistics_hand_worked():
+    # two targets: reference accelerations (3, 4, 0) and (0, 0, 2); the first
+    # is off by (0.03, 0, 0) (relative 0.03 / 5 = 0.006), the second exact;
+    # potentials -2 and -4, the second off by 0.04 (relative 0.01)
+    ref = np.array([[3.0, 4.0, 0.0], [0.0, 0.0, 2.0]])
+    acc = ref + np.array([[0.03, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    e = oracle.errors(acc, np.array([-2.0, -4.04]), ref, np.array([-2.0, -4.0]))
+    assert abs(e["acc_max"] - 0.006) < 1e-15 and abs(e["acc_mean"] - 0.003) < 1e-15
+    assert abs(e["acc_rms"] - 0.006 / np.sqrt(2)) < 1e-15
+    assert abs(e["pot_max"] - 0.01) < 1e-15 and abs(e["pot_rms"] - 0.01 / np.sqrt(2)) < 1e-15
