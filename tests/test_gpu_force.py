@@ -280,3 +280,45 @@ def test_autotuner_search_on_a_small_system(torch):
     a64, _, _ = run(pos, mass, 0.5, best["n_crit"], 1e-2, True, L.OTOO_FP64, tune=tune)
     d = rel(a32, a64)
     assert np.sqrt(np.mean(d * d)) <= 2e-6 and d.max() <= 2e-4
+
+
+@pytest.mark.parametrize("packed", [0, 1])
+def test_every_form_keeps_the_softened_quadrupole_at_large_eps(torch, packed):
+    # eps = 0.3 on a Plummer sphere: the B_2 eps^2 part of the quadrupole term
+    # moves the tree force by about 1e-3 (the batch configuration's regime),
+    # so the FP64 form must match the oracle tree to 1e-6 and the scalar and
+    # packed FP32 forms the FP64 form to their arithmetic bounds
+    pos, mass = ic.plummer(4096, 71)
+    eps = 0.3
+    r = oracle.Tree(pos, mass, 8, 64).eval(0.5, eps, use_quad=True)
+    a64, p64, lists = run(pos, mass, 0.5, 64, eps, True, L.OTOO_FP64)
+    assert lists.cell_interactions > 0.3 * lists.interactions
+    assert rel(a64, r["acc"]).max() <= 1e-6
+    assert (np.abs(p64 - r["pot"]) / np.abs(r["pot"])).max() <= 1e-6
+    tune = L.Tune(block=128, iblock=2, tile=128, split=100000, ctas_per_sm=0, packed=packed)
+    a32, p32, _ = run(pos, mass, 0.5, 64, eps, True, L.OTOO_FP32K, tune=tune)
+    d = rel(a32, a64)
+    assert np.sqrt(np.mean(d * d)) <= 2e-6 and d.max() <= 2e-4
+    assert (np.abs(p32 - p64) / np.abs(p64)).max() <= 1e-5
+
+
+@pytest.mark.parametrize("iblock", [1, 2, 4])
+def test_largest_groups(torch, iblock):
+    # n_crit at its maximum (1024 particles per group): groups are cut into
+    # work items of at most 32 iblock particles; every form against the
+    # oracle tree (FP64) and the FP64 form (FP32, scalar and packed)
+    pos, mass = ic.plummer(12000, 72)
+    tree = S.Tree(pos, mass, 8)
+    lists = tree.lists(0.5, 1024, 0.01, True)
+    assert lists.groups["count"].max() > 512
+    r = oracle.Tree(pos, mass, 8, 1024).eval(0.5, 0.01, use_quad=True)
+    tune = L.Tune(block=128, iblock=iblock, tile=128, split=4096, ctas_per_sm=0, packed=0)
+    dev = S.DeviceSystem.upload(lists, lists.plan(tune), "cuda")
+    a64, p64 = (x.cpu().numpy() for x in S.force(dev, precision=L.OTOO_FP64, tune=tune))
+    assert rel(a64, r["acc"]).max() <= 1e-6
+    for packed in ((0, 1) if iblock < 4 else (0,)):
+        t32 = L.Tune(block=128, iblock=iblock, tile=128, split=4096, ctas_per_sm=0, packed=packed)
+        d32 = S.DeviceSystem.upload(lists, lists.plan(t32), "cuda")
+        a32, _ = S.force(d32, precision=L.OTOO_FP32K, tune=t32)
+        d = rel(a32.cpu().numpy(), a64)
+        assert np.sqrt(np.mean(d * d)) <= 2e-6 and d.max() <= 2e-4, (iblock, packed)

@@ -141,3 +141,16 @@ def test_fused_rejects_what_it_cannot_do(torch):
     with pytest.raises(L.OtooError) as ei:
         bad(acc, pot)
     assert ei.value.code == L.OTOO_EINVAL
+
+
+def test_fused_keeps_the_softened_quadrupole_at_large_eps(torch):
+    # eps = 0.3: the quadrupole's B_2 eps^2 part is large; the fused kernel
+    # stages it as the split kernels do
+    pos, mass = ic.plummer(4096, 71)
+    t = S.Tree(pos, mass, 8)
+    hl = t.lists(0.5, 64, 0.3, True)
+    a64, p64 = fp64_on_host_lists(hl, 64)
+    fs = S.DeviceTree(t, 64, True).fused(0.5, 0.3, 2)
+    a32, p32 = run_fused(torch, fs, 4096)
+    assert fs.totals() == (hl.n_list, hl.interactions, hl.cell_interactions)
+    check_fp32(a32, p32, a64, p64)

@@ -111,6 +111,10 @@ def test_trained_network_on_an_independent_realisation(LR):
     ev = LR.Evaluator(pos, mass, w["eps"], w["n_crit"])
     res = LR.compare(ev, net, 1e-3, n_sub=4096, precision_fp64=False, bisect_steps=8)
     lr, fx = res["learned"], res["fixed_equal_rms"]
+    print("learned angles on an independent realisation: RMS %.3e (fixed %.3e), gain %.3f interactions, %.3f time, "
+          "p99 %.2e (fixed %.2e), max %.2e (fixed %.2e)" % (lr["rms"], fx["rms"], res["gain_interactions"],
+                                                           res["gain_time"], lr["p99"], fx["p99"], lr["max"],
+                                                           fx["max"]))
     assert 0.6e-3 <= lr["rms"] <= 1.1e-3, lr
     assert abs(fx["rms"] - lr["rms"]) < 0.1 * lr["rms"], (fx, lr)
     assert res["gain_interactions"] >= GAIN_MIN, res
