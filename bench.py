@@ -447,8 +447,8 @@ def run_device_walk(args, dev_name, tree, w, tune, lists, a32, stream, host_walk
     wall = (time.perf_counter() - tw) / k
     med = np.median(np.array(times), axis=0)
     g, hg = dl.groups, lists.groups
-    same = bool(np.array_equal(g["n_cell"], hg["n_cell"]) and np.array_equal(g["n_part"], hg["n_part"])
-                and np.array_equal(g["list_off"], hg["list_off"]))
+    # entry counts per group (the offsets depend on the layout: slots of the one-pass walk)
+    same = bool(np.array_equal(g["n_cell"], hg["n_cell"]) and np.array_equal(g["n_part"], hg["n_part"]))
     rms, mx = rel_err(acc.cpu().numpy(), a32)
     return {"walk_ms": float(med[0]), "plan_ms": float(med[1]), "force_ms": float(med[2]),
             "step_ms": float(med.sum()), "step_wall_ms": wall * 1e3, "steps": k,

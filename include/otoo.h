@@ -505,19 +505,29 @@ int otoo_walk_fill(const otoo_dev_walk* walk, const otoo_group* groups, int32_t*
                    void* stream);
 
 /* The walk in one pass (the steady state of a time loop, where the list
-   sizes of the previous step bound the next): like otoo_walk_count, and each
-   group's entries go to fixed slots, cells to cell_pool[g * cell_cap ...],
-   particles to part_pool[g * part_cap ...] (device pools of n_groups slots);
-   totals[5] counts the groups with more entries than their slots (their
-   entries are cut, their counts and offsets stay exact: follow with
-   otoo_walk_fill instead of otoo_walk_compact).  otoo_walk_compact then
-   copies the slots into the list at the offsets (nothing when totals[5] > 0
-   or the list is shorter than totals[0]: status set). */
-int otoo_walk_single(const otoo_dev_walk* walk, otoo_group* groups, int32_t* cell_pool, int64_t cell_cap,
-                     int32_t* part_pool, int64_t part_cap, void* stream);
-int otoo_walk_compact(const otoo_dev_walk* walk, const otoo_group* groups, const int32_t* cell_pool,
-                      int64_t cell_cap, const int32_t* part_pool, int64_t part_cap, int32_t* list,
-                      int64_t capacity, void* stream);
+   sizes of the previous step bound the next): like otoo_walk_count, but each
+   group's entries go straight to its fixed slot of slots (device, n_groups *
+   (cell_cap + part_cap) int32), and the slots are the list.  Slot g starts
+   at S g, S = cell_cap + part_cap; its cells are written backwards from
+   S g + cell_cap - 1, its particles forwards from S g + cell_cap, so the
+   group's entries lie contiguous, cells (in the reverse of the order
+   otoo_walk_fill writes them) then particles, at list_off = S g + cell_cap -
+   n_cell.  otoo_force and otoo_sph_density take slots as their list with
+   n_list = n_groups S; no offsets are scanned.  totals[5] counts the groups
+   with more entries than their slot: their entries are cut, their counts
+   stay exact and their list_off is -1 (the force kernels reject it); walk
+   again with otoo_walk_count and otoo_walk_fill.  Errors: OTOO_EINVAL
+   (arguments, slot sizes below 1 or S above INT32_MAX).
+
+   otoo_walk_compact copies the slots of a single pass into a dense list in
+   group order, exactly what otoo_walk_count + otoo_walk_fill write (cells
+   back in walk order), and rewrites groups[g].list_off to the dense offsets.
+   list: device, capacity entries; nothing is copied (status word set) when
+   totals[5] > 0 or totals[0] > capacity.  Asynchronous on stream. */
+int otoo_walk_single(const otoo_dev_walk* walk, otoo_group* groups, int32_t* slots, int64_t cell_cap,
+                     int64_t part_cap, void* stream);
+int otoo_walk_compact(const otoo_dev_walk* walk, otoo_group* groups, const int32_t* slots, int64_t cell_cap,
+                      int64_t part_cap, int32_t* list, int64_t capacity, void* stream);
 
 /* The walk fused with the FP32 force (Section III-D: the paper's GPU kernel
    walks the tree for each group of particles and evaluates the interactions

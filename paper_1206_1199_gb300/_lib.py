@@ -177,8 +177,8 @@ _SIGS = {
     "otoo_walk_fill": [ctypes.POINTER(DevWalk), vp, vp, i64, vp],
     "otoo_walk_check_status": [ctypes.POINTER(DevWalk), vp],
     "otoo_walk_force": [ctypes.POINTER(DevWalk), vp, vp, vp, i32, vp, vp, vp],
-    "otoo_walk_single": [ctypes.POINTER(DevWalk), vp, vp, i64, vp, i64, vp],
-    "otoo_walk_compact": [ctypes.POINTER(DevWalk), vp, vp, i64, vp, i64, vp, i64, vp],
+    "otoo_walk_single": [ctypes.POINTER(DevWalk), vp, vp, i64, i64, vp],
+    "otoo_walk_compact": [ctypes.POINTER(DevWalk), vp, vp, i64, i64, vp, i64, vp],
     "otoo_plan_scratch_ints": [i64],
     "otoo_plan_count": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp],
     "otoo_plan_fill": [vp, i32, ctypes.POINTER(Tune), vp, vp, vp, i64, vp, i64, vp, vp],

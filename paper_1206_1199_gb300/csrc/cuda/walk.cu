@@ -455,12 +455,13 @@ __device__ __forceinline__ void walk_push(uint32_t* stk, int& sp, const StepCell
 // levels below any cell), so the stack never overflows.
 // kMode 0: count (group records, totals); 1: fill the list at the offsets
 // of pass 0; 2: single pass -- count as pass 0 and write each group's entries
-// into fixed slots of two pools (cells: list = cell pool, capacity = slot
-// size; particles: ppool, pcap), for otoo_walk_compact.
+// into its fixed slot of list (capacity cells + pcap particles per slot):
+// cells backwards from slot position capacity - 1, particles forwards from
+// capacity, so that they end up contiguous, cells first, and the slots serve
+// as the list (list_off set here; groups that outgrow their slot get -1).
 template <int kMode>
 __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(WalkArgs a, otoo_group* __restrict__ groups,
-                                                          int32_t* __restrict__ list, int64_t capacity,
-                                                          int32_t* __restrict__ ppool, int64_t pcap)
+                                                          int32_t* __restrict__ list, int64_t capacity, int64_t pcap)
 {
     constexpr bool kFill = kMode == 1;
     constexpr bool kCount = kMode != 1;
@@ -497,11 +498,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
         group_walk_setup(a, g, first, count, lane, w);
         int64_t off_c = 0, off_p = 0;
         int32_t want_c = 0, want_p = 0;
-        int32_t* pdst = kMode == 2 ? ppool : list;
         if (kMode == 2) {
-            off_c = (int64_t)g * capacity;
+            // cell r at off_c - r, particle k at off_p + k
+            off_p = (int64_t)g * (capacity + pcap) + capacity;
+            off_c = off_p - 1;
             want_c = (int32_t)capacity;
-            off_p = (int64_t)g * pcap;
             want_p = (int32_t)pcap;
         }
         if (kFill) {
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
                 const unsigned am = __ballot_sync(kFull, sc.kind[h] == 1 && !w.drop);
                 if (kWrite && sc.kind[h] == 1 && !w.drop) {
                     const int32_t r = ncell + __popc(am & lt);
-                    if (r < want_c) list[off_c + r] = (int32_t)(a.n_part + sc.node[h]);
+                    if (r < want_c) list[kMode == 2 ? off_c - r : off_c + r] = (int32_t)(a.n_part + sc.node[h]);
                 }
                 ncell += __popc(am);
             }
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
                 if (kWrite && np > 0) {
                     const int32_t base = npart + pin - np;
                     for (int k = 0; k < np; ++k)
-                        if (base + k < want_p) pdst[off_p + base + k] = sc.pb[h] + k;
+                        if (base + k < want_p) list[off_p + base + k] = sc.pb[h] + k;
                 }
                 npart += __shfl_sync(kFull, pin, 31);
             }
@@ -563,7 +564,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS) k_walk(
                 r.count = count;
                 r.n_cell = ncell;
                 r.n_part = npart;
-                r.list_off = 0;
+                // pass 0: the offsets come from the scan that follows
+                r.list_off = kMode == 2 ? (ncell <= want_c && npart <= want_p ? off_p - ncell : -1) : 0;
                 r.eps2 = a.eps2;
                 r.cx = w.c[0];
                 r.cy = w.c[1];
@@ -857,13 +859,14 @@ __global__ void __launch_bounds__(kFuseWarps * 32, OTOO_FUSE_MIN_BLOCKS) k_walk_
     }
 }
 
-// One warp per group: the group's slots of the two pools (filled by the
-// single pass) copied to its place in the list, cells then particles.
-// Nothing is copied when a group did not fit its slots (totals[5] > 0: the
-// caller runs otoo_walk_fill instead) or when the list is too small.
-__global__ void k_compact(const otoo_group* __restrict__ groups, int32_t G, const int32_t* __restrict__ cpool,
-                          int64_t ccap, const int32_t* __restrict__ ppool, int64_t pcap, int32_t* __restrict__ list,
-                          int64_t capacity, const int64_t* __restrict__ totals, uint32_t* __restrict__ status)
+// One warp per group: the group's slot (filled by the single pass) copied to
+// its place in the dense list (list_off, already rewritten by the scan),
+// cells back in walk order, then particles.  Nothing is copied when a group
+// did not fit its slot (totals[5] > 0: the caller walks again in two passes)
+// or when the list is too small.
+__global__ void k_compact(const otoo_group* __restrict__ groups, int32_t G, const int32_t* __restrict__ slots,
+                          int64_t ccap, int64_t pcap, int32_t* __restrict__ list, int64_t capacity,
+                          const int64_t* __restrict__ totals, uint32_t* __restrict__ status)
 {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -878,10 +881,9 @@ __global__ void k_compact(const otoo_group* __restrict__ groups, int32_t G, cons
         if (lane == 0) atomicOr(status, kWalkNoRoom);
         return;
     }
-    const int32_t* cs = cpool + g * ccap;
-    const int32_t* ps = ppool + g * pcap;
+    const int32_t* ps = slots + g * (ccap + pcap) + ccap;  // particle 0; cell k at ps[-1 - k]
     int32_t* d = list + gr.list_off;
-    for (int k = lane; k < gr.n_cell; k += 32) d[k] = cs[k];
+    for (int k = lane; k < gr.n_cell; k += 32) d[k] = ps[-1 - k];
     d += gr.n_cell;
     for (int k = lane; k < gr.n_part; k += 32) d[k] = ps[k];
 }
@@ -1235,7 +1237,7 @@ WalkArgs walk_args(const otoo_dev_walk* w)
 
 template <int kMode>
 int launch_walk(const otoo_dev_walk* w, otoo_group* groups, int32_t* list, int64_t capacity, cudaStream_t s,
-                int32_t* ppool = nullptr, int64_t pcap = 0)
+                int64_t pcap = 0)
 {
     int dev = 0, sms = 0, occ = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -1246,7 +1248,7 @@ int launch_walk(const otoo_dev_walk* w, otoo_group* groups, int32_t* list, int64
     const int64_t need = ((int64_t)w->n_groups + kWalkWarps - 1) / kWalkWarps;
     if (blocks > need) blocks = need;
     CUDA_TRY(cudaMemsetAsync(w->counter, 0, sizeof(uint32_t), s));
-    k_walk<kMode><<<(unsigned)blocks, kWalkWarps * 32, 0, s>>>(walk_args(w), groups, list, capacity, ppool, pcap);
+    k_walk<kMode><<<(unsigned)blocks, kWalkWarps * 32, 0, s>>>(walk_args(w), groups, list, capacity, pcap);
     CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }
@@ -1272,36 +1274,36 @@ int otoo_walk_count(const otoo_dev_walk* w, otoo_group* groups, void* stream)
     return OTOO_OK;
 }
 
-int otoo_walk_single(const otoo_dev_walk* w, otoo_group* groups, int32_t* cell_pool, int64_t cell_cap,
-                     int32_t* part_pool, int64_t part_cap, void* stream)
+int otoo_walk_single(const otoo_dev_walk* w, otoo_group* groups, int32_t* slots, int64_t cell_cap, int64_t part_cap,
+                     void* stream)
 {
     otoo::Range range_("otoo_walk_single");
     const int rc = check_walk(w);
     if (rc) return rc;
-    OTOO_REQUIRE(groups && cell_pool && part_pool, OTOO_EINVAL, "otoo_walk_single: NULL pointer");
-    OTOO_REQUIRE(cell_cap >= 1 && part_cap >= 1 && cell_cap <= INT32_MAX && part_cap <= INT32_MAX, OTOO_EINVAL,
+    OTOO_REQUIRE(groups && slots, OTOO_EINVAL, "otoo_walk_single: NULL pointer");
+    OTOO_REQUIRE(cell_cap >= 1 && part_cap >= 1 && cell_cap + part_cap <= INT32_MAX, OTOO_EINVAL,
                  "otoo_walk_single: slot sizes out of range");
+    OTOO_REQUIRE(w->n_groups <= INT64_MAX / (cell_cap + part_cap), OTOO_EINVAL, "otoo_walk_single: slots too large");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(cudaMemsetAsync(w->counter, 0, 4 * sizeof(uint32_t), s));
     CUDA_TRY(cudaMemsetAsync(w->totals, 0, kTotals * sizeof(int64_t), s));
-    const int r2 = launch_walk<2>(w, groups, cell_pool, cell_cap, s, part_pool, part_cap);
-    if (r2) return r2;
-    CUDA_TRY(excl_scan(GroupLen{groups}, GroupOff{groups}, w->n_groups, w->totals + kTotals, nullptr, s));
-    return OTOO_OK;
+    return launch_walk<2>(w, groups, slots, cell_cap, s, part_cap);
 }
 
-int otoo_walk_compact(const otoo_dev_walk* w, const otoo_group* groups, const int32_t* cell_pool, int64_t cell_cap,
-                      const int32_t* part_pool, int64_t part_cap, int32_t* list, int64_t capacity, void* stream)
+int otoo_walk_compact(const otoo_dev_walk* w, otoo_group* groups, const int32_t* slots, int64_t cell_cap,
+                      int64_t part_cap, int32_t* list, int64_t capacity, void* stream)
 {
     otoo::Range range_("otoo_walk_compact");
     const int rc = check_walk(w);
     if (rc) return rc;
-    OTOO_REQUIRE(groups && cell_pool && part_pool && list, OTOO_EINVAL, "otoo_walk_compact: NULL pointer");
+    OTOO_REQUIRE(groups && slots && list, OTOO_EINVAL, "otoo_walk_compact: NULL pointer");
+    OTOO_REQUIRE(cell_cap >= 1 && part_cap >= 1 && cell_cap + part_cap <= INT32_MAX, OTOO_EINVAL,
+                 "otoo_walk_compact: slot sizes out of range");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(excl_scan(GroupLen{groups}, GroupOff{groups}, w->n_groups, w->totals + kTotals, nullptr, s));
     const int64_t warps = w->n_groups;
-    k_compact<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(groups, w->n_groups, cell_pool, cell_cap, part_pool,
-                                                                   part_cap, list, capacity, w->totals,
-                                                                   w->counter + 1);
+    k_compact<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(groups, w->n_groups, slots, cell_cap, part_cap,
+                                                                   list, capacity, w->totals, w->counter + 1);
     CUDA_TRY(cudaGetLastError());
     return OTOO_OK;
 }

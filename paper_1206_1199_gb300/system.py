@@ -485,12 +485,12 @@ class DeviceTree:
     def walk(self, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None, max_entries=None,
              single=True):
         """Groups and lists on the device.  Without a BufferPool: two passes
-        (otoo_walk_count, otoo_walk_fill).  With one, the buffers of the
-        previous walk are reused (and overwritten), and once a walk has set
-        the slot sizes (1.25 x its largest n_cell / n_part) the walk is one
-        pass (otoo_walk_single + otoo_walk_compact), falling back to
-        otoo_walk_fill when a group outgrows its slots.  max_entries: raise
-        ValueError instead of allocating a longer list."""
+        (otoo_walk_count, otoo_walk_fill) into a dense list.  With one, the
+        buffers of the previous walk are reused (and overwritten), and once a
+        walk has set the slot sizes (1.25 x its largest n_cell / n_part) the
+        walk is one pass (otoo_walk_single) whose slots serve as the list,
+        falling back to two passes when a group outgrows its slot.
+        max_entries: raise ValueError instead of allocating a longer list."""
         return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool, max_entries, single)
 
 
@@ -544,7 +544,10 @@ class FusedStep:
 
 
 class DeviceLists:
-    """Groups and lists made by the device walk (device buffers)."""
+    """Groups and lists made by the device walk (device buffers).  bufs["list"]
+    holds list_len entries: the dense list of the two-pass walk (list_len =
+    n_list), or the slots of the one-pass walk (in_place; each group's
+    entries contiguous inside its slot, cells in reverse walk order)."""
 
     SLOT_BYTES_MAX = 24 << 30  # device memory the one-pass walk's slots may take
 
@@ -580,23 +583,26 @@ class DeviceLists:
         gp = b["groups"].data_ptr()
         key = (dtree.n_groups, dtree.mac)
         slots = pool.meta.get(key) if (pool is not None and single) else None
+        self.slots = None
         if slots:
             ccap, pcap = slots
-            cpool = alloc("cpool", G * ccap, torch.int32)
-            ppool = alloc("ppool", G * pcap, torch.int32)
-            L.call("otoo_walk_single", ctypes.byref(w), gp, cpool.data_ptr(), ccap, ppool.data_ptr(), pcap, st)
-        else:
-            L.call("otoo_walk_count", ctypes.byref(w), gp, st)
-        tot = [int(x) for x in b["totals"][:6].tolist()]
-        self.n_list, self.interactions, self.cell_interactions = tot[:3]
+            spool = alloc("slots", G * (ccap + pcap), torch.int32)
+            L.call("otoo_walk_single", ctypes.byref(w), gp, spool.data_ptr(), ccap, pcap, st)
+        tot = [int(x) for x in b["totals"][:6].tolist()] if slots else None
         self.one_pass = bool(slots) and tot[5] == 0
+        if not self.one_pass:
+            L.call("otoo_walk_count", ctypes.byref(w), gp, st)
+            tot = [int(x) for x in b["totals"][:6].tolist()]
+        self.n_list, self.interactions, self.cell_interactions = tot[:3]
         if max_entries is not None and self.n_list > max_entries:
             raise ValueError("walk: %d list entries exceed max_entries %d" % (self.n_list, max_entries))
-        b["list"] = alloc("list", self.n_list, torch.int32)
         if self.one_pass:
-            L.call("otoo_walk_compact", ctypes.byref(w), gp, cpool.data_ptr(), ccap, ppool.data_ptr(), pcap,
-                   b["list"].data_ptr(), self.n_list, st)
+            self.slots = (ccap, pcap)
+            b["list"] = spool
+            self.list_len = G * (ccap + pcap)
         else:
+            b["list"] = alloc("list", self.n_list, torch.int32)
+            self.list_len = self.n_list
             L.call("otoo_walk_fill", ctypes.byref(w), gp, b["list"].data_ptr(), self.n_list, st)
         L.call("otoo_walk_check_status", ctypes.byref(w), st)
         if pool is not None and single:
@@ -610,8 +616,41 @@ class DeviceLists:
         return self.bufs["groups"].cpu().numpy().view(np.dtype(L.Group))
 
     @property
+    def in_place(self):
+        return self.slots is not None
+
+    @property
     def list(self):
-        return self.bufs["list"][:self.n_list].cpu().numpy()
+        """The dense list on the host, in group order with each group's cells
+        in walk order (what otoo_walk_fill writes), whichever layout the
+        device holds."""
+        if not self.in_place:
+            return self.bufs["list"][:self.n_list].cpu().numpy()
+        g = self.groups
+        raw = self.bufs["list"].cpu().numpy()
+        out = np.empty(self.n_list, np.int32)
+        o = 0
+        for off, nc, npt in zip(g["list_off"], g["n_cell"], g["n_part"]):
+            out[o:o + nc] = raw[off:off + nc][::-1]
+            out[o + nc:o + nc + npt] = raw[off + nc:off + nc + npt]
+            o += nc + npt
+        return out
+
+    def compact(self, stream=None):
+        """Moves the lists of a one-pass walk into a dense device list in
+        group order (otoo_walk_compact: the list and offsets the two-pass walk
+        writes); nothing to do for a dense list."""
+        import torch
+        if not self.in_place:
+            return self
+        st = _stream(stream, self.tree.device)
+        ccap, pcap = self.slots
+        dense = _alloc(self.pool, self.tree.device)("list", self.n_list, torch.int32)
+        L.call("otoo_walk_compact", ctypes.byref(self.struct), self.bufs["groups"].data_ptr(),
+               self.bufs["list"].data_ptr(), ccap, pcap, dense.data_ptr(), self.n_list, st)
+        L.call("otoo_walk_check_status", ctypes.byref(self.struct), st)
+        self.bufs["list"], self.list_len, self.slots = dense, self.n_list, None
+        return self
 
     def plan(self, tune, stream=None):
         return DevicePlan(self, tune, stream)
@@ -667,7 +706,7 @@ class DeviceStep:
                          counter=alloc("fcounter", 4, torch.int32),
                          split=alloc("split", dl.n_src * 8, torch.float32))
         s = L.DevSystem()
-        s.n_part, s.n_src, s.n_list = dl.n_part, dl.n_src, dl.n_list
+        s.n_part, s.n_src, s.n_list = dl.n_part, dl.n_src, dl.list_len
         s.partial_doubles = self.bufs["partial"].numel()
         s.n_groups, s.n_items, s.n_splits, s.n_crit_max = dl.n_groups, plan.n_items, plan.n_splits, plan.n_crit_max
         for k in ("src", "quad", "groups", "list", "items", "splits", "perm", "partial", "counter", "split"):

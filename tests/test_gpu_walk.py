@@ -108,17 +108,57 @@ def test_one_pass_walk_equals_two_pass(torch, mac):
     pool = S.BufferPool("cuda")
     first = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
     assert not first.one_pass
-    ref_list, ref_groups = two.list, two.groups.view(np.uint8)
+    ref_list, ref_groups = two.list, two.groups
     one = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
-    assert one.one_pass
+    assert one.one_pass and one.in_place
+    # in place: each group's entries contiguous in its slot, cells reversed
+    ccap, pcap = one.slots
+    g = one.groups
+    G = len(g)
+    assert one.list_len == G * (ccap + pcap)
+    np.testing.assert_array_equal(g["list_off"], np.arange(G) * (ccap + pcap) + ccap - g["n_cell"])
+    for f in ("first", "count", "n_cell", "n_part", "eps2", "cx", "cy", "cz", "theta", "sys"):
+        np.testing.assert_array_equal(g[f], ref_groups[f], err_msg=f)
     np.testing.assert_array_equal(one.list, ref_list)
-    np.testing.assert_array_equal(one.groups.view(np.uint8), ref_groups)
+    # the dense copy (otoo_walk_compact) is the two-pass walk's, byte for byte
+    one.compact()
+    assert not one.in_place and one.list_len == one.n_list
+    np.testing.assert_array_equal(one.bufs["list"][:one.n_list].cpu().numpy(), ref_list)
+    np.testing.assert_array_equal(one.groups.view(np.uint8), ref_groups.view(np.uint8))
     # slots too small: the walk notices and fills the list in a second pass
     key = (dt.n_groups, dt.mac)
     pool.meta[key] = (4, 4)
     small = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
-    assert not small.one_pass
+    assert not small.one_pass and not small.in_place
     np.testing.assert_array_equal(small.list, ref_list)
+    np.testing.assert_array_equal(small.groups.view(np.uint8), ref_groups.view(np.uint8))
+
+
+def test_forces_on_in_place_lists(torch):
+    # the one-pass walk's slots as the list of a force step: the FP64 form
+    # equals the dense lists' (cell order differs: rounding only), the FP32
+    # form within its bound, and a too-small slot pool falls back cleanly
+    pos, mass = ic.hernquist(1 << 15, 49)
+    t = S.Tree(pos, mass, 8)
+    dt = S.DeviceTree(t, 64, True)
+    tune = L.default_tune(64)
+    tune.split, tune.packed, tune.tile = 700, 1, 128
+    dense = dt.walk(0.5, 1e-3)
+    d_step = S.DeviceStep(dense, dense.plan(tune))
+    pool = S.BufferPool("cuda")
+    dt.walk(0.5, 1e-3, pool=pool)
+    one = dt.walk(0.5, 1e-3, pool=pool)
+    assert one.in_place
+    step = S.DeviceStep(one, one.plan(tune))
+    assert step.struct.n_list == one.list_len > one.n_list
+    rel = lambda a, b: np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    a64, p64 = (x.cpu().numpy() for x in S.force(step, precision=L.OTOO_FP64))
+    r64, q64 = (x.cpu().numpy() for x in S.force(d_step, precision=L.OTOO_FP64))
+    assert rel(a64, r64).max() <= 1e-12 and (np.abs(p64 - q64) / np.abs(q64)).max() <= 1e-12
+    a32, p32 = (x.cpu().numpy() for x in S.force(step, precision=L.OTOO_FP32K, tune=tune))
+    d = rel(a32, r64)
+    assert np.sqrt(np.mean(d * d)) <= 2e-6 and d.max() <= 2e-4
+    assert (np.abs(p32 - q64) / np.abs(q64)).max() <= 1e-5
 
 
 def test_device_walk_theta_zero_and_per_group(torch):
