@@ -12,8 +12,8 @@ from paper_1206_1199_gb300 import system as S
 pytestmark = pytest.mark.gpu
 
 # interactions saved by the learned angles at equal RMS error on an
-# independent realisation (measured with the committed network: see DESIGN)
-GAIN_MIN = 1.02
+# independent realisation (1.081 measured with the committed network)
+GAIN_MIN = 1.05
 
 
 @pytest.fixture(scope="module")
@@ -118,7 +118,7 @@ def test_trained_network_on_an_independent_realisation(LR):
     assert 0.6e-3 <= lr["rms"] <= 1.1e-3, lr
     assert abs(fx["rms"] - lr["rms"]) < 0.1 * lr["rms"], (fx, lr)
     assert res["gain_interactions"] >= GAIN_MIN, res
-    assert lr["p99"] <= 1.05 * fx["p99"], (lr, fx)
+    assert lr["p99"] <= fx["p99"], (lr, fx)
 
 
 def test_direct_sum_helper_matches_oracle(LR):
