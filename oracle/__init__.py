@@ -19,6 +19,9 @@ with the GPU path (the two sides read the same seeded inputs and nothing else).
 * ``cell_moments`` / ``cell_field``  the multipole of one particle set and
                   its field at a point.
 * ``group_mac``   the opening-angle acceptance test of the group walk.
+* ``Tree.features``  the five list statistics of each group's walk that feed
+                  the learned opening angle (a reading of this project; the
+                  paper's accuracy control is Delta, Section II-B).
 * ``errors``      relative force error statistics against a reference.
 
 The C part is compiled by ``__graft_entry__.build()`` (gcc, -O2 -fopenmp
@@ -87,6 +90,8 @@ def _load():
         lib.oracle_sph_density_direct.restype = ctypes.c_int
         lib.oracle_tree_sph_density.argtypes = [ctypes.c_void_p, _dp, _dp, _lp, _lp, _lp]
         lib.oracle_tree_sph_density.restype = ctypes.c_int
+        lib.oracle_tree_features.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _lp, _dp]
+        lib.oracle_tree_features.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -263,6 +268,21 @@ def _tree_sph_density(self, h):
 
 
 Tree.sph_density = _tree_sph_density
+
+
+def _tree_features(self, theta, eps):
+    """The five list statistics of each group's walk at opening angle theta
+    (oracle_tree_features: list length, nearest cell distance over size, box
+    radius over eps, cell mass fraction, truncation estimate over the net
+    pull); returns (key [n_groups], feat [n_groups][5])."""
+    key = np.zeros(self.n_groups, np.int64)
+    feat = np.zeros((self.n_groups, 5), np.float64)
+    if self._lib.oracle_tree_features(self._h, float(theta), float(eps), _l(key), _d(feat)) != 0:
+        raise ValueError("oracle_tree_features failed")
+    return key, feat
+
+
+Tree.features = _tree_features
 
 
 def errors(acc, pot, acc_ref, pot_ref):

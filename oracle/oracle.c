@@ -26,6 +26,9 @@
  *                      with B_2 of Eq. B2 and the m_limit rule of Section
  *                      III-C) -- forces summed over the walk's cell and
  *                      particle entries.
+ *   oracle_tree_features  the five list statistics of each group that feed
+ *                      the learned opening angle (a reading of this
+ *                      project: the paper's accuracy control is Delta).
  *   oracle_sw_radius   B_2, b_max and the bounding radius r_b of one particle
  *                      set (Eq. B2, Eq. SW_MAC).
  *   oracle_sph_*       SPH sums (Section II, "Bounding Radius for SPH"): the
@@ -759,6 +762,108 @@ int oracle_tree_eval(const void* handle, double theta, const double* theta_by_ke
         free(ent.part);
     }
     if (interactions) *interactions = total;
+    return err ? -2 : 0;
+}
+
+/*
+ * List statistics of each group for the learned opening angle (a reading of
+ * this project, not of the paper: the paper controls accuracy by Delta,
+ * Section II-B).  The group walks the tree with opening angle theta; with
+ * [blo, bhi] its particles' box, c = (blo + bhi) / 2, eps the softening and
+ * d_c the distance from cell c's centre of mass to the box:
+ *   f0 = log2 max(1, n_cell + n_part)                (list length)
+ *   f1 = log10 max(min over cells of d_c / l_c, 1e-3), 3 without cells
+ *   f2 = log10 (max(h, 1e-3 eps) / eps), h = half the box diagonal
+ *   f3 = cell mass / mass of all entries (0 when that is 0)
+ *   f4 = log10 max(T / max(|A|, 1e-300), 1e-12) with T = sum over cells of
+ *        B_2 b_max / max(d_c, 1e-300)^5 (Eq. B2) and A = sum over all
+ *        entries of m (x - c) / (|x - c|^2 + eps^2)^(3/2), x the entry's
+ *        position (a cell's centre of mass).
+ * g_key[g] receives the group's lowest particle index, feat[5 g + k] = f_k.
+ */
+int oracle_tree_features(const void* handle, double theta, double eps, int64_t* g_key, double* feat)
+{
+    const OracleTree* t = (const OracleTree*)handle;
+    if (!t || !(eps > 0.0) || !(theta >= 0.0) || !g_key || !feat) return -1;
+    int err = 0;
+    int64_t g;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (g = 0; g < t->n_groups; ++g) {
+        int64_t b = t->grp_begin[g], e_ = t->grp_end[g];
+        double blo[3], bhi[3];
+        int64_t key = t->idx[b];
+        for (int a = 0; a < 3; ++a) blo[a] = bhi[a] = t->pos[3 * t->idx[b] + a];
+        for (int64_t k = b; k < e_; ++k) {
+            int64_t i = t->idx[k];
+            if (i < key) key = i;
+            for (int a = 0; a < 3; ++a) {
+                if (t->pos[3 * i + a] < blo[a]) blo[a] = t->pos[3 * i + a];
+                if (t->pos[3 * i + a] > bhi[a]) bhi[a] = t->pos[3 * i + a];
+            }
+        }
+        Mac mac;
+        memset(&mac, 0, sizeof(mac));
+        mac.kind = 0;
+        mac.theta = theta;
+        Entries ent;
+        memset(&ent, 0, sizeof(ent));
+        if (walk(t, t->root, blo, bhi, &mac, &ent)) {
+            err |= 1;
+            free((void*)ent.cell);
+            free(ent.part);
+            continue;
+        }
+        double c[3], diag2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            c[a] = 0.5 * (blo[a] + bhi[a]);
+            diag2 += (bhi[a] - blo[a]) * (bhi[a] - blo[a]);
+        }
+        double h = 0.5 * sqrt(diag2);
+        if (h < 1e-3 * eps) h = 1e-3 * eps;
+        double A[3] = {0.0, 0.0, 0.0};
+        double m_cells = 0.0, m_all = 0.0, T = 0.0, min_ratio = 1e3;
+        for (int64_t k = 0; k < ent.n_cell + ent.n_part; ++k) {
+            const int is_cell = k < ent.n_cell;
+            const Node* cn = is_cell ? ent.cell[k] : NULL;
+            const double* x = is_cell ? cn->com : t->pos + 3 * ent.part[k - ent.n_cell];
+            const double m = is_cell ? cn->m : t->mass[ent.part[k - ent.n_cell]];
+            double r2 = 0.0, r[3];
+            for (int a = 0; a < 3; ++a) {
+                r[a] = x[a] - c[a];
+                r2 += r[a] * r[a];
+            }
+            const double s2 = r2 + eps * eps;
+            for (int a = 0; a < 3; ++a) A[a] += m * r[a] / (s2 * sqrt(s2));
+            m_all += m;
+            if (is_cell) {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    double d = 0.0;
+                    if (blo[a] - x[a] > d) d = blo[a] - x[a];
+                    if (x[a] - bhi[a] > d) d = x[a] - bhi[a];
+                    d2 += d * d;
+                }
+                const double d = sqrt(d2);
+                if (d / cn->side < min_ratio) min_ratio = d / cn->side;
+                m_cells += m;
+                const double dd = d > 1e-300 ? d : 1e-300;
+                T += cn->b2 * cn->bmax / (dd * dd * dd * dd * dd);
+            }
+        }
+        const int64_t len = ent.n_cell + ent.n_part;
+        double A_abs = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+        if (A_abs < 1e-300) A_abs = 1e-300;
+        double tr = T / A_abs;
+        if (tr < 1e-12) tr = 1e-12;
+        g_key[g] = key;
+        feat[5 * g + 0] = log2((double)(len > 1 ? len : 1));
+        feat[5 * g + 1] = log10(min_ratio > 1e-3 ? min_ratio : 1e-3);
+        feat[5 * g + 2] = log10(h / eps);
+        feat[5 * g + 3] = m_all > 0.0 ? m_cells / m_all : 0.0;
+        feat[5 * g + 4] = log10(tr);
+        free((void*)ent.cell);
+        free(ent.part);
+    }
     return err ? -2 : 0;
 }
 

@@ -406,6 +406,28 @@ def test_features_are_finite_and_consistent():
     assert np.all(f0[:, 3] == 0) and np.all(f0[:, 1] == np.float32(3.0)) and np.all(f0[:, 4] == np.float32(-12.0))
 
 
+@pytest.mark.parametrize("model,n,theta,ncrit,eps", [("hernquist", 20000, 0.9, 64, 5e-4), ("plummer", 8000, 0.5, 32, 1e-2),
+                                                      ("polytrope_pair", 16000, 1.2, 128, 1e-4)])
+def test_features_match_oracle(model, n, theta, ncrit, eps):
+    # the library's list statistics against the oracle's restatement on its
+    # own tree and walk, group by group (matched by lowest particle index)
+    pos, mass = ic.make(model, n, 30)
+    t, lists = tree_and_lists(pos, mass, theta, ncrit, eps)
+    f = lists.features(t)
+    g, perm = lists.groups, lists.perm
+    keys = np.array([perm[a:a + c].min() for a, c in zip(g["first"], g["count"])])
+    okey, of = oracle.Tree(pos, mass, 8, ncrit).features(theta, eps)
+    order = np.argsort(okey)
+    pos_in = np.searchsorted(okey[order], keys)
+    assert np.array_equal(okey[order][pos_in], keys)
+    ref = of[order][pos_in]
+    np.testing.assert_array_equal(f[:, 0], ref[:, 0].astype(np.float32))
+    np.testing.assert_allclose(f[:, 1:3], ref[:, 1:3], rtol=0, atol=2e-6)
+    np.testing.assert_allclose(f[:, 3], ref[:, 3], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(f[:, 4], ref[:, 4], rtol=0, atol=2e-6)
+    assert np.mean(ref[:, 3] > 0) > 0.5
+
+
 def device_arrays(t, use_quad, mac="theta", delta=0.0, m_limit=0.0):
     e = t.export()
     n, nc = e["n_part"], e["n_cell"]

@@ -219,6 +219,55 @@ def test_tree_groups_partition_and_list_mass():
     assert np.all(np.isfinite(r["acc"]))
 
 
+def test_tree_features_hand_worked_two_clusters():
+    # Two clusters of four: A (unit masses) at the corners 0, e x, e y, e z
+    # and B (masses 2) at (100, 10, 10) + 2 {0, x, y, z}, e = 0.02.  The root
+    # cube is centred on the bounding box, side S = 102 (1 + 1e-12); its
+    # first split puts A in octant 0 and B in octant 7, two leaves of four
+    # that are the two groups (n_crit = 4).  For group A the walk opens the
+    # root and its own leaf (4 particle entries); leaf B, side l = S/2 and
+    # centre lo + 3S/4, is accepted at theta = 1 (d > l + s) and opened at
+    # theta = 0.5 (d < 2l + s), where its particles become entries.  The
+    # softening (eps = 1) keeps A's own pull at its centre finite and large
+    # against B's, so that every entry's share of it counts.
+    e, eps = 0.02, 1.0
+    a_pos = np.array([[0, 0, 0], [e, 0, 0], [0, e, 0], [0, 0, e]], float)
+    b_pos = np.array([100.0, 10.0, 10.0]) + 2.0 * np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    pos = np.vstack([a_pos, b_pos])
+    mass = np.array([1.0] * 4 + [2.0] * 4)
+    t = oracle.Tree(pos, mass, 4, 4)
+    assert t.n_groups == 2
+    S = 102.0 * (1 + 1e-12)   # the largest extent, x: 0 .. 102
+    lo = 0.5 * (pos.min(0) + pos.max(0)) - 0.5 * S
+    l, gc_b = S / 2, lo + 0.75 * S
+    com_b = b_pos.mean(0)
+    box_lo, box_hi = a_pos.min(0), a_pos.max(0)
+    d = np.linalg.norm(np.maximum(0.0, np.maximum(box_lo - com_b, com_b - box_hi)))
+    s = np.linalg.norm(com_b - gc_b)
+    assert l + s < d < 2 * l + s
+    c = 0.5 * (box_lo + box_hi)
+    h = 0.5 * np.linalg.norm(box_hi - box_lo)
+    b2 = (2.0 * ((b_pos - com_b) ** 2).sum(1)).sum()       # 18
+    bmax = np.sqrt(((b_pos - com_b) ** 2).sum(1)).max()     # sqrt(2.75)
+    assert abs(b2 - 18.0) < 1e-12 and abs(bmax - math.sqrt(2.75)) < 1e-12
+    xs, ms = np.vstack([com_b, a_pos]), np.array([8.0, 1.0, 1.0, 1.0, 1.0])
+    r = xs - c
+    s2 = (r * r).sum(1) + eps * eps
+    pull = np.linalg.norm((ms[:, None] * r / (s2 * np.sqrt(s2))[:, None]).sum(0))
+    key, f = t.features(1.0, eps)
+    a = int(np.flatnonzero(key == 0)[0])
+    want = [math.log2(5), math.log10(d / l), math.log10(h / eps), 8.0 / 12.0, math.log10(b2 * bmax / d ** 5 / pull)]
+    assert want[4] > -11.0   # above the estimate's floor
+    np.testing.assert_allclose(f[a], want, rtol=0, atol=1e-10)
+    # theta = 0.5: no cell in A's list; the sentinels of the cell statistics
+    key, f = t.features(0.5, eps)
+    a = int(np.flatnonzero(key == 0)[0])
+    np.testing.assert_allclose(f[a], [3.0, 3.0, math.log10(h / eps), 0.0, -12.0], rtol=0, atol=1e-12)
+    # groups smaller than 1e-3 eps: their radius is clamped to 1e-3 eps
+    key, f = t.features(1.0, 1e4)
+    np.testing.assert_array_equal(f[:, 2], [-3.0, -3.0])
+
+
 def test_tree_converges_as_theta_to_zero():
     pos, mass = ic.plummer(8192, 18)
     a, p = oracle.direct(pos, mass, 0.01)
