@@ -628,13 +628,12 @@ class DeviceLists:
             return self.bufs["list"][:self.n_list].cpu().numpy()
         g = self.groups
         raw = self.bufs["list"].cpu().numpy()
-        out = np.empty(self.n_list, np.int32)
-        o = 0
-        for off, nc, npt in zip(g["list_off"], g["n_cell"], g["n_part"]):
-            out[o:o + nc] = raw[off:off + nc][::-1]
-            out[o + nc:o + nc + npt] = raw[off + nc:off + nc + npt]
-            o += nc + npt
-        return out
+        nc = g["n_cell"].astype(np.int64)
+        ln = nc + g["n_part"]
+        gi = np.repeat(np.arange(len(g)), ln)
+        k = np.arange(int(ln.sum()), dtype=np.int64) - np.repeat(np.cumsum(ln) - ln, ln)
+        src = g["list_off"][gi] + np.where(k < nc[gi], nc[gi] - 1 - k, k)
+        return raw[src]
 
     def compact(self, stream=None):
         """Moves the lists of a one-pass walk into a dense device list in
