@@ -22,9 +22,11 @@
 //                     walk's lists are cut at cell level and hold about 12
 //                     times more entries than neighbours); kept entries wait
 //                     in shared memory until 32 are there; each lane sums IB
-//                     targets, plain FP32 within a tile, Kahan-compensated
-//                     FP32 across tiles and lane subsets (pairwise, in a fixed
-//                     order), FP64 output.
+//                     targets over pairs of waiting entries with packed FP32
+//                     (f32x2) arithmetic and the spline as truncated powers
+//                     (no branch), plain FP32 within a batch,
+//                     Kahan-compensated FP32 across batches and lane subsets
+//                     (pairwise, in a fixed order), FP64 output.
 //   k_density_merge   FP64 sum of the list chunks of split groups, in chunk
 //                     order.
 //   k_sph_direct      FP64 brute force over all sources for chosen targets
@@ -70,12 +72,30 @@ __global__ void k_sph_prep(const otoo_src* __restrict__ src, const float* __rest
                                  __double2float_rn(s.z - (double)hz), ih);
 }
 
-// M4 cubic spline shape w(q), q = r / h (zero for q >= 1).
-__device__ __forceinline__ float w_m4(float q)
+// Square roots of both halves of a float pair (the hardware approximation,
+// PTX sqrt.approx.ftz.f32, relative error about 2^-23; sqrt(0) = 0).
+__device__ __forceinline__ f2 f2sqrt(f2 a)
 {
-    const float a = 1.0f - q;
-    const float inner = fmaf(q * q, fmaf(6.0f, q, -6.0f), 1.0f);
-    return q <= 0.5f ? inner : (q < 1.0f ? 2.0f * a * a * a : 0.0f);
+    float lo, hi;
+    f2unpack(a, lo, hi);
+    asm("sqrt.approx.ftz.f32 %0, %0;" : "+f"(lo));
+    asm("sqrt.approx.ftz.f32 %0, %0;" : "+f"(hi));
+    return f2pack(lo, hi);
+}
+
+// M4 cubic spline shape of both halves, q = r / h >= 0, as truncated powers:
+// w(q) = 2 max(1 - q, 0)^3 - max(1 - 2q, 0)^3, which is 1 - 6q^2 + 6q^3 for
+// q <= 1/2, 2 (1 - q)^3 for 1/2 <= q <= 1 and 0 beyond (no branch: the two
+// clamps are the only scalar steps).
+__device__ __forceinline__ f2 f2w_m4(f2 q)
+{
+    const f2 one = f2pack(1.f, 1.f), mone = f2pack(-1.f, -1.f), two = f2pack(2.f, 2.f);
+    float s0, s1, t0, t1;
+    f2unpack(f2fma(q, mone, one), s0, s1);  // 1 - q
+    f2unpack(f2fma(q, two, mone), t0, t1);  // -(1 - 2q)
+    const f2 s = f2pack(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+    const f2 t = f2pack(fminf(t0, 0.f), fminf(t1, 0.f));
+    return f2fma(f2mul(f2mul(s, s), s), two, f2mul(f2mul(t, t), t));
 }
 
 // Partial slots [slot0, slot0 + n) lie inside sys.partial.
@@ -88,8 +108,10 @@ template <int IB>
 __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const float4* __restrict__ rec,
                                                       double* __restrict__ rho)
 {
-    __shared__ float4 tp[kDW][64];  // kept entries waiting: up to 31 plus a tile's 32
-    __shared__ float tih[kDW][64];
+    // kept entries waiting (up to 31 plus a tile's 32), one row per field:
+    // x, y, z relative to the group centre, m 8/(pi h^3), 1/h; entries 2m and
+    // 2m + 1 of a row load as one float pair
+    __shared__ __align__(16) float tq[kDW][5][64];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t* counter = sys.counter;
     for (;;) {
@@ -146,22 +168,46 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
                 blo[a] = fminf(blo[a], __shfl_xor_sync(kFull, blo[a], o));
                 bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(kFull, bhi[a], o));
             }
-        // evaluates the first cnt waiting entries for the lane's targets and
-        // adds the batch into the Kahan sums
-        auto batch = [&](int cnt) {
-            float part[IB];
+        f2 xi2[IB], yi2[IB], zi2[IB];
 #pragma unroll
-            for (int r = 0; r < IB; ++r) part[r] = 0.f;
-            for (int q = active ? js : cnt; q < cnt; q += nsub) {
-                const float4 pj = tp[w][q];
-                const float ihj = tih[w][q];
+        for (int r = 0; r < IB; ++r) {
+            xi2[r] = f2pack(xi[r], xi[r]);
+            yi2[r] = f2pack(yi[r], yi[r]);
+            zi2[r] = f2pack(zi[r], zi[r]);
+        }
+        // evaluates the first cnt waiting entries for the lane's targets, two
+        // entries per packed operation (an odd last entry is paired with a
+        // zero entry, which adds exactly nothing), and adds the batch into
+        // the Kahan sums
+        auto batch = [&](int cnt) {
+            if (cnt & 1) {
+                if (lane < 5) tq[w][lane][cnt] = 0.f;
+                __syncwarp();
+            }
+            const int npair = (cnt + 1) >> 1;
+            const f2* fx = reinterpret_cast<const f2*>(tq[w][0]);
+            const f2* fy = reinterpret_cast<const f2*>(tq[w][1]);
+            const f2* fz = reinterpret_cast<const f2*>(tq[w][2]);
+            const f2* fm = reinterpret_cast<const f2*>(tq[w][3]);
+            const f2* fh = reinterpret_cast<const f2*>(tq[w][4]);
+            f2 part2[IB];
+#pragma unroll
+            for (int r = 0; r < IB; ++r) part2[r] = f2pack(0.f, 0.f);
+            for (int m = active ? js : npair; m < npair; m += nsub) {
+                const f2 px = fx[m], py = fy[m], pz = fz[m], pm = fm[m], ph = fh[m];
 #pragma unroll
                 for (int r = 0; r < IB; ++r) {
-                    const float dx = pj.x - xi[r], dy = pj.y - yi[r], dz = pj.z - zi[r];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float qq = r2 > 0.f ? r2 * rsqrtf(r2) * ihj : 0.f;
-                    part[r] = fmaf(pj.w, w_m4(qq), part[r]);
+                    const f2 dx = f2sub(px, xi2[r]), dy = f2sub(py, yi2[r]), dz = f2sub(pz, zi2[r]);
+                    const f2 r2 = f2fma(dx, dx, f2fma(dy, dy, f2mul(dz, dz)));
+                    part2[r] = f2fma(pm, f2w_m4(f2mul(f2sqrt(r2), ph)), part2[r]);
                 }
+            }
+            float part[IB];
+#pragma unroll
+            for (int r = 0; r < IB; ++r) {
+                float lo, hi;
+                f2unpack(part2[r], lo, hi);
+                part[r] = lo + hi;
             }
 #pragma unroll
             for (int r = 0; r < IB; ++r) {
@@ -200,16 +246,19 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
             const unsigned km = __ballot_sync(kFull, keep);
             if (keep) {
                 const int slot = nk + __popc(km & ((1u << lane) - 1u));
-                tp[w][slot] = p;
-                tih[w][slot] = ih;
+                tq[w][0][slot] = p.x;
+                tq[w][1][slot] = p.y;
+                tq[w][2][slot] = p.z;
+                tq[w][3][slot] = p.w;
+                tq[w][4][slot] = ih;
             }
             nk += __popc(km);
             __syncwarp();
             if (nk >= 32) {  // a full batch: evaluate it, move the rest to the front
                 batch(32);
                 if (lane < nk - 32) {
-                    tp[w][lane] = tp[w][32 + lane];
-                    tih[w][lane] = tih[w][32 + lane];
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) tq[w][f][lane] = tq[w][f][32 + lane];
                 }
                 nk -= 32;
                 __syncwarp();
