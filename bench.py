@@ -544,7 +544,7 @@ def run_sph(args, dev_name, pos, mass, w, stream):
     h = ic.sph_radii(pos, mass, 64, w["model"])
     n = len(pos)
     tune = L.default_tune(w["n_crit"])
-    tune.iblock = 1   # measured fastest for the density kernel (n_crit 128: 3.25 ms against 3.33 / 3.41 ms at 2 / 4)
+    tune.iblock = 2   # measured fastest for the density kernel (n_crit 128: 3.09 ms against 3.25 / 3.40 ms at 1 / 4)
     rho = torch.empty(n, dtype=torch.float64, device=dev_name)
     h_d = torch.from_numpy(h).to(dev_name)
     pos_d = torch.from_numpy(np.ascontiguousarray(pos, np.float64)).to(dev_name)

@@ -218,14 +218,23 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
             }
             __syncwarp();
         };
-        int nk = 0;  // kept entries waiting in tp / tih
+        // list tiles of 32 entries, one per lane; each tile's indices are
+        // loaded one tile ahead
+        auto fetch_idx = [&](int32_t j, bool& has) -> int32_t {
+            has = j + lane < it.j1;
+            return has ? sys.list[g.list_off + j + lane] : 0;
+        };
+        bool has0;
+        int32_t e0 = fetch_idx(it.j0, has0);
+        int nk = 0;  // kept entries waiting in tq
         for (int32_t j = it.j0; j < it.j1; j += 32) {
-            const int32_t jj = j + lane;
+            bool has1;
+            const int32_t e1 = fetch_idx(j + 32, has1);
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
             float ih = 0.f;
             bool keep = false;
-            if (jj < it.j1) {
-                const int32_t e = sys.list[g.list_off + jj];
+            if (has0) {
+                const int32_t e = e0;
                 if (e >= 0 && e < sys.n_part) {
                     float4 a, b;
                     ld256x2(rec + 2 * (int64_t)e, a, b);
@@ -263,6 +272,7 @@ __global__ void __launch_bounds__(kDW * 32) k_density(otoo_dev_system sys, const
                 nk -= 32;
                 __syncwarp();
             }
+            has0 = has1, e0 = e1;
         }
         if (nk > 0) batch(nk);
         // merge the lane subsets into js == 0 (pairwise, a fixed order)
