@@ -362,9 +362,11 @@ def run_ours(args):
 
 
 def fma_probe(dev_name, local, stream):
-    """FP32 FMA throughput of this GPU (otoo_fma_probe: dependent chains of
-    scalar fma.rn.f32 and packed fma.rn.f32x2 on every resident thread),
-    CUDA events around 5 launches after one warm-up, clocks sampled."""
+    """Arithmetic throughput of this GPU (otoo_fma_probe: dependent chains of
+    scalar fma.rn.f32 and packed fma.rn.f32x2 on every resident thread, the
+    FP32 peak; fma.rn.f64 and rsqrt.approx.f32 for the rates the design
+    weighs against it), CUDA events around 5 launches after one warm-up,
+    clocks sampled.  Rates in T flop/s (T operations/s for rsqrt)."""
     import ctypes
 
     import torch
@@ -375,13 +377,14 @@ def fma_probe(dev_name, local, stream):
     out = {}
     st = ctypes.c_void_p(stream.cuda_stream)
     with Clocks(local) as clk:
-        for packed, iters, key in ((0, 1 << 17, "fma_f32"), (1, 1 << 16, "fma_f32x2")):
+        for kind, iters, key in ((0, 1 << 17, "fma_f32"), (1, 1 << 16, "fma_f32x2"), (2, 1 << 11, "fma_f64"),
+                                 (3, 1 << 14, "rsqrt_f32")):
             fl = ctypes.c_double(0.0)
-            L.call("otoo_fma_probe", iters, packed, sink.data_ptr(), ctypes.byref(fl), st)
+            L.call("otoo_fma_probe", iters, kind, sink.data_ptr(), ctypes.byref(fl), st)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(5):
-                L.call("otoo_fma_probe", iters, packed, sink.data_ptr(), ctypes.byref(fl), st)
+                L.call("otoo_fma_probe", iters, kind, sink.data_ptr(), ctypes.byref(fl), st)
             e1.record(stream)
             torch.cuda.synchronize()
             out[key] = 5 * fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12

@@ -387,16 +387,18 @@ int64_t otoo_direct_chunks(int64_t n_src, int64_t n_tgt);
 int otoo_direct(const otoo_src* src, int64_t n_src, const int64_t* targets, int64_t n_tgt, double eps2,
                 double* accel, double* pot, double* scratch, uint32_t* status, void* stream);
 
-/* FP32 FMA throughput probe, the measured counterpart of the peak the FP32
+/* Arithmetic throughput probe, the measured counterpart of the peak the FP32
    form's roofline divides by (not part of the force step): a grid of all
    resident 256-thread blocks, each thread running 8 independent chains of
-   iters dependent fused multiply-adds, scalar fma.rn.f32 (packed = 0, 2 flop
-   each) or packed fma.rn.f32x2 (packed = 1, 4 flop each).  *flops (host)
-   receives the flop count of the launch; time the call with CUDA events on
-   stream.  sink: device, otoo_fma_probe_threads() floats (never written in
-   practice; it keeps the chains live).  Errors: OTOO_EINVAL, OTOO_ECUDA. */
+   iters dependent operations of one kind: 0 scalar fma.rn.f32 (2 flop
+   each), 1 packed fma.rn.f32x2 (4 flop each), 2 fma.rn.f64 (2 flop each),
+   3 rsqrt.approx.ftz.f32 (1 operation each).  *flops (host) receives the
+   operation count of the launch (flop for kinds 0-2); time the call with
+   CUDA events on stream.  sink: device, otoo_fma_probe_threads() floats
+   (never written in practice; it keeps the chains live).  Errors:
+   OTOO_EINVAL, OTOO_ECUDA. */
 int64_t otoo_fma_probe_threads(void);
-int otoo_fma_probe(int32_t iters, int32_t packed, float* sink, double* flops, void* stream);
+int otoo_fma_probe(int32_t iters, int32_t kind, float* sink, double* flops, void* stream);
 
 /* ---- the walk on the device ------------------------------------------------------
    Section III-D: the paper walks the tree on the GPU, one group of particles

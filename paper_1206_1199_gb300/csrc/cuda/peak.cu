@@ -1,9 +1,12 @@
-// FP32 FMA throughput probe: the measured counterpart of the peak that the
+// Arithmetic throughput probe: the measured counterpart of the peak that the
 // FP32 force form's roofline divides by (152 SMs x 128 FP32 lanes x 2 flop
-// per clock on GB300).  Every thread runs kChains independent chains of
-// dependent fused multiply-adds, scalar (fma.rn.f32, 2 flop) or packed
-// (fma.rn.f32x2, 4 flop), on a persistent grid of resident blocks.  The
-// caller times the launch with CUDA events on its stream.
+// per clock on GB300), and of the FP64 and reciprocal-square-root rates the
+// design weighs against it.  Every thread runs kChains independent chains of
+// dependent operations on a persistent grid of resident blocks: fused
+// multiply-adds, scalar (fma.rn.f32, 2 flop) or packed (fma.rn.f32x2, 4
+// flop), FP64 fused multiply-adds (fma.rn.f64, 2 flop), or hardware
+// reciprocal square roots (rsqrt.approx.ftz.f32, 1 operation).  The caller
+// times the launch with CUDA events on its stream.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -72,13 +75,56 @@ __global__ void __launch_bounds__(kProbeThreads) k_fma_probe_f32x2(int iters, fl
     if (s == -1.0f) sink[tid] = s;
 }
 
-int probe_grid(int packed, int* grid)
+// a <- a * b + c in FP64 on every chain
+__global__ void __launch_bounds__(kProbeThreads) k_fma_probe_f64(int iters, float seed, float* sink)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = (double)seed * (double)(tid + k + 1);
+    const double b = 0.9999999999999999, c = 1.0e-16;
+#pragma unroll 16
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(a[k]) : "d"(b), "d"(c));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += a[k];
+    if (s == -1.0) sink[tid] = (float)s;
+}
+
+// a <- rsqrt(a) on every chain: the values tend to 1 and stay positive
+__global__ void __launch_bounds__(kProbeThreads) k_rsqrt_probe(int iters, float seed, float* sink)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    float a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = 1.0f + seed * (float)(tid + k + 1);
+#pragma unroll 16
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) asm volatile("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(a[k]));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += a[k];
+    if (s == -1.0f) sink[tid] = s;
+}
+
+typedef void (*ProbeKernel)(int, float, float*);
+
+ProbeKernel probe_kernel(int kind)
+{
+    return kind == 0 ? k_fma_probe_f32 : kind == 1 ? k_fma_probe_f32x2 : kind == 2 ? k_fma_probe_f64 : k_rsqrt_probe;
+}
+
+int probe_grid(int kind, int* grid)
 {
     int dev = 0, nsm = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return set_error(OTOO_ECUDA, "otoo_fma_probe: device query failed");
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, packed ? k_fma_probe_f32x2 : k_fma_probe_f32, kProbeThreads, 0);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, probe_kernel(kind), kProbeThreads, 0);
     if (e != cudaSuccess || occ < 1) return set_error(OTOO_ECUDA, "otoo_fma_probe: occupancy query failed");
     *grid = nsm * occ;
     return OTOO_OK;
@@ -90,27 +136,28 @@ extern "C" {
 
 int64_t otoo_fma_probe_threads(void)
 {
-    int g0 = 0, g1 = 0;
-    if (probe_grid(0, &g0) || probe_grid(1, &g1)) return -1;
-    return (int64_t)(g0 > g1 ? g0 : g1) * kProbeThreads;
+    int gmax = 0;
+    for (int kind = 0; kind < 4; ++kind) {
+        int g = 0;
+        if (probe_grid(kind, &g)) return -1;
+        if (g > gmax) gmax = g;
+    }
+    return (int64_t)gmax * kProbeThreads;
 }
 
-int otoo_fma_probe(int32_t iters, int32_t packed, float* sink, double* flops, void* stream)
+int otoo_fma_probe(int32_t iters, int32_t kind, float* sink, double* flops, void* stream)
 {
     otoo::Range range_("otoo_fma_probe");
-    OTOO_REQUIRE(iters >= 1 && (packed == 0 || packed == 1) && sink && flops, OTOO_EINVAL,
-                 "otoo_fma_probe: bad argument");
+    OTOO_REQUIRE(iters >= 1 && kind >= 0 && kind <= 3 && sink && flops, OTOO_EINVAL, "otoo_fma_probe: bad argument");
     int grid = 0;
-    const int rc = probe_grid(packed, &grid);
+    const int rc = probe_grid(kind, &grid);
     if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (packed)
-        k_fma_probe_f32x2<<<grid, kProbeThreads, 0, s>>>(iters, 1.0e-3f, sink);
-    else
-        k_fma_probe_f32<<<grid, kProbeThreads, 0, s>>>(iters, 1.0e-3f, sink);
+    probe_kernel(kind)<<<grid, kProbeThreads, 0, s>>>(iters, 1.0e-3f, sink);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OTOO_ECUDA, "otoo_fma_probe: %s", cudaGetErrorString(e));
-    *flops = (double)grid * kProbeThreads * kChains * (double)iters * (packed ? 4.0 : 2.0);
+    const double per_op = kind == 1 ? 4.0 : kind == 3 ? 1.0 : 2.0;
+    *flops = (double)grid * kProbeThreads * kChains * (double)iters * per_op;
     return OTOO_OK;
 }
 

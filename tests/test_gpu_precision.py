@@ -170,3 +170,22 @@ def test_compensated_sums_keep_small_terms_after_a_large_one(torch):
     assert float(naive) == float(terms[0])
     dropped = float(terms[1:].sum(dtype=np.float64))
     assert dropped > 1000 * 2e-6 * sp[0]
+
+
+def test_throughput_probe_kinds(torch):
+    # otoo_fma_probe: every kind launches and reports its operation count
+    # (resident threads x 8 chains x iters x operations per instruction);
+    # an unknown kind is refused
+    n = int(L.load().otoo_fma_probe_threads())
+    assert n > 0 and n % 256 == 0
+    sink = torch.empty(n, dtype=torch.float32, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for kind, per_op in ((0, 2.0), (1, 4.0), (2, 2.0), (3, 1.0)):
+        fl = ctypes.c_double(0.0)
+        L.call("otoo_fma_probe", 16, kind, sink.data_ptr(), ctypes.byref(fl), st)
+        torch.cuda.synchronize()
+        ops = fl.value / (8 * 16 * per_op)
+        assert ops == int(ops) and 0 < ops <= n and int(ops) % 256 == 0, (kind, fl.value)
+    with pytest.raises(L.OtooError) as e:
+        L.call("otoo_fma_probe", 16, 4, sink.data_ptr(), ctypes.byref(ctypes.c_double(0.0)), st)
+    assert e.value.code == L.OTOO_EINVAL
