@@ -471,7 +471,12 @@ typedef struct otoo_dev_walk {
     int32_t exact;                 /* 1 = every acceptance test in FP64 (no FP32 filter) */
     int32_t mac;                   /* OTOO_MAC_THETA, OTOO_MAC_SW or OTOO_MAC_SPH (records made
                                       for it; OTOO_MAC_SPH enters no cell) */
-    int32_t pad;
+    int32_t set;                   /* groups one warp walks together (consecutive in group
+                                      order; each cell's record loaded once and tested per
+                                      group): 1..8, or 0 = up to 8 while every resident warp
+                                      gets about three sets.  Same entries per group for
+                                      every value (their order within a group may differ).
+                                      Other values: OTOO_EINVAL */
     double theta;                  /* opening angle when theta_per_group is NULL (>= 0) */
     double eps2;                   /* softening^2, copied into every group record */
     const otoo_src* src;           /* [n_part + n_cell]: particle positions (tree order) */

@@ -109,7 +109,7 @@ class WCell64(ctypes.Structure):
 
 
 class DevWalk(ctypes.Structure):
-    _fields_ = [("n_part", i64), ("n_cell", i64), ("n_groups", i32), ("exact", i32), ("mac", i32), ("pad", i32),
+    _fields_ = [("n_part", i64), ("n_cell", i64), ("n_groups", i32), ("exact", i32), ("mac", i32), ("set", i32),
                 ("theta", f64),
                 ("eps2", f64), ("src", vp), ("cell", vp), ("cell64", vp), ("group_first", vp),
                 ("group_count", vp), ("theta_per_group", vp), ("counter", vp), ("totals", vp)]

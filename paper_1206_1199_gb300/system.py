@@ -483,15 +483,17 @@ class DeviceTree:
         return FusedStep(self, theta, eps, iblock, theta_per_group, pool)
 
     def walk(self, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None, max_entries=None,
-             single=True):
+             single=True, group_set=0):
         """Groups and lists on the device.  Without a BufferPool: two passes
         (otoo_walk_count, otoo_walk_fill) into a dense list.  With one, the
         buffers of the previous walk are reused (and overwritten), and once a
         walk has set the slot sizes (1.25 x its largest n_cell / n_part) the
         walk is one pass (otoo_walk_single) whose slots serve as the list,
         falling back to two passes when a group outgrows its slot.
-        max_entries: raise ValueError instead of allocating a longer list."""
-        return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool, max_entries, single)
+        max_entries: raise ValueError instead of allocating a longer list.
+        group_set: groups one warp walks together (1..8; 0 = as many as
+        keep every resident warp busy, up to 8); same entries per group."""
+        return DeviceLists(self, theta, eps, theta_per_group, exact, stream, pool, max_entries, single, group_set)
 
 
 class FusedStep:
@@ -552,7 +554,7 @@ class DeviceLists:
     SLOT_BYTES_MAX = 24 << 30  # device memory the one-pass walk's slots may take
 
     def __init__(self, dtree, theta, eps, theta_per_group=None, exact=False, stream=None, pool=None,
-                 max_entries=None, single=True):
+                 max_entries=None, single=True, group_set=0):
         import torch
         dev = dtree.device
         G = dtree.n_groups
@@ -571,6 +573,7 @@ class DeviceLists:
         w = L.DevWalk()
         w.n_part, w.n_cell, w.n_groups, w.exact = dtree.n_part, dtree.n_cell, G, int(bool(exact))
         w.mac = dtree.mac
+        w.set = int(group_set)
         w.theta, w.eps2 = float(theta), float(eps) * float(eps)
         tb = dtree.bufs
         w.src, w.cell, w.cell64 = tb["src"].data_ptr(), tb["cell"].data_ptr(), tb["cell64"].data_ptr()

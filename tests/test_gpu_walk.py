@@ -54,35 +54,55 @@ def lattice(k, scale=2.0, shift=10.0):
     ("plummer", 20000, 0.5, 64, 8, True), ("plummer", 20000, 0.3, 128, 8, True),
     ("hernquist", 30000, 0.75, 32, 8, True), ("king", 8000, 1.0, 64, 1, False),
     ("uniform", 10000, 0.5, 16, 4, True), ("lattice", 4096, 0.5, 64, 8, True)])
-def test_device_walk_matches_host_lists(torch, model, n, theta, ncrit, leaf, quad):
+@pytest.mark.parametrize("group_set", [0, 1, 3, 8])
+def test_device_walk_matches_host_lists(torch, model, n, theta, ncrit, leaf, quad, group_set):
+    # group_set: consecutive groups one warp walks together (0: chosen by the library)
     pos, mass = lattice(16) if model == "lattice" else ic.make(model, n, 41)
     t = S.Tree(pos, mass, leaf)
     hl = t.lists(theta, ncrit, 0.01, quad)
     dt = S.DeviceTree(t, ncrit, quad)
-    dl = dt.walk(theta, 0.01)
+    dl = dt.walk(theta, 0.01, group_set=group_set)
     compare_lists(hl, dl)
     # every test in FP64: the same lists in the same order
-    de = dt.walk(theta, 0.01, exact=True)
+    de = dt.walk(theta, 0.01, exact=True, group_set=group_set)
     np.testing.assert_array_equal(de.list, dl.list)
     np.testing.assert_array_equal(de.groups.view(np.uint8), dl.groups.view(np.uint8))
     # run to run: identical
-    np.testing.assert_array_equal(dt.walk(theta, 0.01).list, dl.list)
+    np.testing.assert_array_equal(dt.walk(theta, 0.01, group_set=group_set).list, dl.list)
 
 
 @pytest.mark.parametrize("model,n,delta,m_limit,ncrit", [("plummer", 20000, 1e-2, 0.05, 64),
                                                         ("hernquist", 30000, 1e-4, 0.0, 32),
                                                         ("plummer", 3000, 0.0, 0.0, 64)])
-def test_device_walk_sw_matches_host_lists(torch, model, n, delta, m_limit, ncrit):
+@pytest.mark.parametrize("group_set", [1, 8])
+def test_device_walk_sw_matches_host_lists(torch, model, n, delta, m_limit, ncrit, group_set):
     pos, mass = ic.make(model, n, 46)
     t = S.Tree(pos, mass, 8)
     hl = t.lists(0.0, ncrit, 0.01, True, mac="sw", delta=delta, m_limit=m_limit)
     dt = S.DeviceTree(t, ncrit, True, mac="sw", delta=delta, m_limit=m_limit)
-    dl = dt.walk(0.0, 0.01)
+    dl = dt.walk(0.0, 0.01, group_set=group_set)
     compare_lists(hl, dl)
-    de = dt.walk(0.0, 0.01, exact=True)
+    de = dt.walk(0.0, 0.01, exact=True, group_set=group_set)
     np.testing.assert_array_equal(de.list, dl.list)
     if delta == 0.0:
         assert dl.interactions == n * n
+
+
+def test_set_walk_equals_group_walk(torch):
+    # the set walk against the per-group walk on a larger tree: identical
+    # group records, entries equal as sets per group
+    pos, mass = ic.hernquist(1 << 17, 49)
+    t = S.Tree(pos, mass, 8)
+    dt = S.DeviceTree(t, 128, True)
+    for theta, gs in ((0.5, 8), (0.9, 5), (0.5, 0)):
+        a = dt.walk(theta, 5e-4, group_set=gs)
+        b = dt.walk(theta, 5e-4, group_set=1)
+        np.testing.assert_array_equal(a.groups.view(np.uint8), b.groups.view(np.uint8))
+        la, lb, g = a.list, b.list, a.groups
+        for k in range(len(g)):
+            o, nc, npt = g["list_off"][k], g["n_cell"][k], g["n_part"][k]
+            np.testing.assert_array_equal(np.sort(la[o:o + nc]), np.sort(lb[o:o + nc]))
+            np.testing.assert_array_equal(np.sort(la[o + nc:o + nc + npt]), np.sort(lb[o + nc:o + nc + npt]))
 
 
 @pytest.mark.parametrize("delta", [1e-2, 1e-3])
@@ -99,17 +119,18 @@ def test_sw_lists_force_matches_oracle(torch, delta):
 
 
 @pytest.mark.parametrize("mac", ["theta", "sw", "sph"])
-def test_one_pass_walk_equals_two_pass(torch, mac):
+@pytest.mark.parametrize("group_set", [1, 8])
+def test_one_pass_walk_equals_two_pass(torch, mac, group_set):
     pos, mass = ic.hernquist(30000, 48)
     h = ic.sph_radii(pos, mass, 48, "hernquist") if mac == "sph" else None
     t = S.Tree(pos, mass, 8)
     dt = S.DeviceTree(t, 64, mac != "sph", mac=mac, delta=1e-3, m_limit=0.05, h_sph=h)
-    two = dt.walk(0.6 if mac == "theta" else 0.0, 0.01)
+    two = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, group_set=group_set)
     pool = S.BufferPool("cuda")
-    first = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
+    first = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool, group_set=group_set)
     assert not first.one_pass
     ref_list, ref_groups = two.list, two.groups
-    one = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
+    one = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool, group_set=group_set)
     assert one.one_pass and one.in_place
     # in place: each group's entries contiguous in its slot, cells reversed
     ccap, pcap = one.slots
@@ -128,7 +149,7 @@ def test_one_pass_walk_equals_two_pass(torch, mac):
     # slots too small: the walk notices and fills the list in a second pass
     key = (dt.n_groups, dt.mac)
     pool.meta[key] = (4, 4)
-    small = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool)
+    small = dt.walk(0.6 if mac == "theta" else 0.0, 0.01, pool=pool, group_set=group_set)
     assert not small.one_pass and not small.in_place
     np.testing.assert_array_equal(small.list, ref_list)
     np.testing.assert_array_equal(small.groups.view(np.uint8), ref_groups.view(np.uint8))
