@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--skip-sph", action="store_true", help="skip the SPH density stage")
     ap.add_argument("--fused-only", action="store_true",
                     help="only the walk fused with the force against the split device step, on this workload")
+    ap.add_argument("--walk-group-set", type=int, default=0,
+                    help="groups one warp walks together in the device walks (1..8; 0: chosen by the library)")
     return ap.parse_args()
 
 
@@ -429,7 +431,7 @@ def run_device_walk(args, dev_name, tree, w, tune, lists, a32, stream, host_walk
     def one():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
-        dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool)
+        dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool, group_set=args.walk_group_set)
         ev[1].record(stream)
         dp = dl.plan(tune, stream=stream)
         ev[2].record(stream)
@@ -497,7 +499,7 @@ def run_device_step(args, dev_name, pos, mass, w, tune, tree, lists, a32, stream
                                 cap_cell=cap[0], stream=stream)
         cap[0] = max(cap[0], dt.n_cell)
         ev[2].record(stream)
-        dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool)
+        dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool, group_set=args.walk_group_set)
         ev[3].record(stream)
         dp = dl.plan(tune, stream=stream)
         S.force(S.DeviceStep(dl, dp), acc, pot, L.OTOO_FP32K, tune, stream=stream, check=False)
@@ -560,7 +562,7 @@ def run_sph(args, dev_name, pos, mass, w, stream):
         dt = S.DeviceTree.build(pos_d, mass_d, w["leaf_size"], w["n_crit"], False, dev_name, mac="sph", h_sph=h_d,
                                 cap_cell=n // 2, stream=stream)
         ev[1].record(stream)
-        dl = dt.walk(0.0, 1.0, stream=stream, pool=pool)
+        dl = dt.walk(0.0, 1.0, stream=stream, pool=pool, group_set=args.walk_group_set)
         ev[2].record(stream)
         S.sph_density(S.DeviceStep(dl, dl.plan(tune, stream=stream)), h_d, rho, tune, stream=stream)
         ev[3].record(stream)
@@ -603,7 +605,7 @@ def run_sw_sweep(args, dev_name, tree, w, tune, stream, sub, ad):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         try:
-            dl = dt.walk(0.0, w["eps"], stream=stream, max_entries=int(2.5e9))
+            dl = dt.walk(0.0, w["eps"], stream=stream, max_entries=int(2.5e9), group_set=args.walk_group_set)
         except ValueError as e:
             rows.append({"delta": delta, "skipped": str(e)})
             break
@@ -673,10 +675,10 @@ def run_fused(args, dev_name, pos, mass, w, tune, stream):
         nl, inter, cinter = fs.totals()
         t = L.Tune(block=128, iblock=2, tile=256, split=8192, ctas_per_sm=0, packed=1)
         pool = S.BufferPool(dev_name)
-        dt.walk(w["theta"], w["eps"], stream=stream, pool=pool)
+        dt.walk(w["theta"], w["eps"], stream=stream, pool=pool, group_set=args.walk_group_set)
 
         def split_step():
-            dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool)
+            dl = dt.walk(w["theta"], w["eps"], stream=stream, pool=pool, group_set=args.walk_group_set)
             S.force(S.DeviceStep(dl, dl.plan(t, stream=stream)), acc, pot, L.OTOO_FP32K, t, stream=stream,
                     check=False)
 
@@ -723,7 +725,7 @@ def run_paper_workloads(args, dev_name, tune, stream):
             dt = S.DeviceTree.build(pos_d, mass_d, 16, 128, False, dev_name, mac="sw", delta=delta, m_limit=0.05,
                                     stream=stream)
             ev[1].record(stream)
-            dl = dt.walk(0.0, eps, stream=stream)
+            dl = dt.walk(0.0, eps, stream=stream, group_set=args.walk_group_set)
             ev[2].record(stream)
             S.force(S.DeviceStep(dl, dl.plan(tune, stream=stream)), acc, pot, L.OTOO_FP32K, tune, stream=stream)
             ev[3].record(stream)
