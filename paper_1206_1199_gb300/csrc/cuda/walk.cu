@@ -213,6 +213,70 @@ __device__ __forceinline__ int mac_filter_sw(const otoo_wcell& w, const BoxF& g)
     return -1;
 }
 
+// mac_filter and mac_filter_sw with the parts that depend on the cell alone
+// computed once per cell by the caller (the set walk tests one cell against
+// several groups): acell = |com_hi[0]| + |com_hi[1]| + |com_hi[2]| and, for
+// the opening angle, thr = side / theta + s as mac_filter rounds it.  Only K
+// (the scale of the rounding bound) is summed in another order, which moves
+// it by a few FP32 roundings, far inside the margins.
+template <bool kOverlap>
+__device__ __forceinline__ int mac_filter_pc(const otoo_wcell& w, const BoxF& g, float acell, float thr)
+{
+    float u[3], au = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        u[a] = __fadd_rn(__fsub_rn(w.com_hi[a], g.c32[a]), __fsub_rn(w.com_lo[a], g.cl32[a]));
+        au += fabsf(u[a]);
+    }
+    const float K = au + g.B + thr + w.side + (g.A + acell) * 0x1p-24f;
+    if (kOverlap) {
+        const float del = K * 0x1p-18f;
+        bool sep = false, ovl = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float lo = __fsub_rn(u[a], w.e[a]);
+            const float hi = __fadd_rn(lo, w.side);
+            sep = sep || (lo > g.bh[a] + del) || (g.bl[a] > hi + del);
+            ovl = ovl && (lo < g.bh[a] - del) && (g.bl[a] < hi - del);
+        }
+        if (ovl) return 0;
+        if (!sep) return -1;
+    }
+    float d2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d = fmaxf(0.f, fmaxf(g.bl[a] - u[a], u[a] - g.bh[a]));
+        d2 = fmaf(d, d, d2);
+    }
+    const float thr2 = thr * thr, m = K * K * 0x1p-16f;
+    if (d2 > thr2 + m) return 1;
+    if (d2 < thr2 - m) return 0;
+    return -1;
+}
+
+__device__ __forceinline__ int mac_filter_sw_pc(const otoo_wcell& w, const BoxF& g, float acell)
+{
+    const float rb = w.rb;
+    if (!(rb <= 3.0e38f)) return 0;
+    float u[3], au = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        u[a] = __fadd_rn(__fsub_rn(w.com_hi[a], g.c32[a]), __fsub_rn(w.com_lo[a], g.cl32[a]));
+        au += fabsf(u[a]);
+    }
+    const float K = au + g.B + rb + (g.A + acell) * 0x1p-24f;
+    float d2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d = fmaxf(0.f, fmaxf(g.bl[a] - u[a], u[a] - g.bh[a]));
+        d2 = fmaf(d, d, d2);
+    }
+    const float rb2 = rb * rb, m = K * K * 0x1p-16f;
+    if (d2 > rb2 + m) return 1;
+    if (d2 < rb2 - m) return 0;
+    return -1;
+}
+
 __device__ __forceinline__ otoo_wcell load_wcell(const otoo_wcell* __restrict__ cell, int k)
 {
     float v[16];
@@ -632,23 +696,29 @@ struct SetStep {
 };
 
 // The decision of group j of a set on cell nd (record c): 1 accept, 0 reject.
-__device__ __forceinline__ int set_decide(const WalkArgs& a, const SetGroup& g, bool sw, const otoo_wcell& c, int nd)
+// acell, thr_u: the cell's own parts of the filter (thr_u for the set's
+// common angle, used when uni).
+__device__ __forceinline__ int set_decide(const WalkArgs& a, const SetGroup& g, bool sw, const otoo_wcell& c, int nd,
+                                          float acell, float thr_u, bool uni)
 {
     if (sw) {
-        int dec = a.exact ? -1 : mac_filter_sw(c, g.bf);
+        int dec = a.exact ? -1 : mac_filter_sw_pc(c, g.bf, acell);
         if (dec < 0) dec = sw_exact(a.cell64, nd, g.blo, g.bhi) ? 1 : 0;
         return dec;
     }
     if (g.flags & 1) return 0;
-    int dec = a.exact ? -1 : (g.flags & 2) ? mac_filter<false>(c, g.bf, g.invth) : mac_filter<true>(c, g.bf, g.invth);
+    const float thr = uni ? thr_u : __fadd_rn(__fmul_rn(c.side, g.invth), c.s);
+    int dec = a.exact ? -1 : (g.flags & 2) ? mac_filter_pc<false>(c, g.bf, acell, thr)
+                                           : mac_filter_pc<true>(c, g.bf, acell, thr);
     if (dec < 0) dec = mac_exact(a.cell64, nd, g.blo, g.bhi, g.theta) ? 1 : 0;
     return dec;
 }
 
 // walk_take for a set: takes up to kWide cells with their runs' masks and
 // tests each against the groups of its mask.
-__device__ __forceinline__ bool set_take(const WalkArgs& a, const SetGroup* sg, bool sw, uint32_t* stk, uint8_t* msk,
-                                         int& sp, int64_t& budget, int lane, SetStep& st, uint32_t* status)
+__device__ __forceinline__ bool set_take(const WalkArgs& a, const SetGroup* sg, bool sw, float invth_u, bool uni,
+                                         uint32_t* stk, uint8_t* msk, int& sp, int64_t& budget, int lane, SetStep& st,
+                                         uint32_t* status)
 {
     if (sp + 2 > kStack) return false;
     const int wcap = sp + kWide + 1 + kMaxLevels <= kStack ? kWide : 1;
@@ -714,10 +784,12 @@ __device__ __forceinline__ bool set_take(const WalkArgs& a, const SetGroup* sg, 
                  (st.nch[h] == 0 || (st.c0[h] > nd && (int64_t)st.c0[h] + st.nch[h] <= a.n_cell)) &&
                  st.pb[h] >= 0 && st.pb[h] <= st.pe[h] && (int64_t)st.pe[h] <= a.n_part;
             if (ok) {
+                const float acell = fabsf(c.com_hi[0]) + fabsf(c.com_hi[1]) + fabsf(c.com_hi[2]);
+                const float thr_u = __fadd_rn(__fmul_rn(c.side, invth_u), c.s);
                 unsigned ac = 0u;
                 for (unsigned m = cm[h] & ((1u << kSet) - 1u); m; m &= m - 1u) {
                     const int j = __ffs(m) - 1;
-                    if (set_decide(a, sg[j], sw, c, nd)) ac |= 1u << j;
+                    if (set_decide(a, sg[j], sw, c, nd, acell, thr_u, uni)) ac |= 1u << j;
                 }
                 st.acc[h] = ac;
                 st.rej[h] = cm[h] & ((1u << kSet) - 1u) & ~ac;
@@ -838,6 +910,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS)
             if (w.theta >= 0.0) live |= 1u << j;
         }
         __syncwarp();
+        // one opening angle for all walking groups: the threshold side /
+        // theta + s is computed once per cell
+        float invth_u = 0.f;
+        bool uni = false;
+        if (live) {
+            invth_u = sg[__ffs(live) - 1].invth;
+            uni = true;
+            for (unsigned m = live; m; m &= m - 1u) uni = uni && sg[__ffs(m) - 1].invth == invth_u;
+        }
         int my_nc = 0, my_np = 0;  // lane j: counts of group j
         int sp = 0;
         if (live) {
@@ -852,7 +933,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, OTOO_WALK_MIN_BLOCKS)
         bool failed = false;
         while (sp > 0) {
             SetStep st;
-            if (!set_take(a, sg, sw, stk, msk, sp, budget, lane, st, status)) {
+            if (!set_take(a, sg, sw, invth_u, uni, stk, msk, sp, budget, lane, st, status)) {
                 failed = true;
                 break;
             }
