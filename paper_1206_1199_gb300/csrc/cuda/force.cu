@@ -644,7 +644,7 @@ namespace {
 // float pairs of the FP32 form and the chunk partials of split lists.  Every
 // GPU that loads the library holds this array until the process exits.
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
-__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxStaticDevices = 64;
 std::mutex g_static_mu;
