@@ -312,7 +312,7 @@ def run_ours(args):
                    "leaf_size": w["leaf_size"], "n_crit": w["n_crit"], "quadrupole": bool(lists.use_quad),
                    "groups": lists.n_groups, "list_entries": lists.n_list, "interactions": inter,
                    "cell_interactions": cell_inter, "tune": tune.as_dict(), "tune_source": tune_src,
-                   "items": plan.n_items,
+                   "items": plan.n_items, "list_length": list_length_stats(lists),
                    "l2": "inputs larger than L2 (%.1f GB resident per step)" % (dev.h2d_bytes() / 1e9),
                    "host_tree_s": t1 - t0, "host_walk_s": t2 - t1, "host_plan_s": t3 - t2,
                    "parallelism": "replica per rank (weak)"},
@@ -407,6 +407,21 @@ def guarded_extra(fn, *a):
         return fn(*a)
     except Exception as e:  # reported in the JSON line
         return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
+def list_length_stats(lists):
+    """Distribution of the groups' list lengths (cell + particle entries):
+    quantiles and a histogram in powers of two (bin k: lengths in [2^k,
+    2^(k+1)))."""
+    g = lists.groups
+    ln = (g["n_cell"].astype(np.int64) + g["n_part"].astype(np.int64))
+    if len(ln) == 0:
+        return {}
+    q = np.quantile(ln, [0.0, 0.01, 0.5, 0.99, 1.0])
+    k = np.floor(np.log2(np.maximum(ln, 1))).astype(int)
+    hist = {str(1 << int(b)): int(c) for b, c in zip(*np.unique(k, return_counts=True))}
+    return {"min": int(q[0]), "p01": float(q[1]), "median": float(q[2]), "p99": float(q[3]), "max": int(q[4]),
+            "mean_cell_fraction": float(g["n_cell"].sum() / max(ln.sum(), 1)), "hist_log2": hist}
 
 
 def run_device_walk(args, dev_name, tree, w, tune, lists, a32, stream, host_walk_s, host_plan_s):
