@@ -351,7 +351,8 @@ def run_ours(args):
     if rank == 0 and not args.skip_sw and errors is not None:
         line["sw_sweep"] = guarded_extra(run_sw_sweep, args, dev_name, tree, w, tune, stream, sub, ad)
     if rank == 0 and not args.skip_cpu:
-        line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_fraction, args.cpu_repeats)
+        line["cpu_baseline"] = cpu_baseline(w, pos, mass, args.cpu_fraction, args.cpu_repeats,
+                                            direct=(sub[:128], ad[:128]) if errors is not None else None)
     if rank == 0 and not args.skip_extras and args.workload == "hernquist8m":
         line["fused_walk_force"] = guarded_extra(run_fused, args, dev_name, pos, mass, w, tune, stream)
         line["paper_workloads"] = guarded_extra(run_paper_workloads, args, dev_name, tune, stream)
@@ -935,17 +936,31 @@ def cpu_sample_text(t, sel, fraction, inter, secs):
             % (len(sel), t.n_groups, fraction, CPU_SAMPLE_SEED, inter, secs))
 
 
-def cpu_baseline(w, pos, mass, fraction, repeats, tree=None):
+def cpu_baseline(w, pos, mass, fraction, repeats, tree=None, direct=None):
     """The FP64 oracle tree code (as it stands) on a seeded sample of the
-    workload's groups, timed `repeats` times: median rate and its spread."""
+    workload's groups, timed `repeats` times: median rate and its spread.
+    direct = (targets, acc): also the oracle's FP64 direct sum on those
+    targets, timed, and its largest relative difference from acc (the
+    library's FP64 direct sum on the device, the reference of the line's
+    errors)."""
     t = tree if tree is not None else oracle_tree(w, pos, mass)
     sel = cpu_sample(t, fraction)
     runs = [cpu_time_sample(w, t, sel) for _ in range(max(1, repeats))]
     rates = [i / max(s, 1e-9) for i, s in runs]
     med = float(np.median(rates))
-    return {"value": med, "unit": "interactions/s", "cores": cores(), "kind": "oracle", "repeats": len(runs),
-            "spread": [float(min(rates)), float(max(rates))],
-            "sample": cpu_sample_text(t, sel, fraction, runs[0][0], float(np.median([s for _, s in runs])))}
+    out = {"value": med, "unit": "interactions/s", "cores": cores(), "kind": "oracle", "repeats": len(runs),
+           "spread": [float(min(rates)), float(max(rates))],
+           "sample": cpu_sample_text(t, sel, fraction, runs[0][0], float(np.median([s for _, s in runs])))}
+    if direct is not None:
+        import oracle
+        tgt, acc = direct
+        t0 = time.perf_counter()
+        ao, _ = oracle.direct(pos, mass, w["eps"], tgt)
+        sec = time.perf_counter() - t0
+        pairs = int(len(tgt)) * (len(pos) - 1)
+        out["direct_sum"] = {"targets": int(len(tgt)), "pairs": pairs, "seconds": sec, "pairs_per_s": pairs / sec,
+                             "library_fp64_direct_vs_oracle_max_rel": rel_err(acc, ao)[1]}
+    return out
 
 
 def run_reference(args):
