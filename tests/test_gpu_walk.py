@@ -182,11 +182,14 @@ def test_forces_on_in_place_lists(torch):
     assert (np.abs(p32 - q64) / np.abs(q64)).max() <= 1e-5
 
 
-def test_device_walk_theta_zero_and_per_group(torch):
+@pytest.mark.parametrize("group_set", [0, 3, 8])
+def test_device_walk_theta_zero_and_per_group(torch, group_set):
+    # with several groups per warp, sets mix skipped groups, angle 0 and
+    # different angles
     pos, mass = ic.plummer(3000, 42)
     t = S.Tree(pos, mass, 8)
     dt = S.DeviceTree(t, 64, True)
-    d0 = dt.walk(0.0, 0.02)
+    d0 = dt.walk(0.0, 0.02, group_set=group_set)
     g = d0.groups
     assert np.all(g["n_cell"] == 0) and np.all(g["n_part"] == 3000) and d0.interactions == 3000 * 3000
     compare_lists(t.lists(0.0, 64, 0.02, True), d0)
@@ -195,15 +198,16 @@ def test_device_walk_theta_zero_and_per_group(torch):
     th[1::4] = 0.0
     th[2::4] = 0.9
     hl = t.lists(0.5, 64, 0.02, True, theta_per_group=th)
-    dl = dt.walk(0.5, 0.02, theta_per_group=th)
+    dl = dt.walk(0.5, 0.02, theta_per_group=th, group_set=group_set)
     compare_lists(hl, dl)
     assert np.all(dl.groups["n_cell"][::4] == 0) and np.all(dl.groups["n_part"][::4] == 0)
 
 
-def test_device_walk_edge_cases(torch):
+@pytest.mark.parametrize("group_set", [0, 8])
+def test_device_walk_edge_cases(torch, group_set):
     # one particle: its list is itself
     t = S.Tree(np.array([[0.3, -0.2, 0.1]]), np.array([1.0], np.float32), 8)
-    dl = S.DeviceTree(t, 64, True).walk(0.5, 0.1)
+    dl = S.DeviceTree(t, 64, True).walk(0.5, 0.1, group_set=group_set)
     compare_lists(t.lists(0.5, 64, 0.1, True), dl)
     assert dl.n_list == 1
     # coincident particles: a last-level leaf larger than n_crit is cut into chunks
@@ -214,7 +218,7 @@ def test_device_walk_edge_cases(torch):
     t = S.Tree(pos, mass, 8)
     hl = t.lists(0.5, 32, 0.01, True)
     assert hl.groups["count"].max() == 32
-    compare_lists(hl, S.DeviceTree(t, 32, True).walk(0.5, 0.01))
+    compare_lists(hl, S.DeviceTree(t, 32, True).walk(0.5, 0.01, group_set=group_set))
 
 
 @pytest.mark.parametrize("split,iblock", [(16384, 2), (300, 2), (129, 1), (700, 4)])
@@ -272,11 +276,12 @@ def test_device_step_forces(torch, split):
     np.testing.assert_array_equal(a2, a32)
 
 
-def test_walk_reports_bad_records_and_small_lists(torch):
+@pytest.mark.parametrize("group_set", [0, 8])
+def test_walk_reports_bad_records_and_small_lists(torch, group_set):
     pos, mass = ic.plummer(5000, 45)
     t = S.Tree(pos, mass, 8)
     dt = S.DeviceTree(t, 64, True)
-    dl = dt.walk(0.5, 0.01)
+    dl = dt.walk(0.5, 0.01, group_set=group_set)
     w, b = dl.struct, dl.bufs
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     # a list one entry too short: nothing written, status set
@@ -292,7 +297,7 @@ def test_walk_reports_bad_records_and_small_lists(torch):
     root_child0 = int(cell[0, 11])
     cell[0, 11] = dt.n_cell + 5
     with pytest.raises(L.OtooError) as ei:
-        dt.walk(0.5, 0.01)
+        dt.walk(0.5, 0.01, group_set=group_set)
     assert ei.value.code == L.OTOO_EDEVICE
     cell[0, 11] = root_child0
-    compare_lists(t.lists(0.5, 64, 0.01, True), dt.walk(0.5, 0.01))
+    compare_lists(t.lists(0.5, 64, 0.01, True), dt.walk(0.5, 0.01, group_set=group_set))
