@@ -294,8 +294,13 @@ int otoo_default_tune(int32_t n_crit, otoo_tune* tune);
    extension; Plummer softening with the group's eps2):
      a_i = sum_j m_j r / (r^2 + eps^2)^(3/2) [+ quadrupole terms],
      phi_i = -sum_j m_j / (r^2 + eps^2)^(1/2) [+ ...],   r = x_j - x_i, j != i.
-   sys: device view, all arrays device-resident; accel: device [n_part][3] FP64;
-   pot: device [n_part] FP64; both indexed by perm when sys->perm is set.
+   sys: device view, all arrays device-resident; accel: [n_part][3] FP64;
+   pot: [n_part] FP64; both indexed by perm when sys->perm is set.  accel and
+   pot are device memory or pinned (page-locked) host memory, which the GPU
+   addresses directly: the kernel then writes the results into host memory
+   as it goes, and they are there when the stream has finished (on GB300 the
+   host link takes these writes during the kernel, which replaces the copy
+   that would follow it).
    precision: OTOO_FP32K or OTOO_FP64.  tune: the tuning the plan was made with.
    The step (ticket reset, persistent force kernel, chunk merge) is recorded
    once per distinct argument set into a CUDA graph and replayed on stream.

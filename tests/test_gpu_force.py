@@ -177,6 +177,23 @@ def test_corrupt_list_index_is_reported(torch):
     assert ei.value.code == L.OTOO_EDEVICE
 
 
+def test_outputs_in_pinned_host_memory(torch):
+    # accel and pot in pinned host memory: the kernels write them there
+    # directly, with the same bits as into device memory
+    pos, mass = ic.plummer(30000, 9)
+    tree, lists, plan = S.build_system(pos, mass, 0.5, 64, 1e-2)
+    dev = S.DeviceSystem.upload(lists, plan, "cuda")
+    n = lists.n_part
+    for prec in (L.OTOO_FP32K, L.OTOO_FP64):
+        a, p = S.force(dev, precision=prec)
+        ah = torch.full((n, 3), np.nan, dtype=torch.float64).pin_memory()
+        ph = torch.full((n,), np.nan, dtype=torch.float64).pin_memory()
+        S.force(dev, ah, ph, precision=prec)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ah.numpy(), a.cpu().numpy())
+        np.testing.assert_array_equal(ph.numpy(), p.cpu().numpy())
+
+
 def test_host_entry_point_matches_device(torch):
     pos, mass = ic.plummer(30000, 8)
     tree, lists, plan = S.build_system(pos, mass, 0.5, 64, 1e-2)
