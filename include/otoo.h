@@ -316,7 +316,9 @@ int otoo_force(const otoo_dev_system* sys, double* accel, double* pot, int32_t p
 /* Same computation from HOST arrays: the library copies the lists view and
    the plan to its own device buffers, runs otoo_force on stream and copies
    accel/pot (host, caller order) back; returns after the stream has synced.
-   Device buffers are kept for the next call of the same size. */
+   When accel and pot are both pinned (page-locked) host memory the kernel
+   writes them directly and no copy follows it.  Device buffers are kept for
+   the next call of the same size. */
 int otoo_force_host(const otoo_lists_view* lists, const otoo_plan_info* plan, double* accel,
                     double* pot, int32_t precision, const otoo_tune* tune, void* stream);
 

@@ -569,6 +569,20 @@ extern "C" int otoo_centre_relative(const otoo_src* src, int64_t n, const double
     return OTOO_OK;
 }
 
+namespace {
+// The device address of pinned (page-locked) host memory, or NULL for any
+// other pointer (pageable memory, device memory, an unknown address).
+double* pinned_device_address(double* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the error of an unknown pointer
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? static_cast<double*>(at.devicePointer) : nullptr;
+}
+}  // namespace
+
 extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* pl, double* accel, double* pot,
                                int32_t precision, const otoo_tune* tune, void* stream)
 {
@@ -627,6 +641,14 @@ extern "C" int otoo_force_host(const otoo_lists_view* lv, const otoo_plan_info* 
     sys.partial_doubles = std::max<int64_t>(pl->partial_doubles, 1);
     sys.counter = (uint32_t*)g_host.p[8];
     sys.split = g_host.p[9];
+    // pinned outputs: the kernel writes them in place (no copy after it)
+    double* dacc = pinned_device_address(accel);
+    double* dpot = pinned_device_address(pot);
+    if (dacc && dpot) {
+        int rc = otoo_force(&sys, dacc, dpot, precision, tune, stream);
+        if (rc) return rc;
+        return otoo_check_status(&sys, stream);
+    }
     int rc = otoo_force(&sys, out, out + 3 * lv->n_part, precision, tune, stream);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(accel, out, sizeof(double) * 3 * (size_t)lv->n_part, cudaMemcpyDeviceToHost, s));

@@ -202,6 +202,13 @@ def test_host_entry_point_matches_device(torch):
     ah, ph = S.force_host(lists, plan, precision=L.OTOO_FP32K)
     np.testing.assert_array_equal(a.cpu().numpy(), ah)
     np.testing.assert_array_equal(p.cpu().numpy(), ph)
+    # pinned outputs (written by the kernel in place): the same bits
+    n = lists.n_part
+    ap = torch.full((n, 3), np.nan, dtype=torch.float64).pin_memory()
+    pp = torch.full((n,), np.nan, dtype=torch.float64).pin_memory()
+    S.force_host(lists, plan, precision=L.OTOO_FP32K, accel=ap, pot=pp)
+    np.testing.assert_array_equal(ap.numpy(), ah)
+    np.testing.assert_array_equal(pp.numpy(), ph)
 
 
 def test_batch_packed_equals_separate(torch):
