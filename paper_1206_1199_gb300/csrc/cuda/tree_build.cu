@@ -310,79 +310,106 @@ struct Cells {
     int32_t* nchild;
 };
 
+// The levels' first cells live on the device (lev[L] = first cell of level
+// L, lev[L + 1] = one past its last), so that a level is expanded without the
+// host reading its size: each kernel reads the bounds and runs a grid-stride
+// loop over 8 threads per cell (whole blocks per round, so that the
+// 8-lane shuffles and the ballots see every lane).  stop != 0 (the cell
+// capacity ran out) makes the rest of the expansion return at once.
+
 // Thread (c, d): the start of the run of next-level digit >= d inside cell
 // c = lo + t / 8 (a split cell's keys are sorted and share the cell's prefix,
 // so its next digit does not decrease along the cell).  cnt[c - lo] = number
 // of non-empty runs (children); starts go to dig[(c - lo) * 8 + d].
-__global__ void k_expand_count(int32_t lo, int32_t hi, int L, int leaf_size, const uint64_t* __restrict__ keys,
-                               Cells c, int32_t* __restrict__ dig, int32_t* __restrict__ cnt)
+__global__ void k_expand_count(const int32_t* __restrict__ lev, int L, int leaf_size,
+                               const uint64_t* __restrict__ keys, Cells c, int32_t* __restrict__ dig,
+                               int32_t* __restrict__ cnt, const uint32_t* __restrict__ stop)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t cell = lo + (int32_t)(t >> 3);
-    const int d = (int)(t & 7);
-    const bool in = cell < hi;
-    int32_t b = 0, e = 0;
-    bool split = false;
-    if (in) {
-        b = c.begin[cell];
-        e = c.end[cell];
-        split = e - b > leaf_size && L < kLevels;
-    }
-    int32_t start = e;
-    if (split) {
-        const int shift = 3 * (kLevels - 1 - L);
-        int32_t l = b, r = e;  // first index in [b, e) with digit >= d
-        while (l < r) {
-            const int32_t m = l + ((r - l) >> 1);
-            if ((int)((keys[m] >> shift) & 7u) < d)
-                l = m + 1;
-            else
-                r = m;
+    if (*stop) return;
+    const int32_t lo = lev[L], hi = lev[L + 1];
+    const int64_t nt = 8 * (int64_t)(hi - lo);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nt; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        const int32_t cell = lo + (int32_t)(t >> 3);
+        const int d = (int)(t & 7);
+        const bool in = t < nt;
+        int32_t b = 0, e = 0;
+        bool split = false;
+        if (in) {
+            b = c.begin[cell];
+            e = c.end[cell];
+            split = e - b > leaf_size && L < kLevels;
         }
-        start = l;
-    }
-    // run d is [start_d, start_{d+1}), start_8 = e
-    const int32_t next = __shfl_down_sync(kFull, start, 1, 8);
-    const int32_t nxt = d == 7 ? e : next;
-    const bool nonempty = split && start < nxt;
-    const unsigned m = __ballot_sync(kFull, nonempty);
-    if (in) {
-        dig[(int64_t)(cell - lo) * 8 + d] = start;
-        if (d == 0) cnt[cell - lo] = __popc((m >> (threadIdx.x & 24)) & 0xffu);
+        int32_t start = e;
+        if (split) {
+            const int shift = 3 * (kLevels - 1 - L);
+            int32_t l = b, r = e;  // first index in [b, e) with digit >= d
+            while (l < r) {
+                const int32_t m = l + ((r - l) >> 1);
+                if ((int)((keys[m] >> shift) & 7u) < d)
+                    l = m + 1;
+                else
+                    r = m;
+            }
+            start = l;
+        }
+        // run d is [start_d, start_{d+1}), start_8 = e
+        const int32_t next = __shfl_down_sync(kFull, start, 1, 8);
+        const int32_t nxt = d == 7 ? e : next;
+        const bool nonempty = split && start < nxt;
+        const unsigned m = __ballot_sync(kFull, nonempty);
+        if (in) {
+            dig[(int64_t)(cell - lo) * 8 + d] = start;
+            if (d == 0) cnt[cell - lo] = __popc((m >> (threadIdx.x & 24)) & 0xffu);
+        }
     }
 }
 
-__global__ void k_expand_write(int32_t lo, int32_t hi, int L, int32_t next_base, Cells c,
-                               const int32_t* __restrict__ dig, const int32_t* __restrict__ coff,
-                               int64_t cap)
+// Writes level L + 1: the children of level L's cells at lev[L + 1] +
+// coff[c - lo] (coff: the exclusive scan of cnt, *total its sum), and
+// lev[L + 2].  Children past cap are not written and set stop.
+__global__ void k_expand_write(int32_t* __restrict__ lev, int L, Cells c, const int32_t* __restrict__ dig,
+                               const int32_t* __restrict__ coff, const int64_t* __restrict__ total, int64_t cap,
+                               uint32_t* __restrict__ stop)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t cell = lo + (int32_t)(t >> 3);
-    const int d = (int)(t & 7);
-    const bool in = cell < hi;
-    int32_t start = 0, e = 0;
-    if (in) {
-        start = dig[(int64_t)(cell - lo) * 8 + d];
-        e = c.end[cell];
+    if (*stop) return;
+    const int32_t lo = lev[L], hi = lev[L + 1];
+    const int32_t next_base = hi;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t end = (int64_t)hi + *total;
+        lev[L + 2] = (int32_t)(end < cap ? end : cap);
+        if (end > cap) *stop = 1u;
     }
-    const int32_t next = __shfl_down_sync(kFull, start, 1, 8);
-    const int32_t nxt = d == 7 ? e : next;
-    const bool nonempty = in && start < nxt;  // a cell that does not split has start = end for every digit
-    const unsigned m = __ballot_sync(kFull, nonempty);
-    const unsigned mine = (m >> (threadIdx.x & 24)) & 0xffu;
-    if (!in) return;
-    const int32_t first = next_base + coff[cell - lo];
-    if (d == 0) {
-        c.child0[cell] = mine ? first : 0;
-        c.nchild[cell] = __popc(mine);
-    }
-    if (nonempty) {
-        const int64_t k = (int64_t)first + __popc(mine & ((1u << d) - 1u));
-        if (k < cap) {
-            c.begin[k] = start;
-            c.end[k] = nxt;
-            c.level[k] = L + 1;
-            c.parent[k] = cell;
+    const int64_t nt = 8 * (int64_t)(hi - lo);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nt; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        const int32_t cell = lo + (int32_t)(t >> 3);
+        const int d = (int)(t & 7);
+        const bool in = t < nt;
+        int32_t start = 0, e = 0;
+        if (in) {
+            start = dig[(int64_t)(cell - lo) * 8 + d];
+            e = c.end[cell];
+        }
+        const int32_t next = __shfl_down_sync(kFull, start, 1, 8);
+        const int32_t nxt = d == 7 ? e : next;
+        const bool nonempty = in && start < nxt;  // a cell that does not split has start = end for every digit
+        const unsigned m = __ballot_sync(kFull, nonempty);
+        const unsigned mine = (m >> (threadIdx.x & 24)) & 0xffu;
+        if (!in) continue;
+        const int32_t first = next_base + coff[cell - lo];
+        if (d == 0) {
+            c.child0[cell] = mine ? first : 0;
+            c.nchild[cell] = __popc(mine);
+        }
+        if (nonempty) {
+            const int64_t k = (int64_t)first + __popc(mine & ((1u << d) - 1u));
+            if (k < cap) {
+                c.begin[k] = start;
+                c.end[k] = nxt;
+                c.level[k] = L + 1;
+                c.parent[k] = cell;
+            }
         }
     }
 }
@@ -771,6 +798,54 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int32_t* __restrict
     } while (0)
 
 // exclusive scan of a[0, n) in place; the total to *total (device)
+// The same three scans over a[0, n) with n = lev[L + 1] - lev[L] read on the
+// device: grid-stride over blocks of kScanThreads (whole blocks per round).
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums_lev(const int32_t* __restrict__ a,
+                                                                 const int32_t* __restrict__ lev, int L,
+                                                                 int64_t* __restrict__ bsum)
+{
+    __shared__ int64_t ws[33];
+    const int64_t n = lev[L + 1] - lev[L];
+    for (int64_t blk = blockIdx.x; blk * kScanThreads < n; blk += gridDim.x) {
+        const int64_t i = blk * kScanThreads + threadIdx.x;
+        int64_t tot;
+        block_excl_scan64(i < n ? a[i] : 0, ws, &tot);
+        if (threadIdx.x == 0) bsum[blk] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top_lev(int64_t* __restrict__ bsum,
+                                                                const int32_t* __restrict__ lev, int L,
+                                                                int64_t* __restrict__ total)
+{
+    const int64_t n = lev[L + 1] - lev[L];
+    const int64_t nblk = (n + kScanThreads - 1) / kScanThreads;
+    __shared__ int64_t ws[33];
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nblk; b0 += kScanThreads) {
+        const int64_t i = b0 + threadIdx.x;
+        int64_t tot;
+        const int64_t e = block_excl_scan64(i < nblk ? bsum[i] : 0, ws, &tot);
+        if (i < nblk) bsum[i] = carry + e;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply_lev(int32_t* __restrict__ a,
+                                                                  const int32_t* __restrict__ lev, int L,
+                                                                  const int64_t* __restrict__ bsum)
+{
+    __shared__ int64_t ws[33];
+    const int64_t n = lev[L + 1] - lev[L];
+    for (int64_t blk = blockIdx.x; blk * kScanThreads < n; blk += gridDim.x) {
+        const int64_t i = blk * kScanThreads + threadIdx.x;
+        int64_t tot;
+        const int64_t e = block_excl_scan64(i < n ? a[i] : 0, ws, &tot) + bsum[blk];
+        if (i < n) a[i] = (int32_t)e;
+    }
+}
+
 int scan32(int32_t* a, int64_t n, int64_t* bsum, int64_t* total, cudaStream_t s)
 {
     const int64_t nblk = (n + kScanThreads - 1) / kScanThreads;
@@ -788,7 +863,7 @@ int scan32(int32_t* a, int64_t n, int64_t* bsum, int64_t* total, cudaStream_t s)
 // Scratch layout (byte offsets, each part 256-byte aligned).
 struct Layout {
     size_t keys0, keys1, vals0, vals1, hist, bsum, part, geom, gq, cells[6], mom_m, mom_com, mom_q, mom_b2,
-        mom_dmax, dig, cnt, flag, tot, total;
+        mom_dmax, dig, cnt, flag, tot, lev, total;
 };
 
 size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -823,6 +898,7 @@ Layout layout(int64_t n, int64_t cap)
     l.cnt = take(4 * (big + 1));
     l.flag = take(4 * (n + 1));
     l.tot = take(64);
+    l.lev = take(4 * (kLevels + 4) + 4);  // level bounds, then the stop word
     l.total = o;
     return l;
 }
@@ -918,35 +994,50 @@ int otoo_devtree_build(const double* pos, const float* mass, otoo_devtree* t, vo
     if (st & kTreeBadSort) return set_error(OTOO_EDEVICE, "otoo_devtree_build: sort produced an invalid order");
     const uint64_t* skeys = keys[cur];
 
-    // cells, level by level (the host reads each level's size)
+    // cells, level by level, the levels' bounds on the device (one read at
+    // the end instead of one per level)
     const int32_t root[6] = {0, (int32_t)n, 0, -1, 0, 0};
     for (int k = 0; k < 6; ++k) {
         int32_t* arr = k == 0 ? c.begin : k == 1 ? c.end : k == 2 ? c.level : k == 3 ? c.parent : k == 4 ? c.child0 : c.nchild;
         CUDA_TRY(cudaMemcpyAsync(arr, &root[k], sizeof(int32_t), cudaMemcpyHostToDevice, s));
     }
-    std::vector<int32_t> lev_lo{0, 1};
-    int depth = 0;
-    for (int L = 0; L <= kLevels; ++L) {
-        const int32_t lo = lev_lo[L], hi = lev_lo[L + 1];
-        const int64_t nc = hi - lo;
-        if (nc == 0) break;
-        depth = L;
-        const int64_t threads = 8 * nc;
-        const unsigned grid = (unsigned)((threads + 255) / 256);
-        k_expand_count<<<grid, 256, 0, s>>>(lo, hi, L, t->leaf_size, skeys, c, dig, cnt);
-        const int r = scan32(cnt, nc, bsum, tot, s);
-        if (r) return r;
-        int64_t nnext = 0;
-        CUDA_TRY(cudaMemcpyAsync(&nnext, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        if ((int64_t)hi + nnext > cap) {
-            t->n_cell = -1;
-            return set_error(OTOO_ENOMEM, "otoo_devtree_build: more than cap_cell = %lld cells", (long long)cap);
-        }
-        k_expand_write<<<grid, 256, 0, s>>>(lo, hi, L, hi, c, dig, cnt, cap);
-        CUDA_TRY(cudaGetLastError());
-        lev_lo.push_back(hi + (int32_t)nnext);
+    int32_t* lev = reinterpret_cast<int32_t*>(base + ly.lev);
+    uint32_t* stop = reinterpret_cast<uint32_t*>(lev + kLevels + 4);
+    {
+        static const int32_t lev01[2] = {0, 1};
+        CUDA_TRY(cudaMemsetAsync(lev, 0, 4 * (kLevels + 4) + 4, s));
+        CUDA_TRY(cudaMemcpyAsync(lev, lev01, sizeof(lev01), cudaMemcpyHostToDevice, s));
     }
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // grid-stride rounds: enough blocks to fill the GPU, no more than the
+    // widest level could use (8 threads per cell, at most cap cells)
+    const unsigned eg = (unsigned)std::min<int64_t>((int64_t)sms * 8, (8 * cap + 255) / 256);
+    const unsigned sg = (unsigned)std::min<int64_t>((int64_t)sms * 2, (cap + kScanThreads - 1) / kScanThreads);
+    for (int L = 0; L <= kLevels; ++L) {
+        k_expand_count<<<eg, 256, 0, s>>>(lev, L, t->leaf_size, skeys, c, dig, cnt, stop);
+        k_scan_sums_lev<<<sg, kScanThreads, 0, s>>>(cnt, lev, L, bsum);
+        k_scan_top_lev<<<1, kScanThreads, 0, s>>>(bsum, lev, L, tot);
+        k_scan_apply_lev<<<sg, kScanThreads, 0, s>>>(cnt, lev, L, bsum);
+        k_expand_write<<<eg, 256, 0, s>>>(lev, L, c, dig, cnt, tot, cap, stop);
+    }
+    CUDA_TRY(cudaGetLastError());
+    int32_t hlev[kLevels + 4];
+    uint32_t hstop = 0;
+    CUDA_TRY(cudaMemcpyAsync(hlev, lev, sizeof(hlev), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&hstop, stop, sizeof(hstop), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hstop) {
+        t->n_cell = -1;
+        return set_error(OTOO_ENOMEM, "otoo_devtree_build: more than cap_cell = %lld cells", (long long)cap);
+    }
+    // level L holds [hlev[L], hlev[L + 1]); the last non-empty level is the depth
+    std::vector<int32_t> lev_lo(hlev, hlev + kLevels + 3);
+    int depth = 0;
+    for (int L = 0; L <= kLevels + 1; ++L)
+        if (hlev[L + 1] > hlev[L]) depth = L;
+    lev_lo.resize(depth + 2);
     const int32_t n_cell = lev_lo.back();
 
     // moments: every leaf in one launch, then the parents level by level,
