@@ -19,8 +19,10 @@ the calls):
               device (otoo_direct);
   training    Adam on the FP32 master weights with the network's own
               forward/backward kernels (bf16 weights in the forward pass);
-  selection   otoo_select_theta on the device, then a re-walk with one
-              angle per group;
+  selection   otoo_learned_theta on the device over a finer angle grid
+              than the training rows' (SELECT_GRID), then a re-walk with one
+              angle per group; calibration scales the targets so that the
+              selection reaches the target RMS on training snapshots;
   evaluation  learned angles against a fixed angle bisected to the same
               RMS error, and against theta = 0.5.
 """
@@ -39,7 +41,11 @@ from . import ic
 from . import system as S
 from .mlp import ThetaNet
 
-THETA_GRID = tuple(round(0.3 + 0.1 * k, 2) for k in range(14))  # 0.3 .. 1.6
+THETA_GRID = tuple(round(0.3 + 0.1 * k, 2) for k in range(14))  # 0.3 .. 1.6: angles of the training rows
+# angles the selection chooses from (the network takes the angle as an input,
+# so it is evaluated between the training angles too): a finer grid lets each
+# group come closer to the angle its error budget allows
+SELECT_GRID = tuple(round(0.3 + 0.025 * k, 3) for k in range(53))  # 0.3 .. 1.6
 THETA0 = 0.9  # angle of the base walk whose list statistics feed the network
 
 
@@ -385,6 +391,8 @@ def main():
     ap.add_argument("--summary", default=None, help="write the evaluation here (.json)")
     ap.add_argument("--checkpoint", default=None,
                     help="snapshot checkpoint (.npz): continued when it exists and matches the run, written after")
+    ap.add_argument("--recalibrate", action="store_true",
+                    help="no training: load --weights, set the selection grid, calibrate, evaluate, write both back")
     args = ap.parse_args()
     log = lambda s: print(s, flush=True)  # noqa: E731
     pos, mass, vel = merger_ic(args.n)
@@ -405,12 +413,26 @@ def main():
     t1 = time.perf_counter()
     log("snapshots: %d in %.1f s" % (len(snaps), t1 - t0))
     train_snaps, held_out = snaps[:args.snaps], snaps[args.snaps]
-    X, y = training_set(train_snaps, mass, args.eps, args.n_crit, args.groups, log=log)
-    t2 = time.perf_counter()
-    log("rows: %d in %.1f s" % (len(y), t2 - t1))
-    net, hist = train(X, y, steps=args.steps)
-    t3 = time.perf_counter()
-    log("training: loss %.4g -> %.4g in %.1f s" % (hist[0], hist[-1], t3 - t2))
+    prev = {}
+    if args.recalibrate:
+        # the trained network as it is; the rows, losses and times of its
+        # training come from the earlier summary
+        net = ThetaNet.load(args.weights)
+        if args.summary and os.path.exists(args.summary):
+            with open(args.summary) as f:
+                prev = json.load(f)
+        n_rows, hist = prev.get("rows", 0), [prev.get("loss_first", float("nan")), prev.get("loss_last", float("nan"))]
+        t2 = t3 = time.perf_counter()
+    else:
+        X, y = training_set(train_snaps, mass, args.eps, args.n_crit, args.groups, log=log)
+        n_rows = int(len(y))
+        t2 = time.perf_counter()
+        log("rows: %d in %.1f s" % (n_rows, t2 - t1))
+        net, hist = train(X, y, steps=args.steps)
+        t3 = time.perf_counter()
+        log("training: loss %.4g -> %.4g in %.1f s" % (hist[0], hist[-1], t3 - t2))
+    net.grid = SELECT_GRID
+    net.calib = 1.0
     # calibration on training snapshots spread over the run
     pick = np.unique(np.linspace(0, args.snaps - 1, args.calib_snaps).round().astype(int))
     calib_hist = calibrate(net, [Evaluator(train_snaps[k], mass, args.eps, args.n_crit) for k in pick], args.target,
@@ -421,10 +443,12 @@ def main():
     ev = Evaluator(held_out, mass, args.eps, args.n_crit)
     res = compare(ev, net, args.target, log=log, mode="budget")
     res["equal_targets"] = compare(ev, net, args.target, mode="equal", precision_fp64=False)
-    res.update(n=args.n, snapshots=args.snaps, every=args.every, dt=dt, rows=int(len(y)), loss_first=hist[0],
+    times = dict(snapshots=t1 - t0, rows=t2 - t1, training=t3 - t2, calibration=t4 - t3)
+    if args.recalibrate:
+        times.update({k: v for k, v in prev.get("times_s", {}).items() if k in ("rows", "training")})
+    res.update(n=args.n, snapshots=args.snaps, every=args.every, dt=dt, rows=n_rows, loss_first=hist[0],
                loss_last=hist[-1], calib=net.calib, calib_rms=calib_hist, theta0=net.theta0, grid=list(net.grid),
-               alpha=net.alpha, beta=net.beta,
-               times_s=dict(snapshots=t1 - t0, rows=t2 - t1, training=t3 - t2, calibration=t4 - t3))
+               train_grid=list(THETA_GRID), alpha=net.alpha, beta=net.beta, times_s=times)
     print(json.dumps(res))
     if args.summary:
         with open(args.summary, "w") as f:

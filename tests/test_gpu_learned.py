@@ -12,8 +12,8 @@ from paper_1206_1199_gb300 import system as S
 pytestmark = pytest.mark.gpu
 
 # interactions saved by the learned angles at equal RMS error on an
-# independent realisation (1.081 measured with the committed network)
-GAIN_MIN = 1.05
+# independent realisation (1.108 measured with the committed network)
+GAIN_MIN = 1.10
 
 
 @pytest.fixture(scope="module")
