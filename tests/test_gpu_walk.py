@@ -90,13 +90,18 @@ def test_device_walk_sw_matches_host_lists(torch, model, n, delta, m_limit, ncri
 
 def test_set_walk_equals_group_walk(torch):
     # the set walk against the per-group walk on a larger tree: identical
-    # group records, entries equal as sets per group
+    # group records, entries equal as sets per group; one angle for all
+    # groups, one angle per group (each group's own threshold), the absolute
+    # MAC
     pos, mass = ic.hernquist(1 << 17, 49)
     t = S.Tree(pos, mass, 8)
     dt = S.DeviceTree(t, 128, True)
-    for theta, gs in ((0.5, 8), (0.9, 5), (0.5, 0)):
-        a = dt.walk(theta, 5e-4, group_set=gs)
-        b = dt.walk(theta, 5e-4, group_set=1)
+    dsw = S.DeviceTree(t, 128, True, mac="sw", delta=1e-3, m_limit=0.05)
+    tpg = np.random.default_rng(5).choice(np.float32([0.4, 0.55, 0.7, 0.85, 1.0]), dt.n_groups).astype(np.float32)
+    cases = [(dt, 0.5, None, 8), (dt, 0.9, None, 5), (dt, 0.5, None, 0), (dt, 0.5, tpg, 8), (dsw, 0.0, None, 8)]
+    for tree, theta, per_group, gs in cases:
+        a = tree.walk(theta, 5e-4, theta_per_group=per_group, group_set=gs)
+        b = tree.walk(theta, 5e-4, theta_per_group=per_group, group_set=1)
         np.testing.assert_array_equal(a.groups.view(np.uint8), b.groups.view(np.uint8))
         la, lb, g = a.list, b.list, a.groups
         for k in range(len(g)):
